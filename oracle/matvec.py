@@ -1,0 +1,193 @@
+"""Matrix-vector products y := alpha*M*x + beta*y (eqn. mvm, Sec. 3).
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
+
+Sequential FP64 versions of the paper's algorithms, one block at a time:
+
+* ``h_mvm``   -- Alg. 1 (loop over leaf blocks; low-rank t := V^H x, y|t += alpha U t).
+* ``uh_mvm``  -- Alg. 4 (forward s_s := X_s^H x|s for every cluster), then
+                 Alg. 5 root to leaves (t_t := sum S_ts s_s, eq. sumcoup;
+                 y' := W_t t_t; y' += D x for dense blocks; y|t += y').
+* ``h2_mvm``  -- Alg. 6 (leaf forward, then s_s += E_s'^H s_s' leaves to root),
+                 then Alg. 7 root to leaves (couplings, t_t' += E_t' t_t at inner
+                 clusters, y' := W_t t_t at leaves, dense blocks, y|t += y').
+
+Compressed matrices are decompressed block by block before the product
+(Alg. 8 computes the same sum, entry by entry).  beta extends the paper's
+update y := alpha M x + y; beta = 1 is the paper's operation.  x and y are in
+the original point order, shape (N,) or (N, r); the products run in the
+cluster order and are permuted back.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from .compress import CH, CH2, CUH, undirect, unvalr
+from .hmatrix import HMatrix, LowRank
+from .nested import H2, Uniform
+
+
+def _perm_in(ct, x, y, beta):
+    xp = np.asarray(x, dtype=np.float64)[ct.perm]
+    yp = beta * np.asarray(y, dtype=np.float64)[ct.perm]
+    return xp, yp
+
+
+def _perm_out(ct, yp):
+    y = np.empty_like(yp)
+    y[ct.perm] = yp
+    return y
+
+
+def h_mvm(m, alpha: float, x, beta: float = 1.0, y=None):
+    """Alg. 1 on an HMatrix (FP64) or a CH (compressed, decoded per block)."""
+    h = m if isinstance(m, HMatrix) else m.h
+    ct = h.ct
+    if y is None:
+        y = np.zeros_like(np.asarray(x, dtype=np.float64))
+    xp, yp = _perm_in(ct, x, y, beta)
+    cl = ct.clusters
+    for i, b in enumerate(h.blocks):
+        t, s = cl[b.row], cl[b.col]
+        xs = xp[s.start:s.end]
+        if isinstance(m, HMatrix):
+            d = m.data[i]
+            if isinstance(d, LowRank):
+                tv = (d.X.T @ xs)
+                tv = (d.s * tv.T).T
+                yp[t.start:t.end] += alpha * (d.W @ tv)
+            else:
+                yp[t.start:t.end] += alpha * (d @ xs)
+        else:
+            blk = m.blocks[i]
+            if blk[0] == "lr":
+                sv, wc, xc = blk[1], blk[2], blk[3]
+                W = unvalr(wc, t.size)
+                X = unvalr(xc, s.size)
+                tv = (X.T @ xs)
+                tv = (sv * tv.T).T
+                yp[t.start:t.end] += alpha * (W @ tv)
+            else:
+                yp[t.start:t.end] += alpha * (undirect(blk[1]) @ xs)
+    return _perm_out(ct, yp)
+
+
+def uh_mvm(m, alpha: float, x, beta: float = 1.0, y=None):
+    """Alg. 4 + Alg. 5 on a Uniform (FP64) or CUH (compressed) matrix."""
+    u = m if isinstance(m, Uniform) else m.u
+    h = u.h
+    ct = h.ct
+    cl = ct.clusters
+    if y is None:
+        y = np.zeros_like(np.asarray(x, dtype=np.float64))
+    xp, yp = _perm_in(ct, x, y, beta)
+    comp = not isinstance(m, Uniform)
+    Wb = [unvalr(m.W[c.id], c.size) for c in cl] if comp else u.W
+    Xb = [unvalr(m.X[c.id], c.size) for c in cl] if comp else u.X
+    # Alg. 4: forward transformation, every cluster independently
+    s = [Xb[c.id].T @ xp[c.start:c.end] for c in cl]
+    rows = [[] for _ in cl]
+    for i, b in enumerate(h.blocks):
+        rows[b.row].append(i)
+
+    def coupling(i):
+        return undirect(m.S[i][1]) if comp else u.S[i]
+
+    def uni(tid: int) -> None:                      # Alg. 5
+        t = cl[tid]
+        shp = (Wb[tid].shape[1],) + xp.shape[1:]
+        tt = np.zeros(shp)
+        for i in rows[tid]:
+            b = h.blocks[i]
+            if b.adm:
+                tt += coupling(i) @ s[b.col]
+        yl = Wb[tid] @ tt
+        for i in rows[tid]:
+            b = h.blocks[i]
+            if not b.adm:
+                sc = cl[b.col]
+                yl = yl + coupling(i) @ xp[sc.start:sc.end]
+        yp[t.start:t.end] += alpha * yl
+        for son in t.sons:
+            uni(son)
+
+    uni(0)
+    return _perm_out(ct, yp)
+
+
+def h2_mvm(m, alpha: float, x, beta: float = 1.0, y=None):
+    """Alg. 6 + Alg. 7 on an H2 (FP64) or CH2 (compressed) matrix."""
+    h2 = m if isinstance(m, H2) else m.m
+    h = h2.h
+    ct = h.ct
+    cl = ct.clusters
+    comp = not isinstance(m, H2)
+    if y is None:
+        y = np.zeros_like(np.asarray(x, dtype=np.float64))
+    xp, yp = _perm_in(ct, x, y, beta)
+    tail = xp.shape[1:]
+
+    def leafW(cid):
+        return unvalr(m.Wleaf[cid], cl[cid].size) if comp else h2.Wleaf[cid]
+
+    def leafX(cid):
+        return unvalr(m.Xleaf[cid], cl[cid].size) if comp else h2.Xleaf[cid]
+
+    def EW(cid):
+        return undirect(m.EW[cid]) if comp else h2.EW[cid]
+
+    def EX(cid):
+        return undirect(m.EX[cid]) if comp else h2.EX[cid]
+
+    def coupling(i):
+        return undirect(m.S[i][1]) if comp else h2.S[i]
+
+    s = [None] * len(cl)
+
+    def forward(sid: int) -> None:                  # Alg. 6
+        c = cl[sid]
+        if c.is_leaf:
+            s[sid] = leafX(sid).T @ xp[c.start:c.end]
+            return
+        s[sid] = np.zeros((h2.kX[sid],) + tail)
+        for son in c.sons:
+            forward(son)
+            s[sid] += EX(son).T @ s[son]
+
+    forward(0)
+    rows = [[] for _ in cl]
+    for i, b in enumerate(h.blocks):
+        rows[b.row].append(i)
+    t = [np.zeros((h2.kW[c.id],) + tail) for c in cl]
+
+    def h2mvm(tid: int) -> None:                     # Alg. 7
+        c = cl[tid]
+        for i in rows[tid]:
+            b = h.blocks[i]
+            if b.adm:
+                t[tid] += coupling(i) @ s[b.col]
+        if c.is_leaf:
+            yl = leafW(tid) @ t[tid]
+        else:
+            yl = np.zeros((c.size,) + tail)
+            for son in c.sons:
+                t[son] += EW(son) @ t[tid]
+        for i in rows[tid]:
+            b = h.blocks[i]
+            if not b.adm:
+                sc = cl[b.col]
+                yl = yl + coupling(i) @ xp[sc.start:sc.end]
+        yp[c.start:c.end] += alpha * yl
+        for son in c.sons:
+            h2mvm(son)
+
+    h2mvm(0)
+    return _perm_out(ct, yp)
+
+
+def dense_mvm(a: np.ndarray, alpha: float, x, beta: float = 1.0, y=None):
+    """y := alpha A x + beta y with a dense FP64 matrix (the plain definition)."""
+    x = np.asarray(x, dtype=np.float64)
+    if y is None:
+        y = np.zeros_like(x)
+    return alpha * (a @ x) + beta * np.asarray(y, dtype=np.float64)
