@@ -1,0 +1,180 @@
+/*
+ * hm.h -- C ABI of libhm: compressed hierarchical-matrix products on one GB300.
+ *
+ * Operation (eqn. mvm, Sec. 3, extended by beta):
+ *     y := alpha * M * x + beta * y
+ * for an H-, uniform-H (UH) or H^2-matrix M (Sec. 2.2-2.4) whose dense
+ * leaves, low-rank factors, cluster bases, coupling and transfer matrices are
+ * stored in the floating point compressed formats of Sec. 4 (AFLP or FPX,
+ * direct compression at eps, VALR per column from the singular values) and are
+ * decompressed inside the GPU kernels during the product.
+ *
+ * Conventions shared by every entry point:
+ *  - Every call returns an hm_status; nothing is thrown across the ABI.
+ *  - "host" pointers are ordinary CPU memory, "device" pointers are CUDA
+ *    global memory of the current device.  The caller owns every pointer it
+ *    passes; the library owns the hm_matrix and everything reachable from it.
+ *  - Vectors are FP64 in the ORIGINAL point order, column-major with a leading
+ *    dimension (ld >= n) and nrhs columns.
+ *  - GPU work is enqueued on the caller's stream (a cudaStream_t passed as
+ *    void*, NULL = legacy default stream) and never synchronised by the
+ *    library unless the entry point says so.
+ */
+#ifndef HM_H
+#define HM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hm_matrix hm_matrix;            /* opaque, library-owned */
+
+typedef enum {
+  HM_OK = 0,
+  HM_ERR_ARG = 1,        /* invalid argument (null pointer, size, enum value) */
+  HM_ERR_OOM = 2,        /* host or device allocation failed */
+  HM_ERR_CUDA = 3,       /* a CUDA runtime call failed */
+  HM_ERR_STATE = 4,      /* call order violated (e.g. matvec before compress) */
+  HM_ERR_TIMEOUT = 5,    /* a device-side wait ran out of iterations */
+  HM_ERR_IO = 6,         /* file could not be read or written */
+  HM_ERR_DEVICE = 7,     /* a kernel latched a bounds / format error */
+  HM_ERR_UNSUPPORTED = 8 /* data outside what the kernels decode (see hm_compress) */
+} hm_status;
+
+typedef enum { HM_FMT_H = 0, HM_FMT_UH = 1, HM_FMT_H2 = 2 } hm_format;
+typedef enum { HM_CODEC_NONE = 0, HM_CODEC_AFLP = 1, HM_CODEC_FPX = 2 } hm_codec;
+typedef enum { HM_KERNEL_LAPLACE = 0, HM_KERNEL_MATERN15 = 1 } hm_kernel;
+
+typedef struct {
+  int32_t kernel;      /* hm_kernel */
+  double kparam;       /* Laplace: diagonal spacing h (<= 0: sqrt(4 pi / n));
+                          Matern: length scale (<= 0: 0.1) */
+  int32_t leaf_size;   /* cluster tree leaf size (Def. Cluster Tree), 1..4096 */
+  double eta;          /* standard admissibility parameter, > 0 */
+  int32_t format;      /* hm_format */
+  double eps_build;    /* low-rank accuracy eps (eqn. epsilon), 0 < eps < 1 */
+  int32_t nthreads;    /* host threads for construction (<= 0: all cores) */
+} hm_build_params;
+
+/*
+ * hm_build -- construct M on the host (Sec. 2): cluster tree by geometric
+ * bisection, block tree with standard admissibility, dense leaves, low-rank
+ * blocks (ACA + SVD recompression, truncated at sigma_k <= eps*sigma_0), and
+ * for UH / H^2 the shared / nested cluster bases and couplings.
+ *   pts : host, n x 3 FP64, row-major (x0 y0 z0 x1 ...); copied.
+ *   out : receives a new matrix (FP64 host copy; nothing on the GPU yet).
+ * Errors: HM_ERR_ARG for null pointers, n < 1 or invalid parameters,
+ *         HM_ERR_OOM if host memory runs out.
+ */
+hm_status hm_build(const hm_build_params* prm, const double* pts, int64_t n, hm_matrix** out);
+
+/*
+ * hm_compress -- pack M for the GPU (Sec. 4.1, 4.2) and upload it.
+ *   eps   : compression accuracy (m_eps = ceil(-log2 eps)), 0 < eps < 1.
+ *   codec : HM_CODEC_NONE (FP64, the uncompressed baseline), AFLP or FPX.
+ *   valr  : nonzero = per-column accuracy from the singular values (VALR) for
+ *           low-rank factors and cluster bases; zero = direct compression at eps.
+ * May be called again (other eps / codec): the previous device copy is freed.
+ * Synchronises the device.  Errors: HM_ERR_ARG, HM_ERR_OOM, HM_ERR_CUDA,
+ * HM_ERR_UNSUPPORTED if a value range exceeds what the kernels decode
+ * (AFLP dynamic range >= 2^127, or |v| >= 2^127).
+ */
+hm_status hm_compress(hm_matrix* m, double eps, int32_t codec, int32_t valr);
+
+/*
+ * hm_matvec -- y := alpha*M*x + beta*y on the GPU, stream-ordered, no sync.
+ *   x : device, FP64, n x nrhs, leading dimension ldx >= n; read only.
+ *   y : device, FP64, n x nrhs, leading dimension ldy >= n; must not overlap x.
+ *   nrhs : 1..64 right-hand sides.
+ *   stream : cudaStream_t as void* (NULL = default stream).
+ * Concurrent calls on one matrix must be ordered by the caller (they share the
+ * matrix's workspace).  Device-side errors are latched, see hm_sync_status.
+ * Errors: HM_ERR_ARG, HM_ERR_STATE (not compressed), HM_ERR_CUDA (launch).
+ */
+hm_status hm_matvec(hm_matrix* m, double alpha, const double* x, int64_t ldx, double beta,
+                    double* y, int64_t ldy, int64_t nrhs, void* stream);
+
+/*
+ * hm_matvec_host -- the same product on HOST buffers: copies x and y to the
+ * device, runs hm_matvec, copies y back, and synchronises the stream.
+ * x, y : host FP64 (n x nrhs, ld n, column-major).  Uses library-owned
+ * device buffers.  Errors as hm_matvec plus HM_ERR_OOM.
+ */
+hm_status hm_matvec_host(hm_matrix* m, double alpha, const double* x, double beta, double* y,
+                         int64_t nrhs, void* stream);
+
+/* hm_free -- release host and device memory of m (NULL is accepted). */
+hm_status hm_free(hm_matrix* m);
+
+typedef struct {
+  int64_t n;                /* matrix dimension */
+  int32_t format, codec, valr;
+  double eps;               /* accuracy of the last hm_compress (0 if none) */
+  int64_t nclusters, nleaves, nblocks, nlowrank, ndense;
+  int32_t depth, max_rank;
+  int64_t bytes_fp64;       /* FP64 bytes of the same data (uncompressed) */
+  int64_t bytes_payload;    /* packed value bytes on the device (with padding) */
+  int64_t bytes_values;     /* packed value bytes without padding (algorithmic) */
+  int64_t bytes_meta;       /* headers, descriptors, work lists on the device */
+  int64_t bytes_workspace;  /* per-product workspace on the device */
+  int64_t bytes_lowrank_fp64; /* FP64 bytes of low-rank factors / bases */
+  int64_t bytes_dense_fp64;   /* FP64 bytes of dense leaves */
+  int64_t nlaunches;        /* kernels launched by one hm_matvec with nrhs = 1 */
+  int32_t tier;             /* 0: FP32 arithmetic, 1: float-float (eps <= 2^-22 or NONE) */
+} hm_info_t;
+
+/* hm_info -- sizes and counts of m.  Errors: HM_ERR_ARG. */
+hm_status hm_info(const hm_matrix* m, hm_info_t* out);
+
+/* hm_status_str -- static English text of a status code. */
+const char* hm_status_str(hm_status s);
+
+/*
+ * hm_sync_status -- synchronise `stream`, then read and clear the matrix's
+ * device error word.  Returns HM_ERR_DEVICE / HM_ERR_TIMEOUT if a kernel
+ * latched an error since the last call, HM_OK otherwise.
+ */
+hm_status hm_sync_status(hm_matrix* m, void* stream);
+
+/*
+ * hm_structure -- export the cluster tree and block tree (host buffers).
+ *   perm      : n int64, perm[position] = original index (may be NULL).
+ *   clusters  : nclusters x 4 int64 rows (start, end, level, parent) (may be NULL).
+ *   blocks    : nblocks x 3 int64 rows (row cluster, col cluster, admissible)
+ *               in depth-first block-tree order (may be NULL).
+ *   ranks     : nblocks int32, rank of each low-rank block, -1 for dense (may be NULL).
+ */
+hm_status hm_structure(const hm_matrix* m, int64_t* perm, int64_t* clusters, int64_t* blocks,
+                       int32_t* ranks);
+
+/*
+ * Codec entry points (Sec. 4.1).  A packed array of n values with one header
+ * is n codes of B bytes each, little-endian, value-contiguous.
+ *   hdr[0..3] = B, format (0 FPX-e8, 1 FPX-e11, 2 AFLP, 3 raw FP64), e, m (m' for AFLP)
+ *   vmin      = AFLP scale (1 for FPX / raw)
+ */
+typedef struct { int32_t B, fmt, e, m; double vmin; } hm_codec_header;
+
+/*
+ * hm_codec_encode -- host: compress n FP64 values (host, contiguous) with
+ * `codec` (AFLP or FPX) at accuracy key (AFLP: m requested mantissa bits;
+ * FPX: table row of the key).  out: host, capacity cap bytes (>= 8n suffices).
+ * Errors: HM_ERR_ARG (null, n < 0, key outside 0..60, cap too small, NaN/Inf).
+ */
+hm_status hm_codec_encode(const double* v, int64_t n, int32_t codec, int32_t key, uint8_t* out,
+                          int64_t cap, hm_codec_header* hdr);
+
+/*
+ * hm_codec_decode -- device (kernel K0): decode n packed values (device bytes,
+ * n*B long) into FP64 (device).  Bit-exact: AFLP uses fl(fl(s-1)*vmin).
+ * Stream-ordered, no sync.  Errors: HM_ERR_ARG, HM_ERR_CUDA.
+ */
+hm_status hm_codec_decode(const uint8_t* packed, int64_t n, const hm_codec_header* hdr,
+                          double* out, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HM_H */

@@ -1,0 +1,219 @@
+"""Thin ctypes binding of libhm (include/hm.h): argument marshalling only.
+
+Every entry point keeps the C name.  Device buffers are plain pointers (for
+example ``torch.Tensor.data_ptr()`` of CUDA tensors) and streams are raw
+``cudaStream_t`` handles (``torch.cuda.current_stream().cuda_stream``).  The
+library must be built (``paper_2405_03456_gb300.build.build()``); loading fails
+loudly otherwise -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+HM_FMT_H, HM_FMT_UH, HM_FMT_H2 = 0, 1, 2
+HM_CODEC_NONE, HM_CODEC_AFLP, HM_CODEC_FPX = 0, 1, 2
+HM_KERNEL_LAPLACE, HM_KERNEL_MATERN15 = 0, 1
+FORMATS = {"h": HM_FMT_H, "uh": HM_FMT_UH, "h2": HM_FMT_H2}
+CODECS = {"none": HM_CODEC_NONE, "aflp": HM_CODEC_AFLP, "fpx": HM_CODEC_FPX}
+KERNELS = {"laplace": HM_KERNEL_LAPLACE, "matern": HM_KERNEL_MATERN15}
+
+DECLARED = ["hm_build", "hm_compress", "hm_matvec", "hm_matvec_host", "hm_free", "hm_info",
+            "hm_status_str", "hm_sync_status", "hm_structure", "hm_codec_encode", "hm_codec_decode"]
+
+
+class hm_build_params(C.Structure):
+    _fields_ = [("kernel", C.c_int32), ("kparam", C.c_double), ("leaf_size", C.c_int32),
+                ("eta", C.c_double), ("format", C.c_int32), ("eps_build", C.c_double),
+                ("nthreads", C.c_int32)]
+
+
+class hm_info_t(C.Structure):
+    _fields_ = [("n", C.c_int64), ("format", C.c_int32), ("codec", C.c_int32), ("valr", C.c_int32),
+                ("eps", C.c_double), ("nclusters", C.c_int64), ("nleaves", C.c_int64),
+                ("nblocks", C.c_int64), ("nlowrank", C.c_int64), ("ndense", C.c_int64),
+                ("depth", C.c_int32), ("max_rank", C.c_int32), ("bytes_fp64", C.c_int64),
+                ("bytes_payload", C.c_int64), ("bytes_values", C.c_int64), ("bytes_meta", C.c_int64),
+                ("bytes_workspace", C.c_int64), ("bytes_lowrank_fp64", C.c_int64),
+                ("bytes_dense_fp64", C.c_int64), ("nlaunches", C.c_int64), ("tier", C.c_int32)]
+
+
+class hm_codec_header(C.Structure):
+    _fields_ = [("B", C.c_int32), ("fmt", C.c_int32), ("e", C.c_int32), ("m", C.c_int32),
+                ("vmin", C.c_double)]
+
+
+class HMError(RuntimeError):
+    pass
+
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(path: str | None = None) -> C.CDLL:
+    """Load libhm; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or _build.LIB
+    if not os.path.exists(p):
+        raise HMError(f"libhm is not built ({p}); run paper_2405_03456_gb300.build.build()")
+    L = C.CDLL(p)
+    vp, i32, i64, dbl = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+    sig = {
+        "hm_build": ([C.POINTER(hm_build_params), vp, i64, C.POINTER(vp)], i32),
+        "hm_compress": ([vp, dbl, i32, i32], i32),
+        "hm_matvec": ([vp, dbl, vp, i64, dbl, vp, i64, i64, vp], i32),
+        "hm_matvec_host": ([vp, dbl, vp, dbl, vp, i64, vp], i32),
+        "hm_free": ([vp], i32),
+        "hm_info": ([vp, C.POINTER(hm_info_t)], i32),
+        "hm_status_str": ([i32], C.c_char_p),
+        "hm_sync_status": ([vp, vp], i32),
+        "hm_structure": ([vp, vp, vp, vp, vp], i32),
+        "hm_codec_encode": ([vp, i64, i32, i32, vp, i64, C.POINTER(hm_codec_header)], i32),
+        "hm_codec_decode": ([vp, i64, C.POINTER(hm_codec_header), vp, vp], i32),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = L
+    return L
+
+
+def check(status: int, what: str = "") -> None:
+    if status != 0:
+        msg = load().hm_status_str(status).decode()
+        raise HMError(f"{what}: {msg} ({status})")
+
+
+def _ptr(a: np.ndarray) -> int:
+    return a.ctypes.data
+
+
+# ---------------------------------------------------------------- C entry points
+def hm_build(pts: np.ndarray, kernel: str = "laplace", leaf_size: int = 64, eta: float = 2.0,
+             fmt: str = "h", eps_build: float = 1e-6, kparam: float = 0.0, nthreads: int = 0) -> int:
+    p = hm_build_params(KERNELS[kernel], kparam, leaf_size, eta, FORMATS[fmt], eps_build, nthreads)
+    pts = np.ascontiguousarray(pts, dtype=np.float64)
+    h = C.c_void_p()
+    check(load().hm_build(C.byref(p), _ptr(pts), pts.shape[0], C.byref(h)), "hm_build")
+    return h.value
+
+
+def hm_compress(h: int, eps: float, codec: str = "aflp", valr: bool = True) -> None:
+    check(load().hm_compress(h, eps, CODECS[codec], 1 if valr else 0), "hm_compress")
+
+
+def hm_matvec(h: int, alpha: float, x_ptr: int, ldx: int, beta: float, y_ptr: int, ldy: int,
+              nrhs: int = 1, stream: int = 0) -> None:
+    check(load().hm_matvec(h, alpha, x_ptr, ldx, beta, y_ptr, ldy, nrhs, stream), "hm_matvec")
+
+
+def hm_matvec_host(h: int, alpha: float, x: np.ndarray, beta: float, y: np.ndarray, stream: int = 0) -> None:
+    """x, y: host FP64 arrays of shape (n,) or (n, nrhs), Fortran order (y updated in place)."""
+    assert x.dtype == np.float64 and y.dtype == np.float64 and x.flags.f_contiguous and y.flags.f_contiguous
+    nrhs = 1 if x.ndim == 1 else x.shape[1]
+    check(load().hm_matvec_host(h, alpha, _ptr(x), beta, _ptr(y), nrhs, stream), "hm_matvec_host")
+
+
+def hm_free(h: int) -> None:
+    check(load().hm_free(h), "hm_free")
+
+
+def hm_info(h: int) -> dict:
+    o = hm_info_t()
+    check(load().hm_info(h, C.byref(o)), "hm_info")
+    return {f: getattr(o, f) for f, _ in hm_info_t._fields_}
+
+
+def hm_sync_status(h: int, stream: int = 0) -> int:
+    return load().hm_sync_status(h, stream)
+
+
+def hm_structure(h: int):
+    info = hm_info(h)
+    n, nc, nb = info["n"], info["nclusters"], info["nblocks"]
+    perm = np.empty(n, dtype=np.int64)
+    cl = np.empty((nc, 4), dtype=np.int64)
+    bl = np.empty((nb, 3), dtype=np.int64)
+    rk = np.empty(nb, dtype=np.int32)
+    check(load().hm_structure(h, _ptr(perm), _ptr(cl), _ptr(bl), _ptr(rk)), "hm_structure")
+    return perm, cl, bl, rk
+
+
+def hm_codec_encode(v: np.ndarray, codec: str, key: int):
+    """Host encode; returns (packed uint8 array, header dict)."""
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    out = np.zeros(max(8 * v.size, 8), dtype=np.uint8)
+    hdr = hm_codec_header()
+    check(load().hm_codec_encode(_ptr(v), v.size, CODECS[codec], key, _ptr(out), out.size, C.byref(hdr)),
+          "hm_codec_encode")
+    h = {"B": hdr.B, "fmt": hdr.fmt, "e": hdr.e, "m": hdr.m, "vmin": hdr.vmin}
+    return out[: v.size * hdr.B].copy(), h
+
+
+def hm_codec_decode(packed_ptr: int, n: int, hdr: dict, out_ptr: int, stream: int = 0) -> None:
+    """Device decode (kernel K0) of n packed values into FP64 device memory."""
+    h = hm_codec_header(hdr["B"], hdr["fmt"], hdr["e"], hdr["m"], hdr["vmin"])
+    check(load().hm_codec_decode(packed_ptr, n, C.byref(h), out_ptr, stream), "hm_codec_decode")
+
+
+# ---------------------------------------------------------------- convenience object
+class HMatrix:
+    """Owns one hm_matrix handle; products take CUDA tensors (torch) or host arrays."""
+
+    def __init__(self, pts, kernel="laplace", leaf_size=64, eta=2.0, fmt="h", eps_build=1e-6,
+                 kparam=0.0, nthreads=0):
+        self.h = hm_build(pts, kernel, leaf_size, eta, fmt, eps_build, kparam, nthreads)
+        self.n = pts.shape[0]
+
+    def compress(self, eps, codec="aflp", valr=True):
+        hm_compress(self.h, eps, codec, valr)
+        return self
+
+    def matvec(self, alpha, x, beta, y, stream=None):
+        """y := alpha*M*x + beta*y for CUDA FP64 tensors x, y of shape (n,) or (n, r) column-major."""
+        import torch
+        if stream is None:
+            stream = torch.cuda.current_stream().cuda_stream
+        nrhs = 1 if x.dim() == 1 else x.shape[1]
+        ldx = x.shape[0] if x.dim() == 1 else x.stride(1)
+        ldy = y.shape[0] if y.dim() == 1 else y.stride(1)
+        assert x.dtype == torch.float64 and y.dtype == torch.float64 and x.is_cuda and y.is_cuda
+        assert x.dim() == 1 or x.stride(0) == 1
+        assert y.dim() == 1 or y.stride(0) == 1
+        hm_matvec(self.h, alpha, x.data_ptr(), ldx, beta, y.data_ptr(), ldy, nrhs, stream)
+        return y
+
+    def matvec_host(self, alpha, x, beta, y, stream=0):
+        hm_matvec_host(self.h, alpha, x, beta, y, stream)
+        return y
+
+    def info(self):
+        return hm_info(self.h)
+
+    def structure(self):
+        return hm_structure(self.h)
+
+    def sync_status(self, stream=0):
+        return hm_sync_status(self.h, stream)
+
+    def close(self):
+        if self.h:
+            hm_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
