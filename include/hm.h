@@ -51,7 +51,7 @@ typedef struct {
   int32_t kernel;      /* hm_kernel */
   double kparam;       /* Laplace: diagonal spacing h (<= 0: sqrt(4 pi / n));
                           Matern: length scale (<= 0: 0.1) */
-  int32_t leaf_size;   /* cluster tree leaf size (Def. Cluster Tree), 1..4096 */
+  int32_t leaf_size;   /* cluster tree leaf size (Def. Cluster Tree), 1..128 */
   double eta;          /* standard admissibility parameter, > 0 */
   int32_t format;      /* hm_format */
   double eps_build;    /* low-rank accuracy eps (eqn. epsilon), 0 < eps < 1 */
@@ -173,6 +173,24 @@ hm_status hm_codec_encode(const double* v, int64_t n, int32_t codec, int32_t key
  */
 hm_status hm_codec_decode(const uint8_t* packed, int64_t n, const hm_codec_header* hdr,
                           double* out, void* stream);
+
+/*
+ * Kernel profiling.  hm_profile(m, 1) makes every later hm_matvec record a
+ * CUDA event pair around each of its kernel launches, on the caller's stream;
+ * hm_profile_read synchronises those events, returns per kernel kind the
+ * summed duration, the launch count and the algorithmic bytes those launches
+ * move (packed values, format words, descriptors, vector reads and writes),
+ * and clears the record.  Kinds: 0 gather, 1 column dots (phase A),
+ * 2 segment sums, 3 row chunks (phase C / couplings / sweeps).
+ * out : host array of nout (<= 4) entries.  Errors: HM_ERR_ARG, HM_ERR_CUDA.
+ */
+typedef struct { double ms; int64_t launches; int64_t bytes; } hm_kernel_stat;
+hm_status hm_profile(hm_matrix* m, int32_t enable);
+hm_status hm_profile_read(hm_matrix* m, hm_kernel_stat* out, int32_t nout);
+
+/* hm_alg_bytes -- algorithmic bytes one hm_matvec moves per right-hand side
+ * (the sum over its launches of the bytes hm_profile_read reports). */
+hm_status hm_alg_bytes(const hm_matrix* m, int64_t* bytes);
 
 #ifdef __cplusplus
 }

@@ -46,30 +46,41 @@ def h_mvm(m, alpha: float, x, beta: float = 1.0, y=None):
     if y is None:
         y = np.zeros_like(np.asarray(x, dtype=np.float64))
     xp, yp = _perm_in(ct, x, y, beta)
-    cl = ct.clusters
-    for i, b in enumerate(h.blocks):
-        t, s = cl[b.row], cl[b.col]
-        xs = xp[s.start:s.end]
-        if isinstance(m, HMatrix):
-            d = m.data[i]
-            if isinstance(d, LowRank):
-                tv = (d.X.T @ xs)
-                tv = (d.s * tv.T).T
-                yp[t.start:t.end] += alpha * (d.W @ tv)
-            else:
-                yp[t.start:t.end] += alpha * (d @ xs)
-        else:
-            blk = m.blocks[i]
-            if blk[0] == "lr":
-                sv, wc, xc = blk[1], blk[2], blk[3]
-                W = unvalr(wc, t.size)
-                X = unvalr(xc, s.size)
-                tv = (X.T @ xs)
-                tv = (sv * tv.T).T
-                yp[t.start:t.end] += alpha * (W @ tv)
-            else:
-                yp[t.start:t.end] += alpha * (undirect(blk[1]) @ xs)
+    for i in range(len(h.blocks)):
+        h_block_apply(m, i, alpha, xp, yp)
     return _perm_out(ct, yp)
+
+
+def h_block_apply(m, i: int, alpha: float, xp, yp) -> None:
+    """One step of Alg. 1: leaf block i of an HMatrix or CH, y|t += alpha M_ts x|s.
+
+    Low-rank: t := V^H x|s with V = X diag(sigma), y|t += alpha W t; dense:
+    y|t += alpha D x|s.  Compressed data are decompressed first (Alg. 8).
+    """
+    h = m if isinstance(m, HMatrix) else m.h
+    cl = h.ct.clusters
+    b = h.blocks[i]
+    t, s = cl[b.row], cl[b.col]
+    xs = xp[s.start:s.end]
+    if isinstance(m, HMatrix):
+        d = m.data[i]
+        if isinstance(d, LowRank):
+            tv = (d.X.T @ xs)
+            tv = (d.s * tv.T).T
+            yp[t.start:t.end] += alpha * (d.W @ tv)
+        else:
+            yp[t.start:t.end] += alpha * (d @ xs)
+        return
+    blk = m.blocks[i]
+    if blk[0] == "lr":
+        sv, wc, xc = blk[1], blk[2], blk[3]
+        W = unvalr(wc, t.size)
+        X = unvalr(xc, s.size)
+        tv = (X.T @ xs)
+        tv = (sv * tv.T).T
+        yp[t.start:t.end] += alpha * (W @ tv)
+    else:
+        yp[t.start:t.end] += alpha * (undirect(blk[1]) @ xs)
 
 
 def uh_mvm(m, alpha: float, x, beta: float = 1.0, y=None):

@@ -62,10 +62,11 @@ struct Packer {
   // append n codes of B bytes (little-endian), column padded to 4 bytes
   uint64_t put(const uint64_t* codes, int64_t n, int64_t inc, int B) {
     uint64_t off = align4();
-    pay.reserve(pay.size() + n * B + 4);
+    pay.resize(off + (uint64_t)(n * B));
+    uint8_t* dst = pay.data() + off;
     for (int64_t i = 0; i < n; ++i) {
       uint64_t c = codes[i * inc];
-      for (int b = 0; b < B; ++b) pay.push_back((uint8_t)(c >> (8 * b)));
+      for (int b = 0; b < B; ++b) dst[i * B + b] = (uint8_t)(c >> (8 * b));
     }
     value_bytes += n * B;
     align4();
@@ -105,6 +106,7 @@ struct Launch {
   int64_t off = 0, n = 0;        // range in the item / out / chunk array
   bool use_pscale = false;
   bool use_rowscale = false;
+  int64_t bytes = 0;             // algorithmic bytes of the launch
 };
 
 template <typename T>
@@ -168,6 +170,25 @@ struct hm_matrix {
   int64_t d_h_cap = 0;
   int grid_cdot = 0, grid_rg = 0;
   std::mutex mu;
+  // profiling: event pairs per launch
+  bool prof = false;
+  struct Rec {
+    int kind;
+    cudaEvent_t e0, e1;
+    int64_t bytes;
+  };
+  std::vector<Rec> recs;
+  std::vector<cudaEvent_t> evpool;
+  cudaEvent_t take_event() {
+    if (!evpool.empty()) {
+      cudaEvent_t e = evpool.back();
+      evpool.pop_back();
+      return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+  }
 
   void release_device() {
     d_pay.release();
@@ -328,13 +349,23 @@ bool pack_dense(Ctx& cx, Program& P, const std::vector<std::vector<int>>& lv, De
   dt.off.assign(H.blocks.size(), {});
   dt.fidx.assign(H.blocks.size(), 0);
   dt.scale.assign(H.blocks.size(), 1.0);
+  const int64_t nb = (int64_t)H.blocks.size();
+  std::vector<std::vector<Enc>> encs(nb);
+  std::atomic<bool> ok{true};
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int64_t b = 0; b < nb; ++b) {
+    if (H.blocks[b].adm) continue;
+    const auto& D = H.dn[H.slot[b]].D;
+    encs[b].resize(1);
+    if (!encode(D.data(), (int64_t)D.size(), 1, cx.codec, cx.key_eps, encs[b][0])) ok = false;
+  }
+  if (!ok) return false;
   for (size_t b = 0; b < H.blocks.size(); ++b) {
     if (H.blocks[b].adm) continue;
     const Cluster& t = ct.cl[H.blocks[b].row];
     const Cluster& s = ct.cl[H.blocks[b].col];
     const auto& D = H.dn[H.slot[b]].D;
-    std::vector<Enc> enc(1);
-    if (!encode(D.data(), (int64_t)D.size(), 1, cx.codec, cx.key_eps, enc[0])) return false;
+    std::vector<Enc> enc = std::move(encs[b]);
     std::vector<std::pair<int64_t, int64_t>> sp;
     for (int c : lv[H.blocks[b].row]) sp.push_back({ct.cl[c].start - t.start, ct.cl[c].end - t.start});
     dt.off[b] = pack_tiled(P.pk, enc, true, t.size(), s.size(), sp);
@@ -449,16 +480,25 @@ bool program_h(Ctx& cx) {
   int64_t pbase = 0;
   int64_t items0 = (int64_t)P.items.size();
   int64_t g0 = (int64_t)P.gouts.size();
+  std::vector<std::vector<Enc>> encx(nb), encw(nb);
+  std::atomic<bool> ok{true};
+#pragma omp parallel for schedule(dynamic, 8)
+  for (int64_t b = 0; b < (int64_t)nb; ++b) {
+    if (!H.blocks[b].adm) continue;
+    const auto& L = H.lr[H.slot[b]];
+    if (L.k == 0) continue;
+    auto keys = keys_lowrank(cx, L.s);
+    if (!enc_matrix_cols(cx, L.X, ct.cl[H.blocks[b].col].size(), L.k, keys, encx[b])) ok = false;
+    if (!enc_matrix_cols(cx, L.W, ct.cl[H.blocks[b].row].size(), L.k, keys, encw[b])) ok = false;
+  }
+  if (!ok) return false;
   for (size_t b = 0; b < nb; ++b) {
     if (!H.blocks[b].adm) continue;
     const auto& L = H.lr[H.slot[b]];
     if (L.k == 0) continue;
     const Cluster& t = ct.cl[H.blocks[b].row];
     const Cluster& s = ct.cl[H.blocks[b].col];
-    auto keys = keys_lowrank(cx, L.s);
-    std::vector<Enc> ex, ew;
-    if (!enc_matrix_cols(cx, L.X, s.size(), L.k, keys, ex)) return false;
-    if (!enc_matrix_cols(cx, L.W, t.size(), L.k, keys, ew)) return false;
+    std::vector<Enc> ex = std::move(encx[b]), ew = std::move(encw[b]);
     P.fp64_lowrank += (t.size() + s.size()) * L.k * 8;
     int32_t fx = push_fmts(P.pk, ex);
     uint64_t xo = pack_cols(P.pk, ex, false, s.size(), L.k);
@@ -879,6 +919,55 @@ bool program_h2(Ctx& cx) {
   return true;
 }
 
+// Algorithmic bytes of every launch (values without padding, format words,
+// descriptors, vector reads / writes).
+void launch_bytes(Program& P) {
+  auto colbytes = [&](int32_t fmt, int ncols, int64_t rows) {
+    int64_t b = 0;
+    if (fmt < 0) {
+      b = rows * (int64_t)(P.pk.fmts[~fmt] & 0xff) * ncols + 4;
+    } else {
+      for (int j = 0; j < ncols; ++j) b += rows * (int64_t)(P.pk.fmts[fmt + j] & 0xff) + 4;
+    }
+    return b;
+  };
+  for (Launch& L : P.launches) {
+    int64_t b = 0;
+    switch (L.kind) {
+      case Launch::GATHER:
+        b = L.n * (4 + 8 + 8);
+        break;
+      case Launch::CDOT:
+        for (int64_t i = L.off; i < L.off + L.n; ++i) {
+          const CdotItem& it = P.items[i];
+          int64_t vb = colbytes(it.fmt, it.ncols, it.seg);
+          if (it.fmt >= 0) vb -= 0;   // format words counted once per item
+          b += vb + (int64_t)sizeof(CdotItem) + 8 * (int64_t)it.seg + 8 * (int64_t)it.ncols;
+        }
+        break;
+      case Launch::GSUM:
+        for (int64_t i = L.off; i < L.off + L.n; ++i) {
+          const GsumOut& o = P.gouts[i];
+          b += (int64_t)(o.p1 - o.p0) * (4 + 8 + 8) + (int64_t)sizeof(GsumOut) + 8;
+        }
+        break;
+      case Launch::RGEMV:
+        for (int64_t i = L.off; i < L.off + L.n; ++i) {
+          const Chunk& c = P.chunks[i];
+          b += (int64_t)sizeof(Chunk);
+          for (int32_t t = c.t0; t < c.t1; ++t) {
+            const Tile& T = P.tiles[t];
+            b += (int64_t)sizeof(Tile) + colbytes(T.fmt, T.ncols, c.nrows) + 8 * (int64_t)T.ncols;
+          }
+          if (L.mode == MODE_Y) b += (int64_t)c.nrows * (4 + 8 + 8);
+          else b += (int64_t)c.nrows * ((L.mode == MODE_VEC_ADD ? 16 : 8) + (L.use_rowscale ? 8 : 0));
+        }
+        break;
+    }
+    L.bytes = b;
+  }
+}
+
 hm_status cuda_status(cudaError_t e) {
   if (e == cudaSuccess) return HM_OK;
   if (e == cudaErrorMemoryAllocation) return HM_ERR_OOM;
@@ -991,6 +1080,7 @@ hm_status hm_compress(hm_matrix* M, double eps, int32_t codec, int32_t valr) {
     return HM_ERR_UNSUPPORTED;
   }
   P.pk.pay.resize(P.pk.pay.size() + 64, 0);   // tail reads of the last column stay in bounds
+  launch_bytes(P);
   hm_status s = upload(M);
   if (s != HM_OK) {
     M->release_device();
@@ -1008,6 +1098,12 @@ static hm_status run_program(hm_matrix* M, double alpha, const double* x, double
   Program& P = M->prog;
   cudaError_t e = cudaSuccess;
   for (const Launch& L : P.launches) {
+    hm_matrix::Rec rec{(int)L.kind, nullptr, nullptr, L.bytes};
+    if (M->prof) {
+      rec.e0 = M->take_event();
+      rec.e1 = M->take_event();
+      cudaEventRecord(rec.e0, st);
+    }
     switch (L.kind) {
       case Launch::GATHER:
         e = launch_gather(x, M->d_perm.p, (int)L.n, M->d_vec, st);
@@ -1027,6 +1123,10 @@ static hm_status run_program(hm_matrix* M, double alpha, const double* x, double
         break;
     }
     if (e != cudaSuccess) return HM_ERR_CUDA;
+    if (M->prof) {
+      cudaEventRecord(rec.e1, st);
+      M->recs.push_back(rec);
+    }
   }
   return HM_OK;
 }
@@ -1074,8 +1174,47 @@ hm_status hm_matvec_host(hm_matrix* M, double alpha, const double* x, double bet
   return HM_OK;
 }
 
+hm_status hm_profile(hm_matrix* M, int32_t enable) {
+  if (!M) return HM_ERR_ARG;
+  M->prof = enable != 0;
+  return HM_OK;
+}
+
+hm_status hm_profile_read(hm_matrix* M, hm_kernel_stat* out, int32_t nout) {
+  if (!M || !out || nout < 0 || nout > 4) return HM_ERR_ARG;
+  hm_kernel_stat acc[4];
+  std::memset(acc, 0, sizeof(acc));
+  hm_status st = HM_OK;
+  for (auto& r : M->recs) {
+    float ms = 0;
+    if (cudaEventSynchronize(r.e1) != cudaSuccess || cudaEventElapsedTime(&ms, r.e0, r.e1) != cudaSuccess)
+      st = HM_ERR_CUDA;
+    acc[r.kind].ms += ms;
+    acc[r.kind].launches += 1;
+    acc[r.kind].bytes += r.bytes;
+    M->evpool.push_back(r.e0);
+    M->evpool.push_back(r.e1);
+  }
+  M->recs.clear();
+  for (int i = 0; i < nout; ++i) out[i] = acc[i];
+  return st;
+}
+
+hm_status hm_alg_bytes(const hm_matrix* M, int64_t* bytes) {
+  if (!M || !bytes) return HM_ERR_ARG;
+  int64_t b = 0;
+  for (const Launch& L : M->prog.launches) b += L.bytes;
+  *bytes = b;
+  return HM_OK;
+}
+
 hm_status hm_free(hm_matrix* M) {
   if (!M) return HM_OK;
+  for (auto& r : M->recs) {
+    cudaEventDestroy(r.e0);
+    cudaEventDestroy(r.e1);
+  }
+  for (auto e : M->evpool) cudaEventDestroy(e);
   M->release_device();
   delete M;
   return HM_OK;

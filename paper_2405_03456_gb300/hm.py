@@ -23,7 +23,9 @@ CODECS = {"none": HM_CODEC_NONE, "aflp": HM_CODEC_AFLP, "fpx": HM_CODEC_FPX}
 KERNELS = {"laplace": HM_KERNEL_LAPLACE, "matern": HM_KERNEL_MATERN15}
 
 DECLARED = ["hm_build", "hm_compress", "hm_matvec", "hm_matvec_host", "hm_free", "hm_info",
-            "hm_status_str", "hm_sync_status", "hm_structure", "hm_codec_encode", "hm_codec_decode"]
+            "hm_status_str", "hm_sync_status", "hm_structure", "hm_codec_encode", "hm_codec_decode",
+            "hm_profile", "hm_profile_read", "hm_alg_bytes"]
+KERNEL_KINDS = ["gather", "cdot", "gsum", "rgemv"]
 
 
 class hm_build_params(C.Structure):
@@ -45,6 +47,10 @@ class hm_info_t(C.Structure):
 class hm_codec_header(C.Structure):
     _fields_ = [("B", C.c_int32), ("fmt", C.c_int32), ("e", C.c_int32), ("m", C.c_int32),
                 ("vmin", C.c_double)]
+
+
+class hm_kernel_stat(C.Structure):
+    _fields_ = [("ms", C.c_double), ("launches", C.c_int64), ("bytes", C.c_int64)]
 
 
 class HMError(RuntimeError):
@@ -80,6 +86,9 @@ def load(path: str | None = None) -> C.CDLL:
         "hm_structure": ([vp, vp, vp, vp, vp], i32),
         "hm_codec_encode": ([vp, i64, i32, i32, vp, i64, C.POINTER(hm_codec_header)], i32),
         "hm_codec_decode": ([vp, i64, C.POINTER(hm_codec_header), vp, vp], i32),
+        "hm_profile": ([vp, i32], i32),
+        "hm_profile_read": ([vp, C.POINTER(hm_kernel_stat), i32], i32),
+        "hm_alg_bytes": ([vp, C.POINTER(i64)], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -167,6 +176,23 @@ def hm_codec_decode(packed_ptr: int, n: int, hdr: dict, out_ptr: int, stream: in
     check(load().hm_codec_decode(packed_ptr, n, C.byref(h), out_ptr, stream), "hm_codec_decode")
 
 
+def hm_profile(h: int, enable: bool) -> None:
+    check(load().hm_profile(h, 1 if enable else 0), "hm_profile")
+
+
+def hm_profile_read(h: int) -> dict:
+    arr = (hm_kernel_stat * 4)()
+    check(load().hm_profile_read(h, arr, 4), "hm_profile_read")
+    return {KERNEL_KINDS[i]: {"ms": arr[i].ms, "launches": arr[i].launches, "bytes": arr[i].bytes}
+            for i in range(4)}
+
+
+def hm_alg_bytes(h: int) -> int:
+    b = C.c_int64()
+    check(load().hm_alg_bytes(h, C.byref(b)), "hm_alg_bytes")
+    return b.value
+
+
 # ---------------------------------------------------------------- convenience object
 class HMatrix:
     """Owns one hm_matrix handle; products take CUDA tensors (torch) or host arrays."""
@@ -200,6 +226,15 @@ class HMatrix:
 
     def info(self):
         return hm_info(self.h)
+
+    def alg_bytes(self):
+        return hm_alg_bytes(self.h)
+
+    def profile(self, enable=True):
+        hm_profile(self.h, enable)
+
+    def profile_read(self):
+        return hm_profile_read(self.h)
 
     def structure(self):
         return hm_structure(self.h)
