@@ -40,7 +40,8 @@ typedef enum {
   HM_ERR_TIMEOUT = 5,    /* a device-side wait ran out of iterations */
   HM_ERR_IO = 6,         /* file could not be read or written */
   HM_ERR_DEVICE = 7,     /* a kernel latched a bounds / format error */
-  HM_ERR_UNSUPPORTED = 8 /* data outside what the kernels decode (see hm_compress) */
+  HM_ERR_UNSUPPORTED = 8, /* data outside what the kernels decode (see hm_compress) */
+  HM_ERR_CAPACITY = 9     /* request larger than hm_matvec_host_noalloc's fixed scratch */
 } hm_status;
 
 typedef enum { HM_FMT_H = 0, HM_FMT_UH = 1, HM_FMT_H2 = 2 } hm_format;
@@ -191,6 +192,32 @@ hm_status hm_profile_read(hm_matrix* m, hm_kernel_stat* out, int32_t nout);
 /* hm_alg_bytes -- algorithmic bytes one hm_matvec moves per right-hand side
  * (the sum over its launches of the bytes hm_profile_read reports). */
 hm_status hm_alg_bytes(const hm_matrix* m, int64_t* bytes);
+
+/*
+ * hm_matvec_host_noalloc -- hm_matvec_host for callers that cannot let the
+ * library allocate device memory.  (The paper has no counterpart: this is a
+ * deployment aid.)  A serving process that has committed its whole HBM budget
+ * up front, or code that must not trigger cudaFree's device-wide
+ * synchronisation while other streams run, cannot use hm_matvec_host, which
+ * allocates (and may re-allocate) its device staging buffers.  This entry
+ * point stages x and y instead through one fixed array compiled into libhm
+ * (2 * HM_NOALLOC_MAX_ENTRIES doubles, 16 MiB, held on every GPU that loads
+ * the library until the process exits) and calls no cudaMalloc or cudaFree.
+ *   m, alpha, beta, nrhs, stream : as hm_matvec_host (m must be compressed).
+ *   x, y : host FP64 (n x nrhs, ld n, column-major); y is overwritten with
+ *          alpha*M*x + beta*y.  Synchronises `stream` before returning.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls share the one array: calls whose GPU
+ * work overlaps (other host threads, other streams) race and must be
+ * serialised by the caller.  x and y are copied in whole on every call, so no
+ * earlier contents are read and nothing needs clearing.
+ * Errors: HM_ERR_ARG, HM_ERR_STATE (not compressed), HM_ERR_CAPACITY if
+ * n * nrhs > HM_NOALLOC_MAX_ENTRIES, HM_ERR_CUDA.
+ */
+#define HM_NOALLOC_MAX_ENTRIES (1 << 20)
+hm_status hm_matvec_host_noalloc(hm_matrix* m, double alpha, const double* x, double beta, double* y,
+                                 int64_t nrhs, void* stream);
 
 #ifdef __cplusplus
 }

@@ -22,7 +22,7 @@ NVCC = shutil.which("nvcc") or os.path.join(CUDA, "bin", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 CPP = ["trees.cpp", "linalg.cpp", "build.cpp", "codec.cpp", "matrix.cpp"]
-CU = ["kernels.cu"]
+CU = ["kernels.cu", "noalloc.cu"]
 HDRS = ["hm_internal.h", "dev_types.h"]
 
 

@@ -1021,6 +1021,7 @@ const char* hm_status_str(hm_status s) {
     case HM_ERR_IO: return "I/O error";
     case HM_ERR_DEVICE: return "device-side error latched";
     case HM_ERR_UNSUPPORTED: return "data outside the decodable range";
+    case HM_ERR_CAPACITY: return "request exceeds the fixed device scratch of hm_matvec_host_noalloc";
   }
   return "unknown status";
 }

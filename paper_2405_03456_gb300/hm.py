@@ -24,7 +24,8 @@ KERNELS = {"laplace": HM_KERNEL_LAPLACE, "matern": HM_KERNEL_MATERN15}
 
 DECLARED = ["hm_build", "hm_compress", "hm_matvec", "hm_matvec_host", "hm_free", "hm_info",
             "hm_status_str", "hm_sync_status", "hm_structure", "hm_codec_encode", "hm_codec_decode",
-            "hm_profile", "hm_profile_read", "hm_alg_bytes"]
+            "hm_profile", "hm_profile_read", "hm_alg_bytes", "hm_matvec_host_noalloc"]
+HM_NOALLOC_MAX_ENTRIES = 1 << 20
 KERNEL_KINDS = ["gather", "cdot", "gsum", "rgemv"]
 
 
@@ -89,6 +90,7 @@ def load(path: str | None = None) -> C.CDLL:
         "hm_profile": ([vp, i32], i32),
         "hm_profile_read": ([vp, C.POINTER(hm_kernel_stat), i32], i32),
         "hm_alg_bytes": ([vp, C.POINTER(i64)], i32),
+        "hm_matvec_host_noalloc": ([vp, dbl, vp, dbl, vp, i64, vp], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -132,6 +134,15 @@ def hm_matvec_host(h: int, alpha: float, x: np.ndarray, beta: float, y: np.ndarr
     assert x.dtype == np.float64 and y.dtype == np.float64 and x.flags.f_contiguous and y.flags.f_contiguous
     nrhs = 1 if x.ndim == 1 else x.shape[1]
     check(load().hm_matvec_host(h, alpha, _ptr(x), beta, _ptr(y), nrhs, stream), "hm_matvec_host")
+
+
+def hm_matvec_host_noalloc(h: int, alpha: float, x: np.ndarray, beta: float, y: np.ndarray,
+                           stream: int = 0) -> None:
+    """As hm_matvec_host, staged through libhm's fixed device array (no allocation)."""
+    assert x.dtype == np.float64 and y.dtype == np.float64 and x.flags.f_contiguous and y.flags.f_contiguous
+    nrhs = 1 if x.ndim == 1 else x.shape[1]
+    check(load().hm_matvec_host_noalloc(h, alpha, _ptr(x), beta, _ptr(y), nrhs, stream),
+          "hm_matvec_host_noalloc")
 
 
 def hm_free(h: int) -> None:
