@@ -21,9 +21,9 @@ CUDA = os.environ.get("CUDA_HOME", "/usr/local/cuda")
 NVCC = shutil.which("nvcc") or os.path.join(CUDA, "bin", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
-CPP = ["trees.cpp", "linalg.cpp", "build.cpp", "codec.cpp", "matrix.cpp"]
+CPP = ["trees.cpp", "linalg.cpp", "build.cpp", "codec.cpp", "program.cpp", "matrix.cpp"]
 CU = ["kernels.cu", "noalloc.cu"]
-HDRS = ["hm_internal.h", "dev_types.h"]
+HDRS = ["hm_internal.h", "dev_types.h", "program.h"]
 
 
 def _run(cmd):

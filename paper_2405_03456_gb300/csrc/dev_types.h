@@ -3,44 +3,67 @@
 #pragma once
 #include <cstdint>
 
+#if defined(__CUDACC__)
+#define HM_HD __host__ __device__
+#else
+#define HM_HD
+#endif
+
 namespace hm {
 
 // Packed value format word: B | fmt << 8 | e << 16 | m << 24.
 //   fmt 0: FPX e8 (B 2..4)   1: FPX e11 (B 5..8)   2: AFLP (B 1..7)   3: raw FP64 (B 8)
 // Every packed column starts 4-byte aligned and occupies pad4(rows * B) bytes.
-__host__ __device__ inline uint32_t fmt_word(int B, int fmt, int e, int m) {
+HM_HD inline uint32_t fmt_word(int B, int fmt, int e, int m) {
   return (uint32_t)B | ((uint32_t)fmt << 8) | ((uint32_t)e << 16) | ((uint32_t)m << 24);
 }
 
-// Column dot products (phase A): partial[pout + j] = sum_{r in segment} M[r, j] * v[vin + r]
-// over the columns j < ncols of a packed matrix with nrows rows per column.
-struct CdotItem {
-  uint64_t off;     // payload byte offset of column 0
-  int32_t fmt;      // >= 0: fmt index of column 0 (one word per column); < 0: ~index of one word
+// Rows per lane in the product kernels: every lane decodes 8 consecutive
+// values of a column (two groups of 4 codes = 2B 32-bit words, one 8-byte
+// aligned run), so columns are padded to 8 bytes.
+constexpr int RPL = 8;
+
+// Column dots (phase A): partial[out + j] = sum_{r < nrows} M[r, j] * v[vin + r]
+// over the ncols columns of one item (one segment of a column set); column j
+// has format word fmts[fmt + j]; columns are contiguous from `off`, each
+// pad8(nrows * B_j) bytes.
+struct Item {
+  uint64_t off;
+  int32_t fmt;      // index of column 0's format word
   int32_t ncols;
-  int32_t nrows;    // rows of every column (column byte length pad4(nrows * B))
-  int32_t row0;     // first row of the segment, a multiple of 4
-  int32_t seg;      // rows in the segment, 1..512
-  int32_t vin;      // vector index of row 0 of the column
-  int32_t pout;     // partial index of column 0
-  int32_t pad;
+  int32_t nrows;    // 1..128
+  int32_t vin;      // vector index of row 0
+  int32_t out;      // partial index of column 0
+  uint32_t fw;      // format word of column 0 (B and kind are uniform)
 };
 
-// One packed column-major tile (rows = the chunk's rows) multiplied by a vector segment.
+// Uniform tile of a row chunk: ncols columns of the chunk's rows, one format
+// word for all of them (direct compression), input v[vin + j] times `scale`.
 struct Tile {
-  uint64_t off;     // payload byte offset of column 0
-  int32_t fmt;      // as CdotItem::fmt
+  uint64_t off;     // payload byte offset of column 0 (8-byte aligned)
   int32_t ncols;
-  int32_t vin;      // vector index of column 0's input value
+  uint32_t fw;      // format word
+  int32_t vin;
   int32_t flags;    // bit 0: multiply by alpha
-  double scale;     // AFLP vmin of a direct-compressed matrix, else 1
+  double scale;     // AFLP vmin of the direct-compressed matrix, else 1
 };
 
-// A run of output rows owned by one thread block; its tiles are [t0, t1).
+// Column of a row chunk's merged VALR columns (W factors, row bases): its
+// format word and the vector index of its multiplier; the columns follow each
+// other from Chunk::coff, each pad8(nrows * B) bytes, sorted by format.
+struct ColMeta {
+  uint32_t fw;
+  int32_t vin;
+};
+
+// A run of output rows owned by one thread block: uniform tiles [t0, t1) and
+// merged columns [c0, c1) starting at payload offset coff.
 struct Chunk {
+  uint64_t coff;
   int32_t row0;     // output index of row 0
   int32_t nrows;    // 1..128
   int32_t t0, t1;
+  int32_t c0, c1;
   int32_t flags;    // bit 0: multiply the result by alpha
   int32_t pad;
 };

@@ -24,8 +24,9 @@ namespace hm {
 
 #define HM_FULL 0xffffffffu
 
-__device__ __forceinline__ int lanes_for(int rows) {
-  int g = (rows + 3) >> 2;
+// lanes (a power of two, <= 32) that hold 8 rows each of a column of `rows`
+__device__ __forceinline__ int lanes_for_rpl(int rows) {
+  int g = (rows + 7) >> 3;
   int p = 1;
   while (p < g) p <<= 1;
   return p > 32 ? 32 : p;
@@ -208,141 +209,342 @@ __device__ __forceinline__ void decode4(const uint32_t (&w)[B], int e, int m, fl
   }
 }
 
+
+// ---------------------------------------------------------------- loads and 8-value decode
+// A lane decodes 8 consecutive values of one column: 2B 32-bit words read as B
+// streaming 64-bit loads (the column and the lane's offset 8*q*B are 8-byte
+// aligned); the payload is read once, so it is loaded with the evict-first hint.
 template <int B>
-__device__ __forceinline__ void load_words(const uint8_t* __restrict__ p, uint32_t (&w)[B]) {
-  const uint32_t* q = reinterpret_cast<const uint32_t*>(p);
+__device__ __forceinline__ void ld8(const uint8_t* __restrict__ p, uint32_t (&w0)[B], uint32_t (&w1)[B]) {
+  const uint2* q = reinterpret_cast<const uint2*>(p);
+  uint32_t w[2 * B];
 #pragma unroll
-  for (int i = 0; i < B; ++i) w[i] = __ldg(q + i);
+  for (int i = 0; i < B; ++i) {
+    const uint2 t = __ldcs(q + i);
+    w[2 * i] = t.x;
+    w[2 * i + 1] = t.y;
+  }
+#pragma unroll
+  for (int i = 0; i < B; ++i) {
+    w0[i] = w[i];
+    w1[i] = w[B + i];
+  }
 }
+
+template <int TIER, int F, int B>
+__device__ __forceinline__ void decode8(const uint8_t* __restrict__ p, int e, int m, float (&h)[8], float (&l)[8]) {
+  uint32_t w0[B], w1[B];
+  ld8<B>(p, w0, w1);
+  float h0[4], l0[4], h1[4], l1[4];
+  decode4<TIER, F, B>(w0, e, m, h0, l0);
+  decode4<TIER, F, B>(w1, e, m, h1, l1);
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    h[u] = h0[u];
+    h[4 + u] = h1[u];
+    l[u] = l0[u];
+    l[4 + u] = l1[u];
+  }
+}
+
+__device__ __forceinline__ uint32_t pad8(uint32_t x) { return (x + 7u) & ~7u; }
+
+// Visit (F, B) as template arguments; false for an unknown format word.
+#define HM_FORMATS(X) \
+  X(0, 2) X(0, 3) X(0, 4) X(1, 5) X(1, 6) X(1, 7) X(1, 8) \
+  X(2, 1) X(2, 2) X(2, 3) X(2, 4) X(2, 5) X(2, 6) X(2, 7) X(3, 8)
 
 // ---------------------------------------------------------------- column dots (phase A)
-template <int TIER>
-struct ColAcc {
-  float s = 0.0f, c = 0.0f;
-};
-
-template <int TIER, int F, int B, int R>
-__device__ __forceinline__ void cdot_col(const uint8_t* __restrict__ base, int G, int e, int m,
-                                         const float (&xh)[R][4], const float (&xl)[R][4],
-                                         const bool (&ok)[R][4], int q, ColAcc<TIER>& acc) {
+// One warp per item (a segment of <= 128 rows of a column set).  G lanes (a
+// power of two) hold 8 rows each of a column, S = 32/G columns are processed
+// side by side (neighbouring columns, which usually share a format), and each
+// column's sum is reduced over its G lanes.  Column offsets come from a warp
+// prefix scan of the widths pad8(nrows * B_j), 32 columns at a time.
+template <int TIER, int F, int B>
+__device__ __forceinline__ void cdot_col(const uint8_t* __restrict__ p, int e, int m, const float (&xh)[8],
+                                         const float (&xl)[8], const bool (&ok)[8], float& s, float& c) {
+  float h[8], l[8];
+  decode8<TIER, F, B>(p, e, m, h, l);
 #pragma unroll
-  for (int r = 0; r < R; ++r) {
-    if (!ok[r][0]) continue;          // whole group beyond the segment: no load
-    uint32_t w[B];
-    load_words<B>(base + (size_t)4 * B * (q + G * r), w);
-    float h[4], l[4];
-    decode4<TIER, F, B>(w, e, m, h, l);
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      float dh = ok[r][u] ? h[u] : 0.0f;
-      if constexpr (TIER == TIER_F32) {
-        acc.s = fmaf(dh, xh[r][u], acc.s);
-      } else {
-        float dl = ok[r][u] ? l[u] : 0.0f;
-        dot2(acc.s, acc.c, dh, dl, xh[r][u], xl[r][u]);
-      }
+  for (int u = 0; u < 8; ++u) {
+    const float dh = ok[u] ? h[u] : 0.0f;
+    if constexpr (TIER == TIER_F32) {
+      s = fmaf(dh, xh[u], s);
+    } else {
+      const float dl = ok[u] ? l[u] : 0.0f;
+      dot2(s, c, dh, dl, xh[u], xl[u]);
     }
-  }
-}
-
-template <int TIER, int R>
-__device__ __forceinline__ bool cdot_dispatch(uint32_t fw, const uint8_t* base, int G,
-                                              const float (&xh)[R][4], const float (&xl)[R][4],
-                                              const bool (&ok)[R][4], int q, ColAcc<TIER>& acc) {
-  Fmt f = unpack_fmt(fw);
-  switch ((f.f << 4) | f.B) {
-#define HM_CASE(F, B) \
-  case ((F) << 4) | (B): cdot_col<TIER, F, B, R>(base, G, f.e, f.m, xh, xl, ok, q, acc); return true;
-    HM_CASE(0, 2) HM_CASE(0, 3) HM_CASE(0, 4)
-    HM_CASE(1, 5) HM_CASE(1, 6) HM_CASE(1, 7) HM_CASE(1, 8)
-    HM_CASE(2, 1) HM_CASE(2, 2) HM_CASE(2, 3) HM_CASE(2, 4) HM_CASE(2, 5) HM_CASE(2, 6) HM_CASE(2, 7)
-    HM_CASE(3, 8)
-#undef HM_CASE
-    default: return false;
-  }
-}
-
-// Width-exclusive prefix over the column slots of a warp (slots of G lanes each).
-__device__ __forceinline__ uint32_t slot_prefix(uint32_t w, int G, int lane, uint32_t& total) {
-  uint32_t v = w;
-  for (int d = G; d < 32; d <<= 1) {
-    uint32_t t = __shfl_up_sync(HM_FULL, v, d);
-    if (lane >= d) v += t;
-  }
-  total = __shfl_sync(HM_FULL, v, 31);
-  return v - w;
-}
-
-template <int TIER, int R>
-__device__ void cdot_item(const CdotItem& I, const uint8_t* __restrict__ pay,
-                          const uint32_t* __restrict__ fmts, const float2* __restrict__ vin,
-                          double* __restrict__ partial, int lane, int* err) {
-  const int G = I.seg >= 128 ? 32 : lanes_for(I.seg);
-  const int slots = 32 / G;
-  const int slot = lane / G, q = lane % G;
-  float xh[R][4], xl[R][4];
-  bool ok[R][4];
-#pragma unroll
-  for (int r = 0; r < R; ++r)
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      int rr = 4 * (q + G * r) + u;
-      ok[r][u] = rr < I.seg;
-      float2 v = ok[r][u] ? vin[I.vin + I.row0 + rr] : make_float2(0.f, 0.f);
-      xh[r][u] = v.x;
-      xl[r][u] = v.y;
-    }
-  const bool direct = I.fmt < 0;
-  uint64_t coloff = I.off;
-  for (int j0 = 0; j0 < I.ncols; j0 += slots) {
-    const int j = j0 + slot;
-    const bool active = j < I.ncols;
-    uint32_t fw = direct ? fmts[~I.fmt] : fmts[I.fmt + (active ? j : j0)];
-    uint32_t width = active ? pad4((uint32_t)I.nrows * (fw & 0xff)) : 0u;
-    uint32_t total;
-    uint32_t pre = slot_prefix(width, G, lane, total);
-    ColAcc<TIER> acc;
-    if (active && 4 * q < I.seg) {
-      const uint8_t* base = pay + coloff + pre + (size_t)I.row0 * (fw & 0xff);
-      if (!cdot_dispatch<TIER, R>(fw, base, G, xh, xl, ok, q, acc)) latch_error(err, 1);
-    }
-    coloff += total;
-    // reduce over the G lanes of the slot
-    for (int d = G >> 1; d > 0; d >>= 1) {
-      float so = __shfl_xor_sync(HM_FULL, acc.s, d);
-      float co = __shfl_xor_sync(HM_FULL, acc.c, d);
-      if constexpr (TIER == TIER_F32) {
-        acc.s += so;
-      } else {
-        float s, e;
-        two_sum(acc.s, so, s, e);
-        acc.s = s;
-        acc.c += co + e;
-      }
-    }
-    if (active && q == 0) partial[I.pout + j] = (double)acc.s + (double)acc.c;
   }
 }
 
 template <int TIER>
-__global__ void __launch_bounds__(256) k_cdot(const CdotItem* __restrict__ items, int nitems,
+__global__ void __launch_bounds__(256) k_cdot(const Item* __restrict__ items, int nitems,
                                               const uint8_t* __restrict__ pay,
                                               const uint32_t* __restrict__ fmts,
-                                              const float2* __restrict__ vin,
-                                              double* __restrict__ partial, int* err) {
+                                              const float2* __restrict__ vin, double* __restrict__ partial,
+                                              int* err) {
   const int lane = threadIdx.x & 31;
   const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nw = (gridDim.x * blockDim.x) >> 5;
   for (int it = wid; it < nitems; it += nw) {
-    CdotItem I = items[it];
-    const int G = I.seg >= 128 ? 32 : lanes_for(I.seg);
-    const int R = (I.seg + 4 * G - 1) / (4 * G);
-    if (R <= 1)
-      cdot_item<TIER, 1>(I, pay, fmts, vin, partial, lane, err);
-    else if (R <= 2)
-      cdot_item<TIER, 2>(I, pay, fmts, vin, partial, lane, err);
+    const Item I = items[it];
+    const int G = lanes_for_rpl(I.nrows);
+    const int S = 32 / G;
+    const int slot = lane / G, q = lane % G;
+    float xh[8], xl[8];
+    bool ok[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int r = RPL * q + u;
+      ok[u] = r < I.nrows;
+      const float2 v = ok[u] ? vin[I.vin + r] : make_float2(0.f, 0.f);
+      xh[u] = v.x;
+      xl[u] = v.y;
+    }
+    const uint8_t* base = pay + I.off;
+    uint32_t run = 0;                                 // bytes of the columns before this group of 32
+    for (int g0 = 0; g0 < I.ncols; g0 += 32) {
+      const int gj = g0 + lane;
+      const uint32_t fwl = gj < I.ncols ? fmts[I.fmt + gj] : 0u;
+      const uint32_t wl = gj < I.ncols ? pad8((uint32_t)I.nrows * (fwl & 0xff)) : 0u;
+      uint32_t inc = wl;
+      for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t t = __shfl_up_sync(HM_FULL, inc, d);
+        if (lane >= d) inc += t;
+      }
+      const uint32_t exl = inc - wl;
+      const uint32_t gtot = __shfl_sync(HM_FULL, inc, 31);
+      const int gn = min(32, I.ncols - g0);
+      for (int k0 = 0; k0 < gn; k0 += S) {
+        const int k = k0 + slot;
+        const bool active = k < gn;
+        const uint32_t fw = __shfl_sync(HM_FULL, fwl, active ? k : 0);
+        const uint32_t off = __shfl_sync(HM_FULL, exl, active ? k : 0);
+        float s = 0.f, c = 0.f;
+        if (active && ok[0]) {
+          const Fmt f = unpack_fmt(fw);
+          const uint8_t* p = base + run + off + (size_t)RPL * q * f.B;
+          switch ((f.f << 4) | f.B) {
+#define HM_CD(F, B) \
+  case ((F) << 4) | (B): cdot_col<TIER, F, B>(p, f.e, f.m, xh, xl, ok, s, c); break;
+            HM_FORMATS(HM_CD)
+#undef HM_CD
+            default:
+              latch_error(err, 1);
+          }
+        }
+        for (int d = G >> 1; d > 0; d >>= 1) {
+          const float so = __shfl_xor_sync(HM_FULL, s, d);
+          const float co = __shfl_xor_sync(HM_FULL, c, d);
+          if constexpr (TIER == TIER_F32) {
+            s += so;
+          } else {
+            float t, ee;
+            two_sum(s, so, t, ee);
+            s = t;
+            c += co + ee;
+          }
+        }
+        if (active && q == 0) partial[I.out + g0 + k] = (double)s + (double)c;
+      }
+      run += gtot;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- row chunks (phase C)
+constexpr int RG_WARPS = 4;
+constexpr int RG_BATCH = 256;      // merged columns staged in shared memory per batch
+
+// s/c: FP32 partial sums of the lane's 8 rows (F32) or Dot2 pairs (FF)
+template <int TIER, int F, int B>
+__device__ __forceinline__ void rg_col8(const uint8_t* __restrict__ p, int e, int m, float vh, float vl,
+                                        float (&s)[8], float (&c)[8]) {
+  float h[8], l[8];
+  decode8<TIER, F, B>(p, e, m, h, l);
+#pragma unroll
+  for (int u = 0; u < 8; ++u) {
+    if constexpr (TIER == TIER_F32)
+      s[u] = fmaf(h[u], vh, s[u]);
     else
-      cdot_item<TIER, 4>(I, pay, fmts, vin, partial, lane, err);
+      dot2(s[u], c[u], h[u], l[u], vh, vl);
+  }
+}
+
+// multiplier of a column: v * scale (scale = vmin, times alpha if asked)
+template <int TIER>
+__device__ __forceinline__ void scaled(float2 v, FF sc, float& vh, float& vl) {
+  if constexpr (TIER == TIER_F32) {
+    vh = v.x * sc.hi;
+    vl = 0.f;
+  } else {
+    const FF r = ff_mul(FF{v.x, v.y}, sc);
+    vh = r.hi;
+    vl = r.lo;
+  }
+}
+
+// fold the FP32 / Dot2 partials into the float-float row sums and clear them
+template <int TIER>
+__device__ __forceinline__ void rg_flush(FF (&acc)[8], float (&s)[8], float (&c)[8]) {
+#pragma unroll
+  for (int u = 0; u < 8; ++u) {
+    if constexpr (TIER == TIER_F32) {
+      acc[u] = ff_add_f(acc[u], s[u]);
+    } else {
+      const float h = s[u] + c[u];
+      acc[u] = ff_add(acc[u], FF{h, c[u] - (h - s[u])});
+    }
+    s[u] = 0.f;
+    c[u] = 0.f;
+  }
+}
+
+// columns [j0, j1) of a uniform tile (format F, B) for the lane's 8 rows
+template <int TIER, int F, int B>
+__device__ __forceinline__ void rg_tile(const uint8_t* __restrict__ p0, uint32_t stride, int j0, int j1,
+                                        const float2* __restrict__ v, FF sc, int e, int m, float (&s)[8],
+                                        float (&c)[8]) {
+#pragma unroll 2
+  for (int j = j0; j < j1; ++j) {
+    float vh, vl;
+    scaled<TIER>(v[j], sc, vh, vl);
+    rg_col8<TIER, F, B>(p0 + (size_t)j * stride, e, m, vh, vl, s, c);
+  }
+}
+
+template <int TIER, int MODE>
+__global__ void __launch_bounds__(RG_WARPS * 32) k_rgemv(
+    const Chunk* __restrict__ chunks, int nchunks, const Tile* __restrict__ tiles,
+    const ColMeta* __restrict__ cols, const uint8_t* __restrict__ pay, const float2* __restrict__ vin,
+    double alpha, double beta, double* __restrict__ y, const int32_t* __restrict__ perm,
+    float2* __restrict__ vout, const double* __restrict__ rowscale, int* err) {
+  __shared__ float2 red[RG_WARPS * 32 * RPL];
+  __shared__ uint32_t s_off[RG_BATCH];
+  __shared__ uint32_t s_fw[RG_BATCH];
+  __shared__ float2 s_v[RG_BATCH];
+  __shared__ uint32_t s_wsum[RG_WARPS];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int ci = blockIdx.x; ci < nchunks; ci += gridDim.x) {
+    const Chunk C = chunks[ci];
+    uint64_t coff = C.coff;
+    const int R = C.nrows;
+    const int G = (R + RPL - 1) / RPL;          // lanes per column (any count)
+    const int S = 32 / G;                        // column slots per warp
+    const int slot = lane / G, q = lane % G;
+    const bool lane_on = slot < S && RPL * q < R;
+    FF acc[8];
+    float s[8], c[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      acc[u] = {0.f, 0.f};
+      s[u] = 0.f;
+      c[u] = 0.f;
+    }
+    // uniform tiles (dense blocks, couplings, transfers): warps round-robin, slots split the columns
+    for (int t = C.t0 + warp; t < C.t1; t += RG_WARPS) {
+      const Tile T = tiles[t];
+      if (!lane_on) continue;
+      const Fmt f = unpack_fmt(T.fw);
+      const uint32_t stride = pad8((uint32_t)R * f.B);
+      const int j0 = (slot * T.ncols) / S, j1 = ((slot + 1) * T.ncols) / S;
+      const FF sc = ff_from_d((T.flags & 1) ? T.scale * alpha : T.scale);
+      const uint8_t* p0 = pay + T.off + (size_t)RPL * q * f.B;
+      switch ((f.f << 4) | f.B) {
+#define HM_RT(F, B)                                                                              \
+  case ((F) << 4) | (B):                                                                         \
+    rg_tile<TIER, F, B>(p0, stride, j0, j1, vin + T.vin, sc, f.e, f.m, s, c); break;
+        HM_FORMATS(HM_RT)
+#undef HM_RT
+        default:
+          latch_error(err, 2);
+      }
+      rg_flush<TIER>(acc, s, c);
+    }
+    // merged VALR columns, staged in batches: format words, multipliers, offsets
+    for (int b0 = C.c0; b0 < C.c1; b0 += RG_BATCH) {
+      const int nb = min(RG_BATCH, C.c1 - b0);
+      __syncthreads();
+      uint32_t wv[2];
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        const int i = threadIdx.x * 2 + k;
+        wv[k] = 0u;
+        if (i < nb) {
+          const ColMeta cm = cols[b0 + i];
+          s_fw[i] = cm.fw;
+          s_v[i] = vin[cm.vin];
+          wv[k] = pad8((uint32_t)R * (cm.fw & 0xff));
+        }
+      }
+      // exclusive scan of the widths (2 per thread) over the block
+      uint32_t tsum = wv[0] + wv[1];
+      uint32_t inc = tsum;
+      for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t t = __shfl_up_sync(HM_FULL, inc, d);
+        if (lane >= d) inc += t;
+      }
+      if (lane == 31) s_wsum[warp] = inc;
+      __syncthreads();
+      uint32_t wbase = 0;
+      for (int w = 0; w < warp; ++w) wbase += s_wsum[w];
+      const uint32_t ex = wbase + inc - tsum;
+      if (threadIdx.x * 2 < nb) s_off[threadIdx.x * 2] = ex;
+      if (threadIdx.x * 2 + 1 < nb) s_off[threadIdx.x * 2 + 1] = ex + wv[0];
+      uint32_t btot = 0;
+      for (int w = 0; w < RG_WARPS; ++w) btot += s_wsum[w];
+      __syncthreads();
+      if (lane_on) {
+        // column i -> warp (i / S) % RG_WARPS, slot i % S: neighbouring columns share a format
+        for (int i = warp * S + slot; i < nb; i += RG_WARPS * S) {
+          const uint32_t fw = s_fw[i];
+          const Fmt f = unpack_fmt(fw);
+          const float2 v = s_v[i];
+          const uint8_t* p = pay + coff + s_off[i] + (size_t)RPL * q * f.B;
+          switch ((f.f << 4) | f.B) {
+#define HM_RC(F, B)                                                                     \
+  case ((F) << 4) | (B): rg_col8<TIER, F, B>(p, f.e, f.m, v.x, v.y, s, c); break;
+            HM_FORMATS(HM_RC)
+#undef HM_RC
+            default:
+              latch_error(err, 3);
+          }
+        }
+        rg_flush<TIER>(acc, s, c);
+      }
+      coff += btot;
+    }
+    // reduce over slots and warps in shared memory (fixed order)
+    if (lane_on) {
+#pragma unroll
+      for (int u = 0; u < 8; ++u) red[(warp * 32 + lane) * RPL + u] = make_float2(acc[u].hi, acc[u].lo);
+    }
+    __syncthreads();
+    for (int r = threadIdx.x; r < R; r += blockDim.x) {
+      const int qq = r / RPL, u = r % RPL;
+      FF t = {0.f, 0.f};
+      for (int w = 0; w < RG_WARPS; ++w)
+        for (int sl = 0; sl < S; ++sl) {
+          const float2 v = red[(w * 32 + sl * G + qq) * RPL + u];
+          t = ff_add(t, FF{v.x, v.y});
+        }
+      const int g = C.row0 + r;
+      double val = ff_to_d(t);
+      if constexpr (MODE == MODE_Y) {
+        const int o = perm[g];
+        y[o] = (beta == 0.0) ? val : fma(beta, y[o], val);
+      } else {
+        if constexpr (MODE == MODE_VEC_ADD) {
+          const float2 old = vout[g];
+          val += (double)old.x + (double)old.y;
+        }
+        if (rowscale) val *= rowscale[g];
+        if (C.flags & 1) val *= alpha;
+        const FF ff = ff_from_d(val);
+        vout[g] = make_float2(ff.hi, ff.lo);
+      }
+    }
+    __syncthreads();
   }
 }
 
@@ -362,137 +564,6 @@ __global__ void k_gsum(const GsumOut* __restrict__ outs, int nouts, const int32_
   if (O.flags & 1) s *= alpha;
   FF f = ff_from_d(s);
   vout[O.out] = make_float2(f.hi, f.lo);
-}
-
-// ---------------------------------------------------------------- row chunks (phase C)
-template <int TIER, int F, int B>
-__device__ __forceinline__ void rg_col(const uint8_t* __restrict__ base, int e, int m, float2 v,
-                                       float (&ps)[4], float (&pc)[4]) {
-  uint32_t w[B];
-  load_words<B>(base, w);
-  float h[4], l[4];
-  decode4<TIER, F, B>(w, e, m, h, l);
-#pragma unroll
-  for (int u = 0; u < 4; ++u) {
-    if constexpr (TIER == TIER_F32)
-      ps[u] = fmaf(h[u], v.x, ps[u]);
-    else
-      dot2(ps[u], pc[u], h[u], l[u], v.x, v.y);
-  }
-}
-
-template <int TIER>
-__device__ __forceinline__ bool rg_dispatch(uint32_t fw, const uint8_t* base, float2 v, float (&ps)[4],
-                                            float (&pc)[4]) {
-  Fmt f = unpack_fmt(fw);
-  switch ((f.f << 4) | f.B) {
-#define HM_CASE(F, B) \
-  case ((F) << 4) | (B): rg_col<TIER, F, B>(base, f.e, f.m, v, ps, pc); return true;
-    HM_CASE(0, 2) HM_CASE(0, 3) HM_CASE(0, 4)
-    HM_CASE(1, 5) HM_CASE(1, 6) HM_CASE(1, 7) HM_CASE(1, 8)
-    HM_CASE(2, 1) HM_CASE(2, 2) HM_CASE(2, 3) HM_CASE(2, 4) HM_CASE(2, 5) HM_CASE(2, 6) HM_CASE(2, 7)
-    HM_CASE(3, 8)
-#undef HM_CASE
-    default: return false;
-  }
-}
-
-constexpr int RG_WARPS = 4;
-
-template <int TIER, int MODE>
-__global__ void __launch_bounds__(RG_WARPS * 32) k_rgemv(
-    const Chunk* __restrict__ chunks, int nchunks, const Tile* __restrict__ tiles,
-    const uint8_t* __restrict__ pay, const uint32_t* __restrict__ fmts,
-    const float2* __restrict__ vin, double alpha, double beta, double* __restrict__ y,
-    const int32_t* __restrict__ perm, float2* __restrict__ vout, const double* __restrict__ rowscale,
-    int* err) {
-  __shared__ float2 red[RG_WARPS][128];
-  const int lane = threadIdx.x & 31;
-  const int warp = threadIdx.x >> 5;
-  for (int ci = blockIdx.x; ci < nchunks; ci += gridDim.x) {
-    const Chunk C = chunks[ci];
-    const int G = lanes_for(C.nrows);
-    const int slots = 32 / G;
-    const int slot = lane / G, q = lane % G;
-    const bool rows_ok = 4 * q < C.nrows;
-    FF acc[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) acc[u] = {0.0f, 0.0f};
-    for (int t = C.t0 + warp; t < C.t1; t += RG_WARPS) {
-      const Tile T = tiles[t];
-      float ps[4] = {0.f, 0.f, 0.f, 0.f}, pc[4] = {0.f, 0.f, 0.f, 0.f};
-      const bool direct = T.fmt < 0;
-      uint64_t coloff = T.off;
-      for (int j0 = 0; j0 < T.ncols; j0 += slots) {
-        const int j = j0 + slot;
-        const bool active = j < T.ncols;
-        uint32_t fw = direct ? fmts[~T.fmt] : fmts[T.fmt + (active ? j : j0)];
-        uint32_t width = active ? pad4((uint32_t)C.nrows * (fw & 0xff)) : 0u;
-        uint32_t total;
-        uint32_t pre = slot_prefix(width, G, lane, total);
-        if (active && rows_ok) {
-          const float2 v = vin[T.vin + j];
-          const uint8_t* base = pay + coloff + pre + (size_t)4 * q * (fw & 0xff);
-          if (!rg_dispatch<TIER>(fw, base, v, ps, pc)) latch_error(err, 2);
-        }
-        coloff += total;
-      }
-      const double sc = (T.flags & 1) ? T.scale * alpha : T.scale;
-      if constexpr (TIER == TIER_F32) {
-        const float s = (float)sc;
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          float p = ps[u] * s;
-          float pe = fmaf(ps[u], s, -p);
-          acc[u] = ff_add(acc[u], FF{p, pe});
-        }
-      } else {
-        const FF s = ff_from_d(sc);
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          float h = ps[u] + pc[u];
-          FF p = {h, pc[u] - (h - ps[u])};
-          acc[u] = ff_add(acc[u], ff_mul(p, s));
-        }
-      }
-    }
-    // reduce the column slots of this warp (lanes with equal q)
-    for (int d = G; d < 32; d <<= 1) {
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        FF o;
-        o.hi = __shfl_xor_sync(HM_FULL, acc[u].hi, d);
-        o.lo = __shfl_xor_sync(HM_FULL, acc[u].lo, d);
-        acc[u] = ff_add(acc[u], o);
-      }
-    }
-    if (slot == 0 && rows_ok) {
-#pragma unroll
-      for (int u = 0; u < 4; ++u) red[warp][4 * q + u] = make_float2(acc[u].hi, acc[u].lo);
-    }
-    __syncthreads();
-    for (int r = threadIdx.x; r < C.nrows; r += blockDim.x) {
-      FF s = {red[0][r].x, red[0][r].y};
-#pragma unroll
-      for (int w = 1; w < RG_WARPS; ++w) s = ff_add(s, FF{red[w][r].x, red[w][r].y});
-      const int g = C.row0 + r;
-      double v = ff_to_d(s);
-      if constexpr (MODE == MODE_Y) {
-        const int o = perm[g];
-        y[o] = (beta == 0.0) ? v : fma(beta, y[o], v);
-      } else {
-        if constexpr (MODE == MODE_VEC_ADD) {
-          float2 old = vout[g];
-          v += (double)old.x + (double)old.y;
-        }
-        if (rowscale) v *= rowscale[g];
-        if (C.flags & 1) v *= alpha;
-        FF f = ff_from_d(v);
-        vout[g] = make_float2(f.hi, f.lo);
-      }
-    }
-    __syncthreads();
-  }
 }
 
 // ---------------------------------------------------------------- gather x
@@ -533,18 +604,19 @@ __global__ void k_decode(const uint8_t* __restrict__ p, int64_t n, int B, int fm
 }
 
 // ---------------------------------------------------------------- launchers
+cudaError_t kernels_init() { return cudaSuccess; }
+
 cudaError_t launch_gather(const double* x, const int32_t* perm, int n, float2* xo, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   k_gather<<<(n + 255) / 256, 256, 0, st>>>(x, perm, n, xo);
   return cudaGetLastError();
 }
 
-cudaError_t launch_cdot(int tier, const CdotItem* items, int nitems, const uint8_t* pay,
-                        const uint32_t* fmts, const float2* vin, double* partial, int* err, int grid,
-                        cudaStream_t st) {
+cudaError_t launch_cdot(int tier, const Item* items, int nitems, const uint8_t* pay, const uint32_t* fmts,
+                        const float2* vin, double* partial, int* err, int grid, cudaStream_t st) {
   if (nitems <= 0) return cudaSuccess;
-  int need = (nitems + 7) / 8;
-  int g = need < grid ? need : grid;
+  const int need = (nitems + 7) / 8;
+  const int g = need < grid ? need : grid;
   if (tier == TIER_F32)
     k_cdot<TIER_F32><<<g, 256, 0, st>>>(items, nitems, pay, fmts, vin, partial, err);
   else
@@ -560,14 +632,13 @@ cudaError_t launch_gsum(const GsumOut* outs, int nouts, const int32_t* plist, co
 }
 
 cudaError_t launch_rgemv(int tier, int mode, const Chunk* chunks, int nchunks, const Tile* tiles,
-                         const uint8_t* pay, const uint32_t* fmts, const float2* vin, double alpha,
-                         double beta, double* y, const int32_t* perm, float2* vout,
-                         const double* rowscale, int* err, int grid, cudaStream_t st) {
+                         const ColMeta* cols, const uint8_t* pay, const float2* vin, double alpha, double beta,
+                         double* y, const int32_t* perm, float2* vout, const double* rowscale, int* err,
+                         cudaStream_t st) {
   if (nchunks <= 0) return cudaSuccess;
-  int g = nchunks < grid ? nchunks : grid;
-#define HM_RG(T, M)                                                                                  \
-  k_rgemv<T, M><<<g, RG_WARPS * 32, 0, st>>>(chunks, nchunks, tiles, pay, fmts, vin, alpha, beta, y, \
-                                             perm, vout, rowscale, err)
+#define HM_RG(T, M)                                                                              \
+  k_rgemv<T, M><<<nchunks, RG_WARPS * 32, 0, st>>>(chunks, nchunks, tiles, cols, pay, vin, alpha, beta, y, \
+                                                   perm, vout, rowscale, err)
   if (tier == TIER_F32) {
     if (mode == MODE_Y) HM_RG(TIER_F32, MODE_Y);
     else if (mode == MODE_VEC) HM_RG(TIER_F32, MODE_VEC);
