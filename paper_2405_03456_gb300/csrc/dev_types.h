@@ -18,23 +18,33 @@ HM_HD inline uint32_t fmt_word(int B, int fmt, int e, int m) {
   return (uint32_t)B | ((uint32_t)fmt << 8) | ((uint32_t)e << 16) | ((uint32_t)m << 24);
 }
 
+// Float-float pair (hi + lo): scales and partial sums, so that no FP64
+// arithmetic runs per column (FP64 is 1/60 of the FP32 rate on GB300).
+struct F2 {
+  float hi, lo;
+};
+
 // Rows per lane in the product kernels: every lane decodes 8 consecutive
 // values of a column (two groups of 4 codes = 2B 32-bit words, one 8-byte
 // aligned run), so columns are padded to 8 bytes.
 constexpr int RPL = 8;
 
-// Column dots (phase A): partial[out + j] = sum_{r < nrows} M[r, j] * v[vin + r]
-// over the ncols columns of one item (one segment of a column set); column j
-// has format word fmts[fmt + j]; columns are contiguous from `off`, each
-// pad8(nrows * B_j) bytes.
+// Column dots (phase A): sum_j = sum_{r < nrows} M[r, j] * v[vin + r] over the
+// ncols columns of one item (one segment of a column set); column j has format
+// word fmts[fmt + j] and output scale cscale[fmt + j] (float-float); columns are contiguous
+// from `off`, each pad8(nrows * B_j) bytes.  A set with a single segment
+// writes its coefficients directly (ITEM_FINAL): vout[out + j] =
+// cscale[fmt + j] * (alpha if ITEM_ALPHA) * sum_j; otherwise partial[out + j] = sum_j.
+constexpr int32_t ITEM_FINAL = 1;
+constexpr int32_t ITEM_ALPHA = 2;
 struct Item {
   uint64_t off;
-  int32_t fmt;      // index of column 0's format word
+  int32_t fmt;
   int32_t ncols;
   int32_t nrows;    // 1..128
   int32_t vin;      // vector index of row 0
-  int32_t out;      // partial index of column 0
-  uint32_t fw;      // format word of column 0 (B and kind are uniform)
+  int32_t out;      // partial index, or vector index with ITEM_FINAL, of column 0
+  int32_t flags;
 };
 
 // Uniform tile of a row chunk: ncols columns of the chunk's rows, one format
@@ -45,7 +55,7 @@ struct Tile {
   uint32_t fw;      // format word
   int32_t vin;
   int32_t flags;    // bit 0: multiply by alpha
-  double scale;     // AFLP vmin of the direct-compressed matrix, else 1
+  F2 scale;         // AFLP vmin of the direct-compressed matrix (float-float), else 1
 };
 
 // Column of a row chunk's merged VALR columns (W factors, row bases): its
@@ -69,11 +79,12 @@ struct Chunk {
 };
 
 // out_vec[out] = scale * (alpha if flags&1) * sum_{p in [p0,p1)} pscale[p] * partial[plist[p]]
+// (float-float arithmetic)
 struct GsumOut {
   int32_t out;
   int32_t p0, p1;
   int32_t flags;
-  double scale;
+  F2 scale;
 };
 
 enum { MODE_Y = 0, MODE_VEC = 1, MODE_VEC_ADD = 2 };

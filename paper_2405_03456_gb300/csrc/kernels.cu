@@ -165,7 +165,9 @@ __device__ __forceinline__ void decode4(const uint32_t (&w)[B], int e, int m, fl
     h[1] = __uint_as_float(top32<B, 1>(w) & mask);
     h[2] = __uint_as_float(top32<B, 2>(w) & mask);
     h[3] = __uint_as_float(top32<B, 3>(w) & mask);
-  } else if constexpr (F == 2 && B <= 3) {                 // AFLP, s exact in FP32
+  } else if constexpr (F == 2 && (B <= 3 || (B == 4 && TIER == TIER_F32))) {
+    // AFLP with s in FP32 (exact for B <= 3; for B = 4 the mantissa is cut to
+    // 23 bits, which is the F32 tier's own precision)
     constexpr uint32_t mask = (0xffffffffu << (8 * (4 - B))) & 0x7fffffffu;
     const int sh = 8 - e;
     uint32_t t[4] = {top32<B, 0>(w), top32<B, 1>(w), top32<B, 2>(w), top32<B, 3>(w)};
@@ -254,35 +256,120 @@ __device__ __forceinline__ uint32_t pad8(uint32_t x) { return (x + 7u) & ~7u; }
   X(0, 2) X(0, 3) X(0, 4) X(1, 5) X(1, 6) X(1, 7) X(1, 8) \
   X(2, 1) X(2, 2) X(2, 3) X(2, 4) X(2, 5) X(2, 6) X(2, 7) X(3, 8)
 
+// ---------------------------------------------------------------- prefetched columns
+// A lane's 8 codes of a column occupy 8*B bytes = B words of 64 bits.  The
+// fetch is format-blind: W such words (W = 4 covers B <= 4, the F32 tier;
+// W = 8 covers every width) are loaded for the next column while the current one is decoded, so
+// two columns' loads are in flight per lane with a single decode path.  The
+// extra bytes of a short code belong to the neighbouring lane's rows and are
+// fetched by the same coalesced request.
+template <int W>
+struct Words {
+  uint2 w[W];
+};
+
+template <int W>
+__device__ __forceinline__ void fetch(const uint8_t* __restrict__ p, Words<W>& out) {
+  const uint2* q = reinterpret_cast<const uint2*>(p);
+#pragma unroll
+  for (int i = 0; i < W; ++i) out.w[i] = __ldcs(q + i);
+}
+
+// decode the 8 codes (format F, width B <= W: 8*B bytes = B 64-bit words) held in `in`
+template <int TIER, int F, int B, int W>
+__device__ __forceinline__ void decode8w(const Words<W>& in, int e, int m, float (&h)[8], float (&l)[8]) {
+  static_assert(B <= W, "fetch window too small");
+  uint32_t w[2 * W];
+#pragma unroll
+  for (int i = 0; i < W; ++i) {
+    w[2 * i] = in.w[i].x;
+    w[2 * i + 1] = in.w[i].y;
+  }
+  uint32_t w0[B], w1[B];
+#pragma unroll
+  for (int i = 0; i < B; ++i) {
+    w0[i] = w[i];
+    w1[i] = w[B + i];
+  }
+  float h0[4], l0[4], h1[4], l1[4];
+  decode4<TIER, F, B>(w0, e, m, h0, l0);
+  decode4<TIER, F, B>(w1, e, m, h1, l1);
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    h[u] = h0[u];
+    h[4 + u] = h1[u];
+    l[u] = l0[u];
+    l[4 + u] = l1[u];
+  }
+}
+
+// Dispatch on the format word; formats wider than the window are decoded from
+// a direct reload at p.  Returns false for an unknown word.
+template <int TIER, int W>
+__device__ __forceinline__ bool decode_any(uint32_t fw, const Words<W>& in, const uint8_t* __restrict__ p,
+                                           float (&h)[8], float (&l)[8]) {
+  const Fmt f = unpack_fmt(fw);
+#define HM_DW(F, B)                                \
+  case ((F) << 4) | (B):                           \
+    if constexpr ((B) <= W) {                      \
+      decode8w<TIER, F, B, W>(in, f.e, f.m, h, l); \
+    } else {                                       \
+      Words<(B)> big;                              \
+      fetch(p, big);                               \
+      decode8w<TIER, F, B, (B)>(big, f.e, f.m, h, l); \
+    }                                              \
+    return true;
+  switch ((f.f << 4) | f.B) {
+    HM_FORMATS(HM_DW)
+    default:
+      return false;
+  }
+#undef HM_DW
+}
+
 // ---------------------------------------------------------------- column dots (phase A)
 // One warp per item (a segment of <= 128 rows of a column set).  G lanes (a
 // power of two) hold 8 rows each of a column, S = 32/G columns are processed
-// side by side (neighbouring columns, which usually share a format), and each
-// column's sum is reduced over its G lanes.  Column offsets come from a warp
-// prefix scan of the widths pad8(nrows * B_j), 32 columns at a time.
-template <int TIER, int F, int B>
-__device__ __forceinline__ void cdot_col(const uint8_t* __restrict__ p, int e, int m, const float (&xh)[8],
-                                         const float (&xl)[8], const bool (&ok)[8], float& s, float& c) {
-  float h[8], l[8];
-  decode8<TIER, F, B>(p, e, m, h, l);
-#pragma unroll
-  for (int u = 0; u < 8; ++u) {
-    const float dh = ok[u] ? h[u] : 0.0f;
+// side by side, and each column's sum is reduced over its G lanes.  Column
+// offsets come from a warp prefix scan of the widths pad8(nrows * B_j), 32
+// columns at a time.
+template <int TIER>
+__device__ __forceinline__ void lane_reduce(float& s, float& c, int G) {
+  for (int d = G >> 1; d > 0; d >>= 1) {
     if constexpr (TIER == TIER_F32) {
-      s = fmaf(dh, xh[u], s);
+      s += __shfl_xor_sync(HM_FULL, s, d);
     } else {
-      const float dl = ok[u] ? l[u] : 0.0f;
-      dot2(s, c, dh, dl, xh[u], xl[u]);
+      const float so = __shfl_xor_sync(HM_FULL, s, d);
+      const float co = __shfl_xor_sync(HM_FULL, c, d);
+      float t, ee;
+      two_sum(s, so, t, ee);
+      s = t;
+      c += co + ee;
     }
   }
 }
 
-template <int TIER>
-__global__ void __launch_bounds__(256) k_cdot(const Item* __restrict__ items, int nitems,
+__device__ __forceinline__ void cdot_out(const Item& I, int j, float s, float c, const F2* __restrict__ cscale,
+                                         F2 alpha, F2* __restrict__ partial, float2* __restrict__ vout) {
+  const float h = s + c;
+  FF v = {h, c - (h - s)};
+  if (I.flags & ITEM_FINAL) {
+    const F2 sc = cscale[I.fmt + j];
+    v = ff_mul(v, FF{sc.hi, sc.lo});
+    if (I.flags & ITEM_ALPHA) v = ff_mul(v, FF{alpha.hi, alpha.lo});
+    vout[I.out + j] = make_float2(v.hi, v.lo);
+  } else {
+    partial[I.out + j] = F2{v.hi, v.lo};
+  }
+}
+
+template <int TIER, int W>
+__global__ void __launch_bounds__(256, (TIER == TIER_F32) ? 4 : 2) k_cdot(const Item* __restrict__ items, int nitems,
                                               const uint8_t* __restrict__ pay,
                                               const uint32_t* __restrict__ fmts,
-                                              const float2* __restrict__ vin, double* __restrict__ partial,
-                                              int* err) {
+                                              const F2* __restrict__ cscale, const float2* __restrict__ vin,
+                                              F2 alpha, F2* __restrict__ partial,
+                                              float2* __restrict__ vout, int* err) {
   const int lane = threadIdx.x & 31;
   const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nw = (gridDim.x * blockDim.x) >> 5;
@@ -315,37 +402,41 @@ __global__ void __launch_bounds__(256) k_cdot(const Item* __restrict__ items, in
       const uint32_t exl = inc - wl;
       const uint32_t gtot = __shfl_sync(HM_FULL, inc, 31);
       const int gn = min(32, I.ncols - g0);
+      // software pipeline over this slot's columns k = slot, slot + S, ...
+      int k = slot;
+      uint32_t fw = __shfl_sync(HM_FULL, fwl, k < gn ? k : 0);
+      uint32_t off = __shfl_sync(HM_FULL, exl, k < gn ? k : 0);
+      const uint8_t* p = base + run + off + (size_t)RPL * q * (fw & 0xff);
+      Words<W> cur;
+      if (k < gn && ok[0]) fetch(p, cur);
       for (int k0 = 0; k0 < gn; k0 += S) {
-        const int k = k0 + slot;
-        const bool active = k < gn;
-        const uint32_t fw = __shfl_sync(HM_FULL, fwl, active ? k : 0);
-        const uint32_t off = __shfl_sync(HM_FULL, exl, active ? k : 0);
+        const int kn = k + S;
+        const uint32_t fwn = __shfl_sync(HM_FULL, fwl, kn < gn ? kn : 0);
+        const uint32_t offn = __shfl_sync(HM_FULL, exl, kn < gn ? kn : 0);
+        const uint8_t* pn = base + run + offn + (size_t)RPL * q * (fwn & 0xff);
+        Words<W> nxt;
+        if (kn < gn && ok[0]) fetch(pn, nxt);
         float s = 0.f, c = 0.f;
-        if (active && ok[0]) {
-          const Fmt f = unpack_fmt(fw);
-          const uint8_t* p = base + run + off + (size_t)RPL * q * f.B;
-          switch ((f.f << 4) | f.B) {
-#define HM_CD(F, B) \
-  case ((F) << 4) | (B): cdot_col<TIER, F, B>(p, f.e, f.m, xh, xl, ok, s, c); break;
-            HM_FORMATS(HM_CD)
-#undef HM_CD
-            default:
-              latch_error(err, 1);
+        if (k < gn && ok[0]) {
+          float h[8], l[8];
+          if (!decode_any<TIER, W>(fw, cur, p, h, l)) latch_error(err, 1);
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const float dh = ok[u] ? h[u] : 0.0f;
+            if constexpr (TIER == TIER_F32) {
+              s = fmaf(dh, xh[u], s);
+            } else {
+              const float dl = ok[u] ? l[u] : 0.0f;
+              dot2(s, c, dh, dl, xh[u], xl[u]);
+            }
           }
         }
-        for (int d = G >> 1; d > 0; d >>= 1) {
-          const float so = __shfl_xor_sync(HM_FULL, s, d);
-          const float co = __shfl_xor_sync(HM_FULL, c, d);
-          if constexpr (TIER == TIER_F32) {
-            s += so;
-          } else {
-            float t, ee;
-            two_sum(s, so, t, ee);
-            s = t;
-            c += co + ee;
-          }
-        }
-        if (active && q == 0) partial[I.out + g0 + k] = (double)s + (double)c;
+        lane_reduce<TIER>(s, c, G);
+        if (q == 0 && k < gn) cdot_out(I, g0 + k, s, c, cscale, alpha, partial, vout);
+        k = kn;
+        fw = fwn;
+        p = pn;
+        cur = nxt;
       }
       run += gtot;
     }
@@ -417,7 +508,7 @@ template <int TIER, int MODE>
 __global__ void __launch_bounds__(RG_WARPS * 32) k_rgemv(
     const Chunk* __restrict__ chunks, int nchunks, const Tile* __restrict__ tiles,
     const ColMeta* __restrict__ cols, const uint8_t* __restrict__ pay, const float2* __restrict__ vin,
-    double alpha, double beta, double* __restrict__ y, const int32_t* __restrict__ perm,
+    double alpha, F2 alpha_ff, double beta, double* __restrict__ y, const int32_t* __restrict__ perm,
     float2* __restrict__ vout, const double* __restrict__ rowscale, int* err) {
   __shared__ float2 red[RG_WARPS * 32 * RPL];
   __shared__ uint32_t s_off[RG_BATCH];
@@ -448,7 +539,8 @@ __global__ void __launch_bounds__(RG_WARPS * 32) k_rgemv(
       const Fmt f = unpack_fmt(T.fw);
       const uint32_t stride = pad8((uint32_t)R * f.B);
       const int j0 = (slot * T.ncols) / S, j1 = ((slot + 1) * T.ncols) / S;
-      const FF sc = ff_from_d((T.flags & 1) ? T.scale * alpha : T.scale);
+      const FF sc = (T.flags & 1) ? ff_mul(FF{T.scale.hi, T.scale.lo}, FF{alpha_ff.hi, alpha_ff.lo})
+                                  : FF{T.scale.hi, T.scale.lo};
       const uint8_t* p0 = pay + T.off + (size_t)RPL * q * f.B;
       switch ((f.f << 4) | f.B) {
 #define HM_RT(F, B)                                                                              \
@@ -550,20 +642,20 @@ __global__ void __launch_bounds__(RG_WARPS * 32) k_rgemv(
 
 // ---------------------------------------------------------------- segment sums (phase A2)
 __global__ void k_gsum(const GsumOut* __restrict__ outs, int nouts, const int32_t* __restrict__ plist,
-                       const double* __restrict__ pscale, const double* __restrict__ partial,
-                       double alpha, float2* __restrict__ vout) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
+                       const F2* __restrict__ pscale, const F2* __restrict__ partial, F2 alpha,
+                       float2* __restrict__ vout) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nouts) return;
-  GsumOut O = outs[i];
-  double s = 0.0;
+  const GsumOut O = outs[i];
+  FF s = {0.f, 0.f};
   for (int p = O.p0; p < O.p1; ++p) {
-    double v = partial[plist[p]];
-    s += pscale ? pscale[p] * v : v;
+    const F2 v = partial[plist[p]];
+    const F2 w = pscale[p];
+    s = ff_add(s, ff_mul(FF{v.hi, v.lo}, FF{w.hi, w.lo}));
   }
-  s *= O.scale;
-  if (O.flags & 1) s *= alpha;
-  FF f = ff_from_d(s);
-  vout[O.out] = make_float2(f.hi, f.lo);
+  s = ff_mul(s, FF{O.scale.hi, O.scale.lo});
+  if (O.flags & 1) s = ff_mul(s, FF{alpha.hi, alpha.lo});
+  vout[O.out] = make_float2(s.hi, s.lo);
 }
 
 // ---------------------------------------------------------------- gather x
@@ -613,32 +705,33 @@ cudaError_t launch_gather(const double* x, const int32_t* perm, int n, float2* x
 }
 
 cudaError_t launch_cdot(int tier, const Item* items, int nitems, const uint8_t* pay, const uint32_t* fmts,
-                        const float2* vin, double* partial, int* err, int grid, cudaStream_t st) {
+                        const F2* cscale, const float2* vin, F2 alpha, F2* partial, float2* vout, int* err,
+                        int grid, cudaStream_t st) {
   if (nitems <= 0) return cudaSuccess;
   const int need = (nitems + 7) / 8;
   const int g = need < grid ? need : grid;
   if (tier == TIER_F32)
-    k_cdot<TIER_F32><<<g, 256, 0, st>>>(items, nitems, pay, fmts, vin, partial, err);
+    k_cdot<TIER_F32, 4><<<g, 256, 0, st>>>(items, nitems, pay, fmts, cscale, vin, alpha, partial, vout, err);
   else
-    k_cdot<TIER_FF><<<g, 256, 0, st>>>(items, nitems, pay, fmts, vin, partial, err);
+    k_cdot<TIER_FF, 8><<<g, 256, 0, st>>>(items, nitems, pay, fmts, cscale, vin, alpha, partial, vout, err);
   return cudaGetLastError();
 }
 
-cudaError_t launch_gsum(const GsumOut* outs, int nouts, const int32_t* plist, const double* pscale,
-                        const double* partial, double alpha, float2* vout, cudaStream_t st) {
+cudaError_t launch_gsum(const GsumOut* outs, int nouts, const int32_t* plist, const F2* pscale, const F2* partial,
+                        F2 alpha, float2* vout, cudaStream_t st) {
   if (nouts <= 0) return cudaSuccess;
   k_gsum<<<(nouts + 255) / 256, 256, 0, st>>>(outs, nouts, plist, pscale, partial, alpha, vout);
   return cudaGetLastError();
 }
 
 cudaError_t launch_rgemv(int tier, int mode, const Chunk* chunks, int nchunks, const Tile* tiles,
-                         const ColMeta* cols, const uint8_t* pay, const float2* vin, double alpha, double beta,
-                         double* y, const int32_t* perm, float2* vout, const double* rowscale, int* err,
-                         cudaStream_t st) {
+                         const ColMeta* cols, const uint8_t* pay, const float2* vin, double alpha, F2 alpha_ff,
+                         double beta, double* y, const int32_t* perm, float2* vout, const double* rowscale,
+                         int* err, cudaStream_t st) {
   if (nchunks <= 0) return cudaSuccess;
-#define HM_RG(T, M)                                                                              \
-  k_rgemv<T, M><<<nchunks, RG_WARPS * 32, 0, st>>>(chunks, nchunks, tiles, cols, pay, vin, alpha, beta, y, \
-                                                   perm, vout, rowscale, err)
+#define HM_RG(T, M)                                                                                    \
+  k_rgemv<T, M><<<nchunks, RG_WARPS * 32, 0, st>>>(chunks, nchunks, tiles, cols, pay, vin, alpha, alpha_ff, beta, \
+                                                   y, perm, vout, rowscale, err)
   if (tier == TIER_F32) {
     if (mode == MODE_Y) HM_RG(TIER_F32, MODE_Y);
     else if (mode == MODE_VEC) HM_RG(TIER_F32, MODE_VEC);

@@ -17,13 +17,14 @@ namespace hm {
 cudaError_t kernels_init();
 cudaError_t launch_gather(const double* x, const int32_t* perm, int n, float2* xo, cudaStream_t st);
 cudaError_t launch_cdot(int tier, const Item* items, int nitems, const uint8_t* pay, const uint32_t* fmts,
-                        const float2* vin, double* partial, int* err, int grid, cudaStream_t st);
-cudaError_t launch_gsum(const GsumOut* outs, int nouts, const int32_t* plist, const double* pscale,
-                        const double* partial, double alpha, float2* vout, cudaStream_t st);
+                        const F2* cscale, const float2* vin, F2 alpha, F2* partial, float2* vout, int* err,
+                        int grid, cudaStream_t st);
+cudaError_t launch_gsum(const GsumOut* outs, int nouts, const int32_t* plist, const F2* pscale, const F2* partial,
+                        F2 alpha, float2* vout, cudaStream_t st);
 cudaError_t launch_rgemv(int tier, int mode, const Chunk* chunks, int nchunks, const Tile* tiles,
-                         const ColMeta* cols, const uint8_t* pay, const float2* vin, double alpha, double beta,
-                         double* y, const int32_t* perm, float2* vout, const double* rowscale, int* err,
-                         cudaStream_t st);
+                         const ColMeta* cols, const uint8_t* pay, const float2* vin, double alpha, F2 alpha_ff,
+                         double beta, double* y, const int32_t* perm, float2* vout, const double* rowscale,
+                         int* err, cudaStream_t st);
 cudaError_t launch_decode(const uint8_t* p, int64_t n, int B, int fmt, int e, int m, double vmin,
                           double* out, cudaStream_t st);
 }  // namespace hm
@@ -67,17 +68,18 @@ struct hm_matrix {
   // device copies of the program
   DevArr<uint8_t> d_pay;
   DevArr<uint32_t> d_fmt;
+  DevArr<F2> d_cscale;
   DevArr<Item> d_items;
   DevArr<GsumOut> d_gout;
   DevArr<int32_t> d_plist;
-  DevArr<double> d_pscale;
+  DevArr<F2> d_pscale;
   DevArr<Tile> d_tiles;
   DevArr<ColMeta> d_cols;
   DevArr<Chunk> d_chunks;
   DevArr<double> d_rowscale;
   DevArr<int32_t> d_perm;
   float2* d_vec = nullptr;     // vector workspace (x, coefficient vectors)
-  double* d_part = nullptr;    // column-dot partial sums
+  F2* d_part = nullptr;        // column-dot partial sums (float-float)
   int* d_err = nullptr;        // latched device error word
   double* d_hx = nullptr;      // host-path staging (hm_matvec_host)
   double* d_hy = nullptr;
@@ -107,6 +109,7 @@ struct hm_matrix {
   void release_device() {
     d_pay.release();
     d_fmt.release();
+    d_cscale.release();
     d_items.release();
     d_gout.release();
     d_plist.release();
@@ -144,6 +147,7 @@ hm_status upload(hm_matrix* M) {
   if ((e = M->arr.upload(vec)) != cudaSuccess) return cuda_status(e);
   UP(d_pay, P.pk.pay)
   UP(d_fmt, P.pk.fmts)
+  UP(d_cscale, P.pk.cscale)
   UP(d_items, P.items)
   UP(d_gout, P.gouts)
   UP(d_plist, P.plist)
@@ -161,7 +165,7 @@ hm_status upload(hm_matrix* M) {
     return cuda_status(e);
   if ((e = cudaMemset(M->d_vec, 0, (std::max<int64_t>(P.nvec, 1) + 16) * sizeof(float2))) != cudaSuccess)
     return cuda_status(e);
-  if ((e = cudaMalloc(&M->d_part, std::max<int64_t>(P.npartial, 1) * sizeof(double))) != cudaSuccess)
+  if ((e = cudaMalloc(&M->d_part, std::max<int64_t>(P.npartial, 1) * sizeof(F2))) != cudaSuccess)
     return cuda_status(e);
   if ((e = cudaMalloc(&M->d_err, sizeof(int))) != cudaSuccess) return cuda_status(e);
   if ((e = cudaMemset(M->d_err, 0, sizeof(int))) != cudaSuccess) return cuda_status(e);
@@ -253,6 +257,7 @@ static hm_status run_program(hm_matrix* M, double alpha, const double* x, double
                              cudaStream_t st) {
   Program& P = M->prog;
   cudaError_t e = cudaSuccess;
+  const F2 aff = split_ff(alpha);
   for (const Launch& L : P.launches) {
     hm_matrix::Rec rec{(int)L.kind, nullptr, nullptr, L.bytes};
     if (M->prof) {
@@ -265,16 +270,15 @@ static hm_status run_program(hm_matrix* M, double alpha, const double* x, double
         e = launch_gather(x, M->d_perm.p, (int)L.n, M->d_vec, st);
         break;
       case Launch::CDOT:
-        e = launch_cdot(P.tier, M->d_items.p + L.off, (int)L.n, M->d_pay.p, M->d_fmt.p, M->d_vec, M->d_part,
-                        M->d_err, M->nsm * 8, st);
+        e = launch_cdot(P.tier, M->d_items.p + L.off, (int)L.n, M->d_pay.p, M->d_fmt.p, M->d_cscale.p, M->d_vec,
+                        aff, M->d_part, M->d_vec, M->d_err, M->nsm * 8, st);
         break;
       case Launch::GSUM:
-        e = launch_gsum(M->d_gout.p + L.off, (int)L.n, M->d_plist.p, M->d_pscale.p, M->d_part, alpha,
-                        M->d_vec, st);
+        e = launch_gsum(M->d_gout.p + L.off, (int)L.n, M->d_plist.p, M->d_pscale.p, M->d_part, aff, M->d_vec, st);
         break;
       case Launch::RGEMV:
         e = launch_rgemv(P.tier, L.mode, M->d_chunks.p + L.off, (int)L.n, M->d_tiles.p, M->d_cols.p, M->d_pay.p,
-                         M->d_vec, alpha, beta, y, M->d_perm.p, M->d_vec,
+                         M->d_vec, alpha, aff, beta, y, M->d_perm.p, M->d_vec,
                          L.use_rowscale ? M->d_rowscale.p : nullptr, M->d_err, st);
         break;
     }

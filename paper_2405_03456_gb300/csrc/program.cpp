@@ -116,12 +116,19 @@ uint32_t kind_width(uint32_t fw) { return fw & 0xffffu; }
 
 // ---------------------------------------------------------------- column-dot items
 // Segment-major layout of a column set (one item per segment of <= 128 rows);
-// input vector index of row 0 is vin.
-// segp[j] receives the partial index of column j in every segment.
-void pack_cdot(Program& P, const ColSet& cs, int32_t vin, int64_t& pbase, std::vector<std::vector<int32_t>>& segp) {
+// input vector index of row 0 is vin.  A set that fits one segment writes its
+// coefficients v[out0 + j] = scale[j] * (alpha if use_alpha) * sum directly
+// (final = true, segp untouched); otherwise segp[j] receives the partial
+// index of column j in every segment.
+void pack_cdot(Program& P, const ColSet& cs, int32_t vin, int64_t& pbase, std::vector<std::vector<int32_t>>& segp,
+               bool allow_final, int64_t out0, const std::vector<double>* scale, bool use_alpha, bool& final_out) {
   segp.assign(cs.n, {});
   const int32_t fbase = (int32_t)P.pk.fmts.size();
-  for (int j = 0; j < cs.n; ++j) P.pk.fmts.push_back(cs.fw(j));
+  for (int j = 0; j < cs.n; ++j) {
+    P.pk.fmts.push_back(cs.fw(j));
+    P.pk.cscale.push_back(split_ff(scale ? (*scale)[j] : 1.0));
+  }
+  final_out = allow_final && cs.m <= SEG_ROWS;
   for (int64_t r0 = 0; r0 < cs.m; r0 += SEG_ROWS) {
     const int64_t r1 = std::min<int64_t>(cs.m, r0 + SEG_ROWS);
     uint64_t off0 = 0;
@@ -135,10 +142,14 @@ void pack_cdot(Program& P, const ColSet& cs, int32_t vin, int64_t& pbase, std::v
     it.ncols = cs.n;
     it.nrows = (int32_t)(r1 - r0);
     it.vin = (int32_t)(vin + r0);
-    it.out = (int32_t)pbase;
-    it.fw = cs.fw(0);
-    for (int j = 0; j < cs.n; ++j) segp[j].push_back((int32_t)(pbase + j));
-    pbase += cs.n;
+    if (final_out) {
+      it.out = (int32_t)out0;
+      it.flags = ITEM_FINAL | (use_alpha ? ITEM_ALPHA : 0);
+    } else {
+      it.out = (int32_t)pbase;
+      for (int j = 0; j < cs.n; ++j) segp[j].push_back((int32_t)(pbase + j));
+      pbase += cs.n;
+    }
     P.items.push_back(it);
   }
 }
@@ -155,7 +166,7 @@ Tile pack_tile(Program& P, const ColSet& cs, int64_t r0, int64_t r1, int32_t vin
   T.fw = cs.fw(0);
   T.vin = vin;
   T.flags = flags;
-  T.scale = cs.scale(0);
+  T.scale = split_ff(cs.scale(0));
   return T;
 }
 
@@ -314,11 +325,11 @@ void gsum_outputs(Program& P, int64_t out0, const std::vector<std::vector<int32_
     o.p0 = (int32_t)P.plist.size();
     for (int32_t p : segp[j]) {
       P.plist.push_back(p);
-      P.pscale.push_back(1.0);
+      P.pscale.push_back(split_ff(1.0));
     }
     o.p1 = (int32_t)P.plist.size();
     o.flags = flags;
-    o.scale = scale[j];
+    o.scale = split_ff(scale[j]);
     P.gouts.push_back(o);
   }
 }
@@ -357,10 +368,11 @@ bool program_h(Ctx& cx) {
     const Cluster& s = ct.cl[H.blocks[b].col];
     P.fp64_lowrank += (t.size() + s.size()) * L.k * 8;
     std::vector<std::vector<int32_t>> segp;
-    pack_cdot(P, csx[b], (int32_t)s.start, pbase, segp);
     std::vector<double> sc(L.k);
     for (int j = 0; j < L.k; ++j) sc[j] = L.s[j] * csx[b].scale(j) * csw[b].scale(j);
-    gsum_outputs(P, vec, segp, sc, 1);
+    bool fin = false;
+    pack_cdot(P, csx[b], (int32_t)s.start, pbase, segp, true, vec, &sc, true, fin);
+    if (!fin) gsum_outputs(P, vec, segp, sc, 1);
     toff[b] = vec;
     vec += L.k;
     csx[b] = ColSet();
@@ -443,10 +455,11 @@ bool forward_bases(Ctx& cx, const std::vector<int>& which, const std::vector<int
     const int k = H.colb.k[c];
     cx.P.fp64_lowrank += ct.cl[c].size() * k * 8;
     std::vector<std::vector<int32_t>> segp;
-    pack_cdot(cx.P, enc[c], (int32_t)ct.cl[c].start, pbase, segp);
     std::vector<double> sc(k);
     for (int j = 0; j < k; ++j) sc[j] = enc[c].scale(j);
-    gsum_outputs(cx.P, soff[c], segp, sc, 0);
+    bool fin = false;
+    pack_cdot(cx.P, enc[c], (int32_t)ct.cl[c].start, pbase, segp, true, soff[c], &sc, false, fin);
+    if (!fin) gsum_outputs(cx.P, soff[c], segp, sc, 0);
     enc[c] = ColSet();
   }
   return true;
@@ -593,7 +606,8 @@ bool program_h2(Ctx& cx) {
         const int sc = ct.cl[c].son[i];
         if (H.colb.k[sc] == 0) continue;
         std::vector<std::vector<int32_t>> segp;
-        pack_cdot(P, ex[sc], (int32_t)soff[sc], pb, segp);
+        bool fin = false;
+        pack_cdot(P, ex[sc], (int32_t)soff[sc], pb, segp, false, 0, nullptr, false, fin);
         for (int j = 0; j < kp; ++j)
           for (int32_t q : segp[j]) {
             all[j].push_back(q);
@@ -606,10 +620,10 @@ bool program_h2(Ctx& cx) {
         o.p0 = (int32_t)P.plist.size();
         for (size_t q = 0; q < all[j].size(); ++q) {
           P.plist.push_back(all[j][q]);
-          P.pscale.push_back(scl[j][q]);
+          P.pscale.push_back(split_ff(scl[j][q]));
         }
         o.p1 = (int32_t)P.plist.size();
-        o.scale = 1.0;
+        o.scale = split_ff(1.0);
         P.gouts.push_back(o);
       }
     }
@@ -658,8 +672,8 @@ void launch_bytes(Program& P) {
       case Launch::CDOT:
         for (int64_t i = L.off; i < L.off + L.n; ++i) {
           const Item& t = P.items[i];
-          b += (int64_t)t.nrows * (t.fw & 0xff) * t.ncols + 4 * (int64_t)t.ncols + (int64_t)sizeof(Item) +
-               8 * (int64_t)t.nrows + 8 * (int64_t)t.ncols;
+          for (int j = 0; j < t.ncols; ++j) b += (int64_t)t.nrows * (P.pk.fmts[t.fmt + j] & 0xff);
+          b += 4 * (int64_t)t.ncols + (int64_t)sizeof(Item) + 8 * (int64_t)t.nrows + 8 * (int64_t)t.ncols;
         }
         break;
       case Launch::GSUM:

@@ -9,9 +9,15 @@
 
 namespace hm {
 
+inline F2 split_ff(double v) {
+  const float h = (float)v;
+  return F2{h, (float)(v - (double)h)};
+}
+
 struct Packer {
   std::vector<uint8_t> pay;       // packed codes, every column 8-byte aligned
   std::vector<uint32_t> fmts;     // format words
+  std::vector<F2> cscale;         // output scale of column-dot columns (parallel to fmts)
   int64_t value_bytes = 0;        // sum of n * B over all packed columns (no padding)
 
   uint64_t align8() {
@@ -47,7 +53,7 @@ struct Program {
   std::vector<Item> items;        // column-dot items
   std::vector<GsumOut> gouts;
   std::vector<int32_t> plist;
-  std::vector<double> pscale;
+  std::vector<F2> pscale;
   std::vector<Tile> tiles;        // uniform row-chunk tiles
   std::vector<ColMeta> cols;      // merged row-chunk columns
   std::vector<Chunk> chunks;
