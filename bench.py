@@ -193,6 +193,7 @@ def gpu_arm(args, rank, world):
         M = hm.HMatrix(pts, "laplace", 64, 2.0, "h", eps)
         for codec in codecs:
             M.compress(eps, codec, True)
+            M.graph(not args.no_graph)
             info = M.info()
             ab = M.alg_bytes()
             if not clocks_started:
@@ -231,6 +232,22 @@ def gpu_arm(args, rank, world):
                 headline["e2e"] = {"value": ab / (ems * 1e-3) / 1e9 * world, "unit": "GB/s",
                                    "ms_per_step": ems, "h2d_bytes_per_step": 16 * n, "d2h_bytes_per_step": 8 * n}
         M.close()
+    # uniform-H and H^2 formats of the same problem (one persistent graph-captured product each)
+    fmt_results = {}
+    for fmt in [f for f in args.formats.split(",") if f]:
+        eps = HEADLINE[0]
+        M = hm.HMatrix(pts, "laplace", 64, 2.0, fmt, eps)
+        for codec in ("none", "aflp"):
+            M.compress(eps, codec, True)
+            M.graph(not args.no_graph)
+            info = M.info()
+            ab = M.alg_bytes()
+            per, total = time_variant(torch, M, x, y, args.steps, args.warmup, stream, world)
+            med = statistics.median(per)
+            fmt_results[(fmt, codec)] = {"ms_p50": med, "ms_p99": pct(per, 0.99), "gbs": ab / (med * 1e-3) / 1e9,
+                                         "payload_bytes": info["bytes_payload"], "value_bytes": info["bytes_values"],
+                                         "fp64_bytes": info["bytes_fp64"], "launches": info["nlaunches"]}
+        M.close()
     clk = clocks.stop()
 
     # ------------------------------------------------------------ multi-rank reduction
@@ -268,6 +285,7 @@ def gpu_arm(args, rank, world):
         "data": "synthetic (seeded jittered Fibonacci sphere, x ~ U(-1,1))",
         "config": {"workload": workload_name(n), "n": n, "eps": HEADLINE[0], "codec": "aflp-valr",
                    "format": "H", "nrhs": 1, "parallelism": "replicas" if world > 1 else "single-gpu",
+                   "cuda_graph": not args.no_graph,
                    "l2": "inputs larger than L2 (packed matrix %.0f MB vs 129 MB L2), no flush"
                          % (headline["payload_bytes"] / 1e6)},
         "matvecs_per_s": round(1e3 / med * world, 1), "ms_p50": round(med, 5),
@@ -284,6 +302,12 @@ def gpu_arm(args, rank, world):
         "gpu_launches": int(headline["launches"] * args.steps),
         "clocks": clk,
         "by_eps": by_eps,
+        "by_format": {f"{f}-{c}": {"gbs": round(r["gbs"], 1), "ms_p50": round(r["ms_p50"], 4),
+                                   "ms_p99": round(r["ms_p99"], 4), "payload_mb": round(r["payload_bytes"] / 1e6, 1),
+                                   "compression_ratio": round(r["fp64_bytes"] / max(r["value_bytes"], 1), 3),
+                                   "hbm_frac": round(r["gbs"] / hbm_peak, 3), "launches": r["launches"],
+                                   "speedup_vs_fp64": round(fmt_results[(f, "none")]["ms_p50"] / r["ms_p50"], 3)}
+                      for (f, c), r in fmt_results.items()},
     }
     if not args.no_cpu:
         try:
@@ -331,6 +355,8 @@ def main():
     ap.add_argument("--eps", default=",".join(f"{e:g}" for e in EPS_LIST))
     ap.add_argument("--codecs", default="none,aflp,fpx")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-graph", action="store_true")
+    ap.add_argument("--formats", default="uh,h2")
     ap.add_argument("--cpu-budget-mb", type=float, default=20.0)
     ap.add_argument("--cpu-passes", type=int, default=30)
     args = ap.parse_args()

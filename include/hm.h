@@ -106,6 +106,17 @@ hm_status hm_matvec(hm_matrix* m, double alpha, const double* x, int64_t ldx, do
 hm_status hm_matvec_host(hm_matrix* m, double alpha, const double* x, double beta, double* y,
                          int64_t nrhs, void* stream);
 
+/*
+ * hm_graph -- enable (nonzero) or disable CUDA-graph replay of hm_matvec.
+ * When enabled, the first hm_matvec with a given (x, y, ldx, ldy, nrhs,
+ * alpha, beta) captures its whole kernel sequence on a library-owned stream
+ * into a CUDA graph; later calls with the same arguments launch that graph on
+ * the caller's stream (one launch instead of one per kernel).  A call with
+ * other arguments re-captures.  hm_compress discards the graph.  Profiling
+ * (hm_profile) bypasses the graph.  Errors: HM_ERR_ARG.
+ */
+hm_status hm_graph(hm_matrix* m, int32_t enable);
+
 /* hm_free -- release host and device memory of m (NULL is accepted). */
 hm_status hm_free(hm_matrix* m);
 

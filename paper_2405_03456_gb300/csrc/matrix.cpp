@@ -86,6 +86,24 @@ struct hm_matrix {
   int64_t d_h_cap = 0;
   int nsm = 0;
   std::mutex mu;
+  // CUDA graph of the whole launch sequence, cached per call signature
+  bool use_graph = false;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  struct GKey {
+    const double* x = nullptr;
+    double* y = nullptr;
+    int64_t ldx = 0, ldy = 0, nrhs = 0;
+    double alpha = 0, beta = 0;
+    bool operator==(const GKey& o) const {
+      return x == o.x && y == o.y && ldx == o.ldx && ldy == o.ldy && nrhs == o.nrhs && alpha == o.alpha &&
+             beta == o.beta;
+    }
+  } gkey;
+  void drop_graph() {
+    if (gexec) cudaGraphExecDestroy(gexec);
+    gexec = nullptr;
+  }
   // profiling: event pairs per launch
   bool prof = false;
   struct Rec {
@@ -107,6 +125,7 @@ struct hm_matrix {
   }
 
   void release_device() {
+    drop_graph();
     d_pay.release();
     d_fmt.release();
     d_cscale.release();
@@ -301,10 +320,45 @@ hm_status hm_matvec(hm_matrix* M, double alpha, const double* x, int64_t ldx, do
   const double* ye = y + ldy * (nrhs - 1) + n;
   if (!(xe <= y || ye <= x)) return HM_ERR_ARG;     // x and y must not overlap
   cudaStream_t st = (cudaStream_t)stream;
+  if (M->use_graph && !M->prof) {
+    hm_matrix::GKey key{x, y, ldx, ldy, nrhs, alpha, beta};
+    if (!M->gexec || !(key == M->gkey)) {
+      M->drop_graph();
+      if (!M->cap_stream && cudaStreamCreateWithFlags(&M->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+        return HM_ERR_CUDA;
+      if (cudaStreamBeginCapture(M->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+        return HM_ERR_CUDA;
+      hm_status s = HM_OK;
+      for (int64_t r = 0; r < nrhs && s == HM_OK; ++r)
+        s = run_program(M, alpha, x + r * ldx, beta, y + r * ldy, M->cap_stream);
+      cudaGraph_t g = nullptr;
+      const cudaError_t ce = cudaStreamEndCapture(M->cap_stream, &g);
+      if (s != HM_OK || ce != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return s != HM_OK ? s : HM_ERR_CUDA;
+      }
+      const cudaError_t ie = cudaGraphInstantiate(&M->gexec, g, 0);
+      cudaGraphDestroy(g);
+      if (ie != cudaSuccess) {
+        M->gexec = nullptr;
+        return HM_ERR_CUDA;
+      }
+      M->gkey = key;
+    }
+    return cudaGraphLaunch(M->gexec, st) == cudaSuccess ? HM_OK : HM_ERR_CUDA;
+  }
   for (int64_t r = 0; r < nrhs; ++r) {
     hm_status s = run_program(M, alpha, x + r * ldx, beta, y + r * ldy, st);
     if (s != HM_OK) return s;
   }
+  return HM_OK;
+}
+
+hm_status hm_graph(hm_matrix* M, int32_t enable) {
+  if (!M) return HM_ERR_ARG;
+  std::lock_guard<std::mutex> g(M->mu);
+  M->use_graph = enable != 0;
+  if (!M->use_graph) M->drop_graph();
   return HM_OK;
 }
 
@@ -370,6 +424,8 @@ hm_status hm_alg_bytes(const hm_matrix* M, int64_t* bytes) {
 
 hm_status hm_free(hm_matrix* M) {
   if (!M) return HM_OK;
+  M->drop_graph();
+  if (M->cap_stream) cudaStreamDestroy(M->cap_stream);
   for (auto& r : M->recs) {
     cudaEventDestroy(r.e0);
     cudaEventDestroy(r.e1);

@@ -24,7 +24,7 @@ KERNELS = {"laplace": HM_KERNEL_LAPLACE, "matern": HM_KERNEL_MATERN15}
 
 DECLARED = ["hm_build", "hm_compress", "hm_matvec", "hm_matvec_host", "hm_free", "hm_info",
             "hm_status_str", "hm_sync_status", "hm_structure", "hm_codec_encode", "hm_codec_decode",
-            "hm_profile", "hm_profile_read", "hm_alg_bytes", "hm_matvec_host_noalloc"]
+            "hm_profile", "hm_profile_read", "hm_alg_bytes", "hm_matvec_host_noalloc", "hm_graph"]
 HM_NOALLOC_MAX_ENTRIES = 1 << 20
 KERNEL_KINDS = ["gather", "cdot", "gsum", "rgemv"]
 
@@ -91,6 +91,7 @@ def load(path: str | None = None) -> C.CDLL:
         "hm_profile_read": ([vp, C.POINTER(hm_kernel_stat), i32], i32),
         "hm_alg_bytes": ([vp, C.POINTER(i64)], i32),
         "hm_matvec_host_noalloc": ([vp, dbl, vp, dbl, vp, i64, vp], i32),
+        "hm_graph": ([vp, i32], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -187,6 +188,10 @@ def hm_codec_decode(packed_ptr: int, n: int, hdr: dict, out_ptr: int, stream: in
     check(load().hm_codec_decode(packed_ptr, n, C.byref(h), out_ptr, stream), "hm_codec_decode")
 
 
+def hm_graph(h: int, enable: bool) -> None:
+    check(load().hm_graph(h, 1 if enable else 0), "hm_graph")
+
+
 def hm_profile(h: int, enable: bool) -> None:
     check(load().hm_profile(h, 1 if enable else 0), "hm_profile")
 
@@ -240,6 +245,10 @@ class HMatrix:
 
     def alg_bytes(self):
         return hm_alg_bytes(self.h)
+
+    def graph(self, enable=True):
+        hm_graph(self.h, enable)
+        return self
 
     def profile(self, enable=True):
         hm_profile(self.h, enable)

@@ -166,6 +166,29 @@ def test_deterministic_and_host_path(hm, problem, fmt):
         M.close()
 
 
+@pytest.mark.parametrize("fmt", ["h", "h2"])
+def test_graph_replay_bitwise(hm, problem, fmt):
+    """CUDA-graph replay equals direct launches bit for bit; new arguments re-capture."""
+    pts, x, y0 = problem
+    M = hm.HMatrix(pts, "laplace", 32, 2.0, fmt, 1e-6)
+    try:
+        M.compress(1e-6, "aflp")
+        xd = torch.from_numpy(x[:, 0].copy()).cuda()
+        ya = torch.from_numpy(y0[:, 0].copy()).cuda()
+        M.matvec(0.5, xd, 1.0, ya)
+        M.graph(True)
+        for alpha in (0.5, 0.5, 2.0):
+            yb = torch.from_numpy(y0[:, 0].copy()).cuda()
+            M.matvec(alpha, xd, 1.0, yb)
+            yb = yb.cpu().numpy()
+            if alpha == 0.5:
+                assert np.array_equal(yb.view(np.uint64), ya.cpu().numpy().view(np.uint64))
+        ref = oracle_ref(pts, fmt, 1e-6, x[:, 0], 2.0, y0[:, 0], 1.0)
+        assert rel(yb, ref) <= 4e-6
+    finally:
+        M.close()
+
+
 def test_matern_cube(hm):
     pts = synth.cube_points(3000)
     x = synth.rhs(3000)[:, 0]
