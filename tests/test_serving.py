@@ -1,0 +1,140 @@
+"""Serving scheduler (continuous batching, admission by memory budget).
+
+Host logic on the CPU with a deterministic fake executor and clock; the GPU
+test at the end serves real compressed matrices and checks that every result
+is the same alone and in the mix.
+"""
+import numpy as np
+import pytest
+
+import synth
+from paper_2405_03456_gb300.serving import MAX_BATCH_RHS, Request, Scheduler, poisson_requests
+
+
+class FakeExecutor:
+    """y = A_mid @ x on the CPU; a product of r RHS takes a + b*r seconds of fake time."""
+
+    def __init__(self, mats, a=1e-3, b=1e-4):
+        self.A = {mid: np.random.default_rng(mid).standard_normal((n, n)) for mid, n in mats.items()}
+        self.a, self.b = a, b
+        self.now = 0.0
+        self.log = []            # (mid, start, end, r)
+
+    @staticmethod
+    def staging_bytes(n, max_rhs):
+        return 2 * 8 * n * max_rhs
+
+    def launch(self, mid, slot, xs):
+        r = sum(x.reshape(x.shape[0], -1).shape[1] for x in xs)
+        end = self.now + self.a + self.b * r
+        self.log.append((mid, self.now, end, r))
+        return (end, mid, xs)
+
+    def poll(self, h):
+        end, mid, xs = h
+        if self.now < end:
+            return None
+        return [self.A[mid] @ x for x in xs]
+
+    def next_finish(self):
+        return min((e for (_, _, e, _) in self.log if e > self.now), default=None)
+
+
+class FakeClock:
+    def __init__(self, ex):
+        self.ex = ex
+
+    def __call__(self):
+        return self.ex.now
+
+    def advance(self, ex, next_arrival):
+        cand = [t for t in (ex.next_finish(), next_arrival) if t is not None]
+        if cand:
+            ex.now = max(ex.now, min(cand))
+
+
+def make(mats, budget=10**12, nslots=2):
+    ex = FakeExecutor(mats)
+    sch = Scheduler(ex, budget, nslots=nslots)
+    for mid, n in mats.items():
+        sch.add_matrix(mid, n, resident_bytes=1000)
+    return ex, sch
+
+
+def test_results_and_continuous_batching():
+    mats = {0: 40, 1: 30, 2: 50}
+    ex, sch = make(mats)
+    reqs = poisson_requests(mats, rate=5000.0, count=200, seed=4)
+    done = sch.run(reqs, clock=FakeClock(ex))
+    assert len(done) == 200
+    for q in done:
+        assert np.allclose(q.y, ex.A[q.mid] @ q.x, rtol=1e-12, atol=1e-12)
+        assert q.done >= q.arrival
+    st = sch.stats()
+    assert st["mean_batch_rhs"] > 20          # later arrivals joined the next launch
+    assert all(r <= MAX_BATCH_RHS for (_, _, _, r) in ex.log)
+    # one matrix never has two products in flight; different matrices do overlap
+    overlap_diff = False
+    for i, (m1, s1, e1, _) in enumerate(ex.log):
+        for (m2, s2, e2, _) in ex.log[i + 1:]:
+            if s2 < e1 and s1 < e2:
+                assert m1 != m2
+                overlap_diff = True
+    assert overlap_diff
+
+
+def test_budget_admission_and_backlog():
+    mats = {0: 64}
+    ex = FakeExecutor(mats)
+    need = 1000 + FakeExecutor.staging_bytes(64, MAX_BATCH_RHS)
+    with pytest.raises(MemoryError):
+        Scheduler(ex, need - 1).add_matrix(0, 64, 1000)
+    # room for the matrix plus 40 queued RHS of data: the rest waits in the backlog
+    sch = Scheduler(ex, need + 16 * 64 * 40, nslots=1)
+    sch.add_matrix(0, 64, 1000)
+    reqs = [Request(k, 0, np.asfortranarray(np.ones((64, 16)) * k), 0.0) for k in range(6)]
+    done = sch.run(reqs, clock=FakeClock(ex))
+    assert [q.rid for q in sorted(done, key=lambda q: q.done)] == list(range(6))
+    assert max(r for (_, _, _, r) in ex.log) <= 32      # at most 2 requests (40 RHS of room) admitted at once
+    for q in done:
+        assert np.allclose(q.y, ex.A[0] @ q.x)
+
+
+def test_rejects_bad_requests():
+    ex, sch = make({0: 8})
+    with pytest.raises(ValueError):
+        sch.submit(Request(0, 5, np.zeros((8, 1)), 0.0), 0.0)
+    with pytest.raises(ValueError):
+        sch.submit(Request(1, 0, np.zeros((8, MAX_BATCH_RHS + 1)), 0.0), 0.0)
+
+
+@pytest.mark.gpu
+def test_gpu_serving_alone_equals_mix():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_2405_03456_gb300 import build, hm
+    from paper_2405_03456_gb300.serving import GpuExecutor
+    build.build()
+    specs = {0: ("laplace", 2048, 1e-6), 1: ("matern", 3000, 1e-4), 2: ("laplace", 4096, 1e-8)}
+    ex = GpuExecutor(nslots=3)
+    sch = Scheduler(ex, budget_bytes=8 << 30, nslots=3)
+    Ms = {}
+    for mid, (kern, n, eps) in specs.items():
+        pts = synth.sphere_points(n) if kern == "laplace" else synth.cube_points(n)
+        M = hm.HMatrix(pts, kern, 64, 2.0, "h", eps).compress(eps, "aflp")
+        Ms[mid] = M
+        info = M.info()
+        sch.add_matrix(mid, n, info["bytes_payload"] + info["bytes_meta"] + info["bytes_workspace"])
+        ex.add(mid, M)
+    reqs = poisson_requests({m: s[1] for m, s in specs.items()}, rate=20000.0, count=60, seed=8)
+    done = sch.run(reqs)
+    assert len(done) == 60
+    assert sch.stats()["mean_batch_rhs"] > 1
+    for q in done:
+        alone = np.asfortranarray(np.zeros_like(q.x))
+        Ms[q.mid].matvec_host(1.0, q.x, 0.0, alone)
+        eps = specs[q.mid][2]
+        assert np.linalg.norm(q.y - alone) <= 4 * eps * np.linalg.norm(alone)
+    for M in Ms.values():
+        M.close()
