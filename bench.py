@@ -193,6 +193,8 @@ def gpu_arm(args, rank, world):
         M = hm.HMatrix(pts, "laplace", 64, 2.0, "h", eps)
         for codec in codecs:
             M.compress(eps, codec, True)
+            if not args.no_tune:
+                M.autotune(5, stream.cuda_stream)
             M.graph(not args.no_graph)
             info = M.info()
             ab = M.alg_bytes()
@@ -204,7 +206,8 @@ def gpu_arm(args, rank, world):
             r = {"ms_p50": med, "ms_p99": pct(per, 0.99), "ms_mean": total / args.steps,
                  "gbs": ab / (med * 1e-3) / 1e9, "matvecs_per_s": 1e3 / med, "alg_bytes": ab,
                  "payload_bytes": info["bytes_payload"], "value_bytes": info["bytes_values"],
-                 "fp64_bytes": info["bytes_fp64"], "tier": info["tier"], "launches": info["nlaunches"]}
+                 "fp64_bytes": info["bytes_fp64"], "tier": info["tier"], "launches": info["nlaunches"],
+                 "shapes": [s for s in M.launch_shapes() if s >= 0]}
             results[(eps, codec)] = r
             if (eps, codec) == HEADLINE:
                 headline = dict(r)
@@ -239,6 +242,8 @@ def gpu_arm(args, rank, world):
         M = hm.HMatrix(pts, "laplace", 64, 2.0, fmt, eps)
         for codec in ("none", "aflp"):
             M.compress(eps, codec, True)
+            if not args.no_tune:
+                M.autotune(5, stream.cuda_stream)
             M.graph(not args.no_graph)
             info = M.info()
             ab = M.alg_bytes()
@@ -277,7 +282,8 @@ def gpu_arm(args, rank, world):
             "payload_mb": round(r["payload_bytes"] / 1e6, 1), "fp64_mb": round(r["fp64_bytes"] / 1e6, 1),
             "compression_ratio": round(r["fp64_bytes"] / max(r["value_bytes"], 1), 3),
             "speedup_vs_fp64": round(base["ms_p50"] / r["ms_p50"], 3) if base else None,
-            "hbm_frac": round(r["gbs"] / hbm_peak, 3), "tier": "ff" if r["tier"] else "f32"}
+            "hbm_frac": round(r["gbs"] / hbm_peak, 3), "tier": "ff" if r["tier"] else "f32",
+            "launch_shapes": r["shapes"]}
     line = {
         "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(med, 5), "higher_is_better": True,
@@ -357,6 +363,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--formats", default="uh,h2")
+    ap.add_argument("--no-tune", action="store_true", help="keep the default launch shape (no autotuning)")
     ap.add_argument("--cpu-budget-mb", type=float, default=20.0)
     ap.add_argument("--cpu-passes", type=int, default=30)
     args = ap.parse_args()

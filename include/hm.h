@@ -187,14 +187,38 @@ hm_status hm_codec_decode(const uint8_t* packed, int64_t n, const hm_codec_heade
                           double* out, void* stream);
 
 /*
+ * Launch shapes and the autotuner (the batching form: one tuned launch per
+ * phase).  Each column-dot and row-chunk launch of a product is split into
+ * per-warp ranges of about equal bytes for every launch shape (warps per block
+ * x shared-memory stages per warp: 0 = 16 x 3, 1 = 12 x 4, 2 = 8 x 6; one
+ * block per SM); which shape a launch uses does not change its result beyond
+ * the order of summation inside a chunk.
+ * hm_autotune -- time every shape of every such launch `reps` times on
+ *   `stream` (on internal zero vectors) and keep the fastest per launch.
+ *   Allocates two n-vectors for the duration of the call, synchronises the
+ *   stream, and discards a captured graph.  Errors: HM_ERR_ARG (reps outside
+ *   1..1000), HM_ERR_STATE (not compressed), HM_ERR_CUDA.
+ * hm_launch_shapes -- the shape of every launch of one product (-1 for the
+ *   gather and segment-sum launches) in shapes[0 .. min(cap, count)); count =
+ *   number of launches.  Errors: HM_ERR_ARG.
+ * hm_set_launch_shapes -- use `shape` (0..2) for every launch (the default
+ *   after hm_compress is 0).  Errors: HM_ERR_ARG.
+ */
+hm_status hm_autotune(hm_matrix* m, int32_t reps, void* stream);
+hm_status hm_launch_shapes(const hm_matrix* m, int32_t* shapes, int32_t cap, int32_t* count);
+hm_status hm_set_launch_shapes(hm_matrix* m, int32_t shape);
+
+/*
  * Kernel profiling.  hm_profile(m, 1) makes every later hm_matvec record a
  * CUDA event pair around each of its kernel launches, on the caller's stream;
  * hm_profile_read synchronises those events, returns per kernel kind the
  * summed duration, the launch count and the algorithmic bytes those launches
  * move (packed values, format words, descriptors, vector reads and writes),
  * and clears the record.  Kinds: 0 gather, 1 column dots (phase A),
- * 2 segment sums, 3 row chunks (phase C / couplings / sweeps).
- * out : host array of nout (<= 4) entries.  Errors: HM_ERR_ARG, HM_ERR_CUDA.
+ * 2 segment sums, 3 row chunks (phase C / couplings / sweeps), 4 multiplier
+ * fan-out (copies the coefficients each row-chunk piece multiplies into
+ * contiguous runs).  out : host array of nout (<= 5) entries.
+ * Errors: HM_ERR_ARG, HM_ERR_CUDA.
  */
 typedef struct { double ms; int64_t launches; int64_t bytes; } hm_kernel_stat;
 hm_status hm_profile(hm_matrix* m, int32_t enable);

@@ -23,7 +23,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 CPP = ["trees.cpp", "linalg.cpp", "build.cpp", "codec.cpp", "program.cpp", "matrix.cpp"]
 CU = ["kernels.cu", "noalloc.cu"]
-HDRS = ["hm_internal.h", "dev_types.h", "program.h"]
+HDRS = ["hm_internal.h", "dev_types.h", "program.h", "decode.cuh"]
 
 
 def _run(cmd):

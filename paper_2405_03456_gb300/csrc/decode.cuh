@@ -1,0 +1,317 @@
+// Device helpers of libhm: float-float arithmetic and the on-the-fly decoders
+// of the packed formats (Sec. 4.1: AFLP and FPX; raw FP64 for the uncompressed
+// baseline), and the bulk-copy / mbarrier primitives of the streaming kernels.
+//
+// Arithmetic (GB300 runs FP64 FMA at 1/60 of the FP32 rate):
+//  * every packed value is decoded to FP32 with integer operations; AFLP
+//    values are decoded as +-(s - 1), their per-array vmin being folded into
+//    the coefficient vectors or tile scales;
+//  * TIER_F32 (eps > 2^-22): one FP32 value per entry;
+//  * TIER_FF (eps <= 2^-22 and the uncompressed baseline): entries and vector
+//    values as float-float pairs, products accumulated with the compensated
+//    dot product of Ogita, Rump and Oishi (2005, "Dot2": TwoProduct by FMA,
+//    TwoSum of Knuth), about 2^-46 relative.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "dev_types.h"
+
+namespace hm {
+
+#define HM_FULL 0xffffffffu
+
+__device__ __forceinline__ uint32_t pad8u(uint32_t x) { return (x + 7u) & ~7u; }
+
+__device__ __forceinline__ void latch_error(int* err, int code) {
+  if (err) atomicCAS(err, 0, code);
+}
+
+// ---------------------------------------------------------------- float-float
+struct FF {
+  float hi, lo;
+};
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  float bp = s - a;
+  e = (a - (s - bp)) + (b - bp);
+}
+
+__device__ __forceinline__ FF ff_add(FF a, FF b) {
+  float s, e;
+  two_sum(a.hi, b.hi, s, e);
+  e += a.lo + b.lo;
+  float h = s + e;
+  return {h, e - (h - s)};
+}
+
+__device__ __forceinline__ FF ff_add_f(FF a, float b) {
+  float s, e;
+  two_sum(a.hi, b, s, e);
+  e += a.lo;
+  float h = s + e;
+  return {h, e - (h - s)};
+}
+
+// (a.hi + a.lo) * (b.hi + b.lo) to about 2^-46
+__device__ __forceinline__ FF ff_mul(FF a, FF b) {
+  float p = a.hi * b.hi;
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e));
+  float h = p + e;
+  return {h, e - (h - p)};
+}
+
+__device__ __forceinline__ FF ff_from_d(double v) {
+  float h = (float)v;
+  return {h, (float)(v - (double)h)};
+}
+
+__device__ __forceinline__ double ff_to_d(FF a) { return (double)a.hi + (double)a.lo; }
+
+// Dot2 accumulation of d*v into (s, c)
+__device__ __forceinline__ void dot2(float& s, float& c, float dh, float dl, float vh, float vl) {
+  float p = dh * vh;
+  float pe = fmaf(dh, vh, -p);
+  float tail = fmaf(dh, vl, fmaf(dl, vh, pe));
+  float s1 = s + p;
+  float bp = s1 - s;
+  float e = (s - (s1 - bp)) + (p - bp);
+  s = s1;
+  c += e + tail;
+}
+
+// ---------------------------------------------------------------- decoding
+// Value i of 4 consecutive B-byte codes held in B little-endian words, placed
+// at the top of a 32-bit (B <= 4) or 64-bit (B >= 5) window.
+template <int B, int I>
+__device__ __forceinline__ uint32_t top32(const uint32_t (&w)[B]) {
+  constexpr int o = I * B + B - 4;
+  if constexpr (o < 0) {
+    return w[0] << (8 * (-o));
+  } else {
+    constexpr int wi = o >> 2, sh = (o & 3) * 8;
+    if constexpr (sh == 0)
+      return w[wi];
+    else
+      return __funnelshift_r(w[wi], w[wi + 1], sh);
+  }
+}
+
+template <int B, int I>
+__device__ __forceinline__ uint64_t top64(const uint32_t (&w)[B]) {
+  constexpr int o = I * B + B - 8;
+  if constexpr (o < 0) {
+    uint64_t v = ((uint64_t)w[1] << 32) | w[0];
+    return v << (8 * (-o));
+  } else {
+    constexpr int wi = o >> 2, sh = (o & 3) * 8;
+    uint64_t v = ((uint64_t)w[wi + 1] << 32) | w[wi];
+    if constexpr (sh == 0) {
+      return v;
+    } else {
+      return (v >> sh) | ((uint64_t)w[wi + 2] << (64 - sh));
+    }
+  }
+}
+
+// FP64 bit pattern -> float-float (hi truncated to 24 bits, lo the rest).
+template <int TIER>
+__device__ __forceinline__ void split_f64bits(uint64_t P, float& hi, float& lo) {
+  uint32_t sgn = (uint32_t)(P >> 32) & 0x80000000u;
+  int E = (int)((P >> 52) & 0x7ff);
+  uint64_t M = P & ((1ull << 52) - 1);
+  uint32_t hb = (E >= 897) ? (((uint32_t)(E - 896) << 23) | (uint32_t)(M >> 29)) : 0u;
+  hi = __uint_as_float(hb | sgn);
+  lo = 0.0f;
+  if constexpr (TIER == TIER_FF) {
+    if (E >= 949) {
+      float l = __uint2float_rn((uint32_t)(M & ((1u << 29) - 1)));
+      l *= __uint_as_float((uint32_t)(E - 948) << 23);
+      lo = __uint_as_float(__float_as_uint(l) ^ sgn);
+    }
+  }
+}
+
+// Decode 4 consecutive values of format (F, B) into hi (and lo for TIER_FF).
+template <int TIER, int F, int B>
+__device__ __forceinline__ void decode4(const uint32_t (&w)[B], int e, int m, float (&h)[4],
+                                        float (&l)[4]) {
+#pragma unroll
+  for (int i = 0; i < 4; ++i) l[i] = 0.0f;
+  if constexpr (F == 0) {                                   // FPX e8: the code is the FP32 top
+    constexpr uint32_t mask = 0xffffffffu << (8 * (4 - B));
+    h[0] = __uint_as_float(top32<B, 0>(w) & mask);
+    h[1] = __uint_as_float(top32<B, 1>(w) & mask);
+    h[2] = __uint_as_float(top32<B, 2>(w) & mask);
+    h[3] = __uint_as_float(top32<B, 3>(w) & mask);
+  } else if constexpr (F == 2 && (B <= 3 || (B == 4 && TIER == TIER_F32))) {
+    // AFLP with s in FP32 (exact for B <= 3; for B = 4 the mantissa is cut to
+    // 23 bits, which is the F32 tier's own precision)
+    constexpr uint32_t mask = (0xffffffffu << (8 * (4 - B))) & 0x7fffffffu;
+    const int sh = 8 - e;
+    uint32_t t[4] = {top32<B, 0>(w), top32<B, 1>(w), top32<B, 2>(w), top32<B, 3>(w)};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      uint32_t sb = ((t[i] & mask) >> sh) + (127u << 23);
+      float d = __uint_as_float(sb) - 1.0f;
+      h[i] = __uint_as_float(__float_as_uint(d) ^ (t[i] & 0x80000000u));
+    }
+  } else if constexpr (F == 2) {                           // AFLP with m' > 23
+    uint64_t c[4];
+    if constexpr (B == 4) {
+      c[0] = w[0]; c[1] = w[1]; c[2] = w[2]; c[3] = w[3];
+    } else {
+      constexpr int rs = 64 - 8 * B;
+      c[0] = top64<B, 0>(w) >> rs;
+      c[1] = top64<B, 1>(w) >> rs;
+      c[2] = top64<B, 2>(w) >> rs;
+      c[3] = top64<B, 3>(w) >> rs;
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      uint32_t sgn = (uint32_t)(c[i] >> (8 * B - 1)) << 31;
+      uint32_t f = (uint32_t)(c[i] >> m) & ((1u << e) - 1u);
+      uint64_t mant = c[i] & ((1ull << m) - 1ull);
+      uint32_t hb = ((f + 127u) << 23) | (uint32_t)(mant >> (m - 23));
+      float d = __uint_as_float(hb) - 1.0f;
+      h[i] = __uint_as_float(__float_as_uint(d) ^ sgn);
+      if constexpr (TIER == TIER_FF) {
+        uint64_t ml = mant & ((1ull << (m - 23)) - 1ull);
+        float lv = __ull2float_rn(ml) * __uint_as_float((uint32_t)(f + 127 - m) << 23);
+        l[i] = __uint_as_float(__float_as_uint(lv) ^ sgn);
+      }
+    }
+  } else {                                                  // FPX e11 or raw FP64
+    constexpr uint64_t mask = (B == 8) ? ~0ull : (~0ull << (8 * (8 - B)));
+    split_f64bits<TIER>(top64<B, 0>(w) & mask, h[0], l[0]);
+    split_f64bits<TIER>(top64<B, 1>(w) & mask, h[1], l[1]);
+    split_f64bits<TIER>(top64<B, 2>(w) & mask, h[2], l[2]);
+    split_f64bits<TIER>(top64<B, 3>(w) & mask, h[3], l[3]);
+  }
+}
+
+// Shared-memory loads by 32-bit shared address.
+__device__ __forceinline__ uint2 lds64(uint32_t a) {
+  uint2 v;
+  asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ uint32_t lds32(uint32_t a) {
+  uint32_t v;
+  asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ uint4 lds128(uint32_t a) {
+  uint4 v;
+  asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(a));
+  return v;
+}
+
+// A lane's 8 consecutive codes of one column in shared memory: 8*B bytes at
+// an 8-byte aligned shared address, read as B 64-bit loads, decoded to 8
+// values (hi, and lo for TIER_FF).
+template <int TIER, int F, int B>
+__device__ __forceinline__ void decode8s(uint32_t a, int e, int m, float (&h)[8], float (&l)[8]) {
+  uint32_t w[2 * B];
+#pragma unroll
+  for (int i = 0; i < B; ++i) {
+    const uint2 t = lds64(a + 8u * i);
+    w[2 * i] = t.x;
+    w[2 * i + 1] = t.y;
+  }
+  uint32_t w0[B], w1[B];
+#pragma unroll
+  for (int i = 0; i < B; ++i) {
+    w0[i] = w[i];
+    w1[i] = w[B + i];
+  }
+  float h0[4], l0[4], h1[4], l1[4];
+  decode4<TIER, F, B>(w0, e, m, h0, l0);
+  decode4<TIER, F, B>(w1, e, m, h1, l1);
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    h[u] = h0[u];
+    h[4 + u] = h1[u];
+    l[u] = l0[u];
+    l[4 + u] = l1[u];
+  }
+}
+
+// The decode classes (F, B) the kernels instantiate.
+#define HM_FORMATS(X) \
+  X(0, 2) X(0, 3) X(0, 4) X(1, 5) X(1, 6) X(1, 7) X(1, 8) \
+  X(2, 1) X(2, 2) X(2, 3) X(2, 4) X(2, 5) X(2, 6) X(2, 7) X(3, 8)
+
+// ---------------------------------------------------------------- bulk copies and mbarriers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_init_fence() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+// Bounded wait: each try suspends the thread until the phase completes or
+// about `hint_ns` pass; gives up after `limit` tries (about 2 s) and returns false.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t limit = 2000u) {
+  const uint32_t hint_ns = 1000000u;
+  for (uint32_t i = 0; i < limit; ++i) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(hint_ns)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
+// Order this thread's earlier generic-proxy shared-memory accesses before its
+// later async-proxy (bulk copy) writes.
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// Global -> shared bulk copy of `bytes` (multiple of 16; both addresses
+// 16-byte aligned) completing on `bar` (transaction bytes).
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// L2 policy for data read exactly once (the packed payload): evict it first,
+// so that the vectors the kernels gather from stay resident in L2.
+__device__ __forceinline__ uint64_t policy_evict_first() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+
+// bulk_g2s with an L2 cache policy.
+__device__ __forceinline__ void bulk_g2s_hint(void* dst, const void* src, uint32_t bytes, uint64_t* bar,
+                                              uint64_t pol) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(pol)
+      : "memory");
+}
+
+}  // namespace hm

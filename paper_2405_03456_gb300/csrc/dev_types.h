@@ -1,5 +1,11 @@
 // Device-side work descriptors shared by the kernels (kernels.cu) and the host
-// layout builder (matrix.cpp).  Plain structs, identical layout on both sides.
+// layout builder (program.cpp).  Plain structs, identical layout on both sides.
+//
+// The packed payload is self-describing: every unit of work a warp streams
+// into shared memory with one bulk copy (a column-dot item, a row-chunk piece)
+// starts with an inline header that holds everything the warp needs to decode
+// it, so the only descriptors read from global memory are the compact copy
+// descriptors (offset, size) the warp prefetches 32 at a time.
 #pragma once
 #include <cstdint>
 
@@ -13,9 +19,15 @@ namespace hm {
 
 // Packed value format word: B | fmt << 8 | e << 16 | m << 24.
 //   fmt 0: FPX e8 (B 2..4)   1: FPX e11 (B 5..8)   2: AFLP (B 1..7)   3: raw FP64 (B 8)
-// Every packed column starts 4-byte aligned and occupies pad4(rows * B) bytes.
 HM_HD inline uint32_t fmt_word(int B, int fmt, int e, int m) {
   return (uint32_t)B | ((uint32_t)fmt << 8) | ((uint32_t)e << 16) | ((uint32_t)m << 24);
+}
+
+// 16-bit form of a format word used inside the streams: B (4 bits) | fmt << 4
+// (2 bits) | e << 6 (4 bits) | m << 10 (6 bits).
+HM_HD inline uint16_t fmt16(uint32_t fw) {
+  const uint32_t B = fw & 0xff, f = (fw >> 8) & 0xff, e = (fw >> 16) & 0xff, m = fw >> 24;
+  return (uint16_t)(B | (f << 4) | (e << 6) | (m << 10));
 }
 
 // Float-float pair (hi + lo): scales and partial sums, so that no FP64
@@ -24,67 +36,130 @@ struct F2 {
   float hi, lo;
 };
 
-// Rows per lane in the product kernels: every lane decodes 8 consecutive
-// values of a column (two groups of 4 codes = 2B 32-bit words, one 8-byte
-// aligned run), so columns are padded to 8 bytes.
-constexpr int RPL = 8;
+// Rows per lane in the product kernels: a lane decodes 8 (float-float tier)
+// or 16 (FP32 tier) consecutive values of a column, i.e. groups of 4 codes,
+// 8*B bytes per 8 rows, from an 8-byte aligned address; every packed column
+// is padded to 8 bytes.
+constexpr int RPL = 8;      // rows per group of two 4-code words
+constexpr int RPL_MAX = 16;
 
-// Column dots (phase A): sum_j = sum_{r < nrows} M[r, j] * v[vin + r] over the
-// ncols columns of one item (one segment of a column set); column j has format
-// word fmts[fmt + j] and output scale cscale[fmt + j] (float-float); columns are contiguous
-// from `off`, each pad8(nrows * B_j) bytes.  A set with a single segment
-// writes its coefficients directly (ITEM_FINAL): vout[out + j] =
-// cscale[fmt + j] * (alpha if ITEM_ALPHA) * sum_j; otherwise partial[out + j] = sum_j.
+// Shared-memory staging of the streaming kernels (per warp: NS stages).
+// Launch shapes (warps per block, stages per warp) the autotuner chooses from;
+// one block per SM.  Column dots also stage an input segment per stage.
+constexpr int NCFG = 3;
+constexpr int CS_CFG_WARPS[NCFG] = {16, 10, 7};
+constexpr int CS_CFG_STAGES[NCFG] = {2, 3, 4};
+constexpr int RS_CFG_WARPS[NCFG] = {16, 11, 8};
+constexpr int RS_CFG_STAGES[NCFG] = {2, 3, 4};
+constexpr int STAGE_BYTES = 6144;          // payload bytes of one stage (item / piece incl. header)
+constexpr int SEG_ROWS = 64;               // rows of a column-dot segment
+constexpr int CHUNK_ROWS = 128;            // rows of a row chunk
+constexpr int PIECE_MAX_COLS = 64;         // columns of one row-chunk piece (2 multipliers per lane)
+
+// ---------------------------------------------------------------- column dots (phase A)
+// A column-dot piece holds <= 32 columns of one decode class over the same
+// <= SEG_ROWS rows (one segment of a column cluster: the columns of every
+// column set that multiplies the same part of the input vector), laid out as
+//   CPieceHdr | CColMeta[ncols] | F2 scale[ncols] (ITEM_FINAL only) | columns
+// where every column holds pad16(nrows) codes (rows past nrows are zero codes),
+// i.e. pad16(nrows) * B bytes.  sum_j = sum_{r < nrows} M[r, j] * v[vin + r];
+// ITEM_FINAL (the set fits one segment): v[out_j] = scale_j * (alpha if
+// ITEM_ALPHA) * sum_j; otherwise partial[out_j] = sum_j.
 constexpr int32_t ITEM_FINAL = 1;
 constexpr int32_t ITEM_ALPHA = 2;
-struct Item {
-  uint64_t off;
-  int32_t fmt;
-  int32_t ncols;
-  int32_t nrows;    // 1..128
-  int32_t vin;      // vector index of row 0
-  int32_t out;      // partial index, or vector index with ITEM_FINAL, of column 0
-  int32_t flags;
-};
-
-// Uniform tile of a row chunk: ncols columns of the chunk's rows, one format
-// word for all of them (direct compression), input v[vin + j] times `scale`.
-struct Tile {
-  uint64_t off;     // payload byte offset of column 0 (8-byte aligned)
-  int32_t ncols;
-  uint32_t fw;      // format word
-  int32_t vin;
-  int32_t flags;    // bit 0: multiply by alpha
-  F2 scale;         // AFLP vmin of the direct-compressed matrix (float-float), else 1
-};
-
-// Column of a row chunk's merged VALR columns (W factors, row bases): its
-// format word and the vector index of its multiplier; the columns follow each
-// other from Chunk::coff, each pad8(nrows * B) bytes, sorted by format.
-struct ColMeta {
-  uint32_t fw;
-  int32_t vin;
-};
-
-// A run of output rows owned by one thread block: uniform tiles [t0, t1) and
-// merged columns [c0, c1) starting at payload offset coff.
-struct Chunk {
-  uint64_t coff;
-  int32_t row0;     // output index of row 0
-  int32_t nrows;    // 1..128
-  int32_t t0, t1;
-  int32_t c0, c1;
-  int32_t flags;    // bit 0: multiply the result by alpha
+constexpr int CPIECE_MAX_COLS = 64;
+struct CPieceHdr {
+  int32_t vin;       // vector index of row 0
+  uint16_t nrows;    // 1..SEG_ROWS
+  uint16_t ncols;    // 1..CPIECE_MAX_COLS
+  uint16_t fb;       // decode class: fmt << 4 | B
+  uint16_t flags;    // ITEM_FINAL | ITEM_ALPHA
   int32_t pad;
 };
+static_assert(sizeof(CPieceHdr) == 16, "CPieceHdr layout");
 
-// out_vec[out] = scale * (alpha if flags&1) * sum_{p in [p0,p1)} pscale[p] * partial[plist[p]]
-// (float-float arithmetic)
+// Per column-dot column: e | m << 8 of its codes and its output index.
+struct CColMeta {
+  uint16_t em;
+  uint16_t pad;
+  int32_t out;
+};
+
+// Copy descriptor of a column-dot piece (pieces start 16-byte aligned):
+// payload offset / 8, total bytes (header included), vector index of row 0,
+// rows.  The input segment is copied only when it differs from the previous
+// piece's of the same warp.
+struct ItemCopy {
+  uint32_t off8;
+  uint32_t bytes;
+  int32_t vin;
+  int32_t nrows;
+};
+
+// ---------------------------------------------------------------- row chunks (phase C)
+// A row chunk (a leaf cluster's rows of y, or <= 128 coefficients) is the sum
+// of many columns restricted to its rows: the uniform tiles of directly
+// compressed matrices (dense leaves, couplings, transfers) and the merged
+// VALR columns (W factors of all low-rank blocks of its ancestors' block rows,
+// or row bases).  They are cut into pieces of <= PIECE_MAX_COLS columns of one
+// decode class (fmt, B) and <= STAGE_BYTES bytes, laid out as
+//   PieceHdr | uint16 em[ncols] (merged pieces, padded to 8) | columns
+// with column j at offset j * pad8(nrows * B) after the metadata.  A piece's
+// multipliers are ncols consecutive vector entries v[moff ..] (a tile's input
+// segment, or a run of multiplier slots that a fan-out launch fills from the
+// scattered coefficients before the chunks run), copied into shared memory
+// with the piece.
+// Piece header flags (properties of the data).
+constexpr uint16_t PH_TILE = 4;     // uniform tile piece (multipliers v[vin0 + j] * scale)
+constexpr uint16_t PH_TALPHA = 8;   // tile piece multiplied by alpha
+constexpr uint16_t PH_CALPHA = 32;  // chunk result multiplied by alpha (coefficient modes)
+struct PieceHdr {
+  int32_t row0;      // output index of the chunk's row 0
+  uint16_t nrows;    // rows of the chunk (1..128)
+  uint16_t flags;
+  uint16_t fb;       // decode class: fmt << 4 | B
+  uint16_t em;       // tile pieces: e | m << 8
+  int32_t vin0;      // tile pieces: multiplier index of the piece's column 0
+  uint16_t ncols;
+  uint16_t pad0;
+  int32_t pad1;
+  F2 scale;          // tile pieces: AFLP vmin of the matrix (float-float), else 1
+  int32_t pad[2];
+};
+static_assert(sizeof(PieceHdr) == 40, "PieceHdr layout");
+
+// Copy descriptor of a piece for one split of the launch into warp ranges:
+// payload offset / 8; bytes (header included) | range flags << 16 | ncols << 24;
+// first multiplier index; for a chunk shared by several warps, its split index
+// << 8 | this part's index (else -1).
+constexpr uint32_t PD_FIRST = 1;    // first piece of this warp's part of the chunk: clear sums
+constexpr uint32_t PD_LAST = 2;     // last piece of the part: emit
+constexpr uint32_t PD_SPLIT = 4;    // the chunk is shared by several warps: emit through the fix-up
+struct PieceCopy {
+  uint32_t off8;
+  uint32_t bytes_flags;
+  int32_t moff;
+  int32_t split_part;
+};
+
+// A chunk whose pieces are spread over several warps: the parts write their
+// row sums to fix[(slot0 + pidx) * CHUNK_ROWS + r]; the last part to finish
+// (counter) adds them in part order and emits.
+struct Split {
+  int32_t slot0;
+  int32_t nparts;
+};
+
+// out_vec[out] = scale * (alpha if flags & 1) * sum_{p in [p0, p1)} w_p * partial[p], with
+// w_p = pscale[ps + p - p0] if flags & 2, else 1 (float-float arithmetic).
+// Each coefficient's partials (one per segment) are contiguous.
 struct GsumOut {
   int32_t out;
   int32_t p0, p1;
   int32_t flags;
   F2 scale;
+  int32_t ps;
+  int32_t pad;
 };
 
 enum { MODE_Y = 0, MODE_VEC = 1, MODE_VEC_ADD = 2 };

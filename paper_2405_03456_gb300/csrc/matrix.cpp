@@ -16,15 +16,15 @@
 namespace hm {
 cudaError_t kernels_init();
 cudaError_t launch_gather(const double* x, const int32_t* perm, int n, float2* xo, cudaStream_t st);
-cudaError_t launch_cdot(int tier, const Item* items, int nitems, const uint8_t* pay, const uint32_t* fmts,
-                        const F2* cscale, const float2* vin, F2 alpha, F2* partial, float2* vout, int* err,
-                        int grid, cudaStream_t st);
-cudaError_t launch_gsum(const GsumOut* outs, int nouts, const int32_t* plist, const F2* pscale, const F2* partial,
-                        F2 alpha, float2* vout, cudaStream_t st);
-cudaError_t launch_rgemv(int tier, int mode, const Chunk* chunks, int nchunks, const Tile* tiles,
-                         const ColMeta* cols, const uint8_t* pay, const float2* vin, double alpha, F2 alpha_ff,
-                         double beta, double* y, const int32_t* perm, float2* vout, const double* rowscale,
-                         int* err, cudaStream_t st);
+cudaError_t launch_cdot(int tier, int cfg, const ItemCopy* items, const int32_t* wbeg, int nw, const uint8_t* pay,
+                        const float2* vec, F2 alpha, F2* partial, float2* vout, int* err, cudaStream_t st);
+cudaError_t launch_fanout(const int32_t* src, int n, float2* dst, const float2* vec, cudaStream_t st);
+cudaError_t launch_gsum(const GsumOut* outs, int nouts, const F2* pscale, const F2* partial, F2 alpha, float2* vout,
+                        cudaStream_t st);
+cudaError_t launch_rgemv(int tier, int mode, int cfg, const PieceCopy* pieces, const int32_t* wbeg, int nw,
+                         const uint8_t* pay, const float2* vec, double alpha, F2 alpha_ff, double beta, double* y,
+                         const int32_t* perm, float2* vout, const double* rowscale, F2* fix, int32_t* fixcnt,
+                         const Split* splits, int* err, cudaStream_t st);
 cudaError_t launch_decode(const uint8_t* p, int64_t n, int B, int fmt, int e, int m, double vmin,
                           double* out, cudaStream_t st);
 }  // namespace hm
@@ -67,17 +67,17 @@ struct hm_matrix {
   Program prog;
   // device copies of the program
   DevArr<uint8_t> d_pay;
-  DevArr<uint32_t> d_fmt;
-  DevArr<F2> d_cscale;
-  DevArr<Item> d_items;
+  DevArr<ItemCopy> d_items;
   DevArr<GsumOut> d_gout;
-  DevArr<int32_t> d_plist;
   DevArr<F2> d_pscale;
-  DevArr<Tile> d_tiles;
-  DevArr<ColMeta> d_cols;
-  DevArr<Chunk> d_chunks;
+  DevArr<PieceCopy> d_pieces;
+  DevArr<int32_t> d_wbeg;
+  DevArr<int32_t> d_fan;
+  DevArr<Split> d_splits;
   DevArr<double> d_rowscale;
   DevArr<int32_t> d_perm;
+  F2* d_fix = nullptr;         // row sums of the parts of chunks shared by warps
+  int32_t* d_fixcnt = nullptr; // arrival counters of those chunks (reset by the last part)
   float2* d_vec = nullptr;     // vector workspace (x, coefficient vectors)
   F2* d_part = nullptr;        // column-dot partial sums (float-float)
   int* d_err = nullptr;        // latched device error word
@@ -127,17 +127,19 @@ struct hm_matrix {
   void release_device() {
     drop_graph();
     d_pay.release();
-    d_fmt.release();
-    d_cscale.release();
     d_items.release();
     d_gout.release();
-    d_plist.release();
     d_pscale.release();
-    d_tiles.release();
-    d_cols.release();
-    d_chunks.release();
+    d_pieces.release();
+    d_wbeg.release();
+    d_fan.release();
+    d_splits.release();
     d_rowscale.release();
     d_perm.release();
+    if (d_fix) cudaFree(d_fix);
+    if (d_fixcnt) cudaFree(d_fixcnt);
+    d_fix = nullptr;
+    d_fixcnt = nullptr;
     if (d_vec) cudaFree(d_vec);
     if (d_part) cudaFree(d_part);
     if (d_err) cudaFree(d_err);
@@ -165,15 +167,17 @@ hm_status upload(hm_matrix* M) {
 #define UP(arr, vec) \
   if ((e = M->arr.upload(vec)) != cudaSuccess) return cuda_status(e);
   UP(d_pay, P.pk.pay)
-  UP(d_fmt, P.pk.fmts)
-  UP(d_cscale, P.pk.cscale)
   UP(d_items, P.items)
   UP(d_gout, P.gouts)
-  UP(d_plist, P.plist)
   UP(d_pscale, P.pscale)
-  UP(d_tiles, P.tiles)
-  UP(d_cols, P.cols)
-  UP(d_chunks, P.chunks)
+  {
+    std::vector<PieceCopy> all;
+    for (int cf = 0; cf < NCFG; ++cf) all.insert(all.end(), P.pdesc[cf].begin(), P.pdesc[cf].end());
+    UP(d_pieces, all)
+  }
+  UP(d_wbeg, P.wbeg)
+  UP(d_fan, P.fan_src)
+  UP(d_splits, P.splits)
   UP(d_rowscale, P.rowscale)
 #undef UP
   std::vector<int32_t> perm(M->H.n);
@@ -186,6 +190,11 @@ hm_status upload(hm_matrix* M) {
     return cuda_status(e);
   if ((e = cudaMalloc(&M->d_part, std::max<int64_t>(P.npartial, 1) * sizeof(F2))) != cudaSuccess)
     return cuda_status(e);
+  if ((e = cudaMalloc(&M->d_fix, std::max<int64_t>(P.nfix, 1) * CHUNK_ROWS * sizeof(F2))) != cudaSuccess)
+    return cuda_status(e);
+  const size_t ncnt = std::max<size_t>(P.splits.size(), 1) * sizeof(int32_t);
+  if ((e = cudaMalloc(&M->d_fixcnt, ncnt)) != cudaSuccess) return cuda_status(e);
+  if ((e = cudaMemset(M->d_fixcnt, 0, ncnt)) != cudaSuccess) return cuda_status(e);
   if ((e = cudaMalloc(&M->d_err, sizeof(int))) != cudaSuccess) return cuda_status(e);
   if ((e = cudaMemset(M->d_err, 0, sizeof(int))) != cudaSuccess) return cuda_status(e);
   return HM_OK;
@@ -272,36 +281,40 @@ hm_status hm_compress(hm_matrix* M, double eps, int32_t codec, int32_t valr) {
   return HM_OK;
 }
 
+static cudaError_t run_launch(hm_matrix* M, const Launch& L, double alpha, const double* x, double beta, double* y,
+                              cudaStream_t st) {
+  Program& P = M->prog;
+  const F2 aff = split_ff(alpha);
+  const int cf = L.cfg;
+  switch (L.kind) {
+    case Launch::GATHER:
+      return launch_gather(x, M->d_perm.p, (int)L.n, M->d_vec, st);
+    case Launch::CDOT:
+      return launch_cdot(P.tier, cf, M->d_items.p, M->d_wbeg.p + L.woff[cf], L.nw[cf], M->d_pay.p, M->d_vec, aff,
+                         M->d_part, M->d_vec, M->d_err, st);
+    case Launch::GSUM:
+      return launch_gsum(M->d_gout.p + L.off, (int)L.n, M->d_pscale.p, M->d_part, aff, M->d_vec, st);
+    case Launch::FANOUT:
+      return launch_fanout(M->d_fan.p + L.off, (int)L.n, M->d_vec + P.fan_base + L.off, M->d_vec, st);
+    case Launch::RGEMV:
+      return launch_rgemv(P.tier, L.mode, cf, M->d_pieces.p + (size_t)cf * P.npieces, M->d_wbeg.p + L.woff[cf],
+                          L.nw[cf], M->d_pay.p, M->d_vec, alpha, aff, beta, y, M->d_perm.p, M->d_vec,
+                          L.use_rowscale ? M->d_rowscale.p : nullptr, M->d_fix, M->d_fixcnt, M->d_splits.p,
+                          M->d_err, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
 static hm_status run_program(hm_matrix* M, double alpha, const double* x, double beta, double* y,
                              cudaStream_t st) {
-  Program& P = M->prog;
-  cudaError_t e = cudaSuccess;
-  const F2 aff = split_ff(alpha);
-  for (const Launch& L : P.launches) {
+  for (const Launch& L : M->prog.launches) {
     hm_matrix::Rec rec{(int)L.kind, nullptr, nullptr, L.bytes};
     if (M->prof) {
       rec.e0 = M->take_event();
       rec.e1 = M->take_event();
       cudaEventRecord(rec.e0, st);
     }
-    switch (L.kind) {
-      case Launch::GATHER:
-        e = launch_gather(x, M->d_perm.p, (int)L.n, M->d_vec, st);
-        break;
-      case Launch::CDOT:
-        e = launch_cdot(P.tier, M->d_items.p + L.off, (int)L.n, M->d_pay.p, M->d_fmt.p, M->d_cscale.p, M->d_vec,
-                        aff, M->d_part, M->d_vec, M->d_err, M->nsm * 8, st);
-        break;
-      case Launch::GSUM:
-        e = launch_gsum(M->d_gout.p + L.off, (int)L.n, M->d_plist.p, M->d_pscale.p, M->d_part, aff, M->d_vec, st);
-        break;
-      case Launch::RGEMV:
-        e = launch_rgemv(P.tier, L.mode, M->d_chunks.p + L.off, (int)L.n, M->d_tiles.p, M->d_cols.p, M->d_pay.p,
-                         M->d_vec, alpha, aff, beta, y, M->d_perm.p, M->d_vec,
-                         L.use_rowscale ? M->d_rowscale.p : nullptr, M->d_err, st);
-        break;
-    }
-    if (e != cudaSuccess) return HM_ERR_CUDA;
+    if (run_launch(M, L, alpha, x, beta, y, st) != cudaSuccess) return HM_ERR_CUDA;
     if (M->prof) {
       cudaEventRecord(rec.e1, st);
       M->recs.push_back(rec);
@@ -388,6 +401,70 @@ hm_status hm_matvec_host(hm_matrix* M, double alpha, const double* x, double bet
   return HM_OK;
 }
 
+hm_status hm_autotune(hm_matrix* M, int32_t reps, void* stream) {
+  if (!M || reps < 1 || reps > 1000) return HM_ERR_ARG;
+  std::lock_guard<std::mutex> g(M->mu);
+  if (!M->compressed) return HM_ERR_STATE;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t n = M->H.n;
+  double *x = nullptr, *y = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  hm_status out = HM_OK;
+  if (cudaMalloc(&x, n * sizeof(double)) != cudaSuccess || cudaMalloc(&y, n * sizeof(double)) != cudaSuccess ||
+      cudaMemsetAsync(x, 0, n * sizeof(double), st) != cudaSuccess ||
+      cudaMemsetAsync(y, 0, n * sizeof(double), st) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+      cudaEventCreate(&e1) != cudaSuccess) {
+    out = HM_ERR_CUDA;
+  }
+  if (out == HM_OK && run_program(M, 1.0, x, 0.0, y, st) != HM_OK) out = HM_ERR_CUDA;   // warm-up
+  for (Launch& L : M->prog.launches) {
+    if (out != HM_OK) break;
+    if (L.kind != Launch::CDOT && L.kind != Launch::RGEMV) continue;
+    float best = 0.f;
+    int bestc = 0;
+    for (int cf = 0; cf < NCFG && out == HM_OK; ++cf) {
+      L.cfg = cf;
+      if (run_launch(M, L, 1.0, x, 0.0, y, st) != cudaSuccess) out = HM_ERR_CUDA;
+      cudaEventRecord(e0, st);
+      for (int r = 0; r < reps && out == HM_OK; ++r)
+        if (run_launch(M, L, 1.0, x, 0.0, y, st) != cudaSuccess) out = HM_ERR_CUDA;
+      cudaEventRecord(e1, st);
+      float ms = 0.f;
+      if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+        out = HM_ERR_CUDA;
+      if (cf == 0 || ms < best) {
+        best = ms;
+        bestc = cf;
+      }
+    }
+    L.cfg = bestc;
+  }
+  if (cudaStreamSynchronize(st) != cudaSuccess && out == HM_OK) out = HM_ERR_CUDA;
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (x) cudaFree(x);
+  if (y) cudaFree(y);
+  M->drop_graph();
+  return out;
+}
+
+hm_status hm_launch_shapes(const hm_matrix* M, int32_t* shapes, int32_t cap, int32_t* count) {
+  if (!M || !count || cap < 0 || (cap > 0 && !shapes)) return HM_ERR_ARG;
+  const auto& Ls = M->prog.launches;
+  *count = (int32_t)Ls.size();
+  for (int32_t i = 0; i < cap && i < (int32_t)Ls.size(); ++i)
+    shapes[i] = (Ls[i].kind == Launch::CDOT || Ls[i].kind == Launch::RGEMV) ? Ls[i].cfg : -1;
+  return HM_OK;
+}
+
+hm_status hm_set_launch_shapes(hm_matrix* M, int32_t shape) {
+  if (!M || shape < 0 || shape >= NCFG) return HM_ERR_ARG;
+  std::lock_guard<std::mutex> g(M->mu);
+  for (Launch& L : M->prog.launches) L.cfg = shape;
+  M->drop_graph();
+  return HM_OK;
+}
+
 hm_status hm_profile(hm_matrix* M, int32_t enable) {
   if (!M) return HM_ERR_ARG;
   M->prof = enable != 0;
@@ -395,8 +472,8 @@ hm_status hm_profile(hm_matrix* M, int32_t enable) {
 }
 
 hm_status hm_profile_read(hm_matrix* M, hm_kernel_stat* out, int32_t nout) {
-  if (!M || !out || nout < 0 || nout > 4) return HM_ERR_ARG;
-  hm_kernel_stat acc[4];
+  if (!M || !out || nout < 0 || nout > 5) return HM_ERR_ARG;
+  hm_kernel_stat acc[5];
   std::memset(acc, 0, sizeof(acc));
   hm_status st = HM_OK;
   for (auto& r : M->recs) {
@@ -472,11 +549,12 @@ hm_status hm_info(const hm_matrix* M, hm_info_t* o) {
   o->bytes_dense_fp64 = P.fp64_dense;
   o->bytes_payload = (int64_t)P.pk.pay.size();
   o->bytes_values = P.pk.value_bytes;
-  o->bytes_meta = (int64_t)(P.pk.fmts.size() * 4 + P.items.size() * sizeof(Item) +
-                            P.gouts.size() * sizeof(GsumOut) + P.plist.size() * 12 +
-                            P.tiles.size() * sizeof(Tile) + P.cols.size() * sizeof(ColMeta) +
-                            P.chunks.size() * sizeof(Chunk) + P.rowscale.size() * 8 + H.n * 4);
-  o->bytes_workspace = P.nvec * 8 + P.npartial * 8;
+  o->bytes_meta = P.pk.meta_bytes +
+                  (int64_t)(P.items.size() * sizeof(ItemCopy) + NCFG * P.npieces * sizeof(PieceCopy) +
+                            P.wbeg.size() * 4 + P.splits.size() * sizeof(Split) + P.gouts.size() * sizeof(GsumOut) +
+                            P.pscale.size() * 8 + P.rowscale.size() * 8 + P.fan_src.size() * 4) +
+                  H.n * 4;
+  o->bytes_workspace = P.nvec * 8 + P.npartial * 8 + P.nfix * CHUNK_ROWS * 8;
   o->nlaunches = (int64_t)P.launches.size();
   o->tier = P.tier;
   return HM_OK;

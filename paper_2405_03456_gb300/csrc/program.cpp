@@ -1,25 +1,33 @@
 // Packed layout of compressed H / UH / H^2 matrices and the launch program of
 // one product (Sec. 3 algorithms mapped onto the GPU kernels).
 //
-// Layout (one payload buffer, every column 8-byte aligned):
+// Layout (one payload buffer; every unit a warp copies into shared memory
+// starts 16-byte aligned with an inline header, every column is 8-byte aligned):
 //  * column dots (phase A: X factors of H blocks, UH column bases, H^2 leaf
 //    column bases, transfer matrices for the up-sweep) are stored
 //    segment-major: for each run of <= 128 rows, the rows of every column of
-//    the set.  An item is one such segment (all columns of the set).
+//    the set.  An item is one such segment of a group of columns (<= one
+//    stage of bytes), with the columns' format words (and output scales).
 //  * row chunks (phase C; couplings; down-sweep): each output chunk (a leaf
 //    cluster, or <= 128 coefficients) reads
 //      - uniform tiles: the chunk's rows of every column of one directly
-//        compressed matrix (dense leaf, coupling, transfer), contiguous;
+//        compressed matrix (dense leaf, coupling, transfer);
 //      - merged columns: the chunk's rows of every VALR-compressed column
 //        that reaches it (W factors of all low-rank blocks of its ancestors'
-//        block rows, or row bases), stored contiguously per chunk and sorted
-//        by format, with one (format word, multiplier index) per column.
-// A leaf chunk owns its rows of y and gathers the contributions of all its
-// ancestors' block rows itself: the race freedom of Alg. 3 without a
-// root-to-leaf traversal.
+//        block rows, or row bases), sorted by decode class, with one
+//        (e, m, multiplier index) per column.
+//    A chunk's data is cut into pieces (one decode class, <= 64 columns,
+//    <= one stage of bytes) stored contiguously in chunk order.
+// Every launch's items / pieces are split into contiguous ranges of about
+// equal bytes, one per warp.  A leaf chunk owns its rows of y and gathers the
+// contributions of all its ancestors' block rows itself: the race freedom of
+// Alg. 3 without a root-to-leaf traversal.  A chunk that straddles two warp
+// ranges is finished by whichever of its parts ends last (fixed summation
+// order, so results stay bitwise reproducible).
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <deque>
 #include <functional>
 #include <numeric>
 
@@ -29,8 +37,6 @@ namespace hm {
 
 namespace {
 
-constexpr int SEG_ROWS = 128;    // rows of a column-dot segment (16 lanes x 8 rows)
-constexpr int CHUNK_ROWS = 128;  // rows of a coefficient chunk
 
 struct Enc {
   CodeHdr h;
@@ -53,6 +59,18 @@ bool encode(const double* v, int64_t n, int codec, int key, Enc& out) {
   return kernel_decodable(out.h, v, n);
 }
 
+// Packed rows [r0, r1) of every column of a direct column set, columns
+// pad8(rows * B) apart: a uniform tile of a row chunk before it is cut into pieces.
+struct TileData {
+  std::vector<uint8_t> bytes;
+  int ncols = 0;
+  int64_t R = 0;
+  uint32_t fw = 0;
+  int32_t vin = 0;       // multiplier index of column 0
+  int32_t flags = 0;     // bit 0: multiply by alpha
+  F2 scale{1.0f, 0.0f};  // AFLP vmin of the matrix
+};
+
 struct Ctx {
   const HostMatrix& H;
   Program& P;
@@ -60,6 +78,8 @@ struct Ctx {
   double eps;
   int valr;
   int key_eps;
+  int nsm;
+  std::deque<TileData> tiles;   // storage of every tile until the program is laid out
 };
 
 // ---------------------------------------------------------------- VALR keys
@@ -111,63 +131,151 @@ bool make_direct(const Ctx& cx, const double* A, int64_t m, int n, ColSet& cs) {
   return encode(A, m * n, cx.codec, cx.key_eps, cs.enc[0]);
 }
 
-// format kind and byte width: columns with equal keys can share an item
-uint32_t kind_width(uint32_t fw) { return fw & 0xffffu; }
+int64_t pad8(int64_t x) { return (x + 7) & ~int64_t(7); }
+uint16_t class_of(uint32_t fw) { return (uint16_t)((((fw >> 8) & 0xff) << 4) | (fw & 0xff)); }
+uint16_t em_of(uint32_t fw) { return (uint16_t)(((fw >> 16) & 0xff) | ((fw >> 24) << 8)); }
 
-// ---------------------------------------------------------------- column-dot items
-// Segment-major layout of a column set (one item per segment of <= 128 rows);
-// input vector index of row 0 is vin.  A set that fits one segment writes its
-// coefficients v[out0 + j] = scale[j] * (alpha if use_alpha) * sum directly
-// (final = true, segp untouched); otherwise segp[j] receives the partial
-// index of column j in every segment.
-void pack_cdot(Program& P, const ColSet& cs, int32_t vin, int64_t& pbase, std::vector<std::vector<int32_t>>& segp,
-               bool allow_final, int64_t out0, const std::vector<double>* scale, bool use_alpha, bool& final_out) {
-  segp.assign(cs.n, {});
-  const int32_t fbase = (int32_t)P.pk.fmts.size();
-  for (int j = 0; j < cs.n; ++j) {
-    P.pk.fmts.push_back(cs.fw(j));
-    P.pk.cscale.push_back(split_ff(scale ? (*scale)[j] : 1.0));
+// ---------------------------------------------------------------- warp ranges
+// Split units (items / pieces) [0, n) of `bytes` into nw contiguous ranges of
+// about equal bytes: unit i goes to the warp holding the midpoint of its
+// bytes.  Appends nw + 1 absolute range starts (base + index) to wbeg.
+int partition(const std::vector<int64_t>& bytes, int64_t base, int nw_max, std::vector<int32_t>& wbeg) {
+  int64_t total = 0;
+  for (int64_t b : bytes) total += b;
+  const int64_t n = (int64_t)bytes.size();
+  int nw = (int)std::min<int64_t>(nw_max, std::max<int64_t>(1, (total + MIN_WARP_BYTES - 1) / MIN_WARP_BYTES));
+  nw = (int)std::max<int64_t>(1, std::min<int64_t>(nw, n));
+  std::vector<int32_t> start(nw + 1, (int32_t)(base + n));
+  int64_t cum = 0;
+  int w = 0;
+  start[0] = (int32_t)base;
+  for (int64_t i = 0; i < n; ++i) {
+    const int64_t mid = cum + bytes[i] / 2;
+    const int wi = (int)std::min<int64_t>(nw - 1, (__int128)mid * nw / std::max<int64_t>(total, 1));
+    while (w < wi) start[++w] = (int32_t)(base + i);
+    cum += bytes[i];
   }
-  final_out = allow_final && cs.m <= SEG_ROWS;
-  for (int64_t r0 = 0; r0 < cs.m; r0 += SEG_ROWS) {
-    const int64_t r1 = std::min<int64_t>(cs.m, r0 + SEG_ROWS);
-    uint64_t off0 = 0;
-    for (int j = 0; j < cs.n; ++j) {
-      const uint64_t o = P.pk.put(cs.col(j) + r0, r1 - r0, cs.B(j));
-      if (j == 0) off0 = o;
+  while (w < nw) start[++w] = (int32_t)(base + n);
+  wbeg.insert(wbeg.end(), start.begin(), start.end());
+  return nw;
+}
+
+// ---------------------------------------------------------------- column-dot pieces
+// One column of a column set that takes part in a column dot, with where a
+// single-segment result goes (out_final, scaled by scale_final).
+struct CdotCol {
+  const ColSet* cs;
+  int j;
+  int64_t out_final;
+  double scale_final;
+};
+
+int64_t nseg_of(int64_t m) { return (m + SEG_ROWS - 1) / SEG_ROWS; }
+
+// Pieces of the column dots of `cols` (all over the same m rows, input vector
+// index of row 0 = vin): segments of <= SEG_ROWS rows, columns sorted by
+// decode class, <= CPIECE_MAX_COLS columns and <= STAGE_BYTES bytes per piece.
+// If m fits one segment and allow_final, the results go straight to
+// v[out_final] (final_out = true); otherwise segment s of column c writes
+// partial[pout[c] + s].
+void pack_cdot(Program& P, const std::vector<CdotCol>& cols, int64_t m, int32_t vin, bool allow_final,
+               bool use_alpha, const std::vector<int64_t>& pout, bool& final_out) {
+  final_out = allow_final && m <= SEG_ROWS;
+  std::vector<int> ord(cols.size());
+  std::iota(ord.begin(), ord.end(), 0);
+  std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) {
+    return class_of(cols[a].cs->fw(cols[a].j)) < class_of(cols[b].cs->fw(cols[b].j));
+  });
+  for (int64_t r0 = 0; r0 < m; r0 += SEG_ROWS) {
+    const int64_t R = std::min<int64_t>(m, r0 + SEG_ROWS) - r0, R8 = (R + 15) & ~int64_t(15);
+    for (size_t k = 0; k < ord.size();) {
+      const uint32_t fw = cols[ord[k]].cs->fw(cols[ord[k]].j);
+      const uint16_t cls = class_of(fw);
+      size_t k1 = k;
+      while (k1 < ord.size() && class_of(cols[ord[k1]].cs->fw(cols[ord[k1]].j)) == cls) ++k1;
+      const int B = (int)(fw & 0xff);
+      const int64_t stride = R8 * B;
+      const int64_t percol = stride + (int64_t)sizeof(CColMeta) + (final_out ? 8 : 0);
+      const int per = (int)std::min<int64_t>(CPIECE_MAX_COLS, (STAGE_BYTES - (int64_t)sizeof(CPieceHdr)) / percol);
+      for (size_t a = k; a < k1; a += per) {
+        const int nc = (int)std::min<size_t>(per, k1 - a);
+        const uint64_t off = P.pk.align(16);
+        CPieceHdr h{};
+        h.vin = (int32_t)(vin + r0);
+        h.nrows = (uint16_t)R;
+        h.ncols = (uint16_t)nc;
+        h.fb = cls;
+        h.flags = (uint16_t)(final_out ? (ITEM_FINAL | (use_alpha ? ITEM_ALPHA : 0)) : 0);
+        P.pk.raw(&h, sizeof h);
+        std::vector<CColMeta> cm(nc);
+        std::vector<F2> sc;
+        for (int t = 0; t < nc; ++t) {
+          const int c = ord[a + t];
+          cm[t].em = em_of(cols[c].cs->fw(cols[c].j));
+          if (final_out) {
+            cm[t].out = (int32_t)cols[c].out_final;
+            sc.push_back(split_ff(cols[c].scale_final));
+          } else {
+            cm[t].out = (int32_t)(pout[c] + r0 / SEG_ROWS);
+          }
+        }
+        P.pk.raw(cm.data(), cm.size() * sizeof(CColMeta));
+        if (final_out) P.pk.raw(sc.data(), sc.size() * sizeof(F2));
+        for (int t = 0; t < nc; ++t) {
+          const CdotCol& cc = cols[ord[a + t]];
+          P.pk.put_rows(cc.cs->col(cc.j) + r0, R, R8, B);
+        }
+        const uint64_t end = P.pk.align(8);
+        P.items.push_back(ItemCopy{(uint32_t)(off >> 3), (uint32_t)(end - off), h.vin, (int32_t)R});
+        // values, header, column metadata, scales, input rows, outputs, copy descriptor
+        P.item_alg.push_back(R * B * nc + (int64_t)sizeof(CPieceHdr) + (8 + 8 + (final_out ? 8 : 0)) * nc + 8 * R +
+                             (int64_t)sizeof(ItemCopy));
+      }
+      k = k1;
     }
-    Item it{};
-    it.off = off0;
-    it.fmt = fbase;
-    it.ncols = cs.n;
-    it.nrows = (int32_t)(r1 - r0);
-    it.vin = (int32_t)(vin + r0);
-    if (final_out) {
-      it.out = (int32_t)out0;
-      it.flags = ITEM_FINAL | (use_alpha ? ITEM_ALPHA : 0);
-    } else {
-      it.out = (int32_t)pbase;
-      for (int j = 0; j < cs.n; ++j) segp[j].push_back((int32_t)(pbase + j));
-      pbase += cs.n;
-    }
-    P.items.push_back(it);
   }
+}
+
+// coefficient out = scale * (alpha if flags & 1) * sum_p w_p partial[p], p in [p0, p1)
+// (w_p = pscale[p - p0] when given, else 1)
+void gsum_one(Program& P, int64_t out, int64_t p0, int64_t p1, const std::vector<double>& pscale, double scale,
+              int flags) {
+  GsumOut o{};
+  o.out = (int32_t)out;
+  o.p0 = (int32_t)p0;
+  o.p1 = (int32_t)p1;
+  o.flags = flags;
+  o.ps = -1;
+  if (!pscale.empty()) {
+    o.flags |= 2;
+    o.ps = (int32_t)P.pscale.size();
+    for (double w : pscale) P.pscale.push_back(split_ff(w));
+  }
+  o.scale = split_ff(scale);
+  P.gouts.push_back(o);
 }
 
 // ---------------------------------------------------------------- row-chunk pieces
 // Uniform tile: rows [r0, r1) of every column of a direct column set.
-Tile pack_tile(Program& P, const ColSet& cs, int64_t r0, int64_t r1, int32_t vin, int32_t flags) {
-  Tile T{};
+const TileData* pack_tile(Ctx& cx, const ColSet& cs, int64_t r0, int64_t r1, int32_t vin, int32_t flags) {
+  cx.tiles.emplace_back();
+  TileData& T = cx.tiles.back();
+  const int B = cs.B(0);
+  const int64_t R = r1 - r0, stride = pad8(R * B);
+  T.bytes.assign((size_t)(stride * cs.n), 0);
   for (int j = 0; j < cs.n; ++j) {
-    const uint64_t o = P.pk.put(cs.col(j) + r0, r1 - r0, cs.B(j));
-    if (j == 0) T.off = o;
+    const uint64_t* c = cs.col(j) + r0;
+    uint8_t* dst = T.bytes.data() + j * stride;
+    for (int64_t i = 0; i < R; ++i)
+      for (int b = 0; b < B; ++b) dst[i * B + b] = (uint8_t)(c[i] >> (8 * b));
   }
   T.ncols = cs.n;
+  T.R = R;
   T.fw = cs.fw(0);
   T.vin = vin;
   T.flags = flags;
   T.scale = split_ff(cs.scale(0));
-  return T;
+  return &T;
 }
 
 // One column of a VALR set restricted to rows [r0, r1), with its multiplier.
@@ -179,8 +287,8 @@ struct ColRef {
 };
 
 struct ChunkWork {
-  Chunk c{};
-  std::vector<Tile> t;
+  int32_t row0 = 0, nrows = 0, flags = 0;   // flags bit 0: multiply the result by alpha
+  std::vector<const TileData*> t;
   std::vector<ColRef> cols;
 };
 
@@ -194,47 +302,178 @@ void add_launch(Program& P, Launch::Kind k, int64_t off, int64_t n, int mode = 0
   P.launches.push_back(L);
 }
 
-// Pack the merged columns of every chunk (sorted by format, contiguous), append
-// the chunks (largest first) and one RGEMV launch.
+// Cut the chunks of one output launch into pieces, split the pieces into
+// per-warp ranges, lay them out (headers, column metadata, columns) and append
+// one RGEMV launch.
 void add_rgemv(Ctx& cx, std::vector<ChunkWork>& cw, int mode, bool rowscale) {
   Program& P = cx.P;
-  std::vector<int64_t> w(cw.size());
-  for (size_t i = 0; i < cw.size(); ++i) {
-    ChunkWork& c = cw[i];
-    const int64_t R = c.c.nrows;
-    int64_t b = 64;
-    for (const Tile& t : c.t) b += R * (int64_t)(t.fw & 0xff) * t.ncols;
-    for (const ColRef& r : c.cols) b += R * r.cs->B(r.j) + 16;
-    w[i] = b;
-  }
-  std::vector<int64_t> order(cw.size());
-  std::iota(order.begin(), order.end(), 0);
-  std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return w[a] > w[b]; });
-  const int64_t first = (int64_t)P.chunks.size();
-  for (int64_t i : order) {
-    ChunkWork& c = cw[i];
-    const int64_t R = c.c.nrows;
-    c.c.t0 = (int32_t)P.tiles.size();
-    P.tiles.insert(P.tiles.end(), c.t.begin(), c.t.end());
-    c.c.t1 = (int32_t)P.tiles.size();
-    std::stable_sort(c.cols.begin(), c.cols.end(), [](const ColRef& a, const ColRef& b) {
-      return kind_width(a.cs->fw(a.j)) < kind_width(b.cs->fw(b.j));
-    });
-    c.c.c0 = (int32_t)P.cols.size();
-    c.c.coff = P.pk.align8();
-    for (const ColRef& r : c.cols) {
-      P.pk.put(r.cs->col(r.j) + r.r0, R, r.cs->B(r.j));
-      P.cols.push_back(ColMeta{r.cs->fw(r.j), r.vin});
+  struct PW {
+    int32_t chunk;
+    const TileData* t;   // tile piece, or nullptr for merged columns
+    int32_t j0;          // tile: first column; merged: first entry of the chunk's sorted list
+    int32_t ncols;
+    uint16_t cls;
+    int64_t bytes;
+  };
+  std::vector<PW> pw;
+  for (size_t ci = 0; ci < cw.size(); ++ci) {
+    ChunkWork& c = cw[ci];
+    const int64_t R = c.nrows;
+    for (const TileData* t : c.t) {
+      const int64_t stride = pad8(R * (int64_t)(t->fw & 0xff));
+      const int per = (int)std::min<int64_t>(PIECE_MAX_COLS, (STAGE_BYTES - (int64_t)sizeof(PieceHdr)) / stride);
+      for (int j0 = 0; j0 < t->ncols; j0 += per) {
+        const int nc = std::min(per, t->ncols - j0);
+        pw.push_back(PW{(int32_t)ci, t, j0, nc, class_of(t->fw), (int64_t)sizeof(PieceHdr) + nc * stride});
+      }
     }
-    c.c.c1 = (int32_t)P.cols.size();
-    P.chunks.push_back(c.c);
+    std::stable_sort(c.cols.begin(), c.cols.end(), [](const ColRef& a, const ColRef& b) {
+      return class_of(a.cs->fw(a.j)) < class_of(b.cs->fw(b.j));
+    });
+    for (size_t k = 0; k < c.cols.size();) {
+      const uint32_t fw = c.cols[k].cs->fw(c.cols[k].j);
+      const uint16_t cls = class_of(fw);
+      size_t k1 = k;
+      while (k1 < c.cols.size() && class_of(c.cols[k1].cs->fw(c.cols[k1].j)) == cls) ++k1;
+      const int64_t stride = pad8(R * (int64_t)(fw & 0xff));
+      const int per = (int)std::min<int64_t>(PIECE_MAX_COLS,
+                                             (STAGE_BYTES - (int64_t)sizeof(PieceHdr) - 8) / (stride + 2));
+      for (size_t a = k; a < k1; a += per) {
+        const int nc = (int)std::min<size_t>(per, k1 - a);
+        pw.push_back(PW{(int32_t)ci, nullptr, (int32_t)a, nc, cls,
+                        (int64_t)sizeof(PieceHdr) + pad8(2 * nc) + nc * stride});
+      }
+      k = k1;
+    }
+    if (c.t.empty() && c.cols.empty())   // nothing to add: the chunk still writes its (zero / scaled) rows
+      pw.push_back(PW{(int32_t)ci, nullptr, 0, 0, (uint16_t)((FMT_AFLP << 4) | 3), (int64_t)sizeof(PieceHdr)});
   }
   Launch L;
   L.kind = Launch::RGEMV;
   L.mode = mode;
-  L.off = first;
-  L.n = (int64_t)cw.size();
   L.use_rowscale = rowscale;
+  L.off = P.npieces;
+  L.n = (int64_t)pw.size();
+  const int64_t fan0 = (int64_t)P.fan_src.size();
+  // lay out (partition-independent headers, decode parameters, columns)
+  std::vector<PieceCopy> base(pw.size());
+  for (size_t i = 0; i < pw.size(); ++i) {
+    const PW& p = pw[i];
+    const ChunkWork& c = cw[p.chunk];
+    const int64_t R = c.nrows;
+    const uint64_t off = P.pk.align(16);
+    PieceHdr h{};
+    h.row0 = c.row0;
+    h.nrows = (uint16_t)R;
+    h.flags = (c.flags & 1) ? PH_CALPHA : 0;
+    h.fb = p.cls;
+    h.ncols = (uint16_t)p.ncols;
+    h.scale = F2{1.0f, 0.0f};
+    int64_t vals = 0, meta = (int64_t)sizeof(PieceHdr) + (int64_t)sizeof(PieceCopy);
+    int64_t moff = 0;
+    if (p.t) {
+      const TileData& t = *p.t;
+      const int B = (int)(t.fw & 0xff);
+      const int64_t stride = pad8(R * B);
+      h.flags |= PH_TILE | ((t.flags & 1) ? PH_TALPHA : 0);
+      h.em = em_of(t.fw);
+      h.vin0 = t.vin + p.j0;
+      h.scale = t.scale;
+      moff = h.vin0;
+      P.pk.raw(&h, sizeof h);
+      P.pk.align(8);
+      P.pk.pay.insert(P.pk.pay.end(), t.bytes.begin() + p.j0 * stride, t.bytes.begin() + (p.j0 + p.ncols) * stride);
+      vals = R * B * p.ncols;
+      P.pk.value_bytes += vals;
+      meta += 8 * p.ncols;   // multipliers
+    } else {
+      P.pk.raw(&h, sizeof h);
+      std::vector<uint16_t> em(p.ncols);
+      bool consecutive = true;
+      for (int k = 0; k < p.ncols; ++k) {
+        const ColRef& r = c.cols[p.j0 + k];
+        em[k] = em_of(r.cs->fw(r.j));
+        consecutive = consecutive && r.vin == c.cols[p.j0].vin + k;
+      }
+      if (p.ncols == 0) consecutive = false;
+      P.pk.raw(em.data(), em.size() * sizeof(uint16_t));
+      for (int k = 0; k < p.ncols; ++k) {
+        const ColRef& r = c.cols[p.j0 + k];
+        P.pk.put(r.cs->col(r.j) + r.r0, R, r.cs->B(r.j));
+        vals += R * r.cs->B(r.j);
+      }
+      if (p.ncols == 0) {
+        moff = 0;
+      } else if (consecutive) {
+        moff = c.cols[p.j0].vin;
+      } else {   // a run of fan-out slots (resolved to vector indices at the end)
+        moff = -1 - (int64_t)P.fan_src.size();
+        for (int k = 0; k < p.ncols; ++k) P.fan_src.push_back(c.cols[p.j0 + k].vin);
+      }
+      meta += (2 + 8) * p.ncols;   // decode parameters + multipliers
+    }
+    const uint64_t end = P.pk.align(8);
+    base[i] = PieceCopy{(uint32_t)(off >> 3), (uint32_t)(end - off) | ((uint32_t)p.ncols << 24), (int32_t)moff, -1};
+    int64_t alg = vals + meta;
+    const bool last_of_chunk = (i + 1 == pw.size()) || pw[i + 1].chunk != p.chunk;
+    if (last_of_chunk) {   // output rows of the chunk
+      if (mode == MODE_Y)
+        alg += R * (4 + 8 + 8);
+      else
+        alg += R * ((mode == MODE_VEC_ADD ? 16 : 8) + (rowscale ? 8 : 0));
+    }
+    P.piece_alg.push_back(alg);
+  }
+  if ((int64_t)P.fan_src.size() > fan0)   // the slots of this launch are filled right before it
+    add_launch(P, Launch::FANOUT, fan0, (int64_t)P.fan_src.size() - fan0);
+  // per launch shape: warp ranges, range flags, shared chunks
+  std::vector<int64_t> pb(pw.size());
+  for (size_t i = 0; i < pw.size(); ++i) pb[i] = pw[i].bytes + 8 * pw[i].ncols;
+  int64_t nfix = 0;
+  for (int cf = 0; cf < NCFG; ++cf) {
+    L.woff[cf] = (int64_t)P.wbeg.size();
+    if (pw.empty()) {
+      L.nw[cf] = 0;
+      continue;
+    }
+    L.nw[cf] = partition(pb, L.off, cx.nsm * RS_CFG_WARPS[cf], P.wbeg);
+    std::vector<PieceCopy> d = base;
+    std::vector<int32_t> nparts(cw.size(), 0), partof(pw.size(), 0);
+    const int32_t* wb = P.wbeg.data() + L.woff[cf];
+    for (int w = 0; w < L.nw[cf]; ++w) {
+      const int64_t a = wb[w] - L.off, b = wb[w + 1] - L.off;
+      for (int64_t i = a; i < b; ++i) {
+        const int32_t ch = pw[i].chunk;
+        const bool first = (i == a) || pw[i - 1].chunk != ch;
+        const bool last = (i == b - 1) || pw[i + 1].chunk != ch;
+        if (first) {
+          d[i].bytes_flags |= PD_FIRST << 16;
+          partof[i] = nparts[ch]++;
+        } else {
+          partof[i] = partof[i - 1];
+        }
+        if (last) d[i].bytes_flags |= PD_LAST << 16;
+      }
+    }
+    std::vector<int32_t> splitof(cw.size(), -1);
+    int64_t fix = 0;
+    for (size_t ch = 0; ch < cw.size(); ++ch)
+      if (nparts[ch] > 1) {
+        splitof[ch] = (int32_t)P.splits.size();
+        P.splits.push_back(Split{(int32_t)fix, nparts[ch]});
+        fix += nparts[ch];
+      }
+    nfix = std::max(nfix, fix);
+    for (size_t i = 0; i < pw.size(); ++i)
+      if (splitof[pw[i].chunk] >= 0) {
+        d[i].bytes_flags |= PD_SPLIT << 16;
+        d[i].split_part = (splitof[pw[i].chunk] << 8) | partof[i];
+      }
+    P.pdesc[cf].insert(P.pdesc[cf].end(), d.begin(), d.end());
+  }
+  P.nfix = std::max(P.nfix, nfix);
+  P.npieces += (int64_t)pw.size();
+  P.nchunks += (int64_t)cw.size();
   P.launches.push_back(L);
 }
 
@@ -262,7 +501,7 @@ std::vector<int> ancestors_root_first(const ClusterTree& ct, int c) {
 
 // Dense blocks: direct compression, one uniform tile per leaf of the row cluster.
 // dt[b][i] = tile for the i-th leaf under the block's row cluster.
-bool pack_dense(Ctx& cx, const std::vector<std::vector<int>>& lv, std::vector<std::vector<Tile>>& dt) {
+bool pack_dense(Ctx& cx, const std::vector<std::vector<int>>& lv, std::vector<std::vector<const TileData*>>& dt) {
   const HostMatrix& H = cx.H;
   const auto& ct = H.ct;
   const int64_t nb = (int64_t)H.blocks.size();
@@ -282,7 +521,7 @@ bool pack_dense(Ctx& cx, const std::vector<std::vector<int>>& lv, std::vector<st
     const Cluster& t = ct.cl[H.blocks[b].row];
     const Cluster& s = ct.cl[H.blocks[b].col];
     for (int l : lv[H.blocks[b].row])
-      dt[b].push_back(pack_tile(cx.P, cs[b], ct.cl[l].start - t.start, ct.cl[l].end - t.start, (int32_t)s.start, 1));
+      dt[b].push_back(pack_tile(cx, cs[b], ct.cl[l].start - t.start, ct.cl[l].end - t.start, (int32_t)s.start, 1));
     cx.P.fp64_dense += (int64_t)H.dn[H.slot[b]].D.size() * 8;
     cs[b] = ColSet();
   }
@@ -297,7 +536,8 @@ size_t leaf_index(const ClusterTree& ct, const std::vector<int>& leaves, int c) 
 
 // Leaf chunks producing y: merged VALR columns from `rowcols(c, out)` and the
 // dense tiles of c's ancestors' block rows (root first, as Alg. 3).
-void leaf_chunks(Ctx& cx, const std::vector<std::vector<int>>& lv, const std::vector<std::vector<Tile>>& dt,
+void leaf_chunks(Ctx& cx, const std::vector<std::vector<int>>& lv,
+                 const std::vector<std::vector<const TileData*>>& dt,
                  const std::function<void(int, std::vector<ColRef>&)>& rowcols) {
   const HostMatrix& H = cx.H;
   const auto& ct = H.ct;
@@ -307,31 +547,14 @@ void leaf_chunks(Ctx& cx, const std::vector<std::vector<int>>& lv, const std::ve
   std::vector<ChunkWork> cw;
   for (int c : lv[0]) {
     ChunkWork w;
-    w.c.row0 = (int32_t)ct.cl[c].start;
-    w.c.nrows = (int32_t)ct.cl[c].size();
+    w.row0 = (int32_t)ct.cl[c].start;
+    w.nrows = (int32_t)ct.cl[c].size();
     rowcols(c, w.cols);
     for (int a : ancestors_root_first(ct, c))
       for (int b : rowdense[a]) w.t.push_back(dt[b][leaf_index(ct, lv[a], c)]);
     cw.push_back(std::move(w));
   }
   add_rgemv(cx, cw, MODE_Y, false);
-}
-
-void gsum_outputs(Program& P, int64_t out0, const std::vector<std::vector<int32_t>>& segp,
-                  const std::vector<double>& scale, int flags) {
-  for (size_t j = 0; j < segp.size(); ++j) {
-    GsumOut o{};
-    o.out = (int32_t)(out0 + (int64_t)j);
-    o.p0 = (int32_t)P.plist.size();
-    for (int32_t p : segp[j]) {
-      P.plist.push_back(p);
-      P.pscale.push_back(split_ff(1.0));
-    }
-    o.p1 = (int32_t)P.plist.size();
-    o.flags = flags;
-    o.scale = split_ff(scale[j]);
-    P.gouts.push_back(o);
-  }
 }
 
 // ---------------------------------------------------------------- H (Alg. 1 / 3)
@@ -341,7 +564,7 @@ bool program_h(Ctx& cx) {
   const auto& ct = H.ct;
   const int64_t N = H.n;
   const auto lv = leaves_under(ct);
-  std::vector<std::vector<Tile>> dt;
+  std::vector<std::vector<const TileData*>> dt;
   if (!pack_dense(cx, lv, dt)) return false;
   const int64_t nb = (int64_t)H.blocks.size();
   std::vector<ColSet> csx(nb), csw(nb);
@@ -357,25 +580,40 @@ bool program_h(Ctx& cx) {
   }
   if (!ok) return false;
   add_launch(P, Launch::GATHER, 0, N);
+  // t_b = alpha * sigma_b * (X_b^T x|sigma): coefficient vectors after x; the
+  // column dots of all blocks of one block column share the input segment
   std::vector<int64_t> toff(nb, -1);
   int64_t vec = N, pbase = 0;
-  const int64_t i0 = (int64_t)P.items.size(), g0 = (int64_t)P.gouts.size();
+  std::vector<std::vector<int>> collr(ct.cl.size());
   for (int64_t b = 0; b < nb; ++b) {
     if (!H.blocks[b].adm) continue;
     const auto& L = H.lr[H.slot[b]];
     if (L.k == 0) continue;
-    const Cluster& t = ct.cl[H.blocks[b].row];
-    const Cluster& s = ct.cl[H.blocks[b].col];
-    P.fp64_lowrank += (t.size() + s.size()) * L.k * 8;
-    std::vector<std::vector<int32_t>> segp;
-    std::vector<double> sc(L.k);
-    for (int j = 0; j < L.k; ++j) sc[j] = L.s[j] * csx[b].scale(j) * csw[b].scale(j);
-    bool fin = false;
-    pack_cdot(P, csx[b], (int32_t)s.start, pbase, segp, true, vec, &sc, true, fin);
-    if (!fin) gsum_outputs(P, vec, segp, sc, 1);
+    P.fp64_lowrank += (ct.cl[H.blocks[b].row].size() + ct.cl[H.blocks[b].col].size()) * L.k * 8;
     toff[b] = vec;
     vec += L.k;
-    csx[b] = ColSet();
+    collr[H.blocks[b].col].push_back((int)b);
+  }
+  const int64_t i0 = (int64_t)P.items.size(), g0 = (int64_t)P.gouts.size();
+  for (size_t sg = 0; sg < ct.cl.size(); ++sg) {
+    if (collr[sg].empty()) continue;
+    std::vector<CdotCol> cols;
+    for (int b : collr[sg]) {
+      const auto& L = H.lr[H.slot[b]];
+      for (int j = 0; j < L.k; ++j)
+        cols.push_back(CdotCol{&csx[b], j, toff[b] + j, L.s[j] * csx[b].scale(j) * csw[b].scale(j)});
+    }
+    const int64_t ns = nseg_of(ct.cl[sg].size());
+    std::vector<int64_t> pout(cols.size());
+    for (size_t c = 0; c < cols.size(); ++c) pout[c] = pbase + (int64_t)c * ns;
+    bool fin = false;
+    pack_cdot(P, cols, ct.cl[sg].size(), (int32_t)ct.cl[sg].start, true, true, pout, fin);
+    if (!fin) {
+      for (size_t c = 0; c < cols.size(); ++c)
+        gsum_one(P, cols[c].out_final, pout[c], pout[c] + ns, {}, cols[c].scale_final, 1);
+      pbase += (int64_t)cols.size() * ns;
+    }
+    for (int b : collr[sg]) csx[b] = ColSet();
   }
   P.npartial = std::max(P.npartial, pbase);
   add_launch(P, Launch::CDOT, i0, (int64_t)P.items.size() - i0);
@@ -423,15 +661,15 @@ bool coupling_chunks(Ctx& cx, const std::vector<int64_t>& soff, const std::vecto
       if (H.colb.k[s] == 0) continue;
       for (int i = 0; i < nsplit; ++i) {
         const int64_t r0 = (int64_t)i * CHUNK_ROWS, r1 = std::min<int64_t>(kt, r0 + CHUNK_ROWS);
-        per[i].t.push_back(pack_tile(cx.P, enc[b], r0, r1, (int32_t)soff[s], 0));
+        per[i].t.push_back(pack_tile(cx, enc[b], r0, r1, (int32_t)soff[s], 0));
       }
       cx.P.fp64_lowrank += (int64_t)enc[b].m * enc[b].n * 8;
       enc[b] = ColSet();
     }
     for (int i = 0; i < nsplit; ++i) {
-      per[i].c.row0 = (int32_t)(toff[t] + (int64_t)i * CHUNK_ROWS);
-      per[i].c.nrows = std::min(CHUNK_ROWS, kt - i * CHUNK_ROWS);
-      per[i].c.flags = flags;
+      per[i].row0 = (int32_t)(toff[t] + (int64_t)i * CHUNK_ROWS);
+      per[i].nrows = std::min(CHUNK_ROWS, kt - i * CHUNK_ROWS);
+      per[i].flags = flags;
       cw.push_back(std::move(per[i]));
     }
   }
@@ -454,12 +692,17 @@ bool forward_bases(Ctx& cx, const std::vector<int>& which, const std::vector<int
   for (int c : which) {
     const int k = H.colb.k[c];
     cx.P.fp64_lowrank += ct.cl[c].size() * k * 8;
-    std::vector<std::vector<int32_t>> segp;
-    std::vector<double> sc(k);
-    for (int j = 0; j < k; ++j) sc[j] = enc[c].scale(j);
+    std::vector<CdotCol> cols;
+    for (int j = 0; j < k; ++j) cols.push_back(CdotCol{&enc[c], j, soff[c] + j, enc[c].scale(j)});
+    const int64_t ns = nseg_of(ct.cl[c].size());
+    std::vector<int64_t> pout(k);
+    for (int j = 0; j < k; ++j) pout[j] = pbase + (int64_t)j * ns;
     bool fin = false;
-    pack_cdot(cx.P, enc[c], (int32_t)ct.cl[c].start, pbase, segp, true, soff[c], &sc, false, fin);
-    if (!fin) gsum_outputs(cx.P, soff[c], segp, sc, 0);
+    pack_cdot(cx.P, cols, ct.cl[c].size(), (int32_t)ct.cl[c].start, true, false, pout, fin);
+    if (!fin) {
+      for (int j = 0; j < k; ++j) gsum_one(cx.P, soff[c] + j, pout[j], pout[j] + ns, {}, enc[c].scale(j), 0);
+      pbase += (int64_t)k * ns;
+    }
     enc[c] = ColSet();
   }
   return true;
@@ -493,7 +736,7 @@ bool program_uh(Ctx& cx) {
   const int64_t N = H.n;
   const int nc = (int)ct.cl.size();
   const auto lv = leaves_under(ct);
-  std::vector<std::vector<Tile>> dt;
+  std::vector<std::vector<const TileData*>> dt;
   if (!pack_dense(cx, lv, dt)) return false;
   std::vector<int64_t> soff(nc, -1), toff(nc, -1);
   int64_t vec = N;
@@ -544,7 +787,7 @@ bool program_h2(Ctx& cx) {
   for (int c = 0; c < nc; ++c)
     if (H.rowb.k[c] > CHUNK_ROWS) return false;      // a down-sweep chunk holds <= 128 coefficients
   const auto lv = leaves_under(ct);
-  std::vector<std::vector<Tile>> dt;
+  std::vector<std::vector<const TileData*>> dt;
   if (!pack_dense(cx, lv, dt)) return false;
   std::vector<int64_t> soff(nc, -1), toff(nc, -1);
   int64_t vec = N;
@@ -599,33 +842,31 @@ bool program_h2(Ctx& cx) {
     int64_t pb = 0;
     for (int c = 0; c < nc; ++c) {
       if (height[c] != h || H.colb.k[c] == 0) continue;
+      // partials of output j: the segments of son 0, then those of son 1
       const int kp = H.colb.k[c];
-      std::vector<std::vector<int32_t>> all(kp);
-      std::vector<std::vector<double>> scl(kp);
+      int64_t ns[2] = {0, 0};
+      for (int i = 0; i < 2; ++i)
+        if (H.colb.k[ct.cl[c].son[i]]) ns[i] = nseg_of(H.colb.k[ct.cl[c].son[i]]);
+      const int64_t per = ns[0] + ns[1];
       for (int i = 0; i < 2; ++i) {
         const int sc = ct.cl[c].son[i];
-        if (H.colb.k[sc] == 0) continue;
-        std::vector<std::vector<int32_t>> segp;
+        if (ns[i] == 0) continue;
+        std::vector<CdotCol> cols;
+        std::vector<int64_t> pout(kp);
+        for (int j = 0; j < kp; ++j) {
+          cols.push_back(CdotCol{&ex[sc], j, 0, 1.0});
+          pout[j] = pb + (int64_t)j * per + (i ? ns[0] : 0);
+        }
         bool fin = false;
-        pack_cdot(P, ex[sc], (int32_t)soff[sc], pb, segp, false, 0, nullptr, false, fin);
-        for (int j = 0; j < kp; ++j)
-          for (int32_t q : segp[j]) {
-            all[j].push_back(q);
-            scl[j].push_back(ex[sc].scale(0));
-          }
+        pack_cdot(P, cols, H.colb.k[sc], (int32_t)soff[sc], false, false, pout, fin);
       }
       for (int j = 0; j < kp; ++j) {
-        GsumOut o{};
-        o.out = (int32_t)(soff[c] + j);
-        o.p0 = (int32_t)P.plist.size();
-        for (size_t q = 0; q < all[j].size(); ++q) {
-          P.plist.push_back(all[j][q]);
-          P.pscale.push_back(split_ff(scl[j][q]));
-        }
-        o.p1 = (int32_t)P.plist.size();
-        o.scale = split_ff(1.0);
-        P.gouts.push_back(o);
+        std::vector<double> w;
+        for (int i = 0; i < 2; ++i)
+          for (int64_t t = 0; t < ns[i]; ++t) w.push_back(ex[ct.cl[c].son[i]].scale(0));
+        gsum_one(P, soff[c] + j, pb + (int64_t)j * per, pb + (int64_t)(j + 1) * per, w, 1.0, 0);
       }
+      pb += (int64_t)kp * per;
     }
     P.npartial = std::max(P.npartial, pb);
     add_launch(P, Launch::CDOT, i0, (int64_t)P.items.size() - i0);
@@ -644,10 +885,10 @@ bool program_h2(Ctx& cx) {
       if (ct.cl[c].level != lev || H.rowb.k[c] == 0) continue;
       const int p = ct.cl[c].parent;
       ChunkWork w;
-      w.c.row0 = (int32_t)toff[c];
-      w.c.nrows = H.rowb.k[c];
-      w.c.flags = ct.cl[c].leaf() ? 1 : 0;
-      if (H.rowb.k[p] > 0) w.t.push_back(pack_tile(P, ew[c], 0, H.rowb.k[c], (int32_t)toff[p], 0));
+      w.row0 = (int32_t)toff[c];
+      w.nrows = H.rowb.k[c];
+      w.flags = ct.cl[c].leaf() ? 1 : 0;
+      if (H.rowb.k[p] > 0) w.t.push_back(pack_tile(cx, ew[c], 0, H.rowb.k[c], (int32_t)toff[p], 0));
       dw.push_back(std::move(w));
     }
     if (!dw.empty()) add_rgemv(cx, dw, MODE_VEC_ADD, true);
@@ -660,43 +901,40 @@ bool program_h2(Ctx& cx) {
   return true;
 }
 
-// Algorithmic bytes of every launch: packed values (no padding), format
-// words, descriptors, vector reads and writes.
-void launch_bytes(Program& P) {
+// Algorithmic bytes of every launch (packed values without padding, inline
+// metadata, descriptors, vector reads and writes) and the warp ranges of the
+// column-dot launches.
+void finish_launches(Ctx& cx) {
+  Program& P = cx.P;
   for (Launch& L : P.launches) {
     int64_t b = 0;
     switch (L.kind) {
       case Launch::GATHER:
         b = L.n * (4 + 8 + 8);
         break;
-      case Launch::CDOT:
-        for (int64_t i = L.off; i < L.off + L.n; ++i) {
-          const Item& t = P.items[i];
-          for (int j = 0; j < t.ncols; ++j) b += (int64_t)t.nrows * (P.pk.fmts[t.fmt + j] & 0xff);
-          b += 4 * (int64_t)t.ncols + (int64_t)sizeof(Item) + 8 * (int64_t)t.nrows + 8 * (int64_t)t.ncols;
+      case Launch::CDOT: {
+        std::vector<int64_t> ib((size_t)L.n);
+        for (int64_t i = 0; i < L.n; ++i) {
+          ib[i] = P.items[L.off + i].bytes;
+          b += P.item_alg[L.off + i];
+        }
+        for (int cf = 0; cf < NCFG; ++cf) {
+          L.woff[cf] = (int64_t)P.wbeg.size();
+          L.nw[cf] = L.n > 0 ? partition(ib, L.off, cx.nsm * CS_CFG_WARPS[cf], P.wbeg) : 0;
         }
         break;
+      }
       case Launch::GSUM:
         for (int64_t i = L.off; i < L.off + L.n; ++i) {
           const GsumOut& o = P.gouts[i];
-          b += (int64_t)(o.p1 - o.p0) * (4 + 8 + 8) + (int64_t)sizeof(GsumOut) + 8;
+          b += (int64_t)(o.p1 - o.p0) * ((o.flags & 2) ? 16 : 8) + (int64_t)sizeof(GsumOut) + 8;
         }
         break;
       case Launch::RGEMV:
-        for (int64_t i = L.off; i < L.off + L.n; ++i) {
-          const Chunk& c = P.chunks[i];
-          b += (int64_t)sizeof(Chunk);
-          for (int32_t k = c.t0; k < c.t1; ++k) {
-            const Tile& t = P.tiles[k];
-            b += (int64_t)sizeof(Tile) + (int64_t)c.nrows * (t.fw & 0xff) * t.ncols + 8 * (int64_t)t.ncols;
-          }
-          for (int32_t k = c.c0; k < c.c1; ++k)
-            b += (int64_t)sizeof(ColMeta) + (int64_t)c.nrows * (P.cols[k].fw & 0xff) + 8;
-          if (L.mode == MODE_Y)
-            b += (int64_t)c.nrows * (4 + 8 + 8);
-          else
-            b += (int64_t)c.nrows * ((L.mode == MODE_VEC_ADD ? 16 : 8) + (L.use_rowscale ? 8 : 0));
-        }
+        for (int64_t i = L.off; i < L.off + L.n; ++i) b += P.piece_alg[i];
+        break;
+      case Launch::FANOUT:
+        b = L.n * (4 + 8 + 8);
         break;
     }
     L.bytes = b;
@@ -706,24 +944,36 @@ void launch_bytes(Program& P) {
 }  // namespace
 
 bool build_program(const HostMatrix& H, int codec, double eps, int valr, int nsm, Program& P) {
-  (void)nsm;
   P = Program();
   P.tier = (codec == HM_CODEC_NONE || eps <= 0x1p-22) ? TIER_FF : TIER_F32;
-  Ctx cx{H, P, codec, eps, valr ? 1 : 0, m_eps(eps)};
+  Ctx cx{H, P, codec, eps, valr ? 1 : 0, m_eps(eps), std::max(1, nsm), {}};
   bool ok;
   switch (H.prm.format) {
     case HM_FMT_H: ok = program_h(cx); break;
     case HM_FMT_UH: ok = program_uh(cx); break;
     default: ok = program_h2(cx); break;
   }
+  cx.tiles.clear();
+  if (ok && P.pk.pay.size() >= (1ull << 35)) ok = false;   // copy descriptors hold offset / 8 in 32 bits
   if (!ok) {
     P = Program();
     return false;
   }
-  P.pk.align8();
-  P.pk.pay.resize(P.pk.pay.size() + 128, 0);   // tail reads of the last column stay in bounds
+  P.pk.align(16);
+  P.pk.pay.resize(P.pk.pay.size() + 256, 0);   // 16-byte rounded copies and lane over-reads stay in bounds
+  // fan-out slots follow every other vector entry
+  P.fan_base = P.nvec;
+  P.nvec += (int64_t)P.fan_src.size();
+  for (int cf = 0; cf < NCFG; ++cf)
+    for (PieceCopy& d : P.pdesc[cf])
+      if (d.moff < 0) d.moff = (int32_t)(P.fan_base + (-1 - (int64_t)d.moff));
+  if (P.rowscale.size() > 1) P.rowscale.resize(P.nvec, 1.0);
   if (P.rowscale.empty()) P.rowscale.assign(1, 1.0);
-  launch_bytes(P);
+  if (P.nvec >= INT32_MAX) {
+    P = Program();
+    return false;
+  }
+  finish_launches(cx);
   return true;
 }
 

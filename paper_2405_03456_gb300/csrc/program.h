@@ -15,18 +15,17 @@ inline F2 split_ff(double v) {
 }
 
 struct Packer {
-  std::vector<uint8_t> pay;       // packed codes, every column 8-byte aligned
-  std::vector<uint32_t> fmts;     // format words
-  std::vector<F2> cscale;         // output scale of column-dot columns (parallel to fmts)
+  std::vector<uint8_t> pay;       // packed stream: items and pieces, each 16-byte aligned
   int64_t value_bytes = 0;        // sum of n * B over all packed columns (no padding)
+  int64_t meta_bytes = 0;         // inline headers, format lists, scales, column metadata
 
-  uint64_t align8() {
-    while (pay.size() & 7) pay.push_back(0);
+  uint64_t align(int a) {
+    while (pay.size() & (uint64_t)(a - 1)) pay.push_back(0);
     return pay.size();
   }
-  // append n codes of B bytes (little-endian); returns the 8-byte aligned offset
+  // append n codes of B bytes (little-endian) at the next 8-byte boundary; returns the offset
   uint64_t put(const uint64_t* codes, int64_t n, int B) {
-    uint64_t off = align8();
+    uint64_t off = align(8);
     pay.resize(off + (uint64_t)(n * B));
     uint8_t* dst = pay.data() + off;
     for (int64_t i = 0; i < n; ++i) {
@@ -34,35 +33,67 @@ struct Packer {
       for (int b = 0; b < B; ++b) dst[i * B + b] = (uint8_t)(c >> (8 * b));
     }
     value_bytes += n * B;
-    align8();
+    align(8);
+    return off;
+  }
+  // append R codes of B bytes plus R8 - R zero codes (rows padded to R8)
+  uint64_t put_rows(const uint64_t* codes, int64_t R, int64_t R8, int B) {
+    uint64_t off = align(8);
+    pay.resize(off + (uint64_t)(R8 * B), 0);
+    uint8_t* dst = pay.data() + off;
+    for (int64_t i = 0; i < R; ++i) {
+      const uint64_t c = codes[i];
+      for (int b = 0; b < B; ++b) dst[i * B + b] = (uint8_t)(c >> (8 * b));
+    }
+    value_bytes += R * B;
+    align(8);
+    return off;
+  }
+  // append raw bytes (metadata) at the next 8-byte boundary
+  uint64_t raw(const void* p, size_t n) {
+    uint64_t off = align(8);
+    const uint8_t* s = static_cast<const uint8_t*>(p);
+    pay.insert(pay.end(), s, s + n);
+    meta_bytes += (int64_t)n;
     return off;
   }
 };
 
 struct Launch {
-  enum Kind { GATHER = 0, CDOT = 1, GSUM = 2, RGEMV = 3 } kind = GATHER;
+  enum Kind { GATHER = 0, CDOT = 1, GSUM = 2, RGEMV = 3, FANOUT = 4 } kind = GATHER;
   int mode = 0;                   // RGEMV output mode
-  int64_t off = 0, n = 0;         // range of items / outputs
+  int64_t off = 0, n = 0;         // range of items / outputs / pieces / fan-out slots
   bool use_rowscale = false;
   int64_t bytes = 0;              // algorithmic bytes moved by the launch
+  int64_t woff[NCFG] = {};        // CDOT / RGEMV, per launch shape: warp ranges wbeg[woff .. woff + nw]
+  int nw[NCFG] = {};              // warps of the launch per launch shape
+  int cfg = 0;                    // launch shape in use (autotuner choice)
 };
 
 struct Program {
   int tier = TIER_F32;
   std::vector<Launch> launches;
-  std::vector<Item> items;        // column-dot items
+  std::vector<ItemCopy> items;    // column-dot items (copy descriptors)
+  std::vector<int64_t> item_alg;  // algorithmic bytes of each item
   std::vector<GsumOut> gouts;
-  std::vector<int32_t> plist;
-  std::vector<F2> pscale;
-  std::vector<Tile> tiles;        // uniform row-chunk tiles
-  std::vector<ColMeta> cols;      // merged row-chunk columns
-  std::vector<Chunk> chunks;
+  std::vector<F2> pscale;         // per-partial weights of the outputs that use them
+  std::vector<PieceCopy> pdesc[NCFG];  // row-chunk piece descriptors, one list per launch shape
+  int64_t npieces = 0;
+  std::vector<int64_t> piece_alg; // algorithmic bytes of each piece
+  std::vector<int32_t> wbeg;      // per launch and shape: nw + 1 range starts (item / piece indices)
+  std::vector<Split> splits;      // chunks shared by several warps (all launch shapes)
+  int64_t nfix = 0;               // fix-up slots (CHUNK_ROWS float-float rows each), largest shape
+  int64_t nchunks = 0;
+  std::vector<int32_t> fan_src;   // fan-out: slot s takes v[fan_src[s]]; slot s is v[fan_base + s]
+  int64_t fan_base = 0;
   std::vector<double> rowscale;   // per vector entry (1 where unused)
   int64_t nvec = 0;               // float2 vector workspace entries (x first)
   int64_t npartial = 0;           // partials of the largest column-dot launch
   Packer pk;
   int64_t fp64_lowrank = 0, fp64_dense = 0;
 };
+
+constexpr int64_t MIN_WARP_BYTES = 16384;   // smallest share of a launch worth a warp
 
 // Pack a built matrix with `codec` at accuracy eps (VALR if valr) and build its
 // launch program for a GPU with nsm multiprocessors.  Returns false if a value

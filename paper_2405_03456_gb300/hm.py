@@ -24,9 +24,11 @@ KERNELS = {"laplace": HM_KERNEL_LAPLACE, "matern": HM_KERNEL_MATERN15}
 
 DECLARED = ["hm_build", "hm_compress", "hm_matvec", "hm_matvec_host", "hm_free", "hm_info",
             "hm_status_str", "hm_sync_status", "hm_structure", "hm_codec_encode", "hm_codec_decode",
-            "hm_profile", "hm_profile_read", "hm_alg_bytes", "hm_matvec_host_noalloc", "hm_graph"]
+            "hm_profile", "hm_profile_read", "hm_alg_bytes", "hm_matvec_host_noalloc", "hm_graph",
+            "hm_autotune", "hm_launch_shapes", "hm_set_launch_shapes"]
+NSHAPES = 3
 HM_NOALLOC_MAX_ENTRIES = 1 << 20
-KERNEL_KINDS = ["gather", "cdot", "gsum", "rgemv"]
+KERNEL_KINDS = ["gather", "cdot", "gsum", "rgemv", "fanout"]
 
 
 class hm_build_params(C.Structure):
@@ -92,6 +94,9 @@ def load(path: str | None = None) -> C.CDLL:
         "hm_alg_bytes": ([vp, C.POINTER(i64)], i32),
         "hm_matvec_host_noalloc": ([vp, dbl, vp, dbl, vp, i64, vp], i32),
         "hm_graph": ([vp, i32], i32),
+        "hm_autotune": ([vp, i32, vp], i32),
+        "hm_launch_shapes": ([vp, vp, i32, C.POINTER(i32)], i32),
+        "hm_set_launch_shapes": ([vp, i32], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -192,15 +197,32 @@ def hm_graph(h: int, enable: bool) -> None:
     check(load().hm_graph(h, 1 if enable else 0), "hm_graph")
 
 
+def hm_autotune(h: int, reps: int = 5, stream: int = 0) -> None:
+    check(load().hm_autotune(h, reps, stream), "hm_autotune")
+
+
+def hm_launch_shapes(h: int) -> list:
+    cnt = C.c_int32()
+    check(load().hm_launch_shapes(h, None, 0, C.byref(cnt)), "hm_launch_shapes")
+    out = np.zeros(max(cnt.value, 1), dtype=np.int32)
+    check(load().hm_launch_shapes(h, _ptr(out), cnt.value, C.byref(cnt)), "hm_launch_shapes")
+    return [int(v) for v in out[: cnt.value]]
+
+
+def hm_set_launch_shapes(h: int, shape: int) -> None:
+    check(load().hm_set_launch_shapes(h, shape), "hm_set_launch_shapes")
+
+
 def hm_profile(h: int, enable: bool) -> None:
     check(load().hm_profile(h, 1 if enable else 0), "hm_profile")
 
 
 def hm_profile_read(h: int) -> dict:
-    arr = (hm_kernel_stat * 4)()
-    check(load().hm_profile_read(h, arr, 4), "hm_profile_read")
+    nk = len(KERNEL_KINDS)
+    arr = (hm_kernel_stat * nk)()
+    check(load().hm_profile_read(h, arr, nk), "hm_profile_read")
     return {KERNEL_KINDS[i]: {"ms": arr[i].ms, "launches": arr[i].launches, "bytes": arr[i].bytes}
-            for i in range(4)}
+            for i in range(nk)}
 
 
 def hm_alg_bytes(h: int) -> int:
@@ -248,6 +270,17 @@ class HMatrix:
 
     def graph(self, enable=True):
         hm_graph(self.h, enable)
+        return self
+
+    def autotune(self, reps=5, stream=0):
+        hm_autotune(self.h, reps, stream)
+        return self
+
+    def launch_shapes(self):
+        return hm_launch_shapes(self.h)
+
+    def set_launch_shapes(self, shape):
+        hm_set_launch_shapes(self.h, shape)
         return self
 
     def profile(self, enable=True):

@@ -189,6 +189,40 @@ def test_graph_replay_bitwise(hm, problem, fmt):
         M.close()
 
 
+@pytest.mark.parametrize("fmt", ["h", "uh", "h2"])
+def test_launch_shapes_and_autotune(hm, problem, fmt):
+    """Every launch shape (warps x stages per warp, with its own split of the
+    work into warp ranges) gives a product within 4 eps of the oracle and is
+    bitwise reproducible; the autotuner keeps one of them per launch."""
+    pts, x, y0 = problem
+    eps = 1e-6
+    ref = oracle_ref(pts, fmt, eps, x[:, 0], 1.0, y0[:, 0], 1.0)
+    M = hm.HMatrix(pts, "laplace", 32, 2.0, fmt, eps)
+    try:
+        M.compress(eps, "aflp")
+        xd = torch.from_numpy(x[:, 0].copy()).cuda()
+        for shape in range(hm.NSHAPES):
+            M.set_launch_shapes(shape)
+            outs = []
+            for _ in range(3):
+                yd = torch.from_numpy(y0[:, 0].copy()).cuda()
+                M.matvec(1.0, xd, 1.0, yd)
+                outs.append(yd.cpu().numpy())
+            assert rel(outs[0], ref) <= 4 * eps
+            for o in outs[1:]:
+                assert np.array_equal(o.view(np.uint64), outs[0].view(np.uint64))
+        M.autotune(2)
+        shapes = M.launch_shapes()
+        assert len(shapes) == M.info()["nlaunches"]
+        assert all(s in (-1, 0, 1, 2) for s in shapes) and any(s >= 0 for s in shapes)
+        yd = torch.from_numpy(y0[:, 0].copy()).cuda()
+        M.matvec(1.0, xd, 1.0, yd)
+        assert rel(yd.cpu().numpy(), ref) <= 4 * eps
+        assert M.sync_status() == 0
+    finally:
+        M.close()
+
+
 def test_matern_cube(hm):
     pts = synth.cube_points(3000)
     x = synth.rhs(3000)[:, 0]
