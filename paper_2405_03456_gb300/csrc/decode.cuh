@@ -239,6 +239,78 @@ __device__ __forceinline__ void decode8s(uint32_t a, int e, int m, float (&h)[8]
   }
 }
 
+// ---------------------------------------------------------------- FP32-tier paired decode
+// Blackwell issues two FP32 operations per instruction on register pairs
+// (__fadd2_rn / __ffma2_rn); the FP32 tier decodes and accumulates rows in
+// pairs (2k, 2k+1).
+
+// a - b per component, one rounding (FFMA2 with a -1 multiplier).
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a); }
+
+// two_sum on pairs: (s, e) with s + e = a + b exactly, per component (Knuth).
+__device__ __forceinline__ void two_sum2(float2 a, float2 b, float2& s, float2& e) {
+  s = __fadd2_rn(a, b);
+  const float2 bp = sub2(s, a);
+  e = __fadd2_rn(sub2(a, sub2(s, bp)), sub2(b, bp));
+}
+
+// (hi, lo) += s per component (float-float accumulation of FP32 partial sums).
+__device__ __forceinline__ void ff_add_f2(float2& hi, float2& lo, float2 s) {
+  float2 t, e;
+  two_sum2(hi, s, t, e);
+  e = __fadd2_rn(e, lo);
+  const float2 h = __fadd2_rn(t, e);
+  lo = sub2(e, sub2(h, t));
+  hi = h;
+}
+
+// 8 consecutive codes of format (F, B) at shared address a -> 4 FP32 pairs
+// (FP32 tier: AFLP as +-(s - 1), FPX e8 exactly, e11 / raw truncated to FP32).
+template <int F, int B>
+__device__ __forceinline__ void decode8p(uint32_t a, int e, int m, float2 (&h2)[4]) {
+  uint32_t w[2 * B];
+#pragma unroll
+  for (int i = 0; i < B; ++i) {
+    const uint2 t = lds64(a + 8u * i);
+    w[2 * i] = t.x;
+    w[2 * i + 1] = t.y;
+  }
+  uint32_t w0[B], w1[B];
+#pragma unroll
+  for (int i = 0; i < B; ++i) {
+    w0[i] = w[i];
+    w1[i] = w[B + i];
+  }
+  if constexpr (F == 2 && B <= 4) {
+    constexpr uint32_t mask = (0xffffffffu << (8 * (4 - B))) & 0x7fffffffu;
+    const int sh = 8 - e;
+    const uint32_t t[8] = {top32<B, 0>(w0), top32<B, 1>(w0), top32<B, 2>(w0), top32<B, 3>(w0),
+                           top32<B, 0>(w1), top32<B, 1>(w1), top32<B, 2>(w1), top32<B, 3>(w1)};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const float2 sv = make_float2(__uint_as_float(((t[2 * k] & mask) >> sh) + (127u << 23)),
+                                    __uint_as_float(((t[2 * k + 1] & mask) >> sh) + (127u << 23)));
+      const float2 d = __fadd2_rn(sv, make_float2(-1.0f, -1.0f));
+      h2[k] = make_float2(__uint_as_float(__float_as_uint(d.x) ^ (t[2 * k] & 0x80000000u)),
+                          __uint_as_float(__float_as_uint(d.y) ^ (t[2 * k + 1] & 0x80000000u)));
+    }
+  } else if constexpr (F == 0) {
+    constexpr uint32_t mask = 0xffffffffu << (8 * (4 - B));
+    h2[0] = make_float2(__uint_as_float(top32<B, 0>(w0) & mask), __uint_as_float(top32<B, 1>(w0) & mask));
+    h2[1] = make_float2(__uint_as_float(top32<B, 2>(w0) & mask), __uint_as_float(top32<B, 3>(w0) & mask));
+    h2[2] = make_float2(__uint_as_float(top32<B, 0>(w1) & mask), __uint_as_float(top32<B, 1>(w1) & mask));
+    h2[3] = make_float2(__uint_as_float(top32<B, 2>(w1) & mask), __uint_as_float(top32<B, 3>(w1) & mask));
+  } else {
+    float h0[4], l0[4], h1[4], l1[4];
+    decode4<TIER_F32, F, B>(w0, e, m, h0, l0);
+    decode4<TIER_F32, F, B>(w1, e, m, h1, l1);
+    h2[0] = make_float2(h0[0], h0[1]);
+    h2[1] = make_float2(h0[2], h0[3]);
+    h2[2] = make_float2(h1[0], h1[1]);
+    h2[3] = make_float2(h1[2], h1[3]);
+  }
+}
+
 // The decode classes (F, B) the kernels instantiate.
 #define HM_FORMATS(X) \
   X(0, 2) X(0, 3) X(0, 4) X(1, 5) X(1, 6) X(1, 7) X(1, 8) \

@@ -165,6 +165,77 @@ __device__ __forceinline__ void cs_piece(uint32_t sa, int R, int nc, int flags, 
   }
 }
 
+// FP32-tier column-dot piece: lanes (g, q) = (lane / 8, lane % 8) take rows
+// 8q .. 8q+7 of the columns g, g + 4, ...; two columns per step (independent
+// decodes), products summed in FP32 pairs, the partials rotated down two
+// registers per step so that after 4 steps p[t] holds column g + 4t; a round
+// of 32 columns ends with the reduce-scatter over the 8 lanes.  Steps past the
+// last column are skipped as a whole; a ragged step masks its results.
+template <int F, int B>
+__device__ __forceinline__ void cs_piece_f32(uint32_t sa, int R, int nc, int flags, const float2 (&x2)[4], int lane,
+                                             F2 alpha, F2* __restrict__ partial, float2* __restrict__ vout) {
+  constexpr int NG = 4;
+  const int g = lane >> 3, q = lane & 7;
+  const uint32_t stride = (((uint32_t)R + 15u) & ~15u) * B;
+  const bool fin = (flags & ITEM_FINAL) != 0;
+  const uint32_t cm = sa + (uint32_t)sizeof(CPieceHdr);          // CColMeta[nc]
+  const uint32_t sc = cm + 8u * nc;                                // F2[nc] (final only)
+  const uint32_t cb = cm + (fin ? 16u : 8u) * nc + (uint32_t)(RPL * q * B);
+  const bool rows_on = RPL * q < R;
+  for (int j0 = 0; j0 < nc; j0 += 8 * NG) {
+    float p[8], pc[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      p[t] = 0.f;
+      pc[t] = 0.f;
+    }
+    const int tmax = (nc - j0 + NG - 1) / NG;   // steps holding a column (same for the warp)
+#pragma unroll 1
+    for (int t = 0; t < 8; t += 2) {
+      float r[2] = {0.f, 0.f};
+      if (t < tmax) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int j = j0 + g + NG * (t + h);
+          const bool v = j < nc && rows_on;
+          const int jj = v ? j : 0;
+          int e = 0, m = 0;
+          if constexpr (F == 2) {
+            const uint32_t em = lds32(cm + 8u * jj) & 0xffffu;
+            e = em & 0xff;
+            m = em >> 8;
+          }
+          float2 h2[4];
+          decode8p<F, B>(cb + (uint32_t)jj * stride, e, m, h2);
+          float2 a2 = __fmul2_rn(h2[0], x2[0]);
+          a2 = __ffma2_rn(h2[1], x2[1], a2);
+          a2 = __ffma2_rn(h2[2], x2[2], a2);
+          a2 = __ffma2_rn(h2[3], x2[3], a2);
+          r[h] = v ? a2.x + a2.y : 0.f;
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < 6; ++k) p[k] = p[k + 2];
+      p[6] = r[0];
+      p[7] = r[1];
+    }
+    reduce_scatter8<TIER_F32, 8>(p, pc, q);
+    const int j = j0 + g + NG * q;
+    if (j < nc) {
+      FF v = {p[0], 0.f};
+      const int32_t out = (int32_t)lds32(cm + 8u * j + 4u);
+      if (fin) {
+        const uint2 f = lds64(sc + 8u * j);
+        v = ff_mul(v, FF{__uint_as_float(f.x), __uint_as_float(f.y)});
+        if (flags & ITEM_ALPHA) v = ff_mul(v, FF{alpha.hi, alpha.lo});
+        vout[out] = make_float2(v.hi, v.lo);
+      } else {
+        partial[out] = F2{v.hi, v.lo};
+      }
+    }
+  }
+}
+
 template <int TIER, int NW, int NS>
 __global__ void __launch_bounds__(NW * 32, 1)
     k_cstream(const ItemCopy* __restrict__ cps, const int32_t* __restrict__ wbeg, int nwt,
@@ -248,6 +319,18 @@ __global__ void __launch_bounds__(NW * 32, 1)
       xv = hvin;
       xr = R;
     }
+    if constexpr (TIER == TIER_F32) {
+      const float2 x2[4] = {make_float2(xh[0], xh[1]), make_float2(xh[2], xh[3]), make_float2(xh[4], xh[5]),
+                            make_float2(xh[6], xh[7])};
+      switch (fb) {
+#define HM_CS(FF_, BB_) \
+  case ((FF_) << 4) | (BB_): cs_piece_f32<FF_, BB_>(sa, R, nc, (int)flags, x2, lane, alpha, partial, vout); break;
+        HM_FORMATS(HM_CS)
+#undef HM_CS
+        default:
+          latch_error(err, 1);
+      }
+    } else {
     switch (fb) {
 #define HM_CS(FF_, BB_) \
   case ((FF_) << 4) | (BB_): cs_piece<TIER, FF_, BB_, RL>(sa, R, nc, (int)flags, xh, xl, lane, alpha, partial, vout); break;
@@ -256,77 +339,92 @@ __global__ void __launch_bounds__(NW * 32, 1)
       default:
         latch_error(err, 1);
     }
+    }
     __syncwarp();
     if (issued < n) issue(issued);
   }
 }
 
 // ---------------------------------------------------------------- row chunks (phase C)
-// Sum of the piece's columns into this lane's RL rows: lanes (slot, q) take
-// rows RL q .. RL q + RL-1 of the columns slot, slot + S, ...; FP32 sums (or
-// Dot2 pairs) per piece, folded into the float-float row sums at the end.
-template <int TIER, int F, int B, int RL>
+// Sum of the piece's columns into this lane's 8 rows: lanes (slot, q) take
+// rows 8q .. 8q+7 of the columns slot, slot + S, ...; FP32 sums (or Dot2
+// pairs) per piece, folded into the float-float row sums (row pairs
+// (2k, 2k+1): hi[k], lo[k]) at the end.
+template <int TIER, int F, int B>
 __device__ __forceinline__ void rs_piece(uint32_t sa, const PieceHdr& H, uint32_t tbl, F2 alpha_ff, int lane,
-                                         FF (&acc)[RL]) {
+                                         float2 (&ahi)[4], float2 (&alo)[4]) {
   const int R = H.nrows;
-  const int G = (R + RL - 1) / RL;
+  const int G = (R + RPL - 1) / RPL;
   const int S = 32 / G;
   const int slot = lane / G, q = lane - slot * G;
   const bool tile = (H.flags & PH_TILE) != 0;
   const uint32_t stride = pad8u((uint32_t)R * B);
   const uint32_t cm = sa + (uint32_t)sizeof(PieceHdr);   // merged pieces: uint16 em[ncols]
-  const uint32_t cb = cm + (tile ? 0u : pad8u(2u * H.ncols)) + (uint32_t)(RL * q * B);
+  const uint32_t cb = cm + (tile ? 0u : pad8u(2u * H.ncols)) + (uint32_t)(RPL * q * B);
   const int e_t = H.em & 0xff, m_t = H.em >> 8;
   FF sc = {1.f, 0.f};
   if (tile) {
     sc = FF{H.scale.hi, H.scale.lo};
     if (H.flags & PH_TALPHA) sc = ff_mul(sc, FF{alpha_ff.hi, alpha_ff.lo});
   }
-  float s[RL], c[RL];
-#pragma unroll
-  for (int u = 0; u < RL; ++u) {
-    s[u] = 0.f;
-    c[u] = 0.f;
-  }
   const int nc = slot < S ? H.ncols : 0;
-#pragma unroll(RL == 8 ? 2 : 1)
-  for (int j = slot; j < nc; j += S) {
-    const uint2 vb = lds64(tbl + 8u * j);
-    float vh = __uint_as_float(vb.x), vl = __uint_as_float(vb.y);
-    int e = e_t, m = m_t;
-    if (tile) {
-      if constexpr (TIER == TIER_F32) {
-        vh *= sc.hi;
-      } else {
+  if constexpr (TIER == TIER_F32) {
+    float2 s2[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) s2[k] = make_float2(0.f, 0.f);
+#pragma unroll 2
+    for (int j = slot; j < nc; j += S) {
+      const float vh = __uint_as_float(lds32(tbl + 8u * j)) * sc.hi;
+      int e = e_t, m = m_t;
+      if constexpr (F == 2) {
+        if (!tile) {
+          const uint32_t em = lds32((cm + 2u * j) & ~3u) >> (16u * (j & 1));
+          e = em & 0xff;
+          m = (em >> 8) & 0xff;
+        }
+      }
+      float2 h2[4];
+      decode8p<F, B>(cb + (uint32_t)j * stride, e, m, h2);
+      const float2 v2 = make_float2(vh, vh);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) s2[k] = __ffma2_rn(h2[k], v2, s2[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) ff_add_f2(ahi[k], alo[k], s2[k]);
+  } else {
+    float s[8], c[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      s[u] = 0.f;
+      c[u] = 0.f;
+    }
+#pragma unroll 2
+    for (int j = slot; j < nc; j += S) {
+      const uint2 vb = lds64(tbl + 8u * j);
+      float vh = __uint_as_float(vb.x), vl = __uint_as_float(vb.y);
+      int e = e_t, m = m_t;
+      if (tile) {
         const FF r = ff_mul(FF{vh, vl}, sc);
         vh = r.hi;
         vl = r.lo;
+      } else if constexpr (F == 2) {
+        const uint32_t em = lds32((cm + 2u * j) & ~3u) >> (16u * (j & 1));
+        e = em & 0xff;
+        m = (em >> 8) & 0xff;
       }
-    } else if constexpr (F == 2) {
-      const uint32_t em = lds32((cm + 2u * j) & ~3u) >> (16u * (j & 1));
-      e = em & 0xff;
-      m = (em >> 8) & 0xff;
-    }
-#pragma unroll
-    for (int hb = 0; hb < RL / RPL; ++hb) {
       float h[8], l[8];
-      decode8s<TIER, F, B>(cb + (uint32_t)j * stride + (uint32_t)(hb * RPL * B), e, m, h, l);
+      decode8s<TIER, F, B>(cb + (uint32_t)j * stride, e, m, h, l);
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        if constexpr (TIER == TIER_F32)
-          s[hb * RPL + u] = fmaf(h[u], vh, s[hb * RPL + u]);
-        else
-          dot2(s[hb * RPL + u], c[hb * RPL + u], h[u], l[u], vh, vl);
-      }
+      for (int u = 0; u < 8; ++u) dot2(s[u], c[u], h[u], l[u], vh, vl);
     }
-  }
 #pragma unroll
-  for (int u = 0; u < RL; ++u) {
-    if constexpr (TIER == TIER_F32) {
-      acc[u] = ff_add_f(acc[u], s[u]);
-    } else {
-      const float h = s[u] + c[u];
-      acc[u] = ff_add(acc[u], FF{h, c[u] - (h - s[u])});
+    for (int k = 0; k < 4; ++k) {
+      float hs = s[2 * k] + c[2 * k];
+      FF a = ff_add(FF{ahi[k].x, alo[k].x}, FF{hs, c[2 * k] - (hs - s[2 * k])});
+      hs = s[2 * k + 1] + c[2 * k + 1];
+      FF b = ff_add(FF{ahi[k].y, alo[k].y}, FF{hs, c[2 * k + 1] - (hs - s[2 * k + 1])});
+      ahi[k] = make_float2(a.hi, b.hi);
+      alo[k] = make_float2(a.lo, b.lo);
     }
   }
 }
@@ -481,9 +579,12 @@ __global__ void __launch_bounds__(NW * 32, 1)
   };
   for (int i = 0; i < NS && i < n; ++i) issue(i);
   constexpr int RL = RPL;   // rows per lane
-  FF acc[RL];
+  float2 ahi[4], alo[4];     // float-float row sums, rows (2k, 2k+1)
 #pragma unroll
-  for (int u = 0; u < RL; ++u) acc[u] = {0.f, 0.f};
+  for (int k = 0; k < 4; ++k) {
+    ahi[k] = make_float2(0.f, 0.f);
+    alo[k] = make_float2(0.f, 0.f);
+  }
   for (int i = 0; i < n; ++i) {
     const int s = i % NS;
     if (!mbar_wait(&bars[s], (uint32_t)((i / NS) & 1))) {
@@ -507,12 +608,15 @@ __global__ void __launch_bounds__(NW * 32, 1)
     const int4 rinfo = info[s];   // range flags, split / part, multiplier parity of this piece
     if (rinfo.x & PD_FIRST) {
 #pragma unroll
-      for (int u = 0; u < RL; ++u) acc[u] = {0.f, 0.f};
+      for (int k = 0; k < 4; ++k) {
+        ahi[k] = make_float2(0.f, 0.f);
+        alo[k] = make_float2(0.f, 0.f);
+      }
     }
     const uint32_t tbl = sa + C_MOFF + 8u * (uint32_t)rinfo.z;
     switch (H.fb) {
 #define HM_RS(FF_, BB_) \
-  case ((FF_) << 4) | (BB_): rs_piece<TIER, FF_, BB_, RL>(sa, H, tbl, alpha_ff, lane, acc); break;
+  case ((FF_) << 4) | (BB_): rs_piece<TIER, FF_, BB_>(sa, H, tbl, alpha_ff, lane, ahi, alo); break;
       HM_FORMATS(HM_RS)
 #undef HM_RS
       default:
@@ -521,7 +625,10 @@ __global__ void __launch_bounds__(NW * 32, 1)
     if (rinfo.x & PD_LAST) {
       AccR<RL> a8;
 #pragma unroll
-      for (int u = 0; u < RL; ++u) a8.v[u] = acc[u];
+      for (int k = 0; k < 4; ++k) {
+        a8.v[2 * k] = FF{ahi[k].x, alo[k].x};
+        a8.v[2 * k + 1] = FF{ahi[k].y, alo[k].y};
+      }
       rs_emit<MODE, RL>(a8, H.row0, H.nrows, H.flags | ((rinfo.x & PD_SPLIT) ? 0x10000 : 0), rinfo.y >> 8,
                         rinfo.y & 0xff, lane, alpha, beta, y, perm, vout, rowscale, fix, fixcnt, splits);
     }
