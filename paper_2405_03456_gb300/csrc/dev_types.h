@@ -51,6 +51,13 @@ constexpr int CS_CFG_WARPS[NCFG] = {16, 10, 7};
 constexpr int CS_CFG_STAGES[NCFG] = {2, 3, 4};
 constexpr int RS_CFG_WARPS[NCFG] = {16, 11, 8};
 constexpr int RS_CFG_STAGES[NCFG] = {2, 3, 4};
+// Multi-RHS products run in panels of RP right-hand sides on a separate split
+// of every launch into one range per block (MR_BLOCKS_PER_SM blocks per SM);
+// its descriptors are the extra launch shape index MR_SHAPE.
+constexpr int RP = 32;
+constexpr int MR_BLOCKS_PER_SM = 2;
+constexpr int MR_SHAPE = NCFG;
+constexpr int NSHAPES = NCFG + 1;
 constexpr int STAGE_BYTES = 6144;          // payload bytes of one stage (item / piece incl. header)
 constexpr int SEG_ROWS = 64;               // rows of a column-dot segment
 constexpr int CHUNK_ROWS = 128;            // rows of a row chunk
@@ -74,7 +81,7 @@ struct CPieceHdr {
   uint16_t ncols;    // 1..CPIECE_MAX_COLS
   uint16_t fb;       // decode class: fmt << 4 | B
   uint16_t flags;    // ITEM_FINAL | ITEM_ALPHA
-  int32_t pad;
+  int32_t limbs;     // BF16 limbs (1..3) that hold every decoded value exactly (multi-RHS path)
 };
 static_assert(sizeof(CPieceHdr) == 16, "CPieceHdr layout");
 
@@ -121,7 +128,7 @@ struct PieceHdr {
   uint16_t em;       // tile pieces: e | m << 8
   int32_t vin0;      // tile pieces: multiplier index of the piece's column 0
   uint16_t ncols;
-  uint16_t pad0;
+  uint16_t limbs;    // BF16 limbs (1..3) that hold every decoded value exactly (multi-RHS path)
   int32_t pad1;
   F2 scale;          // tile pieces: AFLP vmin of the matrix (float-float), else 1
   int32_t pad[2];

@@ -25,6 +25,18 @@ cudaError_t launch_rgemv(int tier, int mode, int cfg, const PieceCopy* pieces, c
                          const uint8_t* pay, const float2* vec, double alpha, F2 alpha_ff, double beta, double* y,
                          const int32_t* perm, float2* vout, const double* rowscale, F2* fix, int32_t* fixcnt,
                          const Split* splits, int* err, cudaStream_t st);
+cudaError_t mr_init();
+cudaError_t launch_gather_mr(const double* x, int64_t ldx, int r, const int32_t* perm, int n, float* v,
+                             cudaStream_t st);
+cudaError_t launch_fanout_mr(const int32_t* src, int n, float* dst, const float* v, cudaStream_t st);
+cudaError_t launch_gsum_mr(const GsumOut* outs, int nouts, const F2* pscale, const float* partial, F2 alpha, float* v,
+                           cudaStream_t st);
+cudaError_t launch_cdot_mr(const ItemCopy* items, const int32_t* wbeg, int nblk, const uint8_t* pay, const float* vec,
+                           F2 alpha, float* partial, float* vout, int* err, cudaStream_t st);
+cudaError_t launch_rgemv_mr(int mode, const PieceCopy* pieces, const int32_t* wbeg, int nblk, const uint8_t* pay,
+                            const float* vec, double alpha, F2 alpha_ff, double beta, double* y, int64_t ldy, int r,
+                            const int32_t* perm, float* vout, const double* rowscale, F2* fix, int32_t* fixcnt,
+                            const Split* splits, int* err, cudaStream_t st);
 cudaError_t launch_decode(const uint8_t* p, int64_t n, int B, int fmt, int e, int m, double vmin,
                           double* out, cudaStream_t st);
 }  // namespace hm
@@ -77,6 +89,9 @@ struct hm_matrix {
   DevArr<double> d_rowscale;
   DevArr<int32_t> d_perm;
   F2* d_fix = nullptr;         // row sums of the parts of chunks shared by warps
+  float* d_vmr = nullptr;      // multi-RHS vectors: nvec x RP (FP32 tier)
+  float* d_pmr = nullptr;      // multi-RHS column-dot partials: npartial x RP
+  F2* d_fixmr = nullptr;       // multi-RHS fix-up rows: nfix_mr x CHUNK_ROWS x RP
   int32_t* d_fixcnt = nullptr; // arrival counters of those chunks (reset by the last part)
   float2* d_vec = nullptr;     // vector workspace (x, coefficient vectors)
   F2* d_part = nullptr;        // column-dot partial sums (float-float)
@@ -138,6 +153,11 @@ struct hm_matrix {
     d_perm.release();
     if (d_fix) cudaFree(d_fix);
     if (d_fixcnt) cudaFree(d_fixcnt);
+    if (d_vmr) cudaFree(d_vmr);
+    if (d_pmr) cudaFree(d_pmr);
+    if (d_fixmr) cudaFree(d_fixmr);
+    d_vmr = d_pmr = nullptr;
+    d_fixmr = nullptr;
     d_fix = nullptr;
     d_fixcnt = nullptr;
     if (d_vec) cudaFree(d_vec);
@@ -162,7 +182,10 @@ cudaError_t g_kinit_err = cudaSuccess;
 hm_status upload(hm_matrix* M) {
   Program& P = M->prog;
   cudaError_t e;
-  std::call_once(g_kinit, [] { g_kinit_err = kernels_init(); });
+  std::call_once(g_kinit, [] {
+    g_kinit_err = kernels_init();
+    if (g_kinit_err == cudaSuccess) g_kinit_err = mr_init();
+  });
   if (g_kinit_err != cudaSuccess) return HM_ERR_CUDA;
 #define UP(arr, vec) \
   if ((e = M->arr.upload(vec)) != cudaSuccess) return cuda_status(e);
@@ -172,7 +195,7 @@ hm_status upload(hm_matrix* M) {
   UP(d_pscale, P.pscale)
   {
     std::vector<PieceCopy> all;
-    for (int cf = 0; cf < NCFG; ++cf) all.insert(all.end(), P.pdesc[cf].begin(), P.pdesc[cf].end());
+    for (int cf = 0; cf < NSHAPES; ++cf) all.insert(all.end(), P.pdesc[cf].begin(), P.pdesc[cf].end());
     UP(d_pieces, all)
   }
   UP(d_wbeg, P.wbeg)
@@ -195,6 +218,16 @@ hm_status upload(hm_matrix* M) {
   const size_t ncnt = std::max<size_t>(P.splits.size(), 1) * sizeof(int32_t);
   if ((e = cudaMalloc(&M->d_fixcnt, ncnt)) != cudaSuccess) return cuda_status(e);
   if ((e = cudaMemset(M->d_fixcnt, 0, ncnt)) != cudaSuccess) return cuda_status(e);
+  if (P.tier == TIER_F32) {   // multi-RHS workspace (panels of RP right-hand sides)
+    const size_t nv = (size_t)(std::max<int64_t>(P.nvec, 1) + SEG_ROWS) * RP * sizeof(float);
+    if ((e = cudaMalloc(&M->d_vmr, nv)) != cudaSuccess) return cuda_status(e);
+    if ((e = cudaMemset(M->d_vmr, 0, nv)) != cudaSuccess) return cuda_status(e);
+    if ((e = cudaMalloc(&M->d_pmr, (size_t)std::max<int64_t>(P.npartial, 1) * RP * sizeof(float))) != cudaSuccess)
+      return cuda_status(e);
+    if ((e = cudaMalloc(&M->d_fixmr, (size_t)std::max<int64_t>(P.nfix_mr, 1) * CHUNK_ROWS * RP * sizeof(F2))) !=
+        cudaSuccess)
+      return cuda_status(e);
+  }
   if ((e = cudaMalloc(&M->d_err, sizeof(int))) != cudaSuccess) return cuda_status(e);
   if ((e = cudaMemset(M->d_err, 0, sizeof(int))) != cudaSuccess) return cuda_status(e);
   return HM_OK;
@@ -305,6 +338,71 @@ static cudaError_t run_launch(hm_matrix* M, const Launch& L, double alpha, const
   return cudaErrorInvalidValue;
 }
 
+// One panel of r <= RP right-hand sides (FP32 tier): the same launch sequence
+// with the multi-RHS kernels on the block-range split of every launch.
+static cudaError_t run_launch_mr(hm_matrix* M, const Launch& L, double alpha, const double* x, int64_t ldx,
+                                 double beta, double* y, int64_t ldy, int r, cudaStream_t st) {
+  Program& P = M->prog;
+  const F2 aff = split_ff(alpha);
+  switch (L.kind) {
+    case Launch::GATHER:
+      return launch_gather_mr(x, ldx, r, M->d_perm.p, (int)L.n, M->d_vmr, st);
+    case Launch::CDOT:
+      return launch_cdot_mr(M->d_items.p, M->d_wbeg.p + L.woff[MR_SHAPE], L.nw[MR_SHAPE], M->d_pay.p, M->d_vmr, aff,
+                            M->d_pmr, M->d_vmr, M->d_err, st);
+    case Launch::GSUM:
+      return launch_gsum_mr(M->d_gout.p + L.off, (int)L.n, M->d_pscale.p, M->d_pmr, aff, M->d_vmr, st);
+    case Launch::FANOUT:
+      return launch_fanout_mr(M->d_fan.p + L.off, (int)L.n, M->d_vmr + (size_t)(P.fan_base + L.off) * RP, M->d_vmr,
+                              st);
+    case Launch::RGEMV:
+      return launch_rgemv_mr(L.mode, M->d_pieces.p + (size_t)MR_SHAPE * P.npieces, M->d_wbeg.p + L.woff[MR_SHAPE],
+                             L.nw[MR_SHAPE], M->d_pay.p, M->d_vmr, alpha, aff, beta, y, ldy, r, M->d_perm.p,
+                             M->d_vmr, L.use_rowscale ? M->d_rowscale.p : nullptr, M->d_fixmr, M->d_fixcnt,
+                             M->d_splits.p, M->d_err, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+static hm_status run_program_mr(hm_matrix* M, double alpha, const double* x, int64_t ldx, double beta, double* y,
+                                int64_t ldy, int r, cudaStream_t st) {
+  for (const Launch& L : M->prog.launches) {
+    hm_matrix::Rec rec{(int)L.kind, nullptr, nullptr, L.bytes};
+    if (M->prof) {
+      rec.e0 = M->take_event();
+      rec.e1 = M->take_event();
+      cudaEventRecord(rec.e0, st);
+    }
+    if (run_launch_mr(M, L, alpha, x, ldx, beta, y, ldy, r, st) != cudaSuccess) return HM_ERR_CUDA;
+    if (M->prof) {
+      cudaEventRecord(rec.e1, st);
+      M->recs.push_back(rec);
+    }
+  }
+  return HM_OK;
+}
+
+static hm_status run_program(hm_matrix* M, double alpha, const double* x, double beta, double* y,
+                             cudaStream_t st);
+
+// All right-hand sides: panels of RP through the multi-RHS kernels (FP32
+// tier), the rest (or everything in the float-float tier) as one single-RHS
+// product per right-hand side.  A panel reads the matrix once; it costs about
+// as much as MR_MIN_RHS single products on GB300, so smaller remainders run
+// as single products.
+constexpr int64_t MR_MIN_RHS = 9;
+static hm_status run_all(hm_matrix* M, double alpha, const double* x, int64_t ldx, double beta, double* y,
+                         int64_t ldy, int64_t nrhs, cudaStream_t st) {
+  hm_status s = HM_OK;
+  int64_t r0 = 0;
+  if (M->d_vmr)   // panels of RP; a panel of fewer than MR_MIN_RHS is cheaper as single products
+    for (; r0 < nrhs && nrhs - r0 >= MR_MIN_RHS && s == HM_OK; r0 += RP)
+      s = run_program_mr(M, alpha, x + r0 * ldx, ldx, beta, y + r0 * ldy, ldy, (int)std::min<int64_t>(RP, nrhs - r0),
+                         st);
+  for (int64_t r = r0; r < nrhs && s == HM_OK; ++r) s = run_program(M, alpha, x + r * ldx, beta, y + r * ldy, st);
+  return s;
+}
+
 static hm_status run_program(hm_matrix* M, double alpha, const double* x, double beta, double* y,
                              cudaStream_t st) {
   for (const Launch& L : M->prog.launches) {
@@ -341,9 +439,7 @@ hm_status hm_matvec(hm_matrix* M, double alpha, const double* x, int64_t ldx, do
         return HM_ERR_CUDA;
       if (cudaStreamBeginCapture(M->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
         return HM_ERR_CUDA;
-      hm_status s = HM_OK;
-      for (int64_t r = 0; r < nrhs && s == HM_OK; ++r)
-        s = run_program(M, alpha, x + r * ldx, beta, y + r * ldy, M->cap_stream);
+      hm_status s = run_all(M, alpha, x, ldx, beta, y, ldy, nrhs, M->cap_stream);
       cudaGraph_t g = nullptr;
       const cudaError_t ce = cudaStreamEndCapture(M->cap_stream, &g);
       if (s != HM_OK || ce != cudaSuccess) {
@@ -360,11 +456,7 @@ hm_status hm_matvec(hm_matrix* M, double alpha, const double* x, int64_t ldx, do
     }
     return cudaGraphLaunch(M->gexec, st) == cudaSuccess ? HM_OK : HM_ERR_CUDA;
   }
-  for (int64_t r = 0; r < nrhs; ++r) {
-    hm_status s = run_program(M, alpha, x + r * ldx, beta, y + r * ldy, st);
-    if (s != HM_OK) return s;
-  }
-  return HM_OK;
+  return run_all(M, alpha, x, ldx, beta, y, ldy, nrhs, st);
 }
 
 hm_status hm_graph(hm_matrix* M, int32_t enable) {
@@ -555,6 +647,8 @@ hm_status hm_info(const hm_matrix* M, hm_info_t* o) {
                             P.pscale.size() * 8 + P.rowscale.size() * 8 + P.fan_src.size() * 4) +
                   H.n * 4;
   o->bytes_workspace = P.nvec * 8 + P.npartial * 8 + P.nfix * CHUNK_ROWS * 8;
+  if (M->d_vmr)
+    o->bytes_workspace += ((P.nvec + SEG_ROWS) + P.npartial) * RP * 4 + P.nfix_mr * CHUNK_ROWS * RP * 8;
   o->nlaunches = (int64_t)P.launches.size();
   o->tier = P.tier;
   return HM_OK;

@@ -135,6 +135,18 @@ int64_t pad8(int64_t x) { return (x + 7) & ~int64_t(7); }
 uint16_t class_of(uint32_t fw) { return (uint16_t)((((fw >> 8) & 0xff) << 4) | (fw & 0xff)); }
 uint16_t em_of(uint32_t fw) { return (uint16_t)(((fw >> 16) & 0xff) | ((fw >> 24) << 8)); }
 
+// BF16 limbs that hold a decoded FP32 value of format word fw exactly (the
+// multi-RHS tensor-core path): AFLP +-(s - 1) with s = 2^f (1 + k 2^-m'),
+// f < 2^e, has at most max(f, m') + 1 significant bits; FPX e8 m+1; e11 / raw
+// values are FP32-truncated (24).  Each limb carries 8 significant bits.
+int limbs_of(uint32_t fw) {
+  const int f = (int)((fw >> 8) & 0xff), e = (int)((fw >> 16) & 0xff), m = (int)(fw >> 24);
+  int bits = 24;
+  if (f == FMT_AFLP) bits = std::min(24, std::max((1 << e) - 1, m) + 1);
+  if (f == FMT_FPX8) bits = std::min(24, m + 1);
+  return (bits + 7) / 8;
+}
+
 // ---------------------------------------------------------------- warp ranges
 // Split units (items / pieces) [0, n) of `bytes` into nw contiguous ranges of
 // about equal bytes: unit i goes to the warp holding the midpoint of its
@@ -206,6 +218,10 @@ void pack_cdot(Program& P, const std::vector<CdotCol>& cols, int64_t m, int32_t 
         h.ncols = (uint16_t)nc;
         h.fb = cls;
         h.flags = (uint16_t)(final_out ? (ITEM_FINAL | (use_alpha ? ITEM_ALPHA : 0)) : 0);
+        for (int t = 0; t < nc; ++t) {
+          const CdotCol& cc = cols[ord[a + t]];
+          h.limbs = std::max(h.limbs, (int32_t)limbs_of(cc.cs->fw(cc.j)));
+        }
         P.pk.raw(&h, sizeof h);
         std::vector<CColMeta> cm(nc);
         std::vector<F2> sc;
@@ -369,6 +385,15 @@ void add_rgemv(Ctx& cx, std::vector<ChunkWork>& cw, int mode, bool rowscale) {
     h.fb = p.cls;
     h.ncols = (uint16_t)p.ncols;
     h.scale = F2{1.0f, 0.0f};
+    h.limbs = 1;
+    if (p.t) {
+      h.limbs = (uint16_t)limbs_of(p.t->fw);
+    } else {
+      for (int k = 0; k < p.ncols; ++k) {
+        const ColRef& r = c.cols[p.j0 + k];
+        h.limbs = (uint16_t)std::max<int>(h.limbs, limbs_of(r.cs->fw(r.j)));
+      }
+    }
     int64_t vals = 0, meta = (int64_t)sizeof(PieceHdr) + (int64_t)sizeof(PieceCopy);
     int64_t moff = 0;
     if (p.t) {
@@ -430,13 +455,14 @@ void add_rgemv(Ctx& cx, std::vector<ChunkWork>& cw, int mode, bool rowscale) {
   std::vector<int64_t> pb(pw.size());
   for (size_t i = 0; i < pw.size(); ++i) pb[i] = pw[i].bytes + 8 * pw[i].ncols;
   int64_t nfix = 0;
-  for (int cf = 0; cf < NCFG; ++cf) {
+  int64_t nfix_mr = 0;
+  for (int cf = 0; cf < NSHAPES; ++cf) {
     L.woff[cf] = (int64_t)P.wbeg.size();
     if (pw.empty()) {
       L.nw[cf] = 0;
       continue;
     }
-    L.nw[cf] = partition(pb, L.off, cx.nsm * RS_CFG_WARPS[cf], P.wbeg);
+    L.nw[cf] = partition(pb, L.off, cx.nsm * (cf == MR_SHAPE ? MR_BLOCKS_PER_SM : RS_CFG_WARPS[cf]), P.wbeg);
     std::vector<PieceCopy> d = base;
     std::vector<int32_t> nparts(cw.size(), 0), partof(pw.size(), 0);
     const int32_t* wb = P.wbeg.data() + L.woff[cf];
@@ -463,7 +489,10 @@ void add_rgemv(Ctx& cx, std::vector<ChunkWork>& cw, int mode, bool rowscale) {
         P.splits.push_back(Split{(int32_t)fix, nparts[ch]});
         fix += nparts[ch];
       }
-    nfix = std::max(nfix, fix);
+    if (cf == MR_SHAPE)
+      nfix_mr = std::max(nfix_mr, fix);
+    else
+      nfix = std::max(nfix, fix);
     for (size_t i = 0; i < pw.size(); ++i)
       if (splitof[pw[i].chunk] >= 0) {
         d[i].bytes_flags |= PD_SPLIT << 16;
@@ -472,6 +501,7 @@ void add_rgemv(Ctx& cx, std::vector<ChunkWork>& cw, int mode, bool rowscale) {
     P.pdesc[cf].insert(P.pdesc[cf].end(), d.begin(), d.end());
   }
   P.nfix = std::max(P.nfix, nfix);
+  P.nfix_mr = std::max(P.nfix_mr, nfix_mr);
   P.npieces += (int64_t)pw.size();
   P.nchunks += (int64_t)cw.size();
   P.launches.push_back(L);
@@ -918,9 +948,10 @@ void finish_launches(Ctx& cx) {
           ib[i] = P.items[L.off + i].bytes;
           b += P.item_alg[L.off + i];
         }
-        for (int cf = 0; cf < NCFG; ++cf) {
+        for (int cf = 0; cf < NSHAPES; ++cf) {
           L.woff[cf] = (int64_t)P.wbeg.size();
-          L.nw[cf] = L.n > 0 ? partition(ib, L.off, cx.nsm * CS_CFG_WARPS[cf], P.wbeg) : 0;
+          const int nmax = cx.nsm * (cf == MR_SHAPE ? MR_BLOCKS_PER_SM : CS_CFG_WARPS[cf]);
+          L.nw[cf] = L.n > 0 ? partition(ib, L.off, nmax, P.wbeg) : 0;
         }
         break;
       }
@@ -964,7 +995,7 @@ bool build_program(const HostMatrix& H, int codec, double eps, int valr, int nsm
   // fan-out slots follow every other vector entry
   P.fan_base = P.nvec;
   P.nvec += (int64_t)P.fan_src.size();
-  for (int cf = 0; cf < NCFG; ++cf)
+  for (int cf = 0; cf < NSHAPES; ++cf)
     for (PieceCopy& d : P.pdesc[cf])
       if (d.moff < 0) d.moff = (int32_t)(P.fan_base + (-1 - (int64_t)d.moff));
   if (P.rowscale.size() > 1) P.rowscale.resize(P.nvec, 1.0);

@@ -65,8 +65,8 @@ struct Launch {
   int64_t off = 0, n = 0;         // range of items / outputs / pieces / fan-out slots
   bool use_rowscale = false;
   int64_t bytes = 0;              // algorithmic bytes moved by the launch
-  int64_t woff[NCFG] = {};        // CDOT / RGEMV, per launch shape: warp ranges wbeg[woff .. woff + nw]
-  int nw[NCFG] = {};              // warps of the launch per launch shape
+  int64_t woff[NSHAPES] = {};     // CDOT / RGEMV, per launch shape: ranges wbeg[woff .. woff + nw]
+  int nw[NSHAPES] = {};           // ranges (warps; blocks for the multi-RHS shape) per launch shape
   int cfg = 0;                    // launch shape in use (autotuner choice)
 };
 
@@ -77,12 +77,13 @@ struct Program {
   std::vector<int64_t> item_alg;  // algorithmic bytes of each item
   std::vector<GsumOut> gouts;
   std::vector<F2> pscale;         // per-partial weights of the outputs that use them
-  std::vector<PieceCopy> pdesc[NCFG];  // row-chunk piece descriptors, one list per launch shape
+  std::vector<PieceCopy> pdesc[NSHAPES];  // row-chunk piece descriptors, one list per launch shape
   int64_t npieces = 0;
   std::vector<int64_t> piece_alg; // algorithmic bytes of each piece
   std::vector<int32_t> wbeg;      // per launch and shape: nw + 1 range starts (item / piece indices)
   std::vector<Split> splits;      // chunks shared by several warps (all launch shapes)
-  int64_t nfix = 0;               // fix-up slots (CHUNK_ROWS float-float rows each), largest shape
+  int64_t nfix = 0;               // fix-up slots (CHUNK_ROWS float-float rows each), largest warp shape
+  int64_t nfix_mr = 0;            // fix-up slots of the multi-RHS shape (CHUNK_ROWS x RP each)
   int64_t nchunks = 0;
   std::vector<int32_t> fan_src;   // fan-out: slot s takes v[fan_src[s]]; slot s is v[fan_base + s]
   int64_t fan_base = 0;
