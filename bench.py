@@ -154,6 +154,33 @@ def time_variant(torch, M, x, y, steps, warmup, stream, world=1):
     return per, total
 
 
+def time_multi_rhs(torch, M, n, r_list, steps, warmup, stream, seed=5):
+    """Products Y := M X of r right-hand sides (panels of 32 on the tensor cores):
+    median ms and right-hand sides per second for each r."""
+    import numpy as np
+    import synth
+    out = {}
+    for r in r_list:
+        X = torch.from_numpy(np.asfortranarray(synth.rhs(n, r, seed=seed + r))).cuda().t().contiguous().t()
+        Y = torch.zeros_like(X)
+        for _ in range(warmup):
+            M.matvec(1.0, X, 0.0, Y, stream=stream.cuda_stream)
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        with torch.cuda.stream(stream):
+            for a, b in ev:
+                a.record(stream)
+                M.matvec(1.0, X, 0.0, Y, stream=stream.cuda_stream)
+                b.record(stream)
+        torch.cuda.synchronize()
+        per = sorted(a.elapsed_time(b) for a, b in ev)
+        med = statistics.median(per)
+        out[str(r)] = {"ms_p50": round(med, 4), "ms_p99": round(pct(per, 0.99), 4),
+                       "rhs_per_s": round(r / (med * 1e-3), 1)}
+        del X, Y
+    return out
+
+
 def pct(v, q):
     i = min(len(v) - 1, max(0, int(round(q * (len(v) - 1)))))
     return v[i]
@@ -216,6 +243,11 @@ def gpu_arm(args, rank, world):
                 for _ in range(min(args.steps, 200)):
                     M.matvec(1.0, x, 1.0, y, stream=stream.cuda_stream)
                 prof = M.profile_read()
+                if not args.no_multi_rhs:   # precision / multi-RHS form on the same matrix
+                    M.profile(False)
+                    headline["by_nrhs"] = time_multi_rhs(torch, M, n, (1, 8, 32, 64), max(5, min(50, args.steps // 10)),
+                                                         3, stream)
+                    M.profile(True)
                 M.profile(False)
                 headline["kernels"] = prof
                 # e2e: host buffers, copies inside the timed region
@@ -252,6 +284,23 @@ def gpu_arm(args, rank, world):
             fmt_results[(fmt, codec)] = {"ms_p50": med, "ms_p99": pct(per, 0.99), "gbs": ab / (med * 1e-3) / 1e9,
                                          "payload_bytes": info["bytes_payload"], "value_bytes": info["bytes_values"],
                                          "fp64_bytes": info["bytes_fp64"], "launches": info["nlaunches"]}
+        M.close()
+    matern = None
+    if args.matern:   # Matern nu = 1.5 covariance on the unit cube: multi-RHS products
+        import numpy as np
+        nm = args.matern
+        t0 = time.perf_counter()
+        M = hm.HMatrix(synth.cube_points(nm), "matern", 64, 2.0, "h", 1e-6, 0.1)
+        M.compress(1e-6, "aflp", True)
+        build_s = time.perf_counter() - t0
+        if not args.no_tune:
+            M.autotune(3, stream.cuda_stream)
+        info = M.info()
+        matern = {"workload": f"matern-1.5 l=0.1 N={nm} uniform unit cube, leaf=64 eta=2 H eps=1e-6 AFLP VALR",
+                  "payload_mb": round(info["bytes_payload"] / 1e6, 1), "fp64_mb": round(info["bytes_fp64"] / 1e6, 1),
+                  "build_s": round(build_s, 1),
+                  "by_nrhs": time_multi_rhs(torch, M, nm, (1, 8, 32, 64), max(3, min(20, args.steps // 20)), 2,
+                                            stream)}
         M.close()
     clk = clocks.stop()
 
@@ -308,6 +357,9 @@ def gpu_arm(args, rank, world):
         "gpu_launches": int(headline["launches"] * args.steps),
         "clocks": clk,
         "by_eps": by_eps,
+        "by_nrhs": {"workload": "the headline matrix, Y := M X with r right-hand sides (panels of 32: BF16-limb "
+                                "tensor-core products, FP32 accumulation, float-float sums; r < 9 as single products)",
+                    **headline.get("by_nrhs", {})},
         "by_format": {f"{f}-{c}": {"gbs": round(r["gbs"], 1), "ms_p50": round(r["ms_p50"], 4),
                                    "ms_p99": round(r["ms_p99"], 4), "payload_mb": round(r["payload_bytes"] / 1e6, 1),
                                    "compression_ratio": round(r["fp64_bytes"] / max(r["value_bytes"], 1), 3),
@@ -315,6 +367,8 @@ def gpu_arm(args, rank, world):
                                    "speedup_vs_fp64": round(fmt_results[(f, "none")]["ms_p50"] / r["ms_p50"], 3)}
                       for (f, c), r in fmt_results.items()},
     }
+    if matern is not None:
+        line["matern_multi_rhs"] = matern
     if not args.no_cpu:
         try:
             line["cpu_baseline"] = run_cpu_child(args.cpu_budget_mb, args.cpu_passes, 1)
@@ -364,6 +418,9 @@ def main():
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--formats", default="uh,h2")
     ap.add_argument("--no-tune", action="store_true", help="keep the default launch shape (no autotuning)")
+    ap.add_argument("--no-multi-rhs", action="store_true", help="skip the multi-RHS timings")
+    ap.add_argument("--matern", type=int, default=0,
+                    help="also time multi-RHS products on the Matern cube with this many points (slow to build)")
     ap.add_argument("--cpu-budget-mb", type=float, default=20.0)
     ap.add_argument("--cpu-passes", type=int, default=30)
     args = ap.parse_args()

@@ -250,8 +250,9 @@ class HMatrix:
         if stream is None:
             stream = torch.cuda.current_stream().cuda_stream
         nrhs = 1 if x.dim() == 1 else x.shape[1]
-        ldx = x.shape[0] if x.dim() == 1 else x.stride(1)
-        ldy = y.shape[0] if y.dim() == 1 else y.stride(1)
+        # a single column's leading dimension is n (the stride of a size-1 dimension is arbitrary)
+        ldx = x.shape[0] if nrhs == 1 else x.stride(1)
+        ldy = y.shape[0] if nrhs == 1 else y.stride(1)
         assert x.dtype == torch.float64 and y.dtype == torch.float64 and x.is_cuda and y.is_cuda
         assert x.dim() == 1 or x.stride(0) == 1
         assert y.dim() == 1 or y.stride(0) == 1
