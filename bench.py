@@ -181,6 +181,24 @@ def time_multi_rhs(torch, M, n, r_list, steps, warmup, stream, seed=5):
     return out
 
 
+def profiled_traffic(kernel, n):
+    """DRAM bytes per launch of `kernel` from the committed ncu record, if that
+    record was taken on this workload with the current kernel sources."""
+    import hashlib
+    try:
+        rec = dict(ln.split(" ", 1) for ln in open(os.path.join(ROOT, "profiles", "k_rstream_traffic.txt")).read()
+                   .strip().splitlines())
+        src = b"".join(open(os.path.join(ROOT, "paper_2405_03456_gb300", "csrc", f), "rb").read()
+                       for f in ("kernels.cu", "decode.cuh", "dev_types.h"))
+    except OSError:
+        return None
+    if rec.get("kernel") != kernel or f"N={n} " not in rec.get("workload", ""):
+        return None
+    if hashlib.sha256(src).hexdigest()[:16] != rec.get("sources_sha256_prefix"):
+        return None
+    return int(rec["bytes_per_launch"])
+
+
 def pct(v, q):
     i = min(len(v) - 1, max(0, int(round(q * (len(v) - 1)))))
     return v[i]
@@ -346,7 +364,8 @@ def gpu_arm(args, rank, world):
         "matvecs_per_s": round(1e3 / med * world, 1), "ms_p50": round(med, 5),
         "ms_p99": round(headline["ms_p99"], 5),
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": hbm_peak,
-                     "unit": "GB/s", "frac": round(achieved / hbm_peak, 4), "traffic": None,
+                     "unit": "GB/s", "frac": round(achieved / hbm_peak, 4), "traffic": profiled_traffic(dom, n),
+                     "alg_bytes_per_launch": int(per_launch_bytes),
                      "peak_source": peak_src + " (MEASURED_PEAKS hbm_gbs copy bandwidth)",
                      "share": round(dk["ms"] / tot_ms, 3) if tot_ms else None,
                      "kernels": {k: {"ms_per_launch": round(v["ms"] / max(v["launches"], 1), 5),
