@@ -264,6 +264,31 @@ __device__ __forceinline__ void ff_add_f2(float2& hi, float2& lo, float2 s) {
   hi = h;
 }
 
+// Dot2 (Ogita-Rump-Oishi) on pairs: (s, c) += d * v per component, with d and
+// v float-float (dh + dl, vh + vl): TwoProduct by FMA, TwoSum of Knuth.
+__device__ __forceinline__ void dot2_2(float2& s, float2& c, float2 dh, float2 dl, float2 vh, float2 vl) {
+  const float2 p = __fmul2_rn(dh, vh);
+  const float2 pe = __ffma2_rn(dh, vh, make_float2(-p.x, -p.y));
+  const float2 tail = __ffma2_rn(dh, vl, __ffma2_rn(dl, vh, pe));
+  const float2 s1 = __fadd2_rn(s, p);
+  const float2 bp = sub2(s1, s);
+  const float2 e = __fadd2_rn(sub2(s, sub2(s1, bp)), sub2(p, bp));
+  s = s1;
+  c = __fadd2_rn(c, __fadd2_rn(e, tail));
+}
+
+// (hi, lo) += (s + c) per component, float-float (the Dot2 pair folded first).
+__device__ __forceinline__ void ff_add_dot2(float2& hi, float2& lo, float2 s, float2 c) {
+  const float2 h = __fadd2_rn(s, c);
+  const float2 l = sub2(c, sub2(h, s));
+  float2 t, e;
+  two_sum2(hi, h, t, e);
+  e = __fadd2_rn(e, __fadd2_rn(lo, l));
+  const float2 hh = __fadd2_rn(t, e);
+  lo = sub2(e, sub2(hh, t));
+  hi = hh;
+}
+
 // 8 consecutive codes of format (F, B) at shared address a -> 4 FP32 pairs
 // (FP32 tier: AFLP as +-(s - 1), FPX e8 exactly, e11 / raw truncated to FP32).
 template <int F, int B>

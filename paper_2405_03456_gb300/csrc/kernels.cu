@@ -122,17 +122,27 @@ __device__ __forceinline__ void cs_piece(uint32_t sa, int R, int nc, int flags, 
           e = em & 0xff;
           m = em >> 8;
         }
+        float2 a2 = make_float2(0.f, 0.f), ac2 = make_float2(0.f, 0.f);
 #pragma unroll
         for (int hb = 0; hb < RL / RPL; ++hb) {
           float h[8], l[8];
           decode8s<TIER, F, B>(cb + (uint32_t)j * stride + (uint32_t)(hb * RPL * B), e, m, h, l);
 #pragma unroll
-          for (int u = 0; u < 8; ++u) {
-            if constexpr (TIER == TIER_F32)
+          for (int u = 0; u < 8; u += 2) {
+            if constexpr (TIER == TIER_F32) {
               a = fmaf(h[u], xh[hb * RPL + u], a);
-            else
-              dot2(a, ac, h[u], l[u], xh[hb * RPL + u], xl[hb * RPL + u]);
+              a = fmaf(h[u + 1], xh[hb * RPL + u + 1], a);
+            } else {
+              dot2_2(a2, ac2, make_float2(h[u], h[u + 1]), make_float2(l[u], l[u + 1]),
+                     make_float2(xh[hb * RPL + u], xh[hb * RPL + u + 1]),
+                     make_float2(xl[hb * RPL + u], xl[hb * RPL + u + 1]));
+            }
           }
+        }
+        if constexpr (TIER == TIER_FF) {   // even + odd rows (TwoSum of the leading parts)
+          a = a2.x;
+          ac = ac2.x;
+          pair_add<TIER>(a, ac, a2.y, ac2.y);
         }
       }
 #pragma unroll
@@ -392,11 +402,12 @@ __device__ __forceinline__ void rs_piece(uint32_t sa, const PieceHdr& H, uint32_
 #pragma unroll
     for (int k = 0; k < 4; ++k) ff_add_f2(ahi[k], alo[k], s2[k]);
   } else {
-    float s[8], c[8];
+    // float-float tier: Dot2 on row pairs (2k, 2k+1)
+    float2 s2[4], c2[4];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      s[u] = 0.f;
-      c[u] = 0.f;
+    for (int k = 0; k < 4; ++k) {
+      s2[k] = make_float2(0.f, 0.f);
+      c2[k] = make_float2(0.f, 0.f);
     }
 #pragma unroll 2
     for (int j = slot; j < nc; j += S) {
@@ -414,18 +425,13 @@ __device__ __forceinline__ void rs_piece(uint32_t sa, const PieceHdr& H, uint32_
       }
       float h[8], l[8];
       decode8s<TIER, F, B>(cb + (uint32_t)j * stride, e, m, h, l);
+      const float2 vh2 = make_float2(vh, vh), vl2 = make_float2(vl, vl);
 #pragma unroll
-      for (int u = 0; u < 8; ++u) dot2(s[u], c[u], h[u], l[u], vh, vl);
+      for (int k = 0; k < 4; ++k)
+        dot2_2(s2[k], c2[k], make_float2(h[2 * k], h[2 * k + 1]), make_float2(l[2 * k], l[2 * k + 1]), vh2, vl2);
     }
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      float hs = s[2 * k] + c[2 * k];
-      FF a = ff_add(FF{ahi[k].x, alo[k].x}, FF{hs, c[2 * k] - (hs - s[2 * k])});
-      hs = s[2 * k + 1] + c[2 * k + 1];
-      FF b = ff_add(FF{ahi[k].y, alo[k].y}, FF{hs, c[2 * k + 1] - (hs - s[2 * k + 1])});
-      ahi[k] = make_float2(a.hi, b.hi);
-      alo[k] = make_float2(a.lo, b.lo);
-    }
+    for (int k = 0; k < 4; ++k) ff_add_dot2(ahi[k], alo[k], s2[k], c2[k]);
   }
 }
 
