@@ -435,77 +435,97 @@ __device__ __forceinline__ void rs_piece(uint32_t sa, const PieceHdr& H, uint32_
   }
 }
 
-// Write one finished row of a chunk.
-template <int MODE>
-__device__ __forceinline__ void rs_store(int g, FF t, double alpha, double beta, double* __restrict__ y,
-                                         const int32_t* __restrict__ perm, float2* __restrict__ vout,
-                                         const double* __restrict__ rowscale, bool calpha) {
-  double val = ff_to_d(t);
-  if constexpr (MODE == MODE_Y) {
-    const int o = perm[g];
-    y[o] = (beta == 0.0) ? val : fma(beta, y[o], val);
-  } else {
-    if constexpr (MODE == MODE_VEC_ADD) {
-      const float2 old = vout[g];
-      val += (double)old.x + (double)old.y;
-    }
-    if (rowscale) val *= rowscale[g];
-    if (calpha) val *= alpha;
-    const FF ff = ff_from_d(val);
-    vout[g] = make_float2(ff.hi, ff.lo);
-  }
-}
-
 // Float-float row sums of a lane (RL rows), passed by value to the emit path.
 template <int RL>
 struct AccR {
   FF v[RL];
 };
 
+// Write the finished rows g0 .. g0 + nr - 1 of a chunk (nr <= RL; a lane's rows).
+// Every global load the rows need (y through perm, the old coefficients, the row
+// scales) is issued before the first store, so the lane waits for one round trip
+// instead of one per row.  Coefficient vectors stay in float-float arithmetic
+// (FP64 instructions are scarce on this GPU); y takes the FP64 sum hi + lo.
+template <int MODE, int RL>
+__device__ __forceinline__ void rs_store_rows(const AccR<RL>& acc, int g0, int nr, F2 alpha_ff, double beta,
+                                              double* __restrict__ y, const int32_t* __restrict__ perm,
+                                              float2* __restrict__ vout, const F2* __restrict__ rowscale,
+                                              bool calpha) {
+  if constexpr (MODE == MODE_Y) {
+    int o[RL];
+#pragma unroll
+    for (int u = 0; u < RL; ++u) o[u] = u < nr ? __ldg(perm + g0 + u) : 0;
+    double yo[RL];
+#pragma unroll
+    for (int u = 0; u < RL; ++u) yo[u] = (u < nr && beta != 0.0) ? y[o[u]] : 0.0;
+#pragma unroll
+    for (int u = 0; u < RL; ++u) {
+      if (u < nr) {
+        const double val = ff_to_d(acc.v[u]);
+        y[o[u]] = (beta == 0.0) ? val : fma(beta, yo[u], val);
+      }
+    }
+  } else {
+    float2 old[RL], sc[RL];
+#pragma unroll
+    for (int u = 0; u < RL; ++u) {
+      old[u] = (MODE == MODE_VEC_ADD && u < nr) ? vout[g0 + u] : make_float2(0.f, 0.f);
+      sc[u] = (rowscale && u < nr) ? __ldg(reinterpret_cast<const float2*>(rowscale + g0 + u)) : make_float2(1.f, 0.f);
+    }
+#pragma unroll
+    for (int u = 0; u < RL; ++u) {
+      if (u < nr) {
+        FF v = acc.v[u];
+        if constexpr (MODE == MODE_VEC_ADD) v = ff_add(v, FF{old[u].x, old[u].y});
+        if (rowscale) v = ff_mul(v, FF{sc[u].x, sc[u].y});
+        if (calpha) v = ff_mul(v, FF{alpha_ff.hi, alpha_ff.lo});
+        vout[g0 + u] = make_float2(v.hi, v.lo);
+      }
+    }
+  }
+}
+
 // End of a warp's part of a chunk (hflags: piece header flags, bit 16 set when
 // the chunk is shared by several warps): reduce the column slots (fixed order), then
-// emit the rows, directly or through the fix-up of a chunk shared by warps.
+// emit the rows, directly or through the fix-up of a chunk shared by warps (the
+// last part to arrive sums all parts in part order, so the result does not
+// depend on which warp finishes last).
 // Out of line: it runs once per part and keeps the piece loop compact.
 template <int MODE, int RL>
 __device__ __noinline__ void rs_emit(AccR<RL> acc, int row0, int R, int hflags, int split, int pidx, int lane,
-                                     double alpha, double beta, double* __restrict__ y,
+                                     F2 alpha_ff, double beta, double* __restrict__ y,
                                      const int32_t* __restrict__ perm, float2* __restrict__ vout,
-                                     const double* __restrict__ rowscale, F2* __restrict__ fix,
+                                     const F2* __restrict__ rowscale, F2* __restrict__ fix,
                                      int32_t* __restrict__ fixcnt, const Split* __restrict__ splits) {
   const int G = (R + RL - 1) / RL;
   const int S = 32 / G;
-  const int q = lane % G;
+  const int q = lane % G, slot = lane / G;
+  // pairwise tree over the S column slots (slot s takes s + off when s is a
+  // multiple of 2 off): log2 S shuffle rounds, all rows of a round in flight
+  for (int off = 1; off < S; off <<= 1) {
+    float hi[RL], lo[RL];
 #pragma unroll
-  for (int u = 0; u < RL; ++u) {
-    FF a = acc.v[u];
-    for (int s2 = 1; s2 < S; ++s2) {
-      const float hi = __shfl_sync(HM_FULL, acc.v[u].hi, q + s2 * G);
-      const float lo = __shfl_sync(HM_FULL, acc.v[u].lo, q + s2 * G);
-      a = ff_add(a, FF{hi, lo});
+    for (int u = 0; u < RL; ++u) {
+      hi[u] = __shfl_down_sync(HM_FULL, acc.v[u].hi, off * G);
+      lo[u] = __shfl_down_sync(HM_FULL, acc.v[u].lo, off * G);
     }
-    acc.v[u] = a;
+    if ((slot & (2 * off - 1)) == 0 && slot + off < S) {
+#pragma unroll
+      for (int u = 0; u < RL; ++u) acc.v[u] = ff_add(acc.v[u], FF{hi[u], lo[u]});
+    }
   }
   const bool mine = lane < G;   // slot 0 lanes hold the chunk's rows RL q .. RL q + RL-1
+  const int nr = mine ? min(RL, R - RL * q) : 0;
   const bool calpha = (hflags & PH_CALPHA) != 0;
   if (!(hflags & 0x10000)) {   // not shared with other warps
-    if (mine) {
-#pragma unroll
-      for (int u = 0; u < RL; ++u) {
-        const int r = RL * q + u;
-        if (r < R) rs_store<MODE>(row0 + r, acc.v[u], alpha, beta, y, perm, vout, rowscale, calpha);
-      }
-    }
+    if (nr > 0) rs_store_rows<MODE, RL>(acc, row0 + RL * q, nr, alpha_ff, beta, y, perm, vout, rowscale, calpha);
     return;
   }
   const Split sp = splits[split];
-  F2* mypart = fix + (size_t)(sp.slot0 + pidx) * CHUNK_ROWS;   // split, pidx: from the piece's split / part word
-  if (mine) {
+  F2* mypart = fix + (size_t)(sp.slot0 + pidx) * CHUNK_ROWS + RL * q;   // split, pidx: from the piece's split / part word
 #pragma unroll
-    for (int u = 0; u < RL; ++u) {
-      const int r = RL * q + u;
-      if (r < R) mypart[r] = F2{acc.v[u].hi, acc.v[u].lo};
-    }
-  }
+  for (int u = 0; u < RL; ++u)
+    if (u < nr) mypart[u] = F2{acc.v[u].hi, acc.v[u].lo};
   __threadfence();
   __syncwarp();
   int last = 0;
@@ -513,19 +533,20 @@ __device__ __noinline__ void rs_emit(AccR<RL> acc, int row0, int R, int hflags, 
   last = __shfl_sync(HM_FULL, last, 0);
   if (!last) return;
   __threadfence();
-  if (mine) {
+  if (nr > 0) {
 #pragma unroll
-    for (int u = 0; u < RL; ++u) {
-      const int r = RL * q + u;
-      if (r < R) {
-        FF t = {0.f, 0.f};
-        for (int k = 0; k < sp.nparts; ++k) {
-          const float2 v = __ldcg(reinterpret_cast<const float2*>(fix + (size_t)(sp.slot0 + k) * CHUNK_ROWS + r));
-          t = ff_add(t, FF{v.x, v.y});
-        }
-        rs_store<MODE>(row0 + r, t, alpha, beta, y, perm, vout, rowscale, calpha);
-      }
+    for (int u = 0; u < RL; ++u) acc.v[u] = FF{0.f, 0.f};
+    const F2* base = fix + (size_t)sp.slot0 * CHUNK_ROWS + RL * q;
+    for (int k = 0; k < sp.nparts; ++k) {   // the rows of one part: independent loads, then the sums
+      float2 v[RL];
+#pragma unroll
+      for (int u = 0; u < RL; ++u)
+        v[u] = u < nr ? __ldcg(reinterpret_cast<const float2*>(base + (size_t)k * CHUNK_ROWS + u))
+                      : make_float2(0.f, 0.f);
+#pragma unroll
+      for (int u = 0; u < RL; ++u) acc.v[u] = ff_add(acc.v[u], FF{v[u].x, v[u].y});
     }
+    rs_store_rows<MODE, RL>(acc, row0 + RL * q, nr, alpha_ff, beta, y, perm, vout, rowscale, calpha);
   }
   if (lane == 0) fixcnt[split] = 0;   // ready for the next product
 }
@@ -535,7 +556,7 @@ __global__ void __launch_bounds__(NW * 32, 1)
     k_rstream(const PieceCopy* __restrict__ cps, const int32_t* __restrict__ wbeg, int nwt,
               const uint8_t* __restrict__ pay, const float2* __restrict__ vec, double alpha, F2 alpha_ff,
               double beta, double* __restrict__ y, const int32_t* __restrict__ perm, float2* __restrict__ vout,
-              const double* __restrict__ rowscale, F2* __restrict__ fix, int32_t* __restrict__ fixcnt,
+              const F2* __restrict__ rowscale, F2* __restrict__ fix, int32_t* __restrict__ fixcnt,
               const Split* __restrict__ splits, int* err) {
   extern __shared__ __align__(128) uint8_t smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -636,7 +657,7 @@ __global__ void __launch_bounds__(NW * 32, 1)
         a8.v[2 * k + 1] = FF{ahi[k].y, alo[k].y};
       }
       rs_emit<MODE, RL>(a8, H.row0, H.nrows, H.flags | ((rinfo.x & PD_SPLIT) ? 0x10000 : 0), rinfo.y >> 8,
-                        rinfo.y & 0xff, lane, alpha, beta, y, perm, vout, rowscale, fix, fixcnt, splits);
+                        rinfo.y & 0xff, lane, alpha_ff, beta, y, perm, vout, rowscale, fix, fixcnt, splits);
     }
     __syncwarp();
     if (issued < n) issue(issued);
@@ -805,7 +826,7 @@ cudaError_t launch_gsum(const GsumOut* outs, int nouts, const F2* pscale, const 
 template <int NW, int NS>
 void rgemv_shape(int tier, int mode, const PieceCopy* pieces, const int32_t* wbeg, int nw, const uint8_t* pay,
                  const float2* vec, double alpha, F2 alpha_ff, double beta, double* y, const int32_t* perm,
-                 float2* vout, const double* rowscale, F2* fix, int32_t* fixcnt, const Split* splits, int* err,
+                 float2* vout, const F2* rowscale, F2* fix, int32_t* fixcnt, const Split* splits, int* err,
                  cudaStream_t st) {
   const int grid = (nw + NW - 1) / NW;
 #define HM_RG(T, M)                                                                                         \
@@ -825,7 +846,7 @@ void rgemv_shape(int tier, int mode, const PieceCopy* pieces, const int32_t* wbe
 
 cudaError_t launch_rgemv(int tier, int mode, int cfg, const PieceCopy* pieces, const int32_t* wbeg, int nw,
                          const uint8_t* pay, const float2* vec, double alpha, F2 alpha_ff, double beta, double* y,
-                         const int32_t* perm, float2* vout, const double* rowscale, F2* fix, int32_t* fixcnt,
+                         const int32_t* perm, float2* vout, const F2* rowscale, F2* fix, int32_t* fixcnt,
                          const Split* splits, int* err, cudaStream_t st) {
   if (nw <= 0) return cudaSuccess;
   switch (cfg) {

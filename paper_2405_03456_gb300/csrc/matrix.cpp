@@ -23,7 +23,7 @@ cudaError_t launch_gsum(const GsumOut* outs, int nouts, const F2* pscale, const 
                         cudaStream_t st);
 cudaError_t launch_rgemv(int tier, int mode, int cfg, const PieceCopy* pieces, const int32_t* wbeg, int nw,
                          const uint8_t* pay, const float2* vec, double alpha, F2 alpha_ff, double beta, double* y,
-                         const int32_t* perm, float2* vout, const double* rowscale, F2* fix, int32_t* fixcnt,
+                         const int32_t* perm, float2* vout, const F2* rowscale, F2* fix, int32_t* fixcnt,
                          const Split* splits, int* err, cudaStream_t st);
 cudaError_t mr_init();
 cudaError_t launch_gather_mr(const double* x, int64_t ldx, int r, const int32_t* perm, int n, float* v,
@@ -86,7 +86,8 @@ struct hm_matrix {
   DevArr<int32_t> d_wbeg;
   DevArr<int32_t> d_fan;
   DevArr<Split> d_splits;
-  DevArr<double> d_rowscale;
+  DevArr<double> d_rowscale;   // multi-RHS kernels
+  DevArr<F2> d_rowscale_ff;     // the same scales as float-float pairs (single-RHS kernels)
   DevArr<int32_t> d_perm;
   F2* d_fix = nullptr;         // row sums of the parts of chunks shared by warps
   float* d_vmr = nullptr;      // multi-RHS vectors: nvec x RP (FP32 tier)
@@ -150,6 +151,7 @@ struct hm_matrix {
     d_fan.release();
     d_splits.release();
     d_rowscale.release();
+    d_rowscale_ff.release();
     d_perm.release();
     if (d_fix) cudaFree(d_fix);
     if (d_fixcnt) cudaFree(d_fixcnt);
@@ -202,6 +204,11 @@ hm_status upload(hm_matrix* M) {
   UP(d_fan, P.fan_src)
   UP(d_splits, P.splits)
   UP(d_rowscale, P.rowscale)
+  {
+    std::vector<F2> rs(P.rowscale.size());
+    for (size_t i = 0; i < rs.size(); ++i) rs[i] = split_ff(P.rowscale[i]);
+    UP(d_rowscale_ff, rs)
+  }
 #undef UP
   std::vector<int32_t> perm(M->H.n);
   for (int64_t i = 0; i < M->H.n; ++i) perm[i] = (int32_t)M->H.ct.perm[i];
@@ -332,7 +339,7 @@ static cudaError_t run_launch(hm_matrix* M, const Launch& L, double alpha, const
     case Launch::RGEMV:
       return launch_rgemv(P.tier, L.mode, cf, M->d_pieces.p + (size_t)cf * P.npieces, M->d_wbeg.p + L.woff[cf],
                           L.nw[cf], M->d_pay.p, M->d_vec, alpha, aff, beta, y, M->d_perm.p, M->d_vec,
-                          L.use_rowscale ? M->d_rowscale.p : nullptr, M->d_fix, M->d_fixcnt, M->d_splits.p,
+                          L.use_rowscale ? M->d_rowscale_ff.p : nullptr, M->d_fix, M->d_fixcnt, M->d_splits.p,
                           M->d_err, st);
   }
   return cudaErrorInvalidValue;
@@ -642,9 +649,9 @@ hm_status hm_info(const hm_matrix* M, hm_info_t* o) {
   o->bytes_payload = (int64_t)P.pk.pay.size();
   o->bytes_values = P.pk.value_bytes;
   o->bytes_meta = P.pk.meta_bytes +
-                  (int64_t)(P.items.size() * sizeof(ItemCopy) + NCFG * P.npieces * sizeof(PieceCopy) +
+                  (int64_t)(P.items.size() * sizeof(ItemCopy) + NSHAPES * P.npieces * sizeof(PieceCopy) +
                             P.wbeg.size() * 4 + P.splits.size() * sizeof(Split) + P.gouts.size() * sizeof(GsumOut) +
-                            P.pscale.size() * 8 + P.rowscale.size() * 8 + P.fan_src.size() * 4) +
+                            P.pscale.size() * 8 + P.rowscale.size() * 16 + P.fan_src.size() * 4) +
                   H.n * 4;
   o->bytes_workspace = P.nvec * 8 + P.npartial * 8 + P.nfix * CHUNK_ROWS * 8;
   if (M->d_vmr)

@@ -1005,6 +1005,12 @@ bool build_program(const HostMatrix& H, int codec, double eps, int valr, int nsm
     return false;
   }
   finish_launches(cx);
+  // levels without work (empty top levels of the sweeps) launch nothing
+  P.launches.erase(std::remove_if(P.launches.begin(), P.launches.end(),
+                                  [](const Launch& L) {
+                                    return L.n == 0 && !(L.kind == Launch::RGEMV && L.mode == MODE_Y);
+                                  }),
+                   P.launches.end());
   return true;
 }
 
