@@ -414,6 +414,16 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32
   return false;
 }
 
+// Arrival on a counter at GPU scope with release semantics (this thread's
+// earlier writes, and those of threads ordered before it by a barrier, become
+// visible to whoever acquires the counter) and acquire semantics (writes
+// released by earlier arrivals become visible to this thread).
+__device__ __forceinline__ int atom_add_acq_rel(int* p, int v) {
+  int old;
+  asm volatile("atom.acq_rel.gpu.global.add.s32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+
 // Order this thread's earlier generic-proxy shared-memory accesses before its
 // later async-proxy (bulk copy) writes.
 __device__ __forceinline__ void fence_proxy_async() {

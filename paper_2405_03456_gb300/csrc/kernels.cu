@@ -177,10 +177,10 @@ __device__ __forceinline__ void cs_piece(uint32_t sa, int R, int nc, int flags, 
 
 // FP32-tier column-dot piece: lanes (g, q) = (lane / 8, lane % 8) take rows
 // 8q .. 8q+7 of the columns g, g + 4, ...; two columns per step (independent
-// decodes), products summed in FP32 pairs, the partials rotated down two
-// registers per step so that after 4 steps p[t] holds column g + 4t; a round
-// of 32 columns ends with the reduce-scatter over the 8 lanes.  Steps past the
-// last column are skipped as a whole; a ragged step masks its results.
+// decodes), products summed in FP32 pairs; the 4 steps of a round are unrolled
+// so that p[t] holds column g + 4t; a round of 32 columns ends with the
+// reduce-scatter over the 8 lanes.  Steps past the last column are skipped as a
+// whole; a ragged step masks its results.
 template <int F, int B>
 __device__ __forceinline__ void cs_piece_f32(uint32_t sa, int R, int nc, int flags, const float2 (&x2)[4], int lane,
                                              F2 alpha, F2* __restrict__ partial, float2* __restrict__ vout) {
@@ -200,7 +200,7 @@ __device__ __forceinline__ void cs_piece_f32(uint32_t sa, int R, int nc, int fla
       pc[t] = 0.f;
     }
     const int tmax = (nc - j0 + NG - 1) / NG;   // steps holding a column (same for the warp)
-#pragma unroll 1
+#pragma unroll
     for (int t = 0; t < 8; t += 2) {
       float r[2] = {0.f, 0.f};
       if (t < tmax) {
@@ -224,10 +224,8 @@ __device__ __forceinline__ void cs_piece_f32(uint32_t sa, int R, int nc, int fla
           r[h] = v ? a2.x + a2.y : 0.f;
         }
       }
-#pragma unroll
-      for (int k = 0; k < 6; ++k) p[k] = p[k + 2];
-      p[6] = r[0];
-      p[7] = r[1];
+      p[t] = r[0];
+      p[t + 1] = r[1];
     }
     reduce_scatter8<TIER_F32, 8>(p, pc, q);
     const int j = j0 + g + NG * q;
@@ -526,13 +524,12 @@ __device__ __noinline__ void rs_emit(AccR<RL> acc, int row0, int R, int hflags, 
 #pragma unroll
   for (int u = 0; u < RL; ++u)
     if (u < nr) mypart[u] = F2{acc.v[u].hi, acc.v[u].lo};
-  __threadfence();
-  __syncwarp();
+  __syncwarp();   // the part's rows before lane 0's release
   int last = 0;
-  if (lane == 0) last = atomicAdd(&fixcnt[split], 1) == sp.nparts - 1;
+  if (lane == 0) last = atom_add_acq_rel(&fixcnt[split], 1) == sp.nparts - 1;
   last = __shfl_sync(HM_FULL, last, 0);
   if (!last) return;
-  __threadfence();
+  __syncwarp();   // lane 0's acquire before the lanes read the other parts
   if (nr > 0) {
 #pragma unroll
     for (int u = 0; u < RL; ++u) acc.v[u] = FF{0.f, 0.f};

@@ -35,7 +35,7 @@ cudaError_t launch_cdot_mr(const ItemCopy* items, const int32_t* wbeg, int nblk,
                            F2 alpha, float* partial, float* vout, int* err, cudaStream_t st);
 cudaError_t launch_rgemv_mr(int mode, const PieceCopy* pieces, const int32_t* wbeg, int nblk, const uint8_t* pay,
                             const float* vec, double alpha, F2 alpha_ff, double beta, double* y, int64_t ldy, int r,
-                            const int32_t* perm, float* vout, const double* rowscale, F2* fix, int32_t* fixcnt,
+                            const int32_t* perm, float* vout, const F2* rowscale, F2* fix, int32_t* fixcnt,
                             const Split* splits, int* err, cudaStream_t st);
 cudaError_t launch_decode(const uint8_t* p, int64_t n, int B, int fmt, int e, int m, double vmin,
                           double* out, cudaStream_t st);
@@ -86,8 +86,7 @@ struct hm_matrix {
   DevArr<int32_t> d_wbeg;
   DevArr<int32_t> d_fan;
   DevArr<Split> d_splits;
-  DevArr<double> d_rowscale;   // multi-RHS kernels
-  DevArr<F2> d_rowscale_ff;     // the same scales as float-float pairs (single-RHS kernels)
+  DevArr<F2> d_rowscale_ff;     // row scales of coefficient vectors (float-float pairs)
   DevArr<int32_t> d_perm;
   F2* d_fix = nullptr;         // row sums of the parts of chunks shared by warps
   float* d_vmr = nullptr;      // multi-RHS vectors: nvec x RP (FP32 tier)
@@ -150,7 +149,6 @@ struct hm_matrix {
     d_wbeg.release();
     d_fan.release();
     d_splits.release();
-    d_rowscale.release();
     d_rowscale_ff.release();
     d_perm.release();
     if (d_fix) cudaFree(d_fix);
@@ -203,7 +201,6 @@ hm_status upload(hm_matrix* M) {
   UP(d_wbeg, P.wbeg)
   UP(d_fan, P.fan_src)
   UP(d_splits, P.splits)
-  UP(d_rowscale, P.rowscale)
   {
     std::vector<F2> rs(P.rowscale.size());
     for (size_t i = 0; i < rs.size(); ++i) rs[i] = split_ff(P.rowscale[i]);
@@ -365,7 +362,7 @@ static cudaError_t run_launch_mr(hm_matrix* M, const Launch& L, double alpha, co
     case Launch::RGEMV:
       return launch_rgemv_mr(L.mode, M->d_pieces.p + (size_t)MR_SHAPE * P.npieces, M->d_wbeg.p + L.woff[MR_SHAPE],
                              L.nw[MR_SHAPE], M->d_pay.p, M->d_vmr, alpha, aff, beta, y, ldy, r, M->d_perm.p,
-                             M->d_vmr, L.use_rowscale ? M->d_rowscale.p : nullptr, M->d_fixmr, M->d_fixcnt,
+                             M->d_vmr, L.use_rowscale ? M->d_rowscale_ff.p : nullptr, M->d_fixmr, M->d_fixcnt,
                              M->d_splits.p, M->d_err, st);
   }
   return cudaErrorInvalidValue;
@@ -651,7 +648,7 @@ hm_status hm_info(const hm_matrix* M, hm_info_t* o) {
   o->bytes_meta = P.pk.meta_bytes +
                   (int64_t)(P.items.size() * sizeof(ItemCopy) + NSHAPES * P.npieces * sizeof(PieceCopy) +
                             P.wbeg.size() * 4 + P.splits.size() * sizeof(Split) + P.gouts.size() * sizeof(GsumOut) +
-                            P.pscale.size() * 8 + P.rowscale.size() * 16 + P.fan_src.size() * 4) +
+                            P.pscale.size() * 8 + P.rowscale.size() * 8 + P.fan_src.size() * 4) +
                   H.n * 4;
   o->bytes_workspace = P.nvec * 8 + P.npartial * 8 + P.nfix * CHUNK_ROWS * 8;
   if (M->d_vmr)

@@ -381,28 +381,11 @@ __device__ __forceinline__ void mr_rgemv_decode(uint32_t sa, uint32_t ta, const 
 }
 
 template <int MODE>
-__device__ __forceinline__ void mr_store(int g, int k, FF t, double alpha, double beta, double* __restrict__ y,
-                                         int64_t ldy, const int32_t* __restrict__ perm, float* __restrict__ vout,
-                                         const double* __restrict__ rowscale, bool calpha) {
-  double val = ff_to_d(t);
-  if constexpr (MODE == MODE_Y) {
-    double* p = y + perm[g] + (int64_t)k * ldy;
-    *p = (beta == 0.0) ? val : fma(beta, *p, val);
-  } else {
-    float* p = vout + (int64_t)g * RP + k;
-    if constexpr (MODE == MODE_VEC_ADD) val += (double)*p;
-    if (rowscale) val *= rowscale[g];
-    if (calpha) val *= alpha;
-    *p = (float)val;
-  }
-}
-
-template <int MODE>
 __global__ void __launch_bounds__(MR_THREADS, MR_BLOCKS_PER_SM)
     k_rgemv_mr(const PieceCopy* __restrict__ cps, const int32_t* __restrict__ wbeg, int nblk,
                const uint8_t* __restrict__ pay, const float* __restrict__ vec, double alpha, F2 alpha_ff,
                double beta, double* __restrict__ y, int64_t ldy, int r, const int32_t* __restrict__ perm,
-               float* __restrict__ vout, const double* __restrict__ rowscale, F2* __restrict__ fix,
+               float* __restrict__ vout, const F2* __restrict__ rowscale, F2* __restrict__ fix,
                int32_t* __restrict__ fixcnt, const Split* __restrict__ splits, int* err) {
   extern __shared__ __align__(128) uint8_t smem[];
   __shared__ int4 info[MR_STAGES];
@@ -549,34 +532,87 @@ __global__ void __launch_bounds__(MR_THREADS, MR_BLOCKS_PER_SM)
       }
       bool emit = !split;
       if (split) {
-        __threadfence();
-        __syncthreads();
-        if (threadIdx.x == 0) s_last = atomicAdd(&fixcnt[rinfo.y >> 8], 1) == sp.nparts - 1;
-        __syncthreads();
+        __syncthreads();   // every thread's part rows before thread 0's release
+        if (threadIdx.x == 0) s_last = atom_add_acq_rel(&fixcnt[rinfo.y >> 8], 1) == sp.nparts - 1;
+        __syncthreads();   // thread 0's acquire before the threads read the other parts
         emit = s_last != 0;
-        if (emit) __threadfence();
       }
       if (emit) {
+        // the thread's elements of pair sp2: rows 16 (p / NT) + g + 8 hr, right-hand
+        // sides 8 (p % NT) + 2 tq + c, held as (ahi, alo)[sp2][hr].{x, y}; per pair
+        // all global loads of a phase are issued before their values are used
 #pragma unroll
-        for (int sp2 = 0; sp2 < MR_PAIRS; ++sp2)
+        for (int sp2 = 0; sp2 < MR_PAIRS; ++sp2) {
+          const int p = w + 8 * sp2;
+          const int k0 = 8 * (p % NT) + 2 * tq;
+          int row[2];
 #pragma unroll
-          for (int hr = 0; hr < 2; ++hr)
+          for (int hr = 0; hr < 2; ++hr) row[hr] = 16 * (p / NT) + g + 8 * hr;
+          if (16 * (p / NT) >= R) continue;
+          if (split) {   // the parts in part order
 #pragma unroll
-            for (int c = 0; c < 2; ++c) {
-              const int p = w + 8 * sp2;
-              const int row = 16 * (p / NT) + g + 8 * hr, k = 8 * (p % NT) + 2 * tq + c;
-              if (row >= R || k >= r) continue;
-              FF t = {c ? ahi[sp2][hr].y : ahi[sp2][hr].x, c ? alo[sp2][hr].y : alo[sp2][hr].x};
-              if (split) {
-                t = FF{0.f, 0.f};
-                for (int part = 0; part < sp.nparts; ++part) {
-                  const float2 v = __ldcg(reinterpret_cast<const float2*>(
-                      fix + ((size_t)(sp.slot0 + part) * CHUNK_ROWS + row) * RP + k));
-                  t = ff_add(t, FF{v.x, v.y});
-                }
-              }
-              mr_store<MODE>(H.row0 + row, k, t, alpha, beta, y, ldy, perm, vout, rowscale, calpha);
+            for (int hr = 0; hr < 2; ++hr) {
+              ahi[sp2][hr] = make_float2(0.f, 0.f);
+              alo[sp2][hr] = make_float2(0.f, 0.f);
             }
+            for (int part = 0; part < sp.nparts; ++part) {
+              const F2* src = fix + (size_t)(sp.slot0 + part) * CHUNK_ROWS * RP;
+              float4 v[2];
+#pragma unroll
+              for (int hr = 0; hr < 2; ++hr)
+                v[hr] = row[hr] < R ? __ldcg(reinterpret_cast<const float4*>(src + row[hr] * RP + k0))
+                                    : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+              for (int hr = 0; hr < 2; ++hr) {
+                const FF a = ff_add(FF{ahi[sp2][hr].x, alo[sp2][hr].x}, FF{v[hr].x, v[hr].y});
+                const FF b = ff_add(FF{ahi[sp2][hr].y, alo[sp2][hr].y}, FF{v[hr].z, v[hr].w});
+                ahi[sp2][hr] = make_float2(a.hi, b.hi);
+                alo[sp2][hr] = make_float2(a.lo, b.lo);
+              }
+            }
+          }
+          if constexpr (MODE == MODE_Y) {
+            int o[2];
+            double yo[2][2];
+#pragma unroll
+            for (int hr = 0; hr < 2; ++hr) o[hr] = row[hr] < R ? __ldg(perm + H.row0 + row[hr]) : 0;
+#pragma unroll
+            for (int hr = 0; hr < 2; ++hr)
+#pragma unroll
+              for (int c = 0; c < 2; ++c)
+                yo[hr][c] = (beta != 0.0 && row[hr] < R && k0 + c < r) ? y[o[hr] + (int64_t)(k0 + c) * ldy] : 0.0;
+#pragma unroll
+            for (int hr = 0; hr < 2; ++hr)
+#pragma unroll
+              for (int c = 0; c < 2; ++c)
+                if (row[hr] < R && k0 + c < r) {
+                  const double val = ff_to_d(FF{c ? ahi[sp2][hr].y : ahi[sp2][hr].x, c ? alo[sp2][hr].y : alo[sp2][hr].x});
+                  y[o[hr] + (int64_t)(k0 + c) * ldy] = (beta == 0.0) ? val : fma(beta, yo[hr][c], val);
+                }
+          } else {   // coefficient panels: float-float updates, one rounding to FP32
+            float2 old[2];
+            F2 sc[2];
+#pragma unroll
+            for (int hr = 0; hr < 2; ++hr) {
+              const bool on = row[hr] < R;
+              const int gg = H.row0 + row[hr];
+              old[hr] = (MODE == MODE_VEC_ADD && on) ? *reinterpret_cast<const float2*>(vout + (int64_t)gg * RP + k0)
+                                                     : make_float2(0.f, 0.f);
+              sc[hr] = (rowscale && on) ? rowscale[gg] : F2{1.f, 0.f};
+            }
+#pragma unroll
+            for (int hr = 0; hr < 2; ++hr)
+#pragma unroll
+              for (int c = 0; c < 2; ++c)
+                if (row[hr] < R && k0 + c < r) {
+                  FF v = {c ? ahi[sp2][hr].y : ahi[sp2][hr].x, c ? alo[sp2][hr].y : alo[sp2][hr].x};
+                  if constexpr (MODE == MODE_VEC_ADD) v = ff_add_f(v, c ? old[hr].y : old[hr].x);
+                  if (rowscale) v = ff_mul(v, FF{sc[hr].hi, sc[hr].lo});
+                  if (calpha) v = ff_mul(v, FF{alpha_ff.hi, alpha_ff.lo});
+                  vout[(int64_t)(H.row0 + row[hr]) * RP + k0 + c] = v.hi + v.lo;
+                }
+          }
+        }
       }
       if (split && emit && threadIdx.x == 0) fixcnt[rinfo.y >> 8] = 0;
     }
@@ -633,7 +669,7 @@ cudaError_t launch_cdot_mr(const ItemCopy* items, const int32_t* wbeg, int nblk,
 
 cudaError_t launch_rgemv_mr(int mode, const PieceCopy* pieces, const int32_t* wbeg, int nblk, const uint8_t* pay,
                             const float* vec, double alpha, F2 alpha_ff, double beta, double* y, int64_t ldy, int r,
-                            const int32_t* perm, float* vout, const double* rowscale, F2* fix, int32_t* fixcnt,
+                            const int32_t* perm, float* vout, const F2* rowscale, F2* fix, int32_t* fixcnt,
                             const Split* splits, int* err, cudaStream_t st) {
   if (nblk <= 0) return cudaSuccess;
 #define HM_MRG(M)                                                                                           \

@@ -453,7 +453,10 @@ void add_rgemv(Ctx& cx, std::vector<ChunkWork>& cw, int mode, bool rowscale) {
     add_launch(P, Launch::FANOUT, fan0, (int64_t)P.fan_src.size() - fan0);
   // per launch shape: warp ranges, range flags, shared chunks
   std::vector<int64_t> pb(pw.size());
-  for (size_t i = 0; i < pw.size(); ++i) pb[i] = pw[i].bytes + 8 * pw[i].ncols;
+  for (size_t i = 0; i < pw.size(); ++i) {
+    const bool last_of_chunk = (i + 1 == pw.size()) || pw[i + 1].chunk != pw[i].chunk;
+    pb[i] = pw[i].bytes + 8 * pw[i].ncols + PIECE_COST + (last_of_chunk ? EMIT_COST : 0);
+  }
   int64_t nfix = 0;
   int64_t nfix_mr = 0;
   for (int cf = 0; cf < NSHAPES; ++cf) {
@@ -945,7 +948,7 @@ void finish_launches(Ctx& cx) {
       case Launch::CDOT: {
         std::vector<int64_t> ib((size_t)L.n);
         for (int64_t i = 0; i < L.n; ++i) {
-          ib[i] = P.items[L.off + i].bytes;
+          ib[i] = P.items[L.off + i].bytes + PIECE_COST;
           b += P.item_alg[L.off + i];
         }
         for (int cf = 0; cf < NSHAPES; ++cf) {

@@ -94,7 +94,13 @@ struct Program {
   int64_t fp64_lowrank = 0, fp64_dense = 0;
 };
 
-constexpr int64_t MIN_WARP_BYTES = 16384;   // smallest share of a launch worth a warp
+constexpr int64_t MIN_WARP_BYTES = 4096;    // smallest share of a launch worth a warp
+// Work-split weights: a warp's time is about (bytes + PIECE_COST per piece +
+// EMIT_COST per chunk it finishes) / its streaming rate (measured per-warp
+// timelines: about 0.3 us of fixed cost per piece and 1-2 us per finished chunk
+// at about 4 bytes per ns and warp).
+constexpr int64_t PIECE_COST = 1024;
+constexpr int64_t EMIT_COST = 4096;
 
 // Pack a built matrix with `codec` at accuracy eps (VALR if valr) and build its
 // launch program for a GPU with nsm multiprocessors.  Returns false if a value
