@@ -671,24 +671,37 @@ __global__ void k_fanout(const int32_t* __restrict__ src, int n, float2* __restr
 
 // ---------------------------------------------------------------- segment sums (phase A2)
 // One thread per coefficient: fixed-order float-float sum of its contiguous partials.
+// Segment sums: GS_LANES lanes per output; lane k sums the partials p0 + k,
+// p0 + k + GS_LANES, ... (consecutive lanes read consecutive partials), then a
+// fixed xor tree combines the lanes (deterministic order).
+constexpr int GS_LANES = 8;
 __global__ void k_gsum(const GsumOut* __restrict__ outs, int nouts, const F2* __restrict__ pscale,
                        const F2* __restrict__ partial, F2 alpha, float2* __restrict__ vout) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= nouts) return;
-  const GsumOut O = outs[i];
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = t / GS_LANES, k = t % GS_LANES;
+  const bool on = i < nouts;
+  GsumOut O{};
+  if (on) O = outs[i];
   FF s = {0.f, 0.f};
   if (O.flags & 2) {
-    for (int p = O.p0; p < O.p1; ++p) {
+    for (int p = O.p0 + k; p < O.p1; p += GS_LANES) {
       const F2 v = partial[p];
       const F2 w = pscale[O.ps + (p - O.p0)];
       s = ff_add(s, ff_mul(FF{v.hi, v.lo}, FF{w.hi, w.lo}));
     }
   } else {
-    for (int p = O.p0; p < O.p1; ++p) {
+    for (int p = O.p0 + k; p < O.p1; p += GS_LANES) {
       const F2 v = partial[p];
       s = ff_add(s, FF{v.hi, v.lo});
     }
   }
+#pragma unroll
+  for (int m = GS_LANES / 2; m >= 1; m >>= 1) {   // whole warps: every lane takes part
+    const float hi = __shfl_xor_sync(HM_FULL, s.hi, m);
+    const float lo = __shfl_xor_sync(HM_FULL, s.lo, m);
+    s = (k & m) ? ff_add(FF{hi, lo}, s) : ff_add(s, FF{hi, lo});
+  }
+  if (!on || k != 0) return;
   s = ff_mul(s, FF{O.scale.hi, O.scale.lo});
   if (O.flags & 1) s = ff_mul(s, FF{alpha.hi, alpha.lo});
   vout[O.out] = make_float2(s.hi, s.lo);
@@ -816,7 +829,8 @@ cudaError_t launch_fanout(const int32_t* src, int n, float2* dst, const float2* 
 cudaError_t launch_gsum(const GsumOut* outs, int nouts, const F2* pscale, const F2* partial, F2 alpha, float2* vout,
                         cudaStream_t st) {
   if (nouts <= 0) return cudaSuccess;
-  k_gsum<<<(nouts + 255) / 256, 256, 0, st>>>(outs, nouts, pscale, partial, alpha, vout);
+  const int64_t threads = (int64_t)nouts * GS_LANES;
+  k_gsum<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(outs, nouts, pscale, partial, alpha, vout);
   return cudaGetLastError();
 }
 

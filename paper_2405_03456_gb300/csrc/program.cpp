@@ -948,7 +948,7 @@ void finish_launches(Ctx& cx) {
       case Launch::CDOT: {
         std::vector<int64_t> ib((size_t)L.n);
         for (int64_t i = 0; i < L.n; ++i) {
-          ib[i] = P.items[L.off + i].bytes + PIECE_COST;
+          ib[i] = P.items[L.off + i].bytes + CPIECE_COST;
           b += P.item_alg[L.off + i];
         }
         for (int cf = 0; cf < NSHAPES; ++cf) {

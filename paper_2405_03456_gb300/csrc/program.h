@@ -95,12 +95,14 @@ struct Program {
 };
 
 constexpr int64_t MIN_WARP_BYTES = 4096;    // smallest share of a launch worth a warp
-// Work-split weights: a warp's time is about (bytes + PIECE_COST per piece +
-// EMIT_COST per chunk it finishes) / its streaming rate (measured per-warp
-// timelines: about 0.3 us of fixed cost per piece and 1-2 us per finished chunk
-// at about 4 bytes per ns and warp).
-constexpr int64_t PIECE_COST = 1024;
-constexpr int64_t EMIT_COST = 4096;
+// Work-split weights: a warp's time grows with its bytes, with its pieces
+// (header, input segment, reduction, outputs: column-dot pieces cost several
+// times more than row-chunk pieces) and with the chunks it finishes.  The
+// constants are in byte equivalents; measured per-warp timelines of the
+// headline H product are flat (within noise) from half to twice these values.
+constexpr int64_t PIECE_COST = 2048;    // row-chunk pieces
+constexpr int64_t CPIECE_COST = 8192;   // column-dot pieces
+constexpr int64_t EMIT_COST = 8192;     // finished row chunks
 
 // Pack a built matrix with `codec` at accuracy eps (VALR if valr) and build its
 // launch program for a GPU with nsm multiprocessors.  Returns false if a value
