@@ -117,6 +117,20 @@ hm_status hm_matvec_host(hm_matrix* m, double alpha, const double* x, double bet
  */
 hm_status hm_graph(hm_matrix* m, int32_t enable);
 
+/*
+ * hm_persistent -- enable (nonzero, the default) or disable persistent
+ * launches.  When enabled, every run of two or more consecutive row-chunk
+ * launches (the row-chunk form of Alg. 3 / 5 / 7 and the sweeps of Alg. 6 / 7,
+ * one launch per tree level) and the multiplier fan-outs between them execute
+ * as the phases of ONE cooperative launch with one block per SM: the blocks
+ * meet at a grid barrier between phases (bounded wait; a barrier that does not
+ * complete latches HM_ERR_TIMEOUT, read by hm_sync_status).  The phases use the
+ * warp ranges of launch shape 0 whatever hm_autotune chose.  Results equal the
+ * per-launch path with all shapes 0 bit for bit.  Profiling (hm_profile)
+ * always uses the per-launch path.  Errors: HM_ERR_ARG.
+ */
+hm_status hm_persistent(hm_matrix* m, int32_t enable);
+
 /* hm_free -- release host and device memory of m (NULL is accepted). */
 hm_status hm_free(hm_matrix* m);
 

@@ -58,6 +58,25 @@ constexpr int RP = 32;
 constexpr int MR_BLOCKS_PER_SM = 2;
 constexpr int MR_SHAPE = NCFG;
 constexpr int NSHAPES = NCFG + 1;
+constexpr int SEQ_SHAPE = 0;               // row-chunk shape of the persistent (multi-phase) launch
+
+// One phase of a persistent launch: a row-chunk launch's warp ranges of shape
+// SEQ_SHAPE.
+struct SeqPhase {
+  int32_t mode;      // output mode
+  int32_t woff;      // range starts wbeg[woff .. woff + nw]
+  int32_t nw;
+  int32_t rowscale;  // 1: scale the rows by the row-scale vector
+};
+
+// Dependencies of one piece of a persistent launch, as versions of coefficient
+// chunks (a version counts the emits of the chunk so far in the launch): the
+// piece's multipliers are final once ver[c0] >= v0 (c0 < 0: written before the
+// launch), and its own chunk (c1, whose emit increments ver[c1]) holds the
+// value it adds to once ver[c1] >= v1.
+struct SeqDep {
+  int32_t c0, v0, c1, v1;
+};
 constexpr int STAGE_BYTES = 6144;          // payload bytes of one stage (item / piece incl. header)
 constexpr int SEG_ROWS = 64;               // rows of a column-dot segment
 constexpr int CHUNK_ROWS = 128;            // rows of a row chunk

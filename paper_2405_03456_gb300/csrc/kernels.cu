@@ -32,8 +32,11 @@ __device__ __forceinline__ uint32_t pad16u(uint32_t x) { return (x + 15u) & ~15u
 // After a bounded wait gave up: wait (bounded) for the copies still in flight
 // into this warp's stages [i, issued) so that none lands after the block exits.
 template <int NS>
-__device__ void drain(uint64_t* bars, int i, int issued) {
-  for (int j = i; j < issued; ++j) mbar_wait(&bars[j % NS], (uint32_t)((j / NS) & 1), 50u);
+__device__ void drain(uint64_t* bars, int i, int issued, uint32_t it0 = 0) {
+  for (int j = i; j < issued; ++j) {
+    const uint32_t u = it0 + (uint32_t)j;
+    mbar_wait(&bars[u % NS], (u / NS) & 1u, 50u);
+  }
 }
 
 // ---------------------------------------------------------------- column dots (phase A)
@@ -467,7 +470,7 @@ __device__ __forceinline__ void rs_store_rows(const AccR<RL>& acc, int g0, int n
     float2 old[RL], sc[RL];
 #pragma unroll
     for (int u = 0; u < RL; ++u) {
-      old[u] = (MODE == MODE_VEC_ADD && u < nr) ? vout[g0 + u] : make_float2(0.f, 0.f);
+      old[u] = (MODE == MODE_VEC_ADD && u < nr) ? __ldcg(vout + g0 + u) : make_float2(0.f, 0.f);
       sc[u] = (rowscale && u < nr) ? __ldg(reinterpret_cast<const float2*>(rowscale + g0 + u)) : make_float2(1.f, 0.f);
     }
 #pragma unroll
@@ -490,7 +493,7 @@ __device__ __forceinline__ void rs_store_rows(const AccR<RL>& acc, int g0, int n
 // depend on which warp finishes last).
 // Out of line: it runs once per part and keeps the piece loop compact.
 template <int MODE, int RL>
-__device__ __noinline__ void rs_emit(AccR<RL> acc, int row0, int R, int hflags, int split, int pidx, int lane,
+__device__ __noinline__ bool rs_emit(AccR<RL> acc, int row0, int R, int hflags, int split, int pidx, int lane,
                                      F2 alpha_ff, double beta, double* __restrict__ y,
                                      const int32_t* __restrict__ perm, float2* __restrict__ vout,
                                      const F2* __restrict__ rowscale, F2* __restrict__ fix,
@@ -517,7 +520,7 @@ __device__ __noinline__ void rs_emit(AccR<RL> acc, int row0, int R, int hflags, 
   const bool calpha = (hflags & PH_CALPHA) != 0;
   if (!(hflags & 0x10000)) {   // not shared with other warps
     if (nr > 0) rs_store_rows<MODE, RL>(acc, row0 + RL * q, nr, alpha_ff, beta, y, perm, vout, rowscale, calpha);
-    return;
+    return true;
   }
   const Split sp = splits[split];
   F2* mypart = fix + (size_t)(sp.slot0 + pidx) * CHUNK_ROWS + RL * q;   // split, pidx: from the piece's split / part word
@@ -528,7 +531,7 @@ __device__ __noinline__ void rs_emit(AccR<RL> acc, int row0, int R, int hflags, 
   int last = 0;
   if (lane == 0) last = atom_add_acq_rel(&fixcnt[split], 1) == sp.nparts - 1;
   last = __shfl_sync(HM_FULL, last, 0);
-  if (!last) return;
+  if (!last) return false;
   __syncwarp();   // lane 0's acquire before the lanes read the other parts
   if (nr > 0) {
 #pragma unroll
@@ -546,40 +549,72 @@ __device__ __noinline__ void rs_emit(AccR<RL> acc, int row0, int R, int hflags, 
     rs_store_rows<MODE, RL>(acc, row0 + RL * q, nr, alpha_ff, beta, y, perm, vout, rowscale, calpha);
   }
   if (lane == 0) fixcnt[split] = 0;   // ready for the next product
+  return true;
 }
 
-template <int TIER, int MODE, int NW, int NS>
-__global__ void __launch_bounds__(NW * 32, 1)
-    k_rstream(const PieceCopy* __restrict__ cps, const int32_t* __restrict__ wbeg, int nwt,
-              const uint8_t* __restrict__ pay, const float2* __restrict__ vec, double alpha, F2 alpha_ff,
-              double beta, double* __restrict__ y, const int32_t* __restrict__ perm, float2* __restrict__ vout,
-              const F2* __restrict__ rowscale, F2* __restrict__ fix, int32_t* __restrict__ fixcnt,
-              const Split* __restrict__ splits, int* err) {
-  extern __shared__ __align__(128) uint8_t smem[];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int gw = blockIdx.x * NW + warp;
-  if (gw >= nwt) return;
-  const int p0 = wbeg[gw], n = wbeg[gw + 1] - p0;
-  if (n <= 0) return;
-  uint8_t* ring = smem + (size_t)warp * NS * C_STAGE;
-  const uint32_t sring = smem_u32(ring);
-  int4* info = reinterpret_cast<int4*>(smem + (size_t)NW * NS * C_STAGE) + warp * NS;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + (size_t)NW * NS * (C_STAGE + C_INFO)) + warp * NS;
-  if (lane == 0) {
-    for (int s = 0; s < NS; ++s) mbar_init(&bars[s], 1);
-    mbar_init_fence();
+// Arguments of the row-chunk products shared by every range of a launch.
+struct RsArgs {
+  const PieceCopy* cps;
+  const uint8_t* pay;
+  const float2* vec;
+  double alpha;
+  F2 alpha_ff;
+  double beta;
+  double* y;
+  const int32_t* perm;
+  float2* vout;
+  const F2* rowscale;
+  F2* fix;
+  int32_t* fixcnt;
+  const Split* splits;
+  int* err;
+};
+
+// Dataflow state of a persistent launch: per-piece dependencies, versions of
+// the coefficient chunks, and an abort word (set on the first timeout, so that
+// every other wait gives up at once).
+struct DfArgs {
+  const SeqDep* deps;
+  unsigned* ver;
+  int* abort;
+};
+
+// Wait (lane 0, bounded) until chunk c has reached version v; acquire.
+__device__ __forceinline__ bool wait_version(const DfArgs& D, int c, int v) {
+  if (c < 0 || v <= 0) return true;
+  for (uint32_t i = 0; i < (1u << 22); ++i) {   // each try is an L2 round trip: about 2 s in all
+    unsigned x;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(x) : "l"(D.ver + c) : "memory");
+    if ((int)x >= v) return true;
+    if ((i & 255u) == 255u && *(volatile int*)D.abort) return false;
   }
-  __syncwarp();
+  atomicExch(D.abort, 1);
+  return false;
+}
+
+// One warp's range of row-chunk pieces [p0, p0 + n): a ring of NS shared-memory
+// stages filled by bulk copies (piece + its multiplier run), decoded and summed
+// into float-float row sums, emitted at the end of each chunk.  it counts the
+// stages this warp has used before (their mbarrier phases), and is advanced.
+// DF (persistent launches): a piece's payload is copied at once, its
+// multipliers only after the chunks it depends on have reached their versions;
+// every emit of a coefficient chunk then publishes the next version.
+// Returns false if a copy or a dependency did not arrive in time (error latched).
+template <int TIER, int MODE, int NS, bool DF = false>
+__device__ __forceinline__ bool rs_range(const RsArgs& A, int p0, int n, uint8_t* ring, int4* info,
+                                         uint64_t* bars, int lane, uint32_t& it, const DfArgs* D = nullptr) {
+  const uint32_t sring = smem_u32(ring);
   const PieceCopy zero{0, 0, 0, -1};
-  PieceCopy dc = lane < n ? cps[p0 + lane] : zero;
-  PieceCopy dn = 32 + lane < n ? cps[p0 + 32 + lane] : zero;
+  PieceCopy dc = lane < n ? A.cps[p0 + lane] : zero;
+  PieceCopy dn = 32 + lane < n ? A.cps[p0 + 32 + lane] : zero;
   int dbase = 0, issued = 0;
   const uint64_t pol = policy_evict_first();
-  auto issue = [&](int i) {   // all lanes; copies piece i and its multipliers into stage i % NS
+  const uint32_t it0 = it;
+  auto issue = [&](int i) {   // all lanes; copies piece i and its multipliers into stage (it0 + i) % NS
     if (i - dbase >= 32) {
       dc = dn;
       dbase += 32;
-      dn = dbase + 32 + lane < n ? cps[p0 + dbase + 32 + lane] : zero;
+      dn = dbase + 32 + lane < n ? A.cps[p0 + dbase + 32 + lane] : zero;
     }
     const int sl = i - dbase;
     const uint32_t off8 = __shfl_sync(HM_FULL, dc.off8, sl);
@@ -587,18 +622,27 @@ __global__ void __launch_bounds__(NW * 32, 1)
     const int32_t moff = __shfl_sync(HM_FULL, dc.moff, sl);
     const int32_t sp = __shfl_sync(HM_FULL, dc.split_part, sl);
     if (lane == 0) {
-      uint8_t* st = ring + (i % NS) * C_STAGE;
-      uint64_t* bar = &bars[i % NS];
+      const uint32_t st_i = (it0 + (uint32_t)i) % NS;
+      uint8_t* st = ring + st_i * C_STAGE;
+      uint64_t* bar = &bars[st_i];
       const uint32_t nc = bf >> 24;
       const uint32_t pb = pad16u(bf & 0xffffu);
       const int64_t m0 = (int64_t)moff & ~int64_t(1);
       const uint32_t mb = nc ? pad16u((uint32_t)((moff - m0) + nc) * 8u) : 0u;
-      info[i % NS] = make_int4((int)((bf >> 16) & 0xffu), sp, moff & 1, 0);
+      int ce = -1;
       fence_proxy_async();
       mbar_expect_tx(bar, pb + mb);
-      bulk_g2s_hint(st, pay + (uint64_t)off8 * 8u, pb, bar, pol);
-      if (mb) bulk_g2s(st + C_MOFF, vec + m0, mb, bar);
+      bulk_g2s_hint(st, A.pay + (uint64_t)off8 * 8u, pb, bar, pol);
+      if constexpr (DF) {
+        const SeqDep d = D->deps[p0 + i];
+        ce = d.c1;
+        if (!(wait_version(*D, d.c0, d.v0) && wait_version(*D, d.c1, d.v1))) latch_error(A.err, 99);
+        asm volatile("fence.proxy.async.global;" ::: "memory");   // the multipliers were written by other SMs
+      }
+      info[st_i] = make_int4((int)((bf >> 16) & 0xffu), sp, moff & 1, ce);
+      if (mb) bulk_g2s(st + C_MOFF, A.vec + m0, mb, bar);   // issued even after a failed wait: the stage completes
     }
+    if constexpr (DF) __syncwarp();   // lane 0's acquires before the lanes' reads of this piece's chunk
     issued = i + 1;
   };
   for (int i = 0; i < NS && i < n; ++i) issue(i);
@@ -610,13 +654,18 @@ __global__ void __launch_bounds__(NW * 32, 1)
     alo[k] = make_float2(0.f, 0.f);
   }
   for (int i = 0; i < n; ++i) {
-    const int s = i % NS;
-    if (!mbar_wait(&bars[s], (uint32_t)((i / NS) & 1))) {
-      latch_error(err, 99);
-      drain<NS>(bars, i + 1, issued);
-      return;
+    const uint32_t u = it0 + (uint32_t)i;
+    const uint32_t s = u % NS;
+    if (!mbar_wait(&bars[s], (u / NS) & 1u)) {
+      latch_error(A.err, 99);
+      if constexpr (DF) {
+        if (lane == 0) atomicExch(D->abort, 1);
+      }
+      drain<NS>(bars, i + 1, issued, it0);
+      it = it0 + (uint32_t)issued;
+      return false;
     }
-    const uint32_t sa = sring + (uint32_t)(s * C_STAGE);
+    const uint32_t sa = sring + s * (uint32_t)C_STAGE;
     PieceHdr H;
     {
       const uint4 a = lds128(sa), b = lds128(sa + 16);
@@ -640,11 +689,11 @@ __global__ void __launch_bounds__(NW * 32, 1)
     const uint32_t tbl = sa + C_MOFF + 8u * (uint32_t)rinfo.z;
     switch (H.fb) {
 #define HM_RS(FF_, BB_) \
-  case ((FF_) << 4) | (BB_): rs_piece<TIER, FF_, BB_>(sa, H, tbl, alpha_ff, lane, ahi, alo); break;
+  case ((FF_) << 4) | (BB_): rs_piece<TIER, FF_, BB_>(sa, H, tbl, A.alpha_ff, lane, ahi, alo); break;
       HM_FORMATS(HM_RS)
 #undef HM_RS
       default:
-        latch_error(err, 2);
+        latch_error(A.err, 2);
     }
     if (rinfo.x & PD_LAST) {
       AccR<RL> a8;
@@ -653,11 +702,85 @@ __global__ void __launch_bounds__(NW * 32, 1)
         a8.v[2 * k] = FF{ahi[k].x, alo[k].x};
         a8.v[2 * k + 1] = FF{ahi[k].y, alo[k].y};
       }
-      rs_emit<MODE, RL>(a8, H.row0, H.nrows, H.flags | ((rinfo.x & PD_SPLIT) ? 0x10000 : 0), rinfo.y >> 8,
-                        rinfo.y & 0xff, lane, alpha_ff, beta, y, perm, vout, rowscale, fix, fixcnt, splits);
+      const bool wrote =
+          rs_emit<MODE, RL>(a8, H.row0, H.nrows, H.flags | ((rinfo.x & PD_SPLIT) ? 0x10000 : 0), rinfo.y >> 8,
+                            rinfo.y & 0xff, lane, A.alpha_ff, A.beta, A.y, A.perm, A.vout, A.rowscale, A.fix,
+                            A.fixcnt, A.splits);
+      if constexpr (DF) {
+        if (wrote && rinfo.w >= 0) {   // publish the chunk's next version after all lanes' stores
+          __syncwarp();
+          if (lane == 0) asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(D->ver + rinfo.w) : "memory");
+        }
+      }
     }
     __syncwarp();
     if (issued < n) issue(issued);
+  }
+  it = it0 + (uint32_t)n;
+  return true;
+}
+
+template <int NW, int NS>
+__device__ __forceinline__ void rs_ring_init(uint8_t*& ring, int4*& info, uint64_t*& bars, int warp, int lane) {
+  extern __shared__ __align__(128) uint8_t smem[];
+  ring = smem + (size_t)warp * NS * C_STAGE;
+  info = reinterpret_cast<int4*>(smem + (size_t)NW * NS * C_STAGE) + warp * NS;
+  bars = reinterpret_cast<uint64_t*>(smem + (size_t)NW * NS * (C_STAGE + C_INFO)) + warp * NS;
+  if (lane == 0) {
+    for (int s = 0; s < NS; ++s) mbar_init(&bars[s], 1);
+    mbar_init_fence();
+  }
+  __syncwarp();
+}
+
+template <int TIER, int MODE, int NW, int NS>
+__global__ void __launch_bounds__(NW * 32, 1)
+    k_rstream(RsArgs A, const int32_t* __restrict__ wbeg, int nwt) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int gw = blockIdx.x * NW + warp;
+  if (gw >= nwt) return;
+  const int p0 = wbeg[gw], n = wbeg[gw + 1] - p0;
+  if (n <= 0) return;
+  uint8_t* ring;
+  int4* info;
+  uint64_t* bars;
+  rs_ring_init<NW, NS>(ring, info, bars, warp, lane);
+  uint32_t it = 0;
+  rs_range<TIER, MODE, NS>(A, p0, n, ring, info, bars, lane, it);
+}
+
+// ---------------------------------------------------------------- persistent phases
+// A run of row-chunk launches (the levels of the sweeps, the couplings) as the
+// phases of one cooperative launch (all warps resident): every warp takes its
+// range of each phase in turn, and each piece waits only for the coefficient
+// chunks it reads (versions published by the emits of earlier phases), so the
+// levels of different subtrees overlap instead of meeting at barriers.
+template <int TIER, int NW, int NS>
+__global__ void __launch_bounds__(NW * 32, 1)
+    k_rseq(RsArgs A, const SeqPhase* __restrict__ ph, int nph, const int32_t* __restrict__ wbeg,
+           const F2* __restrict__ rowscale, DfArgs D) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int gw = blockIdx.x * NW + warp;
+  uint8_t* ring;
+  int4* info;
+  uint64_t* bars;
+  rs_ring_init<NW, NS>(ring, info, bars, warp, lane);
+  uint32_t it = 0;
+  for (int p = 0; p < nph; ++p) {
+    const SeqPhase P = ph[p];
+    if (gw >= P.nw) continue;
+    const int p0 = wbeg[P.woff + gw], n = wbeg[P.woff + gw + 1] - p0;
+    if (n <= 0) continue;
+    RsArgs B = A;
+    B.rowscale = P.rowscale ? rowscale : nullptr;
+    bool ok;
+    if (P.mode == MODE_Y)
+      ok = rs_range<TIER, MODE_Y, NS, true>(B, p0, n, ring, info, bars, lane, it, &D);
+    else if (P.mode == MODE_VEC)
+      ok = rs_range<TIER, MODE_VEC, NS, true>(B, p0, n, ring, info, bars, lane, it, &D);
+    else
+      ok = rs_range<TIER, MODE_VEC_ADD, NS, true>(B, p0, n, ring, info, bars, lane, it, &D);
+    if (!ok) return;
   }
 }
 
@@ -755,6 +878,7 @@ constexpr size_t rs_smem() {
 }
 #define HM_CS_CFGS(X) X(0, 16, 2) X(1, 10, 3) X(2, 7, 4)
 #define HM_RS_CFGS(X) X(0, 16, 2) X(1, 11, 3) X(2, 8, 4)
+constexpr int SEQ_NW = RS_CFG_WARPS[SEQ_SHAPE], SEQ_NS = RS_CFG_STAGES[SEQ_SHAPE];   // persistent phases
 #define HM_CHK_CS(I, NW, NS)                                                                      \
   static_assert(CS_CFG_WARPS[I] == NW && CS_CFG_STAGES[I] == NS, "column-dot launch shapes");     \
   static_assert(cs_smem<NW, NS>() <= 227 * 1024, "shared memory per block");
@@ -782,6 +906,8 @@ cudaError_t kernels_init() {
   HM_ATTR((k_rstream<TIER_FF, MODE_VEC_ADD, NW, NS>), (rs_smem<NW, NS>()))
   HM_CS_CFGS(HM_INIT_CS)
   HM_RS_CFGS(HM_INIT)
+  HM_ATTR((k_rseq<TIER_F32, SEQ_NW, SEQ_NS>), (rs_smem<SEQ_NW, SEQ_NS>()))
+  HM_ATTR((k_rseq<TIER_FF, SEQ_NW, SEQ_NS>), (rs_smem<SEQ_NW, SEQ_NS>()))
 #undef HM_INIT_CS
 #undef HM_INIT
 #undef HM_ATTR
@@ -840,9 +966,8 @@ void rgemv_shape(int tier, int mode, const PieceCopy* pieces, const int32_t* wbe
                  float2* vout, const F2* rowscale, F2* fix, int32_t* fixcnt, const Split* splits, int* err,
                  cudaStream_t st) {
   const int grid = (nw + NW - 1) / NW;
-#define HM_RG(T, M)                                                                                         \
-  k_rstream<T, M, NW, NS><<<grid, NW * 32, rs_smem<NW, NS>(), st>>>(                                        \
-      pieces, wbeg, nw, pay, vec, alpha, alpha_ff, beta, y, perm, vout, rowscale, fix, fixcnt, splits, err)
+  const RsArgs A{pieces, pay, vec, alpha, alpha_ff, beta, y, perm, vout, rowscale, fix, fixcnt, splits, err};
+#define HM_RG(T, M) k_rstream<T, M, NW, NS><<<grid, NW * 32, rs_smem<NW, NS>(), st>>>(A, wbeg, nw)
   if (tier == TIER_F32) {
     if (mode == MODE_Y) HM_RG(TIER_F32, MODE_Y);
     else if (mode == MODE_VEC) HM_RG(TIER_F32, MODE_VEC);
@@ -872,6 +997,47 @@ cudaError_t launch_rgemv(int tier, int mode, int cfg, const PieceCopy* pieces, c
       return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
+}
+
+// A run of row-chunk launches as one cooperative launch of nblk blocks (one
+// per SM) of the persistent shape; the chunk versions and the abort word
+// (ver[0 .. nchunks]) are zeroed first.
+cudaError_t launch_rseq(int tier, int nblk, const SeqPhase* phases, int nph, const PieceCopy* pieces,
+                        const int32_t* wbeg, const uint8_t* pay, float2* vec, double alpha, F2 alpha_ff, double beta,
+                        double* y, const int32_t* perm, const F2* rowscale, F2* fix, int32_t* fixcnt,
+                        const Split* splits, const SeqDep* deps, unsigned* ver, int nchunks, int* err,
+                        cudaStream_t st) {
+  if (nph <= 0 || nblk <= 0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(ver, 0, (size_t)(nchunks + 1) * sizeof(unsigned), st);
+  if (e != cudaSuccess) return e;
+  const RsArgs A{pieces, pay, vec, alpha, alpha_ff, beta, y, perm, vec, nullptr, fix, fixcnt, splits, err};
+  const DfArgs D{deps, ver, reinterpret_cast<int*>(ver + nchunks)};
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)nblk);
+  cfg.blockDim = dim3(SEQ_NW * 32);
+  cfg.dynamicSmemBytes = rs_smem<SEQ_NW, SEQ_NS>();
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeCooperative;
+  at[0].val.cooperative = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  if (tier == TIER_F32)
+    e = cudaLaunchKernelEx(&cfg, k_rseq<TIER_F32, SEQ_NW, SEQ_NS>, A, phases, nph, wbeg, rowscale, D);
+  else
+    e = cudaLaunchKernelEx(&cfg, k_rseq<TIER_FF, SEQ_NW, SEQ_NS>, A, phases, nph, wbeg, rowscale, D);
+  return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+// Blocks of the persistent launch that fit on the device at once (0 if none).
+int rseq_max_blocks() {
+  int per_sm = 0, dev = 0, nsm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rseq<TIER_F32, SEQ_NW, SEQ_NS>, SEQ_NW * 32,
+                                                    rs_smem<SEQ_NW, SEQ_NS>()) != cudaSuccess)
+    return 0;
+  return per_sm * nsm;
 }
 
 cudaError_t launch_decode(const uint8_t* p, int64_t n, int B, int fmt, int e, int m, double vmin,

@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstring>
 #include <memory>
+#include <map>
 #include <mutex>
 #include <thread>
 
@@ -25,6 +26,12 @@ cudaError_t launch_rgemv(int tier, int mode, int cfg, const PieceCopy* pieces, c
                          const uint8_t* pay, const float2* vec, double alpha, F2 alpha_ff, double beta, double* y,
                          const int32_t* perm, float2* vout, const F2* rowscale, F2* fix, int32_t* fixcnt,
                          const Split* splits, int* err, cudaStream_t st);
+cudaError_t launch_rseq(int tier, int nblk, const SeqPhase* phases, int nph, const PieceCopy* pieces,
+                        const int32_t* wbeg, const uint8_t* pay, float2* vec, double alpha, F2 alpha_ff, double beta,
+                        double* y, const int32_t* perm, const F2* rowscale, F2* fix, int32_t* fixcnt,
+                        const Split* splits, const SeqDep* deps, unsigned* ver, int nchunks, int* err,
+                        cudaStream_t st);
+int rseq_max_blocks();
 cudaError_t mr_init();
 cudaError_t launch_gather_mr(const double* x, int64_t ldx, int r, const int32_t* perm, int n, float* v,
                              cudaStream_t st);
@@ -100,6 +107,18 @@ struct hm_matrix {
   double* d_hy = nullptr;
   int64_t d_h_cap = 0;
   int nsm = 0;
+  // persistent launches: runs [first, last) of consecutive row-chunk launches
+  // executed as the phases of one cooperative launch (dataflow between phases)
+  bool fuse = true;
+  struct Run {
+    size_t first, last;
+    int64_t ph0;   // first phase in d_phases
+    int nchunks;   // coefficient chunks written in the run (versions ver[0 .. nchunks))
+  };
+  std::vector<Run> runs;
+  DevArr<SeqPhase> d_phases;
+  DevArr<SeqDep> d_deps;       // per piece (pieces of runs only)
+  unsigned* d_ver = nullptr;   // chunk versions + abort word of the largest run
   std::mutex mu;
   // CUDA graph of the whole launch sequence, cached per call signature
   bool use_graph = false;
@@ -150,6 +169,11 @@ struct hm_matrix {
     d_fan.release();
     d_splits.release();
     d_rowscale_ff.release();
+    d_phases.release();
+    d_deps.release();
+    runs.clear();
+    if (d_ver) cudaFree(d_ver);
+    d_ver = nullptr;
     d_perm.release();
     if (d_fix) cudaFree(d_fix);
     if (d_fixcnt) cudaFree(d_fixcnt);
@@ -178,6 +202,82 @@ namespace {
 
 std::once_flag g_kinit;
 cudaError_t g_kinit_err = cudaSuccess;
+
+// Dependencies of the pieces of launches [first, last) run as the phases of one
+// persistent launch.  Coefficient chunks are the output rows [row0, row0 + nrows)
+// of the MODE_VEC / MODE_VEC_ADD chunks of the run; a chunk's version counts the
+// phases that have emitted it.  Each piece waits for the chunk holding its
+// multipliers at the version reached before its phase, and for its own chunk
+// at its current version (read-modify-write, or ordered overwrite).  Returns
+// false (run stays per launch) if a multiplier run straddles chunks, or a
+// chunk is written after a phase that reads it (a reader could see the later
+// value).  deps is sized to the pieces and filled for the run's pieces.
+bool seq_dependencies(const Program& P, size_t first, size_t last, std::vector<SeqDep>& deps, int& nchunks) {
+  const auto& Ls = P.launches;
+  const auto& pd = P.pdesc[SEQ_SHAPE];
+  auto hdr = [&](int64_t i, int32_t& row0, int& nrows) {
+    const uint8_t* h = P.pk.pay.data() + (size_t)pd[i].off8 * 8;
+    std::memcpy(&row0, h, 4);
+    uint16_t nr;
+    std::memcpy(&nr, h + 4, 2);
+    nrows = nr;
+  };
+  std::map<int32_t, std::pair<int, int>> chunk;   // row0 -> (id, nrows)
+  for (size_t k = first; k < last; ++k) {
+    if (Ls[k].mode == MODE_Y) continue;
+    for (int64_t i = Ls[k].off; i < Ls[k].off + Ls[k].n; ++i) {
+      int32_t r0;
+      int nr;
+      hdr(i, r0, nr);
+      if (!chunk.count(r0)) chunk[r0] = {(int)chunk.size(), nr};
+    }
+  }
+  nchunks = (int)chunk.size();
+  std::vector<int> ver(nchunks, 0), last_read(nchunks, -1);
+  auto find = [&](int64_t m0, int64_t nc) -> int {   // chunk holding [m0, m0 + nc), -1 none, -2 straddles
+    auto it = chunk.upper_bound((int32_t)m0);
+    if (it != chunk.begin()) {
+      --it;
+      if (m0 < (int64_t)it->first + it->second.second)
+        return m0 + nc <= (int64_t)it->first + it->second.second ? it->second.first : -2;
+    }
+    auto nx = chunk.lower_bound((int32_t)m0);
+    return (nx != chunk.end() && nx->first < m0 + nc) ? -2 : -1;
+  };
+  if (deps.size() < (size_t)P.npieces) deps.resize((size_t)P.npieces, SeqDep{-1, 0, -1, 0});
+  for (size_t k = first; k < last; ++k) {
+    const Launch& L = Ls[k];
+    std::vector<int> wrote;
+    for (int64_t i = L.off; i < L.off + L.n; ++i) {   // reads of this phase first
+      const int nc = (int)(pd[i].bytes_flags >> 24);
+      SeqDep d{-1, 0, -1, 0};
+      if (nc > 0) {
+        const int c = find(pd[i].moff, nc);
+        if (c == -2) return false;
+        if (c >= 0) {
+          if (ver[c] > 0) d = SeqDep{c, ver[c], -1, 0};
+          last_read[c] = (int)k;
+        }
+      }
+      deps[(size_t)i] = d;
+    }
+    for (int64_t i = L.off; i < L.off + L.n; ++i) {   // then its writes
+      if (L.mode == MODE_Y) continue;
+      int32_t r0;
+      int nr;
+      hdr(i, r0, nr);
+      const int c = chunk[r0].first;
+      if (last_read[c] >= 0) return false;   // read as multipliers in this or an earlier phase, now written
+      deps[(size_t)i].c1 = c;
+      deps[(size_t)i].v1 = ver[c];
+      wrote.push_back(c);
+    }
+    std::sort(wrote.begin(), wrote.end());
+    wrote.erase(std::unique(wrote.begin(), wrote.end()), wrote.end());
+    for (int c : wrote) ++ver[c];
+  }
+  return true;
+}
 
 hm_status upload(hm_matrix* M) {
   Program& P = M->prog;
@@ -234,6 +334,35 @@ hm_status upload(hm_matrix* M) {
   }
   if ((e = cudaMalloc(&M->d_err, sizeof(int))) != cudaSuccess) return cuda_status(e);
   if ((e = cudaMemset(M->d_err, 0, sizeof(int))) != cudaSuccess) return cuda_status(e);
+  // persistent runs: maximal sequences of >= 2 row-chunk launches, when a
+  // cooperative launch of one block per SM fits (phases use the SEQ_SHAPE ranges)
+  {
+    std::vector<SeqPhase> ph;
+    std::vector<SeqDep> deps;
+    int maxchunks = 0;
+    const auto& Ls = P.launches;
+    const bool fits = rseq_max_blocks() >= M->nsm && M->nsm > 0;
+    for (size_t i = 0; fits && i < Ls.size();) {
+      size_t j = i;
+      while (j < Ls.size() && Ls[j].kind == Launch::RGEMV) ++j;
+      hm_matrix::Run R{i, j, (int64_t)ph.size(), 0};
+      if (j - i >= 2 && seq_dependencies(P, i, j, deps, R.nchunks)) {
+        M->runs.push_back(R);
+        maxchunks = std::max(maxchunks, R.nchunks);
+        for (size_t k = i; k < j; ++k) {
+          const Launch& L = Ls[k];
+          ph.push_back(SeqPhase{L.mode, (int32_t)L.woff[SEQ_SHAPE], L.nw[SEQ_SHAPE], L.use_rowscale ? 1 : 0});
+        }
+      }
+      i = std::max(j, i + 1);
+    }
+    if (!ph.empty()) {
+      if ((e = M->d_phases.upload(ph)) != cudaSuccess) return cuda_status(e);
+      if ((e = M->d_deps.upload(deps)) != cudaSuccess) return cuda_status(e);
+      if ((e = cudaMalloc(&M->d_ver, (size_t)(maxchunks + 1) * sizeof(unsigned))) != cudaSuccess)
+        return cuda_status(e);
+    }
+  }
   return HM_OK;
 }
 
@@ -409,7 +538,22 @@ static hm_status run_all(hm_matrix* M, double alpha, const double* x, int64_t ld
 
 static hm_status run_program(hm_matrix* M, double alpha, const double* x, double beta, double* y,
                              cudaStream_t st) {
-  for (const Launch& L : M->prog.launches) {
+  const auto& Ls = M->prog.launches;
+  size_t ri = 0;
+  for (size_t li = 0; li < Ls.size(); ++li) {
+    const Launch& L = Ls[li];
+    if (M->fuse && !M->prof && ri < M->runs.size() && M->runs[ri].first == li) {   // persistent run
+      const hm_matrix::Run& R = M->runs[ri++];
+      Program& P = M->prog;
+      if (launch_rseq(P.tier, M->nsm, M->d_phases.p + R.ph0, (int)(R.last - R.first),
+                      M->d_pieces.p + (size_t)SEQ_SHAPE * P.npieces, M->d_wbeg.p, M->d_pay.p, M->d_vec, alpha,
+                      split_ff(alpha), beta, y, M->d_perm.p, M->d_rowscale_ff.p, M->d_fix, M->d_fixcnt,
+                      M->d_splits.p, M->d_deps.p, M->d_ver, R.nchunks, M->d_err, st) != cudaSuccess)
+        return HM_ERR_CUDA;
+      li = R.last - 1;
+      continue;
+    }
+    if (ri < M->runs.size() && M->runs[ri].first == li) ++ri;
     hm_matrix::Rec rec{(int)L.kind, nullptr, nullptr, L.bytes};
     if (M->prof) {
       rec.e0 = M->take_event();
@@ -468,6 +612,14 @@ hm_status hm_graph(hm_matrix* M, int32_t enable) {
   std::lock_guard<std::mutex> g(M->mu);
   M->use_graph = enable != 0;
   if (!M->use_graph) M->drop_graph();
+  return HM_OK;
+}
+
+hm_status hm_persistent(hm_matrix* M, int32_t enable) {
+  if (!M) return HM_ERR_ARG;
+  std::lock_guard<std::mutex> g(M->mu);
+  M->fuse = enable != 0;
+  M->drop_graph();
   return HM_OK;
 }
 

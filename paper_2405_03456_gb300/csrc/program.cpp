@@ -485,13 +485,17 @@ void add_rgemv(Ctx& cx, std::vector<ChunkWork>& cw, int mode, bool rowscale) {
       }
     }
     std::vector<int32_t> splitof(cw.size(), -1);
-    int64_t fix = 0;
+    // fix-up slots: reused by the next launch, except in the persistent shape,
+    // whose launches may run concurrently as phases of one launch
+    const int64_t fix0 = cf == SEQ_SHAPE ? P.nfix_seq : 0;
+    int64_t fix = fix0;
     for (size_t ch = 0; ch < cw.size(); ++ch)
       if (nparts[ch] > 1) {
         splitof[ch] = (int32_t)P.splits.size();
         P.splits.push_back(Split{(int32_t)fix, nparts[ch]});
         fix += nparts[ch];
       }
+    if (cf == SEQ_SHAPE) P.nfix_seq = fix;
     if (cf == MR_SHAPE)
       nfix_mr = std::max(nfix_mr, fix);
     else
@@ -817,8 +821,8 @@ bool program_h2(Ctx& cx) {
   const auto& ct = H.ct;
   const int64_t N = H.n;
   const int nc = (int)ct.cl.size();
-  for (int c = 0; c < nc; ++c)
-    if (H.rowb.k[c] > CHUNK_ROWS) return false;      // a down-sweep chunk holds <= 128 coefficients
+  for (int c = 0; c < nc; ++c)   // an up- or down-sweep chunk holds <= 128 coefficients
+    if (H.rowb.k[c] > CHUNK_ROWS || H.colb.k[c] > CHUNK_ROWS) return false;
   const auto lv = leaves_under(ct);
   std::vector<std::vector<const TileData*>> dt;
   if (!pack_dense(cx, lv, dt)) return false;
@@ -848,13 +852,19 @@ bool program_h2(Ctx& cx) {
   P.npartial = std::max(P.npartial, pbase);
   add_launch(P, Launch::CDOT, i0, (int64_t)P.items.size() - i0);
   add_launch(P, Launch::GSUM, g0, (int64_t)P.gouts.size() - g0);
-  // transfer matrices, direct compression
-  std::vector<ColSet> ex(nc), ew(nc);
+  // transfer matrices, direct compression; the column-basis ones are stored
+  // transposed (k_parent rows x k_son columns): the up-sweep is a row-chunk
+  // product per parent, s_parent = sum over sons of vmin E_son^T s_son
+  std::vector<ColSet> ext(nc), ew(nc);
   for (int c = 0; c < nc; ++c) {
     const int p = ct.cl[c].parent;
     if (p < 0) continue;
     if (H.colb.k[c] && H.colb.k[p]) {
-      if (!make_direct(cx, H.colb.E[c].data(), H.colb.k[c], H.colb.k[p], ex[c])) return false;
+      const int kc = H.colb.k[c], kp = H.colb.k[p];
+      std::vector<double> et((size_t)kc * kp);
+      for (int j = 0; j < kp; ++j)
+        for (int i = 0; i < kc; ++i) et[(size_t)j + (size_t)i * kp] = H.colb.E[c][(size_t)i + (size_t)j * kc];
+      if (!make_direct(cx, et.data(), kp, kc, ext[c])) return false;
       P.fp64_lowrank += (int64_t)H.colb.E[c].size() * 8;
     }
     if (H.rowb.k[c] && H.rowb.k[p]) {
@@ -862,7 +872,8 @@ bool program_h2(Ctx& cx) {
       P.fp64_lowrank += (int64_t)H.rowb.E[c].size() * 8;
     }
   }
-  // up-sweep by height: s_sigma = sum_i vmin_i * E_i^T s_i (Alg. 6)
+  // up-sweep by height: s_sigma = sum over sons i of vmin_i E_i^T s_i (Alg. 6),
+  // one row-chunk launch per height (chunk = s_sigma, one tile per son)
   std::vector<int> height(nc, 0);
   int maxh = 0;
   for (int c = nc - 1; c >= 0; --c) {
@@ -870,40 +881,19 @@ bool program_h2(Ctx& cx) {
     maxh = std::max(maxh, height[c]);
   }
   for (int h = 1; h <= maxh; ++h) {
-    i0 = (int64_t)P.items.size();
-    g0 = (int64_t)P.gouts.size();
-    int64_t pb = 0;
+    std::vector<ChunkWork> uw;
     for (int c = 0; c < nc; ++c) {
       if (height[c] != h || H.colb.k[c] == 0) continue;
-      // partials of output j: the segments of son 0, then those of son 1
-      const int kp = H.colb.k[c];
-      int64_t ns[2] = {0, 0};
-      for (int i = 0; i < 2; ++i)
-        if (H.colb.k[ct.cl[c].son[i]]) ns[i] = nseg_of(H.colb.k[ct.cl[c].son[i]]);
-      const int64_t per = ns[0] + ns[1];
+      ChunkWork w;
+      w.row0 = (int32_t)soff[c];
+      w.nrows = H.colb.k[c];
       for (int i = 0; i < 2; ++i) {
         const int sc = ct.cl[c].son[i];
-        if (ns[i] == 0) continue;
-        std::vector<CdotCol> cols;
-        std::vector<int64_t> pout(kp);
-        for (int j = 0; j < kp; ++j) {
-          cols.push_back(CdotCol{&ex[sc], j, 0, 1.0});
-          pout[j] = pb + (int64_t)j * per + (i ? ns[0] : 0);
-        }
-        bool fin = false;
-        pack_cdot(P, cols, H.colb.k[sc], (int32_t)soff[sc], false, false, pout, fin);
+        if (H.colb.k[sc]) w.t.push_back(pack_tile(cx, ext[sc], 0, H.colb.k[c], (int32_t)soff[sc], 0));
       }
-      for (int j = 0; j < kp; ++j) {
-        std::vector<double> w;
-        for (int i = 0; i < 2; ++i)
-          for (int64_t t = 0; t < ns[i]; ++t) w.push_back(ex[ct.cl[c].son[i]].scale(0));
-        gsum_one(P, soff[c] + j, pb + (int64_t)j * per, pb + (int64_t)(j + 1) * per, w, 1.0, 0);
-      }
-      pb += (int64_t)kp * per;
+      uw.push_back(std::move(w));
     }
-    P.npartial = std::max(P.npartial, pb);
-    add_launch(P, Launch::CDOT, i0, (int64_t)P.items.size() - i0);
-    add_launch(P, Launch::GSUM, g0, (int64_t)P.gouts.size() - g0);
+    if (!uw.empty()) add_rgemv(cx, uw, MODE_VEC, false);
   }
   std::vector<ColSet> wb;
   if (!row_bases(cx, wl, toff, wb)) return false;

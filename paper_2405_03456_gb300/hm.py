@@ -25,7 +25,7 @@ KERNELS = {"laplace": HM_KERNEL_LAPLACE, "matern": HM_KERNEL_MATERN15}
 DECLARED = ["hm_build", "hm_compress", "hm_matvec", "hm_matvec_host", "hm_free", "hm_info",
             "hm_status_str", "hm_sync_status", "hm_structure", "hm_codec_encode", "hm_codec_decode",
             "hm_profile", "hm_profile_read", "hm_alg_bytes", "hm_matvec_host_noalloc", "hm_graph",
-            "hm_autotune", "hm_launch_shapes", "hm_set_launch_shapes"]
+            "hm_autotune", "hm_launch_shapes", "hm_set_launch_shapes", "hm_persistent"]
 NSHAPES = 3
 HM_NOALLOC_MAX_ENTRIES = 1 << 20
 KERNEL_KINDS = ["gather", "cdot", "gsum", "rgemv", "fanout"]
@@ -90,6 +90,7 @@ def load(path: str | None = None) -> C.CDLL:
         "hm_codec_encode": ([vp, i64, i32, i32, vp, i64, C.POINTER(hm_codec_header)], i32),
         "hm_codec_decode": ([vp, i64, C.POINTER(hm_codec_header), vp, vp], i32),
         "hm_profile": ([vp, i32], i32),
+        "hm_persistent": ([vp, i32], i32),
         "hm_profile_read": ([vp, C.POINTER(hm_kernel_stat), i32], i32),
         "hm_alg_bytes": ([vp, C.POINTER(i64)], i32),
         "hm_matvec_host_noalloc": ([vp, dbl, vp, dbl, vp, i64, vp], i32),
@@ -197,6 +198,10 @@ def hm_graph(h: int, enable: bool) -> None:
     check(load().hm_graph(h, 1 if enable else 0), "hm_graph")
 
 
+def hm_persistent(h: int, enable: bool) -> None:
+    check(load().hm_persistent(h, 1 if enable else 0), "hm_persistent")
+
+
 def hm_autotune(h: int, reps: int = 5, stream: int = 0) -> None:
     check(load().hm_autotune(h, reps, stream), "hm_autotune")
 
@@ -271,6 +276,10 @@ class HMatrix:
 
     def graph(self, enable=True):
         hm_graph(self.h, enable)
+        return self
+
+    def persistent(self, enable=True):
+        hm_persistent(self.h, enable)
         return self
 
     def autotune(self, reps=5, stream=0):

@@ -223,6 +223,36 @@ def test_launch_shapes_and_autotune(hm, problem, fmt):
         M.close()
 
 
+@pytest.mark.parametrize("fmt", ["h", "uh", "h2"])
+@pytest.mark.parametrize("eps", [1e-6, 1e-8])
+def test_persistent_launch_equals_per_launch(hm, problem, fmt, eps):
+    """The persistent form (runs of row-chunk launches and fan-outs as phases of
+    one cooperative launch with grid barriers) gives the per-launch result bit
+    for bit (same warp ranges of shape 0, same order of every sum), within 4 eps
+    of the oracle, also replayed from a CUDA graph."""
+    pts, x, y0 = problem
+    ref = oracle_ref(pts, fmt, eps, x[:, 0], 0.75, y0[:, 0], -0.5)
+    M = hm.HMatrix(pts, "laplace", 32, 2.0, fmt, eps)
+    try:
+        M.compress(eps, "aflp")
+        M.set_launch_shapes(0)
+        xd = torch.from_numpy(x[:, 0].copy()).cuda()
+        outs = []
+        for persistent, graph in ((False, False), (True, False), (True, True), (True, True)):
+            M.persistent(persistent)
+            M.graph(graph)
+            yd = torch.from_numpy(y0[:, 0].copy()).cuda()
+            M.matvec(0.75, xd, -0.5, yd)
+            torch.cuda.synchronize()
+            outs.append(yd.cpu().numpy())
+        assert M.sync_status() == 0
+        assert rel(outs[0], ref) <= 4 * eps
+        for o in outs[1:]:
+            assert np.array_equal(o.view(np.uint64), outs[0].view(np.uint64))
+    finally:
+        M.close()
+
+
 def test_matern_cube(hm):
     pts = synth.cube_points(3000)
     x = synth.rhs(3000)[:, 0]
