@@ -158,17 +158,32 @@ __device__ __forceinline__ void decode4(const uint32_t (&w)[B], int e, int m, fl
       float d = __uint_as_float(sb) - 1.0f;
       h[i] = __uint_as_float(__float_as_uint(d) ^ (t[i] & 0x80000000u));
     }
-  } else if constexpr (F == 2) {                           // AFLP with m' > 23
-    uint64_t c[4];
-    if constexpr (B == 4) {
-      c[0] = w[0]; c[1] = w[1]; c[2] = w[2]; c[3] = w[3];
-    } else {
-      constexpr int rs = 64 - 8 * B;
-      c[0] = top64<B, 0>(w) >> rs;
-      c[1] = top64<B, 1>(w) >> rs;
-      c[2] = top64<B, 2>(w) >> rs;
-      c[3] = top64<B, 3>(w) >> rs;
+  } else if constexpr (F == 2 && B == 4) {
+    // AFLP in 32 bits, float-float tier.  The code fills the word (m' = 31 - e),
+    // so the F32 head s_h = 2^f (1 + top 23 mantissa bits) comes out as in the
+    // F32 tier, and the sh = 8 - e = m' - 23 bits shifted out form the tail
+    // t 2^(f - m'), t < 2^sh, exact in FP32 (t via the 2^23 bit pattern).
+    const int sh = 8 - e;
+    const uint32_t tmask = (1u << sh) - 1u, mexp = (uint32_t)m << 23;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const uint32_t c = w[i];
+      const uint32_t sb = ((c & 0x7fffffffu) >> sh) + (127u << 23);
+      const float d = __uint_as_float(sb) - 1.0f;
+      h[i] = __uint_as_float(__float_as_uint(d) ^ (c & 0x80000000u));
+      if constexpr (TIER == TIER_FF) {
+        const float t = __uint_as_float((c & tmask) | 0x4B000000u) - 8388608.0f;
+        const float lv = t * __uint_as_float((sb & 0x7f800000u) - mexp);
+        l[i] = __uint_as_float(__float_as_uint(lv) ^ (c & 0x80000000u));
+      }
     }
+  } else if constexpr (F == 2) {                           // AFLP with m' > 23, B >= 5
+    uint64_t c[4];
+    constexpr int rs = 64 - 8 * B;
+    c[0] = top64<B, 0>(w) >> rs;
+    c[1] = top64<B, 1>(w) >> rs;
+    c[2] = top64<B, 2>(w) >> rs;
+    c[3] = top64<B, 3>(w) >> rs;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       uint32_t sgn = (uint32_t)(c[i] >> (8 * B - 1)) << 31;
