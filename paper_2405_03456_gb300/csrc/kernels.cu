@@ -357,6 +357,20 @@ __global__ void __launch_bounds__(NW * 32, 1)
 }
 
 // ---------------------------------------------------------------- row chunks (phase C)
+// Lane split of a row-chunk piece: G = ceil(R / 8) lanes per column, S = 32 / G
+// column slots, lane = slot G + q.  The divisions by the runtime G go through a
+// table: slot = (lane * ceil(1024 / G)) >> 10 is exact for lane < 1024 / G,
+// which holds for lane < 32 and G <= 16.
+__constant__ uint16_t c_div1024[17] = {0,    1024, 512, 342, 256, 205, 171, 147, 128,
+                                       114,  103,  94,  86,  79,  74,  69,  64};
+__constant__ uint8_t c_slots[17] = {0, 32, 16, 10, 8, 6, 5, 4, 4, 3, 3, 2, 2, 2, 2, 2, 2};
+__device__ __forceinline__ void lane_split(int R, int lane, int& G, int& S, int& slot, int& q) {
+  G = (R + RPL - 1) / RPL;
+  S = c_slots[G];
+  slot = (lane * (int)c_div1024[G]) >> 10;
+  q = lane - slot * G;
+}
+
 // Sum of the piece's columns into this lane's 8 rows: lanes (slot, q) take
 // rows 8q .. 8q+7 of the columns slot, slot + S, ...; FP32 sums (or Dot2
 // pairs) per piece, folded into the float-float row sums (row pairs
@@ -365,9 +379,8 @@ template <int TIER, int F, int B>
 __device__ __forceinline__ void rs_piece(uint32_t sa, const PieceHdr& H, uint32_t tbl, F2 alpha_ff, int lane,
                                          float2 (&ahi)[4], float2 (&alo)[4]) {
   const int R = H.nrows;
-  const int G = (R + RPL - 1) / RPL;
-  const int S = 32 / G;
-  const int slot = lane / G, q = lane - slot * G;
+  int G, S, slot, q;
+  lane_split(R, lane, G, S, slot, q);
   const bool tile = (H.flags & PH_TILE) != 0;
   const uint32_t stride = pad8u((uint32_t)R * B);
   const uint32_t cm = sa + (uint32_t)sizeof(PieceHdr);   // merged pieces: uint16 em[ncols]
@@ -498,9 +511,9 @@ __device__ __noinline__ bool rs_emit(AccR<RL> acc, int row0, int R, int hflags, 
                                      const int32_t* __restrict__ perm, float2* __restrict__ vout,
                                      const F2* __restrict__ rowscale, F2* __restrict__ fix,
                                      int32_t* __restrict__ fixcnt, const Split* __restrict__ splits) {
-  const int G = (R + RL - 1) / RL;
-  const int S = 32 / G;
-  const int q = lane % G, slot = lane / G;
+  static_assert(RL == RPL, "lanes hold RPL rows");
+  int G, S, slot, q;
+  lane_split(R, lane, G, S, slot, q);
   // pairwise tree over the S column slots (slot s takes s + off when s is a
   // multiple of 2 off): log2 S shuffle rounds, all rows of a round in flight
   for (int off = 1; off < S; off <<= 1) {

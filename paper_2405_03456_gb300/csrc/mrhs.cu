@@ -36,6 +36,10 @@ __device__ __forceinline__ void mr_decode8(uint32_t a, int e, int m, float (&v)[
   }
 }
 
+// ceil(16384 / G): (t * c_div16384[G]) >> 14 == t / G for t < 16384 / G, which
+// holds for the decode tasks of a piece (t < 64 G, G <= 16).
+__constant__ uint16_t c_div16384[17] = {0, 16384, 8192, 5462, 4096, 3277, 2731, 2341, 2048, 1821, 1639, 1490, 1366, 1261, 1171, 1093, 1024};
+
 // ---------------------------------------------------------------- gather, fan-out, segment sums
 // v[i * RP + k] = x[perm[i] + k * ldx] (FP32 hi part), k < r; zero for k >= r.
 __global__ void k_gather_mr(const double* __restrict__ x, int64_t ldx, int r, const int32_t* __restrict__ perm, int n,
@@ -177,8 +181,9 @@ __device__ __forceinline__ void mr_cdot_decode(uint32_t sa, uint32_t ta, int R, 
   const uint32_t cb = cm + (fin ? 16u : 8u) * nc;
   const int Rp = (R + 15) & ~15, ncp = (nc + 15) & ~15;
   const int G = Rp / RPL;   // rows >= R are zero codes
+  const int dG = (int)c_div16384[G];
   for (int task = threadIdx.x; task < ncp * G; task += MR_THREADS) {
-    const int j = task / G, q = task % G;
+    const int j = (task * dG) >> 14, q = task - j * G;   // task / G, task % G (task < 64 G)
     float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     if (j < nc) {
       int e = 0, m = 0;
@@ -343,8 +348,9 @@ __device__ __forceinline__ void mr_rgemv_decode(uint32_t sa, uint32_t ta, const 
   const uint32_t cb = cm + (tile_piece ? 0u : pad8u(2u * nc));
   const int e_t = H.em & 0xff, m_t = H.em >> 8;
   const int G = (R + RPL - 1) / RPL;
+  const int dG = (int)c_div16384[G];
   for (int task = threadIdx.x; task < ncp * G; task += MR_THREADS) {
-    const int j = task / G, q = task % G;
+    const int j = (task * dG) >> 14, q = task - j * G;   // task / G, task % G (task < 64 G)
     float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     if (j < nc) {
       int e = e_t, m = m_t;
