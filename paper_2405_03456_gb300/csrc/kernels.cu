@@ -799,14 +799,27 @@ __global__ void __launch_bounds__(NW * 32, 1)
 
 // ---------------------------------------------------------------- multiplier fan-out
 // Slot i of a row-chunk launch's multiplier runs takes coefficient v[src[i]].
+// FAN_PER slots per thread, all index loads, then all gathers, then all stores
+// (few waves of threads, several loads in flight per thread).
+constexpr int FAN_PER = 4;
 __global__ void k_fanout(const int32_t* __restrict__ src, int n, float2* __restrict__ dst,
                          const float2* __restrict__ vec) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) dst[i] = vec[src[i]];
+  const int base = blockIdx.x * blockDim.x * FAN_PER + threadIdx.x;
+  int ix[FAN_PER];
+#pragma unroll
+  for (int k = 0; k < FAN_PER; ++k) {
+    const int i = base + k * blockDim.x;
+    ix[k] = i < n ? __ldg(src + i) : -1;
+  }
+  float2 v[FAN_PER];
+#pragma unroll
+  for (int k = 0; k < FAN_PER; ++k) v[k] = ix[k] >= 0 ? vec[ix[k]] : make_float2(0.f, 0.f);
+#pragma unroll
+  for (int k = 0; k < FAN_PER; ++k)
+    if (ix[k] >= 0) dst[base + k * blockDim.x] = v[k];
 }
 
 // ---------------------------------------------------------------- segment sums (phase A2)
-// One thread per coefficient: fixed-order float-float sum of its contiguous partials.
 // Segment sums: GS_LANES lanes per output; lane k sums the partials p0 + k,
 // p0 + k + GS_LANES, ... (consecutive lanes read consecutive partials), then a
 // fixed xor tree combines the lanes (deterministic order).
@@ -961,7 +974,7 @@ cudaError_t launch_cdot(int tier, int cfg, const ItemCopy* items, const int32_t*
 
 cudaError_t launch_fanout(const int32_t* src, int n, float2* dst, const float2* vec, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
-  k_fanout<<<(n + 255) / 256, 256, 0, st>>>(src, n, dst, vec);
+  k_fanout<<<(n + 256 * FAN_PER - 1) / (256 * FAN_PER), 256, 0, st>>>(src, n, dst, vec);
   return cudaGetLastError();
 }
 
