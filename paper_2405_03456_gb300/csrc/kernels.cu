@@ -39,6 +39,13 @@ __device__ void drain(uint64_t* bars, int i, int issued, uint32_t it0 = 0) {
   }
 }
 
+// Programmatic dependent launch: a kernel lets the next one in the stream start
+// at once (its blocks take SM resources as they free up and run their prologue),
+// and waits for the previous one (completed, memory visible) before it reads
+// anything that kernel wrote.  Both are no-ops for ordinary launches.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // ---------------------------------------------------------------- column dots (phase A)
 // (s, c) += (s2, c2) for Dot2 pairs (TwoSum of the leading parts).
 template <int TIER>
@@ -253,6 +260,7 @@ __global__ void __launch_bounds__(NW * 32, 1)
               const uint8_t* __restrict__ pay, const float2* __restrict__ vec, F2 alpha,
               F2* __restrict__ partial, float2* __restrict__ vout, int* err) {
   extern __shared__ __align__(128) uint8_t smem[];
+  pdl_trigger();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int gw = blockIdx.x * NW + warp;
   if (gw >= nwt) return;
@@ -300,6 +308,7 @@ __global__ void __launch_bounds__(NW * 32, 1)
     }
     issued = i + 1;
   };
+  pdl_wait();   // the input segments come from the previous kernel
   for (int i = 0; i < NS && i < n; ++i) issue(i);
   constexpr int RL = RPL;   // rows per lane
   float xh[RL], xl[RL];
@@ -749,6 +758,7 @@ __device__ __forceinline__ void rs_ring_init(uint8_t*& ring, int4*& info, uint64
 template <int TIER, int MODE, int NW, int NS>
 __global__ void __launch_bounds__(NW * 32, 1)
     k_rstream(RsArgs A, const int32_t* __restrict__ wbeg, int nwt) {
+  pdl_trigger();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int gw = blockIdx.x * NW + warp;
   if (gw >= nwt) return;
@@ -758,6 +768,7 @@ __global__ void __launch_bounds__(NW * 32, 1)
   int4* info;
   uint64_t* bars;
   rs_ring_init<NW, NS>(ring, info, bars, warp, lane);
+  pdl_wait();   // multipliers and outputs depend on the previous kernels
   uint32_t it = 0;
   rs_range<TIER, MODE, NS>(A, p0, n, ring, info, bars, lane, it);
 }
@@ -804,6 +815,8 @@ __global__ void __launch_bounds__(NW * 32, 1)
 constexpr int FAN_PER = 4;
 __global__ void k_fanout(const int32_t* __restrict__ src, int n, float2* __restrict__ dst,
                          const float2* __restrict__ vec) {
+  pdl_trigger();
+  pdl_wait();
   const int base = blockIdx.x * blockDim.x * FAN_PER + threadIdx.x;
   int ix[FAN_PER];
 #pragma unroll
@@ -826,6 +839,8 @@ __global__ void k_fanout(const int32_t* __restrict__ src, int n, float2* __restr
 constexpr int GS_LANES = 8;
 __global__ void k_gsum(const GsumOut* __restrict__ outs, int nouts, const F2* __restrict__ pscale,
                        const F2* __restrict__ partial, F2 alpha, float2* __restrict__ vout) {
+  pdl_trigger();
+  pdl_wait();
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   const int i = t / GS_LANES, k = t % GS_LANES;
   const bool on = i < nouts;
@@ -859,6 +874,7 @@ __global__ void k_gsum(const GsumOut* __restrict__ outs, int nouts, const F2* __
 // ---------------------------------------------------------------- gather x
 __global__ void k_gather(const double* __restrict__ x, const int32_t* __restrict__ perm, int n,
                          float2* __restrict__ xo) {
+  pdl_trigger();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   FF f = ff_from_d(x[perm[i]]);
@@ -894,6 +910,22 @@ __global__ void k_decode(const uint8_t* __restrict__ p, int64_t n, int B, int fm
 }
 
 // ---------------------------------------------------------------- launchers
+// Launch with programmatic stream serialization (see pdl_trigger / pdl_wait).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*k)(KArgs...), unsigned grid, unsigned block, size_t smem, cudaStream_t st,
+                       Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k, args...);
+}
 template <int NW, int NS>
 constexpr size_t cs_smem() {
   return (size_t)NW * NS * (A_STAGE + 8) + SMEM_TAIL;
@@ -947,23 +979,26 @@ cudaError_t launch_gather(const double* x, const int32_t* perm, int n, float2* x
 }
 
 template <int NW, int NS>
-void cdot_shape(int tier, const ItemCopy* items, const int32_t* wbeg, int nw, const uint8_t* pay, const float2* vec,
+cudaError_t cdot_shape(int tier, const ItemCopy* items, const int32_t* wbeg, int nw, const uint8_t* pay, const float2* vec,
                 F2 alpha, F2* partial, float2* vout, int* err, cudaStream_t st) {
   const int grid = (nw + NW - 1) / NW;
   if (tier == TIER_F32)
-    k_cstream<TIER_F32, NW, NS><<<grid, NW * 32, cs_smem<NW, NS>(), st>>>(items, wbeg, nw, pay, vec, alpha, partial,
-                                                                           vout, err);
-  else
-    k_cstream<TIER_FF, NW, NS><<<grid, NW * 32, cs_smem<NW, NS>(), st>>>(items, wbeg, nw, pay, vec, alpha, partial,
-                                                                          vout, err);
+    return launch_pdl(k_cstream<TIER_F32, NW, NS>, grid, NW * 32, cs_smem<NW, NS>(), st, items, wbeg, nw, pay, vec,
+                      alpha, partial, vout, err);
+  return launch_pdl(k_cstream<TIER_FF, NW, NS>, grid, NW * 32, cs_smem<NW, NS>(), st, items, wbeg, nw, pay, vec,
+                    alpha, partial, vout, err);
 }
 
 cudaError_t launch_cdot(int tier, int cfg, const ItemCopy* items, const int32_t* wbeg, int nw, const uint8_t* pay,
                         const float2* vec, F2 alpha, F2* partial, float2* vout, int* err, cudaStream_t st) {
   if (nw <= 0) return cudaSuccess;
   switch (cfg) {
-#define HM_L(I, NW, NS) \
-  case I: cdot_shape<NW, NS>(tier, items, wbeg, nw, pay, vec, alpha, partial, vout, err, st); break;
+#define HM_L(I, NW, NS)                                                                            \
+  case I: {                                                                                        \
+    const cudaError_t e = cdot_shape<NW, NS>(tier, items, wbeg, nw, pay, vec, alpha, partial, vout, err, st); \
+    if (e != cudaSuccess) return e;                                                                \
+    break;                                                                                         \
+  }
     HM_CS_CFGS(HM_L)
 #undef HM_L
     default:
@@ -974,35 +1009,36 @@ cudaError_t launch_cdot(int tier, int cfg, const ItemCopy* items, const int32_t*
 
 cudaError_t launch_fanout(const int32_t* src, int n, float2* dst, const float2* vec, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
-  k_fanout<<<(n + 256 * FAN_PER - 1) / (256 * FAN_PER), 256, 0, st>>>(src, n, dst, vec);
-  return cudaGetLastError();
+  const cudaError_t e = launch_pdl(k_fanout, (unsigned)((n + 256 * FAN_PER - 1) / (256 * FAN_PER)), 256, 0, st, src,
+                                   n, dst, vec);
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 cudaError_t launch_gsum(const GsumOut* outs, int nouts, const F2* pscale, const F2* partial, F2 alpha, float2* vout,
                         cudaStream_t st) {
   if (nouts <= 0) return cudaSuccess;
   const int64_t threads = (int64_t)nouts * GS_LANES;
-  k_gsum<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(outs, nouts, pscale, partial, alpha, vout);
-  return cudaGetLastError();
+  const cudaError_t e =
+      launch_pdl(k_gsum, (unsigned)((threads + 255) / 256), 256, 0, st, outs, nouts, pscale, partial, alpha, vout);
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 template <int NW, int NS>
-void rgemv_shape(int tier, int mode, const PieceCopy* pieces, const int32_t* wbeg, int nw, const uint8_t* pay,
+cudaError_t rgemv_shape(int tier, int mode, const PieceCopy* pieces, const int32_t* wbeg, int nw, const uint8_t* pay,
                  const float2* vec, double alpha, F2 alpha_ff, double beta, double* y, const int32_t* perm,
                  float2* vout, const F2* rowscale, F2* fix, int32_t* fixcnt, const Split* splits, int* err,
                  cudaStream_t st) {
   const int grid = (nw + NW - 1) / NW;
   const RsArgs A{pieces, pay, vec, alpha, alpha_ff, beta, y, perm, vout, rowscale, fix, fixcnt, splits, err};
-#define HM_RG(T, M) k_rstream<T, M, NW, NS><<<grid, NW * 32, rs_smem<NW, NS>(), st>>>(A, wbeg, nw)
+#define HM_RG(T, M) launch_pdl(k_rstream<T, M, NW, NS>, grid, NW * 32, rs_smem<NW, NS>(), st, A, wbeg, nw)
   if (tier == TIER_F32) {
-    if (mode == MODE_Y) HM_RG(TIER_F32, MODE_Y);
-    else if (mode == MODE_VEC) HM_RG(TIER_F32, MODE_VEC);
-    else HM_RG(TIER_F32, MODE_VEC_ADD);
-  } else {
-    if (mode == MODE_Y) HM_RG(TIER_FF, MODE_Y);
-    else if (mode == MODE_VEC) HM_RG(TIER_FF, MODE_VEC);
-    else HM_RG(TIER_FF, MODE_VEC_ADD);
+    if (mode == MODE_Y) return HM_RG(TIER_F32, MODE_Y);
+    if (mode == MODE_VEC) return HM_RG(TIER_F32, MODE_VEC);
+    return HM_RG(TIER_F32, MODE_VEC_ADD);
   }
+  if (mode == MODE_Y) return HM_RG(TIER_FF, MODE_Y);
+  if (mode == MODE_VEC) return HM_RG(TIER_FF, MODE_VEC);
+  return HM_RG(TIER_FF, MODE_VEC_ADD);
 #undef HM_RG
 }
 
@@ -1013,10 +1049,12 @@ cudaError_t launch_rgemv(int tier, int mode, int cfg, const PieceCopy* pieces, c
   if (nw <= 0) return cudaSuccess;
   switch (cfg) {
 #define HM_L(I, NW, NS)                                                                                    \
-  case I:                                                                                                  \
-    rgemv_shape<NW, NS>(tier, mode, pieces, wbeg, nw, pay, vec, alpha, alpha_ff, beta, y, perm, vout, rowscale, \
-                        fix, fixcnt, splits, err, st);                                                       \
-    break;
+  case I: {                                                                                                \
+    const cudaError_t e = rgemv_shape<NW, NS>(tier, mode, pieces, wbeg, nw, pay, vec, alpha, alpha_ff, beta, y, \
+                                              perm, vout, rowscale, fix, fixcnt, splits, err, st);           \
+    if (e != cudaSuccess) return e;                                                                        \
+    break;                                                                                                 \
+  }
     HM_RS_CFGS(HM_L)
 #undef HM_L
     default:
