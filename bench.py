@@ -313,12 +313,26 @@ def gpu_arm(args, rank, world):
         build_s = time.perf_counter() - t0
         if not args.no_tune:
             M.autotune(3, stream.cuda_stream)
+        M.graph(not args.no_graph)
         info = M.info()
+        xm = torch.from_numpy(synth.rhs(nm)[:, 0].copy()).cuda()
+        ym = torch.zeros_like(xm)
+        reps = max(5, min(50, args.steps))
+        per, _ = time_variant(torch, M, xm, ym, reps, 3, stream, world)
+        ab = M.alg_bytes()
+        single = {"ms_p50": round(statistics.median(per), 4), "gbs": round(ab / (statistics.median(per) * 1e-3) / 1e9, 1),
+                  "hbm_frac": round(ab / (statistics.median(per) * 1e-3) / 1e9 / hbm_peak, 3)}
         matern = {"workload": f"matern-1.5 l=0.1 N={nm} uniform unit cube, leaf=64 eta=2 H eps=1e-6 AFLP VALR",
                   "payload_mb": round(info["bytes_payload"] / 1e6, 1), "fp64_mb": round(info["bytes_fp64"] / 1e6, 1),
-                  "build_s": round(build_s, 1),
+                  "build_s": round(build_s, 1), "single_rhs": single,
                   "by_nrhs": time_multi_rhs(torch, M, nm, (1, 8, 32, 64), max(3, min(20, args.steps // 20)), 2,
                                             stream)}
+        M.compress(1e-6, "none", True)   # the uncompressed FP64 product of the same matrix
+        if not args.no_tune:
+            M.autotune(3, stream.cuda_stream)
+        per, _ = time_variant(torch, M, xm, ym, reps, 3, stream, world)
+        matern["fp64_ms_p50"] = round(statistics.median(per), 4)
+        matern["speedup_vs_fp64"] = round(statistics.median(per) / single["ms_p50"], 3)
         M.close()
     clk = clocks.stop()
 

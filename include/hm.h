@@ -41,7 +41,8 @@ typedef enum {
   HM_ERR_IO = 6,         /* file could not be read or written */
   HM_ERR_DEVICE = 7,     /* a kernel latched a bounds / format error */
   HM_ERR_UNSUPPORTED = 8, /* data outside what the kernels decode (see hm_compress) */
-  HM_ERR_CAPACITY = 9     /* request larger than hm_matvec_host_noalloc's fixed scratch */
+  HM_ERR_CAPACITY = 9     /* request larger than a fixed limit (hm_matvec_host_noalloc's scratch,
+                             hm_compress's addressing) */
 } hm_status;
 
 typedef enum { HM_FMT_H = 0, HM_FMT_UH = 1, HM_FMT_H2 = 2 } hm_format;
@@ -80,7 +81,9 @@ hm_status hm_build(const hm_build_params* prm, const double* pts, int64_t n, hm_
  * May be called again (other eps / codec): the previous device copy is freed.
  * Synchronises the device.  Errors: HM_ERR_ARG, HM_ERR_OOM, HM_ERR_CUDA,
  * HM_ERR_UNSUPPORTED if a value range exceeds what the kernels decode
- * (AFLP dynamic range >= 2^127, or |v| >= 2^127).
+ * (AFLP dynamic range >= 2^127, or |v| >= 2^127), HM_ERR_CAPACITY if the
+ * packed form exceeds the library's addressing (64 GiB of packed payload:
+ * copy descriptors hold offset / 16 in 32 bits; 2^31 vector entries).
  */
 hm_status hm_compress(hm_matrix* m, double eps, int32_t codec, int32_t valr);
 

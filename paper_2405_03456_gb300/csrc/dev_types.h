@@ -112,11 +112,11 @@ struct CColMeta {
 };
 
 // Copy descriptor of a column-dot piece (pieces start 16-byte aligned):
-// payload offset / 8, total bytes (header included), vector index of row 0,
+// payload offset / 16, total bytes (header included), vector index of row 0,
 // rows.  The input segment is copied only when it differs from the previous
 // piece's of the same warp.
 struct ItemCopy {
-  uint32_t off8;
+  uint32_t off16;
   uint32_t bytes;
   int32_t vin;
   int32_t nrows;
@@ -155,14 +155,15 @@ struct PieceHdr {
 static_assert(sizeof(PieceHdr) == 40, "PieceHdr layout");
 
 // Copy descriptor of a piece for one split of the launch into warp ranges:
-// payload offset / 8; bytes (header included) | range flags << 16 | ncols << 24;
+// payload offset / 16 (pieces start 16-byte aligned); bytes (header included) |
+// range flags << 16 | ncols << 24;
 // first multiplier index; for a chunk shared by several warps, its split index
 // << 8 | this part's index (else -1).
 constexpr uint32_t PD_FIRST = 1;    // first piece of this warp's part of the chunk: clear sums
 constexpr uint32_t PD_LAST = 2;     // last piece of the part: emit
 constexpr uint32_t PD_SPLIT = 4;    // the chunk is shared by several warps: emit through the fix-up
 struct PieceCopy {
-  uint32_t off8;
+  uint32_t off16;
   uint32_t bytes_flags;
   int32_t moff;
   int32_t split_part;

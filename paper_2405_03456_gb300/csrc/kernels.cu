@@ -288,7 +288,7 @@ __global__ void __launch_bounds__(NW * 32, 1)
       dn = dbase + 32 + lane < n ? cps[p0 + dbase + 32 + lane] : zero;
     }
     const int sl = i - dbase;
-    const uint32_t off8 = __shfl_sync(HM_FULL, dc.off8, sl);
+    const uint32_t off16 = __shfl_sync(HM_FULL, dc.off16, sl);
     const uint32_t bytes = __shfl_sync(HM_FULL, dc.bytes, sl);
     const int32_t vin = __shfl_sync(HM_FULL, dc.vin, sl);
     const int32_t nrows = __shfl_sync(HM_FULL, dc.nrows, sl);
@@ -303,7 +303,7 @@ __global__ void __launch_bounds__(NW * 32, 1)
       const uint32_t xb = newx ? pad16u((uint32_t)((vin - x0) + nrows) * 8u) : 0u;
       fence_proxy_async();
       mbar_expect_tx(bar, pb + xb);
-      bulk_g2s_hint(st, pay + (uint64_t)off8 * 8u, pb, bar, pol);
+      bulk_g2s_hint(st, pay + (uint64_t)off16 * 16u, pb, bar, pol);
       if (newx) bulk_g2s(st + A_XOFF, vec + x0, xb, bar);
     }
     issued = i + 1;
@@ -639,7 +639,7 @@ __device__ __forceinline__ bool rs_range(const RsArgs& A, int p0, int n, uint8_t
       dn = dbase + 32 + lane < n ? A.cps[p0 + dbase + 32 + lane] : zero;
     }
     const int sl = i - dbase;
-    const uint32_t off8 = __shfl_sync(HM_FULL, dc.off8, sl);
+    const uint32_t off16 = __shfl_sync(HM_FULL, dc.off16, sl);
     const uint32_t bf = __shfl_sync(HM_FULL, dc.bytes_flags, sl);
     const int32_t moff = __shfl_sync(HM_FULL, dc.moff, sl);
     const int32_t sp = __shfl_sync(HM_FULL, dc.split_part, sl);
@@ -654,7 +654,7 @@ __device__ __forceinline__ bool rs_range(const RsArgs& A, int p0, int n, uint8_t
       int ce = -1;
       fence_proxy_async();
       mbar_expect_tx(bar, pb + mb);
-      bulk_g2s_hint(st, A.pay + (uint64_t)off8 * 8u, pb, bar, pol);
+      bulk_g2s_hint(st, A.pay + (uint64_t)off16 * 16u, pb, bar, pol);
       if constexpr (DF) {
         const SeqDep d = D->deps[p0 + i];
         ce = d.c1;

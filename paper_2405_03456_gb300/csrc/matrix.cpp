@@ -216,7 +216,7 @@ bool seq_dependencies(const Program& P, size_t first, size_t last, std::vector<S
   const auto& Ls = P.launches;
   const auto& pd = P.pdesc[SEQ_SHAPE];
   auto hdr = [&](int64_t i, int32_t& row0, int& nrows) {
-    const uint8_t* h = P.pk.pay.data() + (size_t)pd[i].off8 * 8;
+    const uint8_t* h = P.pk.pay.data() + (size_t)pd[i].off16 * 16;
     std::memcpy(&row0, h, 4);
     uint16_t nr;
     std::memcpy(&nr, h + 4, 2);
@@ -382,7 +382,7 @@ const char* hm_status_str(hm_status s) {
     case HM_ERR_IO: return "I/O error";
     case HM_ERR_DEVICE: return "device-side error latched";
     case HM_ERR_UNSUPPORTED: return "data outside the decodable range";
-    case HM_ERR_CAPACITY: return "request exceeds the fixed device scratch of hm_matvec_host_noalloc";
+    case HM_ERR_CAPACITY: return "request exceeds a fixed limit (noalloc scratch, or the packed form's addressing)";
   }
   return "unknown status";
 }
@@ -433,7 +433,7 @@ hm_status hm_compress(hm_matrix* M, double eps, int32_t codec, int32_t valr) {
   } catch (const std::bad_alloc&) {
     return HM_ERR_OOM;
   }
-  if (!ok) return HM_ERR_UNSUPPORTED;
+  if (!ok) return M->prog.too_large ? HM_ERR_CAPACITY : HM_ERR_UNSUPPORTED;
   M->nsm = nsm;
   hm_status s = upload(M);
   if (s != HM_OK) {

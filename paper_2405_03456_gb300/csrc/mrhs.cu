@@ -293,14 +293,14 @@ __global__ void __launch_bounds__(MR_THREADS, MR_BLOCKS_PER_SM)
       dn = dbase + 32 + lane < n ? cps[p0 + dbase + 32 + lane] : zero;
     }
     const int sl = i - dbase;
-    const uint32_t off8 = __shfl_sync(HM_FULL, dc.off8, sl), bytes = __shfl_sync(HM_FULL, dc.bytes, sl);
+    const uint32_t off16 = __shfl_sync(HM_FULL, dc.off16, sl), bytes = __shfl_sync(HM_FULL, dc.bytes, sl);
     const int32_t vin = __shfl_sync(HM_FULL, dc.vin, sl), nrows = __shfl_sync(HM_FULL, dc.nrows, sl);
     if (lane == 0) {
       const int s = i % MR_STAGES;
       const uint32_t pb = pad16m(bytes), xb = (uint32_t)nrows * RP * 4u;
       fence_proxy_async();
       mbar_expect_tx(&ring.bars[s], pb + xb);
-      bulk_g2s_hint(ring.stage(s), pay + (uint64_t)off8 * 8u, pb, &ring.bars[s], pol);
+      bulk_g2s_hint(ring.stage(s), pay + (uint64_t)off16 * 16u, pb, &ring.bars[s], pol);
       bulk_g2s(ring.stage(s) + STAGE_BYTES, vec + (int64_t)vin * RP, xb, &ring.bars[s]);
     }
   };
@@ -418,7 +418,7 @@ __global__ void __launch_bounds__(MR_THREADS, MR_BLOCKS_PER_SM)
       dn = dbase + 32 + lane < n ? cps[p0 + dbase + 32 + lane] : zero;
     }
     const int sl = i - dbase;
-    const uint32_t off8 = __shfl_sync(HM_FULL, dc.off8, sl), bf = __shfl_sync(HM_FULL, dc.bytes_flags, sl);
+    const uint32_t off16 = __shfl_sync(HM_FULL, dc.off16, sl), bf = __shfl_sync(HM_FULL, dc.bytes_flags, sl);
     const int32_t moff = __shfl_sync(HM_FULL, dc.moff, sl), sp = __shfl_sync(HM_FULL, dc.split_part, sl);
     if (lane == 0) {
       const int s = i % MR_STAGES;
@@ -427,7 +427,7 @@ __global__ void __launch_bounds__(MR_THREADS, MR_BLOCKS_PER_SM)
       info[s] = make_int4((int)((bf >> 16) & 0xffu), sp, 0, 0);
       fence_proxy_async();
       mbar_expect_tx(&ring.bars[s], pb + mb);
-      bulk_g2s_hint(ring.stage(s), pay + (uint64_t)off8 * 8u, pb, &ring.bars[s], pol);
+      bulk_g2s_hint(ring.stage(s), pay + (uint64_t)off16 * 16u, pb, &ring.bars[s], pol);
       if (mb) bulk_g2s(ring.stage(s) + STAGE_BYTES, vec + (int64_t)moff * RP, mb, &ring.bars[s]);
     }
   };

@@ -242,7 +242,7 @@ void pack_cdot(Program& P, const std::vector<CdotCol>& cols, int64_t m, int32_t 
           P.pk.put_rows(cc.cs->col(cc.j) + r0, R, R8, B);
         }
         const uint64_t end = P.pk.align(8);
-        P.items.push_back(ItemCopy{(uint32_t)(off >> 3), (uint32_t)(end - off), h.vin, (int32_t)R});
+        P.items.push_back(ItemCopy{(uint32_t)(off >> 4), (uint32_t)(end - off), h.vin, (int32_t)R});
         // values, header, column metadata, scales, input rows, outputs, copy descriptor
         P.item_alg.push_back(R * B * nc + (int64_t)sizeof(CPieceHdr) + (8 + 8 + (final_out ? 8 : 0)) * nc + 8 * R +
                              (int64_t)sizeof(ItemCopy));
@@ -438,7 +438,7 @@ void add_rgemv(Ctx& cx, std::vector<ChunkWork>& cw, int mode, bool rowscale) {
       meta += (2 + 8) * p.ncols;   // decode parameters + multipliers
     }
     const uint64_t end = P.pk.align(8);
-    base[i] = PieceCopy{(uint32_t)(off >> 3), (uint32_t)(end - off) | ((uint32_t)p.ncols << 24), (int32_t)moff, -1};
+    base[i] = PieceCopy{(uint32_t)(off >> 4), (uint32_t)(end - off) | ((uint32_t)p.ncols << 24), (int32_t)moff, -1};
     int64_t alg = vals + meta;
     const bool last_of_chunk = (i + 1 == pw.size()) || pw[i + 1].chunk != p.chunk;
     if (last_of_chunk) {   // output rows of the chunk
@@ -978,9 +978,14 @@ bool build_program(const HostMatrix& H, int codec, double eps, int valr, int nsm
     default: ok = program_h2(cx); break;
   }
   cx.tiles.clear();
-  if (ok && P.pk.pay.size() >= (1ull << 35)) ok = false;   // copy descriptors hold offset / 8 in 32 bits
+  if (ok && P.pk.pay.size() >= (1ull << 36)) {   // copy descriptors hold offset / 16 in 32 bits
+    ok = false;
+    P.too_large = true;
+  }
   if (!ok) {
+    const bool big = P.too_large;
     P = Program();
+    P.too_large = big;
     return false;
   }
   P.pk.align(16);
@@ -995,6 +1000,7 @@ bool build_program(const HostMatrix& H, int codec, double eps, int valr, int nsm
   if (P.rowscale.empty()) P.rowscale.assign(1, 1.0);
   if (P.nvec >= INT32_MAX) {
     P = Program();
+    P.too_large = true;
     return false;
   }
   finish_launches(cx);

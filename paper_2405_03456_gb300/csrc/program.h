@@ -84,6 +84,7 @@ struct Program {
   std::vector<Split> splits;      // chunks shared by several warps (all launch shapes)
   int64_t nfix = 0;               // fix-up slots (CHUNK_ROWS float-float rows each), largest warp shape
   int64_t nfix_seq = 0;           // fix-up slots of shape SEQ_SHAPE, distinct across all launches
+  bool too_large = false;         // build_program failed on an addressing limit (payload, vector)
   int64_t nfix_mr = 0;            // fix-up slots of the multi-RHS shape (CHUNK_ROWS x RP each)
   int64_t nchunks = 0;
   std::vector<int32_t> fan_src;   // fan-out: slot s takes v[fan_src[s]]; slot s is v[fan_base + s]

@@ -66,7 +66,7 @@ def test_noalloc_rejects_oversize(hm):
         M.compress(1e-4, "fpx", True)
         x = np.asfortranarray(np.zeros((n, 64)))
         y = np.asfortranarray(np.zeros((n, 64)))
-        with pytest.raises(hm.HMError, match="fixed device scratch"):
+        with pytest.raises(hm.HMError, match="fixed limit"):
             hm.hm_matvec_host_noalloc(M.h, 1.0, x, 0.0, y)
     finally:
         M.close()
