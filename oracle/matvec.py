@@ -11,6 +11,8 @@ Sequential FP64 versions of the paper's algorithms, one block at a time:
 * ``h2_mvm``  -- Alg. 6 (leaf forward, then s_s += E_s'^H s_s' leaves to root),
                  then Alg. 7 root to leaves (couplings, t_t' += E_t' t_t at inner
                  clusters, y' := W_t t_t at leaves, dense blocks, y|t += y').
+* ``*_adjoint`` -- y := alpha M^H x + beta y (the remark after Alg. 3: the same
+                 steps over the block columns).
 
 Compressed matrices are decompressed block by block before the product
 (Alg. 8 computes the same sum, entry by entry).  beta extends the paper's
@@ -193,6 +195,151 @@ def h2_mvm(m, alpha: float, x, beta: float = 1.0, y=None):
             h2mvm(son)
 
     h2mvm(0)
+    return _perm_out(ct, yp)
+
+
+# ---------------------------------------------------------------- adjoint products
+# The remark after Alg. 3: the adjoint product M^H x runs the same way over the
+# block columns.  The data are real, so M^H = M^T: a low-rank block
+# W diag(sigma) X^T contributes y|s += alpha X diag(sigma) (W^T x|t), a dense
+# block y|s += alpha D^T x|t; for UH / H2 the roles of the row and column
+# bases swap and every coupling is applied transposed.
+
+def h_mvm_adjoint(m, alpha: float, x, beta: float = 1.0, y=None):
+    """y := alpha M^H x + beta y, block by block over an HMatrix or CH."""
+    h = m if isinstance(m, HMatrix) else m.h
+    ct = h.ct
+    cl = ct.clusters
+    if y is None:
+        y = np.zeros_like(np.asarray(x, dtype=np.float64))
+    xp, yp = _perm_in(ct, x, y, beta)
+    for i, b in enumerate(h.blocks):
+        t, s = cl[b.row], cl[b.col]
+        xt = xp[t.start:t.end]
+        if isinstance(m, HMatrix):
+            d = m.data[i]
+            if isinstance(d, LowRank):
+                tv = (d.s * (d.W.T @ xt).T).T
+                yp[s.start:s.end] += alpha * (d.X @ tv)
+            else:
+                yp[s.start:s.end] += alpha * (d.T @ xt)
+            continue
+        blk = m.blocks[i]
+        if blk[0] == "lr":
+            sv = blk[1]
+            W = unvalr(blk[2], t.size)
+            X = unvalr(blk[3], s.size)
+            tv = (sv * (W.T @ xt).T).T
+            yp[s.start:s.end] += alpha * (X @ tv)
+        else:
+            yp[s.start:s.end] += alpha * (undirect(blk[1]).T @ xt)
+    return _perm_out(ct, yp)
+
+
+def uh_mvm_adjoint(m, alpha: float, x, beta: float = 1.0, y=None):
+    """Adjoint of Alg. 4 + 5: forward with the row bases, S^T per block column,
+    backward with the column bases, dense blocks transposed."""
+    u = m if isinstance(m, Uniform) else m.u
+    h = u.h
+    ct = h.ct
+    cl = ct.clusters
+    if y is None:
+        y = np.zeros_like(np.asarray(x, dtype=np.float64))
+    xp, yp = _perm_in(ct, x, y, beta)
+    comp = not isinstance(m, Uniform)
+    Wb = [unvalr(m.W[c.id], c.size) for c in cl] if comp else u.W
+    Xb = [unvalr(m.X[c.id], c.size) for c in cl] if comp else u.X
+    sw = [Wb[c.id].T @ xp[c.start:c.end] for c in cl]     # forward with the row bases
+    cols = [[] for _ in cl]
+    for i, b in enumerate(h.blocks):
+        cols[b.col].append(i)
+
+    def coupling(i):
+        return undirect(m.S[i][1]) if comp else u.S[i]
+
+    for c in cl:                                          # block column c
+        tt = np.zeros((Xb[c.id].shape[1],) + xp.shape[1:])
+        yl = np.zeros((c.size,) + xp.shape[1:])
+        for i in cols[c.id]:
+            b = h.blocks[i]
+            if b.adm:
+                tt += coupling(i).T @ sw[b.row]
+            else:
+                rt = cl[b.row]
+                yl += coupling(i).T @ xp[rt.start:rt.end]
+        yp[c.start:c.end] += alpha * (Xb[c.id] @ tt + yl)
+    return _perm_out(ct, yp)
+
+
+def h2_mvm_adjoint(m, alpha: float, x, beta: float = 1.0, y=None):
+    """Adjoint of Alg. 6 + 7: up-sweep with the row bases (leaf W, transfers
+    E_W), S^T per block column, down-sweep with the column transfers E_X,
+    leaf column bases X, dense blocks transposed."""
+    h2 = m if isinstance(m, H2) else m.m
+    h = h2.h
+    ct = h.ct
+    cl = ct.clusters
+    comp = not isinstance(m, H2)
+    if y is None:
+        y = np.zeros_like(np.asarray(x, dtype=np.float64))
+    xp, yp = _perm_in(ct, x, y, beta)
+    tail = xp.shape[1:]
+
+    def leafW(cid):
+        return unvalr(m.Wleaf[cid], cl[cid].size) if comp else h2.Wleaf[cid]
+
+    def leafX(cid):
+        return unvalr(m.Xleaf[cid], cl[cid].size) if comp else h2.Xleaf[cid]
+
+    def EW(cid):
+        return undirect(m.EW[cid]) if comp else h2.EW[cid]
+
+    def EX(cid):
+        return undirect(m.EX[cid]) if comp else h2.EX[cid]
+
+    def coupling(i):
+        return undirect(m.S[i][1]) if comp else h2.S[i]
+
+    s = [None] * len(cl)
+
+    def up(tid: int) -> None:                         # row side, leaves to root
+        c = cl[tid]
+        if c.is_leaf:
+            s[tid] = leafW(tid).T @ xp[c.start:c.end]
+            return
+        s[tid] = np.zeros((h2.kW[tid],) + tail)
+        for son in c.sons:
+            up(son)
+            s[tid] += EW(son).T @ s[son]
+
+    up(0)
+    cols = [[] for _ in cl]
+    for i, b in enumerate(h.blocks):
+        cols[b.col].append(i)
+    t = [np.zeros((h2.kX[c.id],) + tail) for c in cl]
+
+    def down(sid: int) -> None:                       # column side, root to leaves
+        c = cl[sid]
+        for i in cols[sid]:
+            b = h.blocks[i]
+            if b.adm:
+                t[sid] += coupling(i).T @ s[b.row]
+        if c.is_leaf:
+            yl = leafX(sid) @ t[sid]
+        else:
+            yl = np.zeros((c.size,) + tail)
+            for son in c.sons:
+                t[son] += EX(son) @ t[sid]
+        for i in cols[sid]:
+            b = h.blocks[i]
+            if not b.adm:
+                rt = cl[b.row]
+                yl = yl + coupling(i).T @ xp[rt.start:rt.end]
+        yp[c.start:c.end] += alpha * yl
+        for son in c.sons:
+            down(son)
+
+    down(0)
     return _perm_out(ct, yp)
 
 
