@@ -101,6 +101,22 @@ hm_status hm_matvec(hm_matrix* m, double alpha, const double* x, int64_t ldx, do
                     double* y, int64_t ldy, int64_t nrhs, void* stream);
 
 /*
+ * hm_matvec_adjoint -- y := alpha*M^H*x + beta*y (the remark after Alg. 3: the
+ * adjoint product runs over the block columns; the data are real, so
+ * M^H = M^T).  Same arguments, layout, stream semantics and errors as
+ * hm_matvec.  The first call builds the transposed matrix on the host (blocks
+ * (t, s) -> (s, t): W and X swapped, dense blocks and couplings transposed, row
+ * and column bases exchanged), compresses it with the eps / codec / valr of the
+ * last hm_compress -- the same codes, rearranged -- and uploads it; this first
+ * call synchronises the stream and needs host and device memory about as large
+ * as m's own.  Later calls reuse it until the next hm_compress or hm_free.  The
+ * transposed matrix follows m's hm_graph and hm_persistent settings and runs
+ * launch shape 0 (hm_autotune tunes m only).
+ */
+hm_status hm_matvec_adjoint(hm_matrix* m, double alpha, const double* x, int64_t ldx, double beta,
+                            double* y, int64_t ldy, int64_t nrhs, void* stream);
+
+/*
  * hm_matvec_host -- the same product on HOST buffers: copies x and y to the
  * device, runs hm_matvec, copies y back, and synchronises the stream.
  * x, y : host FP64 (n x nrhs, ld n, column-major).  Uses library-owned

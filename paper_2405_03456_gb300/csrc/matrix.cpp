@@ -119,6 +119,8 @@ struct hm_matrix {
   DevArr<SeqPhase> d_phases;
   DevArr<SeqDep> d_deps;       // per piece (pieces of runs only)
   unsigned* d_ver = nullptr;   // chunk versions + abort word of the largest run
+  // the transposed matrix (adjoint products), built on first use, owned
+  hm_matrix* adj = nullptr;
   std::mutex mu;
   // CUDA graph of the whole launch sequence, cached per call signature
   bool use_graph = false;
@@ -279,6 +281,46 @@ bool seq_dependencies(const Program& P, size_t first, size_t last, std::vector<S
   return true;
 }
 
+// The transpose of an H / UH / H2 matrix on the host: every block (t, s)
+// becomes (s, t) with W and X swapped (low rank), D^T (dense), S^T (couplings),
+// and the row and column bases (with their transfer matrices) trade places.
+// Same cluster tree, same block numbering, same singular values: compressing it
+// gives the codes of the original blocks, rearranged.
+void transpose_host(const HostMatrix& H, HostMatrix& T) {
+  T.prm = H.prm;
+  T.n = H.n;
+  T.kparam = H.kparam;
+  T.pts = H.pts;
+  T.ct = H.ct;
+  T.blocks = H.blocks;
+  for (BlockLeaf& b : T.blocks) std::swap(b.row, b.col);
+  T.slot = H.slot;
+  T.lr = H.lr;
+  for (LowRankBlock& l : T.lr) std::swap(l.W, l.X);
+  T.dn.assign(H.dn.size(), DenseBlock());
+  T.coupling.assign(H.coupling.size(), std::vector<double>());
+  for (size_t b = 0; b < H.blocks.size(); ++b) {
+    const int64_t nt = H.ct.cl[H.blocks[b].row].size(), ns = H.ct.cl[H.blocks[b].col].size();
+    const int sl = H.slot[b];
+    if (!H.blocks[b].adm) {
+      const std::vector<double>& D = H.dn[sl].D;   // nt x ns
+      std::vector<double>& Dt = T.dn[sl].D;        // ns x nt
+      Dt.resize(D.size());
+      for (int64_t j = 0; j < ns; ++j)
+        for (int64_t i = 0; i < nt; ++i) Dt[(size_t)j + (size_t)i * ns] = D[(size_t)i + (size_t)j * nt];
+    } else if ((size_t)sl < H.coupling.size() && !H.coupling[sl].empty()) {
+      const int kt = H.rowb.k[H.blocks[b].row], ks = H.colb.k[H.blocks[b].col];
+      const std::vector<double>& S = H.coupling[sl];   // kt x ks
+      std::vector<double>& St = T.coupling[sl];        // ks x kt
+      St.resize(S.size());
+      for (int j = 0; j < ks; ++j)
+        for (int i = 0; i < kt; ++i) St[(size_t)j + (size_t)i * ks] = S[(size_t)i + (size_t)j * kt];
+    }
+  }
+  T.rowb = H.colb;
+  T.colb = H.rowb;
+}
+
 hm_status upload(hm_matrix* M) {
   Program& P = M->prog;
   cudaError_t e;
@@ -427,6 +469,10 @@ hm_status hm_compress(hm_matrix* M, double eps, int32_t codec, int32_t valr) {
     return HM_ERR_CUDA;
   cudaDeviceSynchronize();
   M->release_device();
+  if (M->adj) {
+    hm_free(M->adj);
+    M->adj = nullptr;
+  }
   bool ok;
   try {
     ok = build_program(M->H, codec, eps, valr, nsm, M->prog);
@@ -649,6 +695,33 @@ hm_status hm_matvec_host(hm_matrix* M, double alpha, const double* x, double bet
   return HM_OK;
 }
 
+hm_status hm_matvec_adjoint(hm_matrix* M, double alpha, const double* x, int64_t ldx, double beta, double* y,
+                            int64_t ldy, int64_t nrhs, void* stream) {
+  if (!M || !x || !y || nrhs < 1 || nrhs > 64) return HM_ERR_ARG;
+  hm_matrix* A = nullptr;
+  {
+    std::lock_guard<std::mutex> g(M->mu);
+    if (!M->compressed) return HM_ERR_STATE;
+    if (!M->adj) {   // first adjoint product: transpose, compress with the same settings, upload
+      std::unique_ptr<hm_matrix> T;
+      try {
+        T.reset(new hm_matrix());
+        transpose_host(M->H, T->H);
+      } catch (const std::bad_alloc&) {
+        return HM_ERR_OOM;
+      }
+      if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return HM_ERR_CUDA;
+      const hm_status s = hm_compress(T.get(), M->eps, M->codec, M->valr);
+      if (s != HM_OK) return s;
+      M->adj = T.release();
+    }
+    M->adj->use_graph = M->use_graph;
+    M->adj->fuse = M->fuse;
+    A = M->adj;
+  }
+  return hm_matvec(A, alpha, x, ldx, beta, y, ldy, nrhs, stream);
+}
+
 hm_status hm_autotune(hm_matrix* M, int32_t reps, void* stream) {
   if (!M || reps < 1 || reps > 1000) return HM_ERR_ARG;
   std::lock_guard<std::mutex> g(M->mu);
@@ -749,6 +822,8 @@ hm_status hm_alg_bytes(const hm_matrix* M, int64_t* bytes) {
 
 hm_status hm_free(hm_matrix* M) {
   if (!M) return HM_OK;
+  if (M->adj) hm_free(M->adj);
+  M->adj = nullptr;
   M->drop_graph();
   if (M->cap_stream) cudaStreamDestroy(M->cap_stream);
   for (auto& r : M->recs) {

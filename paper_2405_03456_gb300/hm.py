@@ -25,7 +25,7 @@ KERNELS = {"laplace": HM_KERNEL_LAPLACE, "matern": HM_KERNEL_MATERN15}
 DECLARED = ["hm_build", "hm_compress", "hm_matvec", "hm_matvec_host", "hm_free", "hm_info",
             "hm_status_str", "hm_sync_status", "hm_structure", "hm_codec_encode", "hm_codec_decode",
             "hm_profile", "hm_profile_read", "hm_alg_bytes", "hm_matvec_host_noalloc", "hm_graph",
-            "hm_autotune", "hm_launch_shapes", "hm_set_launch_shapes", "hm_persistent"]
+            "hm_autotune", "hm_launch_shapes", "hm_set_launch_shapes", "hm_persistent", "hm_matvec_adjoint"]
 NSHAPES = 3
 HM_NOALLOC_MAX_ENTRIES = 1 << 20
 KERNEL_KINDS = ["gather", "cdot", "gsum", "rgemv", "fanout"]
@@ -91,6 +91,7 @@ def load(path: str | None = None) -> C.CDLL:
         "hm_codec_decode": ([vp, i64, C.POINTER(hm_codec_header), vp, vp], i32),
         "hm_profile": ([vp, i32], i32),
         "hm_persistent": ([vp, i32], i32),
+        "hm_matvec_adjoint": ([vp, dbl, vp, i64, dbl, vp, i64, i64, vp], i32),
         "hm_profile_read": ([vp, C.POINTER(hm_kernel_stat), i32], i32),
         "hm_alg_bytes": ([vp, C.POINTER(i64)], i32),
         "hm_matvec_host_noalloc": ([vp, dbl, vp, dbl, vp, i64, vp], i32),
@@ -134,6 +135,11 @@ def hm_compress(h: int, eps: float, codec: str = "aflp", valr: bool = True) -> N
 def hm_matvec(h: int, alpha: float, x_ptr: int, ldx: int, beta: float, y_ptr: int, ldy: int,
               nrhs: int = 1, stream: int = 0) -> None:
     check(load().hm_matvec(h, alpha, x_ptr, ldx, beta, y_ptr, ldy, nrhs, stream), "hm_matvec")
+
+
+def hm_matvec_adjoint(h: int, alpha: float, x_ptr: int, ldx: int, beta: float, y_ptr: int, ldy: int,
+                      nrhs: int = 1, stream: int = 0) -> None:
+    check(load().hm_matvec_adjoint(h, alpha, x_ptr, ldx, beta, y_ptr, ldy, nrhs, stream), "hm_matvec_adjoint")
 
 
 def hm_matvec_host(h: int, alpha: float, x: np.ndarray, beta: float, y: np.ndarray, stream: int = 0) -> None:
@@ -249,8 +255,9 @@ class HMatrix:
         hm_compress(self.h, eps, codec, valr)
         return self
 
-    def matvec(self, alpha, x, beta, y, stream=None):
-        """y := alpha*M*x + beta*y for CUDA FP64 tensors x, y of shape (n,) or (n, r) column-major."""
+    def matvec(self, alpha, x, beta, y, stream=None, adjoint=False):
+        """y := alpha*M*x + beta*y (adjoint: alpha*M^H*x + beta*y) for CUDA FP64
+        tensors x, y of shape (n,) or (n, r) column-major."""
         import torch
         if stream is None:
             stream = torch.cuda.current_stream().cuda_stream
@@ -261,7 +268,8 @@ class HMatrix:
         assert x.dtype == torch.float64 and y.dtype == torch.float64 and x.is_cuda and y.is_cuda
         assert x.dim() == 1 or x.stride(0) == 1
         assert y.dim() == 1 or y.stride(0) == 1
-        hm_matvec(self.h, alpha, x.data_ptr(), ldx, beta, y.data_ptr(), ldy, nrhs, stream)
+        f = hm_matvec_adjoint if adjoint else hm_matvec
+        f(self.h, alpha, x.data_ptr(), ldx, beta, y.data_ptr(), ldy, nrhs, stream)
         return y
 
     def matvec_host(self, alpha, x, beta, y, stream=0):
