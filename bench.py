@@ -127,9 +127,9 @@ def run_cpu_child(budget_mb, passes, warmup, timeout=600):
 
 
 # ------------------------------------------------------------------ GPU arm
-def time_variant(torch, M, x, y, steps, warmup, stream, world=1):
+def time_variant(torch, M, x, y, steps, warmup, stream, world=1, adjoint=False):
     for _ in range(warmup):
-        M.matvec(1.0, x, 1.0, y, stream=stream.cuda_stream)
+        M.matvec(1.0, x, 1.0, y, stream=stream.cuda_stream, adjoint=adjoint)
     torch.cuda.synchronize()
     if world > 1:
         import torch.distributed as dist
@@ -142,7 +142,7 @@ def time_variant(torch, M, x, y, steps, warmup, stream, world=1):
         start.record(stream)
         for a, b in ev:
             a.record(stream)
-            M.matvec(1.0, x, 1.0, y, stream=stream.cuda_stream)
+            M.matvec(1.0, x, 1.0, y, stream=stream.cuda_stream, adjoint=adjoint)
             b.record(stream)
         end.record(stream)
     torch.cuda.synchronize()
@@ -284,6 +284,13 @@ def gpu_arm(args, rank, world):
                 ems = e0.elapsed_time(e1) / esteps
                 headline["e2e"] = {"value": ab / (ems * 1e-3) / 1e9 * world, "unit": "GB/s",
                                    "ms_per_step": ems, "h2d_bytes_per_step": 16 * n, "d2h_bytes_per_step": 8 * n}
+                # adjoint product y := M^H x + y on the same matrix (transposed matrix built on first use)
+                aper, _ = time_variant(torch, M, x, y, max(20, min(args.steps, 200)), 3, stream, world, adjoint=True)
+                amed = statistics.median(aper)
+                headline["adjoint"] = {"ms_p50": round(amed, 4), "ms_p99": round(pct(aper, 0.99), 4),
+                                       "gbs": round(ab / (amed * 1e-3) / 1e9, 1),
+                                       "note": "M^H x on the same compressed matrix (transpose built on first use, "
+                                               "launch shape 0); GB/s counts the forward product's algorithmic bytes"}
         M.close()
     # uniform-H and H^2 formats of the same problem (one persistent graph-captured product each)
     fmt_results = {}
@@ -387,6 +394,7 @@ def gpu_arm(args, rank, world):
                                      "gbs": round(v["bytes"] / max(v["ms"], 1e-9) / 1e6, 1)}
                                  for k, v in prof.items()}},
         "e2e": headline["e2e"],
+        "adjoint": headline.get("adjoint"),
         "gpu_launches": int(headline["launches"] * args.steps),
         "clocks": clk,
         "by_eps": by_eps,
