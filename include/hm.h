@@ -46,6 +46,12 @@ typedef enum {
 } hm_status;
 
 typedef enum { HM_FMT_H = 0, HM_FMT_UH = 1, HM_FMT_H2 = 2 } hm_format;
+/* Admissibility of the block tree (Def. Block Tree and the remark after Def.
+ * H-Matrix): STANDARD min(diam t, diam s) <= eta dist(t, s); HODLR off-diagonal
+ * (every block of two distinct clusters is low rank, dense blocks only on the
+ * diagonal); BLR a single level (only blocks of leaf clusters are tested with the
+ * standard condition, larger blocks are always subdivided). */
+typedef enum { HM_ADM_STANDARD = 0, HM_ADM_HODLR = 1, HM_ADM_BLR = 2 } hm_adm;
 typedef enum { HM_CODEC_NONE = 0, HM_CODEC_AFLP = 1, HM_CODEC_FPX = 2 } hm_codec;
 typedef enum { HM_KERNEL_LAPLACE = 0, HM_KERNEL_MATERN15 = 1 } hm_kernel;
 
@@ -58,6 +64,7 @@ typedef struct {
   int32_t format;      /* hm_format */
   double eps_build;    /* low-rank accuracy eps (eqn. epsilon), 0 < eps < 1 */
   int32_t nthreads;    /* host threads for construction (<= 0: all cores) */
+  int32_t adm;         /* hm_adm: admissibility condition (0 = standard) */
 } hm_build_params;
 
 /*
@@ -83,7 +90,9 @@ hm_status hm_build(const hm_build_params* prm, const double* pts, int64_t n, hm_
  * HM_ERR_UNSUPPORTED if a value range exceeds what the kernels decode
  * (AFLP dynamic range >= 2^127, or |v| >= 2^127), HM_ERR_CAPACITY if the
  * packed form exceeds the library's addressing (64 GiB of packed payload:
- * copy descriptors hold offset / 16 in 32 bits; 2^31 vector entries).
+ * copy descriptors hold offset / 16 in 32 bits; 2^31 vector entries) or its
+ * layout (H^2 cluster bases of rank > 128: a sweep chunk holds <= 128
+ * coefficients).
  */
 hm_status hm_compress(hm_matrix* m, double eps, int32_t codec, int32_t valr);
 

@@ -57,13 +57,15 @@ def truncate_rank(s: np.ndarray, eps: float) -> int:
 
 
 def build_h(pts: np.ndarray, kind: str, leaf: int, eta: float, eps: float,
-            param: float | None = None) -> HMatrix:
-    """Build an H-matrix of the model kernel on ``pts`` (exact SVD per block)."""
+            param: float | None = None, adm: str = "std") -> HMatrix:
+    """Build an H-matrix of the model kernel on ``pts`` (exact SVD per block);
+    ``adm`` picks the admissibility (``trees.block_admissible``: standard,
+    HODLR, BLR)."""
     n = pts.shape[0]
     if param is None:
         param = kernels.default_param(kind, n)
     ct = build_cluster_tree(pts, leaf)
-    blocks = build_block_tree(ct, eta)
+    blocks = build_block_tree(ct, eta, adm)
     data = []
     for b in blocks:
         rt = ct.perm[ct.clusters[b.row].start:ct.clusters[b.row].end]

@@ -113,14 +113,37 @@ class Block:
     adm: bool
 
 
-def build_block_tree(ct: ClusterTree, eta: float) -> list:
+ADM_MODES = ("std", "hodlr", "blr")
+
+
+def block_admissible(a: Cluster, b: Cluster, eta: float, mode: str) -> bool:
+    """The admissibility condition of the block tree.  The remark after Def.
+    H-Matrix: BLR and HODLR are H-matrices whose clustering or admissibility is
+    chosen accordingly.
+
+    * ``std``   -- standard admissibility with parameter eta (``admissible``);
+    * ``hodlr`` -- off-diagonal admissibility: every block of two distinct
+      clusters is admissible, inadmissibility restricted to the diagonal;
+    * ``blr``   -- a single hierarchy level: only blocks of leaf clusters are
+      tested (standard condition), larger blocks are always subdivided.
+    """
+    if mode == "std":
+        return admissible(a, b, eta)
+    if mode == "hodlr":
+        return a.id != b.id
+    if mode == "blr":
+        return (a.is_leaf or b.is_leaf) and admissible(a, b, eta)
+    raise ValueError(mode)
+
+
+def build_block_tree(ct: ClusterTree, eta: float, mode: str = "std") -> list:
     """Leaves of the block tree T_{IxI} (Def. Block Tree), depth-first order."""
     out: list = []
     cl = ct.clusters
 
     def rec(t: int, s: int) -> None:
         a, b = cl[t], cl[s]
-        if admissible(a, b, eta):
+        if block_admissible(a, b, eta, mode):
             out.append(Block(t, s, True))
         elif a.is_leaf or b.is_leaf:
             out.append(Block(t, s, False))

@@ -33,7 +33,7 @@ struct BlockLeaf {
 };
 
 void build_cluster_tree(const double* pts, int64_t n, int leaf, ClusterTree& ct);
-void build_block_tree(const ClusterTree& ct, double eta, std::vector<BlockLeaf>& out);
+void build_block_tree(const ClusterTree& ct, double eta, std::vector<BlockLeaf>& out, int mode = HM_ADM_STANDARD);
 
 // ---------------------------------------------------------------- dense algebra (column-major)
 // Thin Householder QR of an m x n matrix (m >= n or not): A = Q R, Q m x r, R r x n, r = min(m, n).

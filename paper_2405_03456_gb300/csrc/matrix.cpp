@@ -435,6 +435,7 @@ hm_status hm_build(const hm_build_params* prm, const double* pts, int64_t n, hm_
   if (!(prm->eta > 0) || !(prm->eps_build > 0 && prm->eps_build < 1)) return HM_ERR_ARG;
   if (prm->format < HM_FMT_H || prm->format > HM_FMT_H2) return HM_ERR_ARG;
   if (prm->kernel != HM_KERNEL_LAPLACE && prm->kernel != HM_KERNEL_MATERN15) return HM_ERR_ARG;
+  if (prm->adm < HM_ADM_STANDARD || prm->adm > HM_ADM_BLR) return HM_ERR_ARG;
   for (int64_t i = 0; i < 3 * n; ++i)
     if (!std::isfinite(pts[i])) return HM_ERR_ARG;
   std::unique_ptr<hm_matrix> M;
@@ -448,7 +449,7 @@ hm_status hm_build(const hm_build_params* prm, const double* pts, int64_t n, hm_
     H.pts.assign(pts, pts + 3 * n);
     int nth = prm->nthreads > 0 ? prm->nthreads : (int)std::max(1u, std::thread::hardware_concurrency());
     build_cluster_tree(H.pts.data(), n, prm->leaf_size, H.ct);
-    build_block_tree(H.ct, prm->eta, H.blocks);
+    build_block_tree(H.ct, prm->eta, H.blocks, prm->adm);
     build_lowrank_blocks(H, nth);
     if (prm->format == HM_FMT_UH) build_uniform_bases(H, nth);
     if (prm->format == HM_FMT_H2) build_nested_bases(H, nth);

@@ -822,7 +822,10 @@ bool program_h2(Ctx& cx) {
   const int64_t N = H.n;
   const int nc = (int)ct.cl.size();
   for (int c = 0; c < nc; ++c)   // an up- or down-sweep chunk holds <= 128 coefficients
-    if (H.rowb.k[c] > CHUNK_ROWS || H.colb.k[c] > CHUNK_ROWS) return false;
+    if (H.rowb.k[c] > CHUNK_ROWS || H.colb.k[c] > CHUNK_ROWS) {
+      P.too_large = true;
+      return false;
+    }
   const auto lv = leaves_under(ct);
   std::vector<std::vector<const TileData*>> dt;
   if (!pack_dense(cx, lv, dt)) return false;
@@ -983,7 +986,7 @@ bool build_program(const HostMatrix& H, int codec, double eps, int valr, int nsm
     P.too_large = true;
   }
   if (!ok) {
-    const bool big = P.too_large;
+    const bool big = P.too_large;   // set by an addressing or layout limit
     P = Program();
     P.too_large = big;
     return false;

@@ -109,7 +109,7 @@ void build_cluster_tree(const double* pts, int64_t n, int leaf, ClusterTree& ct)
   ct.perm = idx;
 }
 
-void build_block_tree(const ClusterTree& ct, double eta, std::vector<BlockLeaf>& out) {
+void build_block_tree(const ClusterTree& ct, double eta, std::vector<BlockLeaf>& out, int mode) {
   out.clear();
   const double eta2 = eta * eta;
   std::function<void(int, int)> rec = [&](int t, int s) {
@@ -117,7 +117,13 @@ void build_block_tree(const ClusterTree& ct, double eta, std::vector<BlockLeaf>&
     const Cluster& b = ct.cl[s];
     double d2 = dist2(a, b);
     double da = diam2(a), db = diam2(b);
-    bool adm = d2 > 0.0 && (da < db ? da : db) <= eta2 * d2;
+    const bool std_adm = d2 > 0.0 && (da < db ? da : db) <= eta2 * d2;
+    // admissibility modes (the remark after Def. H-Matrix): standard, off-diagonal
+    // (HODLR: inadmissible only on the diagonal), single level (BLR: only blocks
+    // of leaf clusters are tested)
+    bool adm = std_adm;
+    if (mode == HM_ADM_HODLR) adm = t != s;
+    if (mode == HM_ADM_BLR) adm = (a.leaf() || b.leaf()) && std_adm;
     if (adm) {
       out.push_back({t, s, true});
     } else if (a.leaf() || b.leaf()) {

@@ -34,7 +34,7 @@ KERNEL_KINDS = ["gather", "cdot", "gsum", "rgemv", "fanout"]
 class hm_build_params(C.Structure):
     _fields_ = [("kernel", C.c_int32), ("kparam", C.c_double), ("leaf_size", C.c_int32),
                 ("eta", C.c_double), ("format", C.c_int32), ("eps_build", C.c_double),
-                ("nthreads", C.c_int32)]
+                ("nthreads", C.c_int32), ("adm", C.c_int32)]
 
 
 class hm_info_t(C.Structure):
@@ -119,9 +119,13 @@ def _ptr(a: np.ndarray) -> int:
 
 
 # ---------------------------------------------------------------- C entry points
+ADMS = {"std": 0, "hodlr": 1, "blr": 2}
+
+
 def hm_build(pts: np.ndarray, kernel: str = "laplace", leaf_size: int = 64, eta: float = 2.0,
-             fmt: str = "h", eps_build: float = 1e-6, kparam: float = 0.0, nthreads: int = 0) -> int:
-    p = hm_build_params(KERNELS[kernel], kparam, leaf_size, eta, FORMATS[fmt], eps_build, nthreads)
+             fmt: str = "h", eps_build: float = 1e-6, kparam: float = 0.0, nthreads: int = 0,
+             adm: str = "std") -> int:
+    p = hm_build_params(KERNELS[kernel], kparam, leaf_size, eta, FORMATS[fmt], eps_build, nthreads, ADMS[adm])
     pts = np.ascontiguousarray(pts, dtype=np.float64)
     h = C.c_void_p()
     check(load().hm_build(C.byref(p), _ptr(pts), pts.shape[0], C.byref(h)), "hm_build")
@@ -247,8 +251,8 @@ class HMatrix:
     """Owns one hm_matrix handle; products take CUDA tensors (torch) or host arrays."""
 
     def __init__(self, pts, kernel="laplace", leaf_size=64, eta=2.0, fmt="h", eps_build=1e-6,
-                 kparam=0.0, nthreads=0):
-        self.h = hm_build(pts, kernel, leaf_size, eta, fmt, eps_build, kparam, nthreads)
+                 kparam=0.0, nthreads=0, adm="std"):
+        self.h = hm_build(pts, kernel, leaf_size, eta, fmt, eps_build, kparam, nthreads, adm)
         self.n = pts.shape[0]
 
     def compress(self, eps, codec="aflp", valr=True):

@@ -51,6 +51,20 @@ def test_trees_bit_exact(hm, case):
     assert np.all((rk >= 0) == (bl[:, 2] == 1))
 
 
+@pytest.mark.parametrize("adm", ["hodlr", "blr"])
+def test_trees_bit_exact_other_admissibility(hm, adm):
+    pts = synth.sphere_points(2048)
+    h = hm.hm_build(pts, "laplace", 32, 2.0, "h", 1e-4, adm=adm)
+    try:
+        perm, cl, bl, rk = hm.hm_structure(h)
+    finally:
+        hm.hm_free(h)
+    ct = trees.build_cluster_tree(pts, 32)
+    ob = trees.build_block_tree(ct, 2.0, adm)
+    assert np.array_equal(bl, np.array([[x.row, x.col, int(x.adm)] for x in ob]))
+    assert np.all((rk >= 0) == (bl[:, 2] == 1))
+
+
 def _cases():
     out = []
     for seed in range(6):

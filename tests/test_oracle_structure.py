@@ -209,3 +209,49 @@ def test_compressed_products_follow_eps(sphere2048, codec):
     yc2 = matvec.h2_mvm(c2, 1.0, x)
     assert np.linalg.norm(yc2 - y2) / np.linalg.norm(y2) <= 2e-6
     assert compress.payload_bytes(ch) < compress.payload_bytes(compress.compress_h(h, "none")) / 2
+
+
+@pytest.mark.parametrize("adm", ["hodlr", "blr"])
+def test_block_tree_other_admissibility(adm):
+    """HODLR (off-diagonal admissibility) and BLR (a single level), the remark
+    after Def. H-Matrix: the leaves still partition I x I exactly once; HODLR
+    keeps dense blocks only on the diagonal and every block of two distinct
+    clusters low rank; BLR tests admissibility only where a leaf cluster is
+    involved, so no low-rank block sits above the leaf level."""
+    pts = synth.sphere_points(512)
+    ct = trees.build_cluster_tree(pts, 16)
+    blocks = trees.build_block_tree(ct, 2.0, adm)
+    n = pts.shape[0]
+    cover = np.zeros((n, n), dtype=np.int32)
+    for b in blocks:
+        t, s = ct.clusters[b.row], ct.clusters[b.col]
+        cover[t.start:t.end, s.start:s.end] += 1
+        if adm == "hodlr":
+            assert b.adm == (b.row != b.col)
+            if not b.adm:
+                assert t.is_leaf and s.is_leaf
+        else:
+            assert t.is_leaf or s.is_leaf
+            if b.adm:
+                assert trees.admissible(t, s, 2.0)
+    assert np.all(cover == 1)
+    std = trees.build_block_tree(ct, 2.0, "std")
+    if adm == "hodlr":
+        # every level contributes its two off-diagonal sibling blocks
+        nonleaf = sum(1 for c in ct.clusters if not c.is_leaf)
+        assert sum(b.adm for b in blocks) == 2 * nonleaf
+    else:
+        assert len(blocks) > len(std)
+
+
+@pytest.mark.parametrize("adm", ["hodlr", "blr"])
+def test_other_admissibility_products_against_dense(adm):
+    pts = synth.sphere_points(1024)
+    h = hmatrix.build_h(pts, "laplace", 32, 2.0, 1e-6, adm=adm)
+    a = hmatrix.exact_matrix(pts, "laplace", h.param)
+    x = synth.rhs(1024, 2)
+    yd = matvec.dense_mvm(a, 1.0, x)
+    yh = matvec.h_mvm(h, 1.0, x)
+    assert np.linalg.norm(yh - yd) / np.linalg.norm(yd) <= 2e-6
+    ya = matvec.h_mvm_adjoint(h, 1.0, x)
+    assert np.linalg.norm(ya - a.T @ x) / np.linalg.norm(a.T @ x) <= 2e-6
