@@ -341,6 +341,31 @@ def gpu_arm(args, rank, world):
         matern["fp64_ms_p50"] = round(statistics.median(per), 4)
         matern["speedup_vs_fp64"] = round(statistics.median(per) / single["ms_p50"], 3)
         M.close()
+    adm_legs = None
+    if args.adm_legs:   # HODLR / BLR block trees of the sphere problem: huge top-level blocks vs a flat tiling
+        adm_legs = {}
+        na = args.adm_legs
+        pa = synth.sphere_points(na)
+        xa = torch.from_numpy(synth.rhs(na)[:, 0].copy()).cuda()
+        ya = torch.zeros_like(xa)
+        for adm in ("hodlr", "blr"):
+            t0 = time.perf_counter()
+            M = hm.HMatrix(pa, "laplace", 64, 2.0, "h", 1e-6, adm=adm)
+            M.compress(1e-6, "aflp", True)
+            build_s = time.perf_counter() - t0
+            if not args.no_tune:
+                M.autotune(3, stream.cuda_stream)
+            M.graph(not args.no_graph)
+            info = M.info()
+            ab = M.alg_bytes()
+            per, _ = time_variant(torch, M, xa, ya, max(20, min(args.steps, 200)), 3, stream, world)
+            med = statistics.median(per)
+            adm_legs[adm] = {"ms_p50": round(med, 4), "gbs": round(ab / (med * 1e-3) / 1e9, 1),
+                             "hbm_frac": round(ab / (med * 1e-3) / 1e9 / hbm_peak, 3),
+                             "payload_mb": round(info["bytes_payload"] / 1e6, 1), "max_rank": info["max_rank"],
+                             "nblocks": info["nblocks"], "build_s": round(build_s, 1)}
+            M.close()
+        adm_legs["workload"] = f"laplace sphere N={na}, leaf 64, H eps=1e-6 AFLP VALR; HODLR and BLR block trees"
     clk = clocks.stop()
 
     # ------------------------------------------------------------ multi-rank reduction
@@ -410,6 +435,8 @@ def gpu_arm(args, rank, world):
     }
     if matern is not None:
         line["matern_multi_rhs"] = matern
+    if adm_legs is not None:
+        line["hodlr_blr"] = adm_legs
     if not args.no_cpu:
         try:
             line["cpu_baseline"] = run_cpu_child(args.cpu_budget_mb, args.cpu_passes, 1)
@@ -460,6 +487,8 @@ def main():
     ap.add_argument("--formats", default="uh,h2")
     ap.add_argument("--no-tune", action="store_true", help="keep the default launch shape (no autotuning)")
     ap.add_argument("--no-multi-rhs", action="store_true", help="skip the multi-RHS timings")
+    ap.add_argument("--adm-legs", type=int, default=0,
+                    help="also time HODLR and BLR H-matrices of the sphere problem at this N (opt-in)")
     ap.add_argument("--matern", type=int, default=0,
                     help="also time multi-RHS products on the Matern cube with this many points (slow to build)")
     ap.add_argument("--cpu-budget-mb", type=float, default=20.0)
