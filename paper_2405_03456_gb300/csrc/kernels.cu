@@ -599,6 +599,7 @@ struct DfArgs {
   const SeqDep* deps;
   unsigned* ver;
   int* abort;
+  unsigned* claim;   // per phase: ranges handed out so far
 };
 
 // Wait (lane 0, bounded) until chunk c has reached version v; acquire.
@@ -775,16 +776,19 @@ __global__ void __launch_bounds__(NW * 32, 1)
 
 // ---------------------------------------------------------------- persistent phases
 // A run of row-chunk launches (the levels of the sweeps, the couplings) as the
-// phases of one cooperative launch (all warps resident): every warp takes its
-// range of each phase in turn, and each piece waits only for the coefficient
-// chunks it reads (versions published by the emits of earlier phases), so the
-// levels of different subtrees overlap instead of meeting at barriers.
+// phases of one cooperative launch (all warps resident): the warp ranges of a
+// phase are handed out in order from a counter to whichever warp is free (a
+// warp takes phase p + 1 ranges once phase p has none left), and each piece
+// waits only for the coefficient chunks it reads (versions published by the
+// emits of earlier phases), so the levels of different subtrees overlap and a
+// warp held up by a dependency does not hold up the ranges behind it.  A warp
+// holds one range at a time and only waits for chunks of earlier phases, which
+// are held by running warps: no cycle.
 template <int TIER, int NW, int NS>
 __global__ void __launch_bounds__(NW * 32, 1)
     k_rseq(RsArgs A, const SeqPhase* __restrict__ ph, int nph, const int32_t* __restrict__ wbeg,
            const F2* __restrict__ rowscale, DfArgs D) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int gw = blockIdx.x * NW + warp;
   uint8_t* ring;
   int4* info;
   uint64_t* bars;
@@ -792,19 +796,24 @@ __global__ void __launch_bounds__(NW * 32, 1)
   uint32_t it = 0;
   for (int p = 0; p < nph; ++p) {
     const SeqPhase P = ph[p];
-    if (gw >= P.nw) continue;
-    const int p0 = wbeg[P.woff + gw], n = wbeg[P.woff + gw + 1] - p0;
-    if (n <= 0) continue;
     RsArgs B = A;
     B.rowscale = P.rowscale ? rowscale : nullptr;
-    bool ok;
-    if (P.mode == MODE_Y)
-      ok = rs_range<TIER, MODE_Y, NS, true>(B, p0, n, ring, info, bars, lane, it, &D);
-    else if (P.mode == MODE_VEC)
-      ok = rs_range<TIER, MODE_VEC, NS, true>(B, p0, n, ring, info, bars, lane, it, &D);
-    else
-      ok = rs_range<TIER, MODE_VEC_ADD, NS, true>(B, p0, n, ring, info, bars, lane, it, &D);
-    if (!ok) return;
+    for (;;) {   // ranges of this phase are handed out in order to whichever warp is free
+      int r = 0;
+      if (lane == 0) r = (int)atomicAdd(D.claim + p, 1u);
+      r = __shfl_sync(HM_FULL, r, 0);
+      if (r >= P.nw) break;
+      const int p0 = wbeg[P.woff + r], n = wbeg[P.woff + r + 1] - p0;
+      if (n <= 0) continue;
+      bool ok;
+      if (P.mode == MODE_Y)
+        ok = rs_range<TIER, MODE_Y, NS, true>(B, p0, n, ring, info, bars, lane, it, &D);
+      else if (P.mode == MODE_VEC)
+        ok = rs_range<TIER, MODE_VEC, NS, true>(B, p0, n, ring, info, bars, lane, it, &D);
+      else
+        ok = rs_range<TIER, MODE_VEC_ADD, NS, true>(B, p0, n, ring, info, bars, lane, it, &D);
+      if (!ok) return;
+    }
   }
 }
 
@@ -1064,18 +1073,18 @@ cudaError_t launch_rgemv(int tier, int mode, int cfg, const PieceCopy* pieces, c
 }
 
 // A run of row-chunk launches as one cooperative launch of nblk blocks (one
-// per SM) of the persistent shape; the chunk versions and the abort word
-// (ver[0 .. nchunks]) are zeroed first.
+// per SM) of the persistent shape; the chunk versions, the abort word and the
+// per-phase range counters (ver[0 .. nchunks + nph]) are zeroed first.
 cudaError_t launch_rseq(int tier, int nblk, const SeqPhase* phases, int nph, const PieceCopy* pieces,
                         const int32_t* wbeg, const uint8_t* pay, float2* vec, double alpha, F2 alpha_ff, double beta,
                         double* y, const int32_t* perm, const F2* rowscale, F2* fix, int32_t* fixcnt,
                         const Split* splits, const SeqDep* deps, unsigned* ver, int nchunks, int* err,
                         cudaStream_t st) {
   if (nph <= 0 || nblk <= 0) return cudaSuccess;
-  cudaError_t e = cudaMemsetAsync(ver, 0, (size_t)(nchunks + 1) * sizeof(unsigned), st);
+  cudaError_t e = cudaMemsetAsync(ver, 0, (size_t)(nchunks + 1 + nph) * sizeof(unsigned), st);
   if (e != cudaSuccess) return e;
   const RsArgs A{pieces, pay, vec, alpha, alpha_ff, beta, y, perm, vec, nullptr, fix, fixcnt, splits, err};
-  const DfArgs D{deps, ver, reinterpret_cast<int*>(ver + nchunks)};
+  const DfArgs D{deps, ver, reinterpret_cast<int*>(ver + nchunks), ver + nchunks + 1};
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)nblk);
   cfg.blockDim = dim3(SEQ_NW * 32);

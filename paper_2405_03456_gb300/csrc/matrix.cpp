@@ -118,7 +118,7 @@ struct hm_matrix {
   std::vector<Run> runs;
   DevArr<SeqPhase> d_phases;
   DevArr<SeqDep> d_deps;       // per piece (pieces of runs only)
-  unsigned* d_ver = nullptr;   // chunk versions + abort word of the largest run
+  unsigned* d_ver = nullptr;   // chunk versions, abort word and per-phase range counters of the largest run
   // the transposed matrix (adjoint products), built on first use, owned
   hm_matrix* adj = nullptr;
   std::mutex mu;
@@ -401,7 +401,9 @@ hm_status upload(hm_matrix* M) {
     if (!ph.empty()) {
       if ((e = M->d_phases.upload(ph)) != cudaSuccess) return cuda_status(e);
       if ((e = M->d_deps.upload(deps)) != cudaSuccess) return cuda_status(e);
-      if ((e = cudaMalloc(&M->d_ver, (size_t)(maxchunks + 1) * sizeof(unsigned))) != cudaSuccess)
+      int maxph = 0;
+      for (const hm_matrix::Run& R : M->runs) maxph = std::max(maxph, (int)(R.last - R.first));
+      if ((e = cudaMalloc(&M->d_ver, (size_t)(maxchunks + 1 + maxph) * sizeof(unsigned))) != cudaSuccess)
         return cuda_status(e);
     }
   }
