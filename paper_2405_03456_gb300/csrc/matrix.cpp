@@ -105,6 +105,8 @@ struct hm_matrix {
   int* d_err = nullptr;        // latched device error word
   double* d_hx = nullptr;      // host-path staging (hm_matvec_host)
   double* d_hy = nullptr;
+  cudaStream_t h_side = nullptr;          // host path: second copy stream (x and y copies overlap)
+  cudaEvent_t h_ev0 = nullptr, h_ev1 = nullptr;
   int64_t d_h_cap = 0;
   int nsm = 0;
   // persistent launches: runs [first, last) of consecutive row-chunk launches
@@ -688,9 +690,18 @@ hm_status hm_matvec_host(hm_matrix* M, double alpha, const double* x, double bet
     M->d_h_cap = n * nrhs;
   }
   const size_t bytes = n * nrhs * sizeof(double);
+  if (beta != 0.0) {   // y's copy on a second stream, after the stream's earlier work, overlapping x's
+    if (!M->h_side && (cudaStreamCreateWithFlags(&M->h_side, cudaStreamNonBlocking) != cudaSuccess ||
+                       cudaEventCreateWithFlags(&M->h_ev0, cudaEventDisableTiming) != cudaSuccess ||
+                       cudaEventCreateWithFlags(&M->h_ev1, cudaEventDisableTiming) != cudaSuccess))
+      return HM_ERR_CUDA;
+    if (cudaEventRecord(M->h_ev0, st) != cudaSuccess || cudaStreamWaitEvent(M->h_side, M->h_ev0, 0) != cudaSuccess ||
+        cudaMemcpyAsync(M->d_hy, y, bytes, cudaMemcpyHostToDevice, M->h_side) != cudaSuccess ||
+        cudaEventRecord(M->h_ev1, M->h_side) != cudaSuccess)
+      return HM_ERR_CUDA;
+  }
   if (cudaMemcpyAsync(M->d_hx, x, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess) return HM_ERR_CUDA;
-  if (beta != 0.0 && cudaMemcpyAsync(M->d_hy, y, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess)
-    return HM_ERR_CUDA;
+  if (beta != 0.0 && cudaStreamWaitEvent(st, M->h_ev1, 0) != cudaSuccess) return HM_ERR_CUDA;
   hm_status s = hm_matvec(M, alpha, M->d_hx, n, beta, M->d_hy, n, nrhs, stream);
   if (s != HM_OK) return s;
   if (cudaMemcpyAsync(y, M->d_hy, bytes, cudaMemcpyDeviceToHost, st) != cudaSuccess) return HM_ERR_CUDA;
@@ -825,6 +836,9 @@ hm_status hm_alg_bytes(const hm_matrix* M, int64_t* bytes) {
 
 hm_status hm_free(hm_matrix* M) {
   if (!M) return HM_OK;
+  if (M->h_side) cudaStreamDestroy(M->h_side);
+  if (M->h_ev0) cudaEventDestroy(M->h_ev0);
+  if (M->h_ev1) cudaEventDestroy(M->h_ev1);
   if (M->adj) hm_free(M->adj);
   M->adj = nullptr;
   M->drop_graph();
