@@ -113,6 +113,31 @@ def compress_uh(u: Uniform, codec: str) -> CUH:
 
 
 @dataclass
+class CUHSep:
+    m: object          # nested.UniformSep
+    codec: str
+    W: list
+    X: list
+    Sr: list           # per block: direct(Sr) for low-rank, direct(D) for dense
+    Sc: list           # per block: direct(Sc) for low-rank, None for dense
+
+
+def compress_uh_sep(m, codec: str) -> CUHSep:
+    """Bases as compress_uh (VALR), both coupling factors direct at eps."""
+    cu = compress_uh(m.u, codec)
+    eps = m.u.h.eps
+    Sr, Sc = [], []
+    for b, r, c, s in zip(m.u.h.blocks, m.Sr, m.Sc, m.u.S):
+        if b.adm:
+            Sr.append(direct(r, codec, eps))
+            Sc.append(direct(c, codec, eps))
+        else:
+            Sr.append(direct(s, codec, eps))
+            Sc.append(None)
+    return CUHSep(m, codec, cu.W, cu.X, Sr, Sc)
+
+
+@dataclass
 class CH2:
     m: H2
     codec: str

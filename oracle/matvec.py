@@ -198,6 +198,50 @@ def h2_mvm(m, alpha: float, x, beta: float = 1.0, y=None):
     return _perm_out(ct, yp)
 
 
+def uhsep_mvm(m, alpha: float, x, beta: float = 1.0, y=None, adjoint: bool = False):
+    """UH product with separate row and column couplings (the variant discussed
+    after Alg. 5): forward s_s := X_s^H x|s (Alg. 4); per low-rank block the
+    first stage u_b := Sc_b^H s_s; per row cluster t_t := sum_b Sr_b u_b and
+    y|t += alpha (W_t t_t + sum of the dense blocks D x).  adjoint: the same with
+    the roles of rows and columns exchanged (M^H x)."""
+    from .nested import UniformSep
+    comp = not isinstance(m, UniformSep)
+    ms = m.m if comp else m
+    u = ms.u
+    h = u.h
+    ct = h.ct
+    cl = ct.clusters
+    if y is None:
+        y = np.zeros_like(np.asarray(x, dtype=np.float64))
+    xp, yp = _perm_in(ct, x, y, beta)
+    Wb = [unvalr(m.W[c.id], c.size) for c in cl] if comp else u.W
+    Xb = [unvalr(m.X[c.id], c.size) for c in cl] if comp else u.X
+    if adjoint:
+        Wb, Xb = Xb, Wb
+    s = [Xb[c.id].T @ xp[c.start:c.end] for c in cl]
+    t = [np.zeros((Wb[c.id].shape[1],) + xp.shape[1:]) for c in cl]
+    dense = [[] for _ in cl]
+    for i, b in enumerate(h.blocks):
+        row, col = (b.col, b.row) if adjoint else (b.row, b.col)
+        if b.adm:
+            sr = undirect(m.Sr[i]) if comp else ms.Sr[i]
+            sc = undirect(m.Sc[i]) if comp else ms.Sc[i]
+            if adjoint:
+                sr, sc = sc, sr
+            ub = sc.T @ s[col]
+            t[row] += sr @ ub
+        else:
+            d = undirect(m.Sr[i]) if comp else u.S[i]
+            dense[row].append((col, d.T if adjoint else d))
+    for c in cl:
+        yl = Wb[c.id] @ t[c.id]
+        for col, d in dense[c.id]:
+            sc = cl[col]
+            yl = yl + d @ xp[sc.start:sc.end]
+        yp[c.start:c.end] += alpha * yl
+    return _perm_out(ct, yp)
+
+
 # ---------------------------------------------------------------- adjoint products
 # The remark after Alg. 3: the adjoint product M^H x runs the same way over the
 # block columns.  The data are real, so M^H = M^T: a low-rank block

@@ -105,6 +105,30 @@ def build_uniform(h: HMatrix) -> Uniform:
     return Uniform(h, W, SW, X, SX, S)
 
 
+@dataclass
+class UniformSep:
+    """UH-matrix with separate row and column coupling matrices per low-rank
+    block (the variant discussed after Alg. 5): S_ts = Sr_b Sc_b^H with
+    Sr_b = (W_t^T W_b) diag(s_b) (k_t x k_b) and Sc_b = X_s^T X_b (k_s x k_b),
+    the two factors of the coupling above, kept apart."""
+    u: Uniform
+    Sr: list           # per block: (k_t, k_b) for low-rank, None otherwise
+    Sc: list           # per block: (k_s, k_b) for low-rank, None otherwise
+
+
+def build_uniform_sep(h: HMatrix) -> UniformSep:
+    u = build_uniform(h)
+    Sr, Sc = [], []
+    for b, d in zip(h.blocks, h.data):
+        if isinstance(d, LowRank):
+            Sr.append((u.W[b.row].T @ d.W) @ np.diag(d.s))
+            Sc.append(u.X[b.col].T @ d.X)
+        else:
+            Sr.append(None)
+            Sc.append(None)
+    return UniformSep(u, Sr, Sc)
+
+
 def _nested_side(h: HMatrix, side: str):
     """Nested bases for one side ('row' uses W_b, 'col' uses X_b)."""
     cl = h.ct.clusters
