@@ -484,7 +484,7 @@ def main():
     ap.add_argument("--codecs", default="none,aflp,fpx")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-graph", action="store_true")
-    ap.add_argument("--formats", default="uh,h2")
+    ap.add_argument("--formats", default="uh,uh_sep,h2")
     ap.add_argument("--no-tune", action="store_true", help="keep the default launch shape (no autotuning)")
     ap.add_argument("--no-multi-rhs", action="store_true", help="skip the multi-RHS timings")
     ap.add_argument("--adm-legs", type=int, default=0,

@@ -45,7 +45,10 @@ typedef enum {
                              hm_compress's addressing) */
 } hm_status;
 
-typedef enum { HM_FMT_H = 0, HM_FMT_UH = 1, HM_FMT_H2 = 2 } hm_format;
+/* UH_SEP: uniform-H with separate row and column coupling matrices per block,
+ * S = Sr Sc^H (the variant discussed after Alg. 5): the product takes
+ * u_b = Sc_b^H s_sigma per block, then t_tau = sum_b Sr_b u_b. */
+typedef enum { HM_FMT_H = 0, HM_FMT_UH = 1, HM_FMT_H2 = 2, HM_FMT_UH_SEP = 3 } hm_format;
 /* Admissibility of the block tree (Def. Block Tree and the remark after Def.
  * H-Matrix): STANDARD min(diam t, diam s) <= eta dist(t, s); HODLR off-diagonal
  * (every block of two distinct clusters is low rank, dense blocks only on the

@@ -290,8 +290,11 @@ void build_uniform_bases(HostMatrix& hm, int nthreads) {
     svd_basis(m, K, R, eps, bs.B[cid], bs.sig[cid]);
     bs.k[cid] = (int)bs.sig[cid].size();
   }
-  // couplings
+  // couplings (and, for UH_SEP, their two factors)
   hm.coupling.assign(hm.lr.size(), {});
+  const bool sep = hm.prm.format == HM_FMT_UH_SEP;
+  hm.coupling_r.assign(sep ? hm.lr.size() : 0, {});
+  hm.coupling_ct.assign(sep ? hm.lr.size() : 0, {});
 #pragma omp parallel for schedule(dynamic, 4) num_threads(nthreads)
   for (int64_t b = 0; b < (int64_t)hm.blocks.size(); ++b) {
     if (!hm.blocks[b].adm) continue;
@@ -311,6 +314,16 @@ void build_uniform_bases(HostMatrix& hm, int nthreads) {
         double q = Q[j + l * ks] * L.s[l];
         for (int i = 0; i < kt; ++i) S[i + j * kt] += P[i + l * kt] * q;
       }
+    if (sep) {   // Sr = (W_t^T W_b) diag(s_b), Sc^T = X_b^T X_s
+      auto& R = hm.coupling_r[hm.slot[b]];
+      auto& C = hm.coupling_ct[hm.slot[b]];
+      R.assign((size_t)kt * L.k, 0.0);
+      C.assign((size_t)L.k * ks, 0.0);
+      for (int l = 0; l < L.k; ++l)
+        for (int i = 0; i < kt; ++i) R[i + (size_t)l * kt] = P[i + (size_t)l * kt] * L.s[l];
+      for (int j = 0; j < ks; ++j)
+        for (int l = 0; l < L.k; ++l) C[l + (size_t)j * L.k] = Q[j + (size_t)l * ks];
+    }
   }
 }
 

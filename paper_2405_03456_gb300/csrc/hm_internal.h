@@ -85,6 +85,9 @@ struct HostMatrix {
   // UH / H2
   Bases rowb, colb;
   std::vector<std::vector<double>> coupling;   // per low-rank block (k_t x k_s), col-major
+  // UH_SEP: the two factors of each coupling, S = Sr Sc^T, per low-rank block:
+  // Sr (k_t x k_b) and Sc^T (k_b x k_s), col-major
+  std::vector<std::vector<double>> coupling_r, coupling_ct;
 };
 
 void build_lowrank_blocks(HostMatrix& hm, int nthreads);

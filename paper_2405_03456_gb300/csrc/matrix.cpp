@@ -319,6 +319,25 @@ void transpose_host(const HostMatrix& H, HostMatrix& T) {
         for (int i = 0; i < kt; ++i) St[(size_t)j + (size_t)i * ks] = S[(size_t)i + (size_t)j * kt];
     }
   }
+  // UH_SEP: S^T = Sc Sr^T, so Sr' = (Sc^T)^T and Sc'^T = Sr^T
+  T.coupling_r.assign(H.coupling_ct.size(), std::vector<double>());
+  T.coupling_ct.assign(H.coupling_r.size(), std::vector<double>());
+  for (size_t b = 0; b < H.blocks.size(); ++b) {
+    const int sl = H.slot[b];
+    if (!H.blocks[b].adm || (size_t)sl >= H.coupling_r.size() || H.coupling_r[sl].empty()) continue;
+    const int kt = H.rowb.k[H.blocks[b].row], ks = H.colb.k[H.blocks[b].col];
+    const int kb = (int)(H.coupling_r[sl].size() / std::max(kt, 1));
+    const std::vector<double>& R = H.coupling_r[sl];    // kt x kb
+    const std::vector<double>& C = H.coupling_ct[sl];   // kb x ks
+    std::vector<double>& Rt = T.coupling_r[sl];         // ks x kb = C^T
+    std::vector<double>& Ct = T.coupling_ct[sl];        // kb x kt = R^T
+    Rt.resize(C.size());
+    Ct.resize(R.size());
+    for (int l = 0; l < kb; ++l) {
+      for (int j = 0; j < ks; ++j) Rt[(size_t)j + (size_t)l * ks] = C[(size_t)l + (size_t)j * kb];
+      for (int i = 0; i < kt; ++i) Ct[(size_t)l + (size_t)i * kb] = R[(size_t)i + (size_t)l * kt];
+    }
+  }
   T.rowb = H.colb;
   T.colb = H.rowb;
 }
@@ -437,7 +456,7 @@ hm_status hm_build(const hm_build_params* prm, const double* pts, int64_t n, hm_
   if (!prm || !pts || !out || n < 1 || n > (int64_t)INT32_MAX / 2) return HM_ERR_ARG;
   if (prm->leaf_size < 1 || prm->leaf_size > 128) return HM_ERR_ARG;
   if (!(prm->eta > 0) || !(prm->eps_build > 0 && prm->eps_build < 1)) return HM_ERR_ARG;
-  if (prm->format < HM_FMT_H || prm->format > HM_FMT_H2) return HM_ERR_ARG;
+  if (prm->format < HM_FMT_H || prm->format > HM_FMT_UH_SEP) return HM_ERR_ARG;
   if (prm->kernel != HM_KERNEL_LAPLACE && prm->kernel != HM_KERNEL_MATERN15) return HM_ERR_ARG;
   if (prm->adm < HM_ADM_STANDARD || prm->adm > HM_ADM_BLR) return HM_ERR_ARG;
   for (int64_t i = 0; i < 3 * n; ++i)
@@ -455,7 +474,7 @@ hm_status hm_build(const hm_build_params* prm, const double* pts, int64_t n, hm_
     build_cluster_tree(H.pts.data(), n, prm->leaf_size, H.ct);
     build_block_tree(H.ct, prm->eta, H.blocks, prm->adm);
     build_lowrank_blocks(H, nth);
-    if (prm->format == HM_FMT_UH) build_uniform_bases(H, nth);
+    if (prm->format == HM_FMT_UH || prm->format == HM_FMT_UH_SEP) build_uniform_bases(H, nth);
     if (prm->format == HM_FMT_H2) build_nested_bases(H, nth);
   } catch (const std::bad_alloc&) {
     return HM_ERR_OOM;

@@ -766,6 +766,61 @@ bool row_bases(Ctx& cx, const std::vector<int>& which, const std::vector<int64_t
 }
 
 // ---------------------------------------------------------------- UH (Alg. 4 + 5)
+// UH with separate couplings (the variant discussed after Alg. 5): first stage
+// u_b = Sc_b^T s_sigma, one chunk (of <= 128 rows) per low-rank block with the
+// tile Sc_b^T; second stage t_tau = alpha sum_b Sr_b u_b, one chunk per row
+// cluster with the tiles Sr_b (rows scaled as the single-coupling t_tau).  Both
+// factors are compressed directly at eps.
+bool separate_coupling_chunks(Ctx& cx, const std::vector<int64_t>& soff, const std::vector<int64_t>& toff,
+                              const std::vector<int64_t>& uoff) {
+  const HostMatrix& H = cx.H;
+  const auto& ct = H.ct;
+  const int nc = (int)ct.cl.size();
+  const int64_t nb = (int64_t)H.blocks.size();
+  std::vector<ColSet> encr(nb), encc(nb);
+  std::atomic<bool> ok{true};
+#pragma omp parallel for schedule(dynamic, 8)
+  for (int64_t b = 0; b < nb; ++b) {
+    if (uoff[b] < 0) continue;
+    const int kt = H.rowb.k[H.blocks[b].row], ks = H.colb.k[H.blocks[b].col], kb = H.lr[H.slot[b]].k;
+    if (!make_direct(cx, H.coupling_r[H.slot[b]].data(), kt, kb, encr[b])) ok = false;
+    if (!make_direct(cx, H.coupling_ct[H.slot[b]].data(), kb, ks, encc[b])) ok = false;
+  }
+  if (!ok) return false;
+  std::vector<ChunkWork> first, second;
+  std::vector<std::vector<int>> rowlr(nc);
+  for (int64_t b = 0; b < nb; ++b) {
+    if (uoff[b] < 0) continue;
+    rowlr[H.blocks[b].row].push_back((int)b);
+    const int kb = H.lr[H.slot[b]].k;
+    for (int64_t r0 = 0; r0 < kb; r0 += CHUNK_ROWS) {
+      const int64_t r1 = std::min<int64_t>(kb, r0 + CHUNK_ROWS);
+      ChunkWork w;
+      w.row0 = (int32_t)(uoff[b] + r0);
+      w.nrows = (int32_t)(r1 - r0);
+      w.t.push_back(pack_tile(cx, encc[b], r0, r1, (int32_t)soff[H.blocks[b].col], 0));
+      first.push_back(std::move(w));
+    }
+    cx.P.fp64_lowrank += (int64_t)(encc[b].m * encc[b].n + encr[b].m * encr[b].n) * 8;
+  }
+  for (int t = 0; t < nc; ++t) {
+    const int kt = H.rowb.k[t];
+    if (kt == 0) continue;
+    for (int64_t r0 = 0; r0 < kt; r0 += CHUNK_ROWS) {
+      const int64_t r1 = std::min<int64_t>(kt, r0 + CHUNK_ROWS);
+      ChunkWork w;
+      w.row0 = (int32_t)(toff[t] + r0);
+      w.nrows = (int32_t)(r1 - r0);
+      w.flags = 1;
+      for (int b : rowlr[t]) w.t.push_back(pack_tile(cx, encr[b], r0, r1, (int32_t)uoff[b], 0));
+      second.push_back(std::move(w));
+    }
+  }
+  if (!first.empty()) add_rgemv(cx, first, MODE_VEC, false);
+  add_rgemv(cx, second, MODE_VEC, true);
+  return true;
+}
+
 bool program_uh(Ctx& cx) {
   const HostMatrix& H = cx.H;
   Program& P = cx.P;
@@ -790,6 +845,17 @@ bool program_uh(Ctx& cx) {
       vec += H.rowb.k[c];
       ws.push_back(c);
     }
+  // UH_SEP: one coefficient vector u_b = Sc_b^T s_sigma per low-rank block
+  const bool sep = H.prm.format == HM_FMT_UH_SEP;
+  std::vector<int64_t> uoff(H.blocks.size(), -1);
+  if (sep)
+    for (size_t b = 0; b < H.blocks.size(); ++b) {
+      if (!H.blocks[b].adm) continue;
+      const int kb = H.lr[H.slot[b]].k;
+      if (kb == 0 || H.rowb.k[H.blocks[b].row] == 0 || H.colb.k[H.blocks[b].col] == 0) continue;
+      uoff[b] = vec;
+      vec += kb;
+    }
   P.rowscale.assign(vec, 1.0);
   add_launch(P, Launch::GATHER, 0, N);
   int64_t pbase = 0;
@@ -801,8 +867,12 @@ bool program_uh(Ctx& cx) {
   std::vector<ColSet> wb;
   if (!row_bases(cx, ws, toff, wb)) return false;
   std::vector<ChunkWork> cw;
-  if (!coupling_chunks(cx, soff, toff, cw, 1)) return false;
-  add_rgemv(cx, cw, MODE_VEC, true);
+  if (!sep) {
+    if (!coupling_chunks(cx, soff, toff, cw, 1)) return false;
+    add_rgemv(cx, cw, MODE_VEC, true);
+  } else if (!separate_coupling_chunks(cx, soff, toff, uoff)) {
+    return false;
+  }
   leaf_chunks(cx, lv, dt, [&](int c, std::vector<ColRef>& out) {
     for (int a : ancestors_root_first(ct, c)) {
       if (H.rowb.k[a] == 0) continue;
@@ -977,7 +1047,8 @@ bool build_program(const HostMatrix& H, int codec, double eps, int valr, int nsm
   bool ok;
   switch (H.prm.format) {
     case HM_FMT_H: ok = program_h(cx); break;
-    case HM_FMT_UH: ok = program_uh(cx); break;
+    case HM_FMT_UH:
+    case HM_FMT_UH_SEP: ok = program_uh(cx); break;
     default: ok = program_h2(cx); break;
   }
   cx.tiles.clear();
