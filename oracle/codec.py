@@ -3,7 +3,7 @@
 TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
 
 Plain FP64 / integer definitions.  A code is an unsigned integer of 8*B bits
-(B = bytes per value).  Readings of the paper (each also listed in the design doc):
+(B = bytes per value).  Readings of the paper where it is silent or ambiguous:
 
 * Rounding is round-to-nearest, ties-to-even, for both codecs (Sec. 4.1 states
   round-to-nearest for FPX and is silent on ties and on AFLP).

@@ -3,7 +3,7 @@
 * K0 decode: bit-exact with the oracle's decoder for every codec and width.
 * Products: y := alpha*M*x + beta*y for H, UH, H^2 at N = 2048 (several
   tiles, ragged leaves) within 4*eps relative of the oracle's uncompressed
-  FP64 product -- the bound the task states -- and, at the benchmark's full
+  FP64 product -- the stated accuracy of the compressed product -- and, at the benchmark's full
   size (N = 131072), on sampled rows of the exact dense product.
 * Determinism (no atomics), host path, beta = 0, multi-RHS, error word.
 """
