@@ -199,6 +199,23 @@ def profiled_traffic(kernel, n):
     return int(rec["bytes_per_launch"])
 
 
+def max_over_ranks(ms: float, world: int, device: str = "cuda") -> float:
+    """The slowest rank's step time (every rank takes part; replicas only: the
+    ranks run independent copies of the workload and exchange nothing else)."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_gbs(alg_bytes: int, ms: float, world: int) -> float:
+    """Algorithmic bytes all ranks moved per step over the slowest rank's time."""
+    return alg_bytes / (ms * 1e-3) / 1e9 * world
+
+
 def pct(v, q):
     i = min(len(v) - 1, max(0, int(round(q * (len(v) - 1)))))
     return v[i]
@@ -369,16 +386,11 @@ def gpu_arm(args, rank, world):
     clk = clocks.stop()
 
     # ------------------------------------------------------------ multi-rank reduction
-    med = headline["ms_p50"]
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([med], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        med = float(t.item())
+    med = max_over_ranks(headline["ms_p50"], world)
     if rank != 0:
         return None
     ab = headline["alg_bytes"]
-    value = ab / (med * 1e-3) / 1e9 * world
+    value = whole_job_gbs(ab, med, world)
     prof = headline["kernels"]
     dom = max(prof, key=lambda k: prof[k]["ms"])
     dk = prof[dom]
