@@ -2,7 +2,7 @@
  * hm.h -- C ABI of libhm: compressed hierarchical-matrix products on one GB300.
  *
  * Operation (eqn. mvm, Sec. 3, extended by beta):
- *     y := alpha * M * x + beta * y
+ *     y := alpha * M * x + beta * y      (and alpha * M^H * x + beta * y)
  * for an H-, uniform-H (UH) or H^2-matrix M (Sec. 2.2-2.4) whose dense
  * leaves, low-rank factors, cluster bases, coupling and transfer matrices are
  * stored in the floating point compressed formats of Sec. 4 (AFLP or FPX,
@@ -72,9 +72,10 @@ typedef struct {
 
 /*
  * hm_build -- construct M on the host (Sec. 2): cluster tree by geometric
- * bisection, block tree with standard admissibility, dense leaves, low-rank
- * blocks (ACA + SVD recompression, truncated at sigma_k <= eps*sigma_0), and
- * for UH / H^2 the shared / nested cluster bases and couplings.
+ * bisection, block tree with the admissibility of prm->adm (standard, HODLR or
+ * BLR), dense leaves, low-rank blocks (ACA + SVD recompression, truncated at
+ * sigma_k <= eps*sigma_0), and for UH / UH_SEP / H^2 the shared / nested cluster
+ * bases and couplings (UH_SEP: the two factors of every coupling).
  *   pts : host, n x 3 FP64, row-major (x0 y0 z0 x1 ...); copied.
  *   out : receives a new matrix (FP64 host copy; nothing on the GPU yet).
  * Errors: HM_ERR_ARG for null pointers, n < 1 or invalid parameters,
