@@ -9,7 +9,10 @@ multi-RHS product y := M X on that slot's stream: upload of X, hm_matvec,
 download of Y.  Requests that arrive while others run wait only for their
 matrix and a slot, so products of different matrices overlap on the device
 and later arrivals join the next launch ("continuous batching").  Products of
-one matrix never overlap, because they share its device workspace.
+one matrix never overlap, because they share its device workspace.  A request
+may ask for the adjoint product y := M^H X instead (hm_matvec_adjoint); a launch
+packs consecutive requests of one direction only, so the FIFO order of every
+matrix is kept.
 
 The scheduler is host logic with a pluggable executor: ``GpuExecutor`` runs
 the products through libhm on CUDA streams; tests drive the same scheduler
@@ -35,6 +38,7 @@ class Request:
     admitted: float = -1.0
     done: float = -1.0
     y: np.ndarray | None = None
+    adjoint: bool = False         # y := M^H x instead of M x
 
     @property
     def r(self) -> int:
@@ -115,15 +119,16 @@ class Scheduler:
             if not ready:
                 return
             m = min(ready, key=lambda m: m.queue[0].arrival)       # oldest waiting request first
+            adj = m.queue[0].adjoint                                 # one direction per launch
             batch, r = [], 0
-            while m.queue and r + m.queue[0].r <= self.max_rhs:
+            while m.queue and m.queue[0].adjoint == adj and r + m.queue[0].r <= self.max_rhs:
                 req = m.queue.pop(0)
                 batch.append(req)
                 r += req.r
             slot = self.free_slots.pop(0)
             m.busy = True
             L = Launch(m.mid, slot, batch)
-            L.handle = self.ex.launch(m.mid, slot, [q.x for q in batch])
+            L.handle = self.ex.launch(m.mid, slot, [q.x for q in batch], adjoint=adj)
             self.inflight.append(L)
             self.launches += 1
             self.rhs_launched += r
@@ -188,8 +193,10 @@ class _WallClock:
         return time.perf_counter() - self.t0
 
 
-def poisson_requests(mats: dict, rate: float, count: int, seed: int, rhs_max: int = 32) -> list:
-    """Seeded Poisson arrivals (rate per second), matrix uniform, RHS count U{1..rhs_max}, x ~ U(-1,1)."""
+def poisson_requests(mats: dict, rate: float, count: int, seed: int, rhs_max: int = 32,
+                     adjoint_frac: float = 0.0) -> list:
+    """Seeded Poisson arrivals (rate per second), matrix uniform, RHS count U{1..rhs_max}, x ~ U(-1,1);
+    a fraction adjoint_frac of the requests asks for M^H x (drawn only when adjoint_frac > 0)."""
     rng = np.random.default_rng(seed)
     mids = sorted(mats)
     t = 0.0
@@ -199,7 +206,8 @@ def poisson_requests(mats: dict, rate: float, count: int, seed: int, rhs_max: in
         mid = mids[int(rng.integers(len(mids)))]
         r = int(rng.integers(1, rhs_max + 1))
         x = np.asfortranarray(rng.uniform(-1.0, 1.0, (mats[mid], r)))
-        out.append(Request(k, mid, x, t))
+        adj = bool(rng.random() < adjoint_frac) if adjoint_frac > 0 else False
+        out.append(Request(k, mid, x, t, adjoint=adj))
     return out
 
 
@@ -218,9 +226,15 @@ class GpuExecutor:
     def staging_bytes(n: int, max_rhs: int) -> int:
         return 2 * 8 * n * max_rhs          # device X and Y blocks
 
-    def add(self, mid: int, M) -> None:
+    def add(self, mid: int, M, prepare_adjoint: bool = False) -> None:
+        """Register M; prepare_adjoint builds its transposed matrix now (one adjoint
+        product of zeros), so that no adjoint request waits for it."""
         torch = self.torch
         n = M.n
+        if prepare_adjoint:
+            z = torch.zeros(n, dtype=torch.float64, device="cuda")
+            M.matvec(1.0, z, 0.0, torch.zeros_like(z), adjoint=True)
+            torch.cuda.synchronize()
         self.mats[mid] = {
             "M": M, "n": n,
             "dx": torch.empty((self.max_rhs, n), dtype=torch.float64, device="cuda"),
@@ -229,7 +243,7 @@ class GpuExecutor:
             "hy": torch.empty((self.max_rhs, n), dtype=torch.float64).pin_memory(),
         }
 
-    def launch(self, mid: int, slot: int, xs: list):
+    def launch(self, mid: int, slot: int, xs: list, adjoint: bool = False):
         from . import hm
         torch = self.torch
         e = self.mats[mid]
@@ -244,7 +258,8 @@ class GpuExecutor:
             k += c.shape[1]
         with torch.cuda.stream(st):
             e["dx"][:r].copy_(e["hx"][:r], non_blocking=True)
-            hm.hm_matvec(e["M"].h, 1.0, e["dx"].data_ptr(), n, 0.0, e["dy"].data_ptr(), n, r, st.cuda_stream)
+            f = hm.hm_matvec_adjoint if adjoint else hm.hm_matvec
+            f(e["M"].h, 1.0, e["dx"].data_ptr(), n, 0.0, e["dy"].data_ptr(), n, r, st.cuda_stream)
             e["hy"][:r].copy_(e["dy"][:r], non_blocking=True)
             ev = torch.cuda.Event()
             ev.record(st)

@@ -24,17 +24,18 @@ class FakeExecutor:
     def staging_bytes(n, max_rhs):
         return 2 * 8 * n * max_rhs
 
-    def launch(self, mid, slot, xs):
+    def launch(self, mid, slot, xs, adjoint=False):
         r = sum(x.reshape(x.shape[0], -1).shape[1] for x in xs)
         end = self.now + self.a + self.b * r
         self.log.append((mid, self.now, end, r))
-        return (end, mid, xs)
+        return (end, mid, xs, adjoint)
 
     def poll(self, h):
-        end, mid, xs = h
+        end, mid, xs, adjoint = h
         if self.now < end:
             return None
-        return [self.A[mid] @ x for x in xs]
+        a = self.A[mid].T if adjoint else self.A[mid]
+        return [a @ x for x in xs]
 
     def next_finish(self):
         return min((e for (_, _, e, _) in self.log if e > self.now), default=None)
@@ -98,6 +99,35 @@ def test_budget_admission_and_backlog():
     assert max(r for (_, _, _, r) in ex.log) <= 32      # at most 2 requests (40 RHS of room) admitted at once
     for q in done:
         assert np.allclose(q.y, ex.A[0] @ q.x)
+
+
+def test_adjoint_requests_one_direction_per_launch():
+    """Mixed M x and M^H x requests: every result is its own direction's product,
+    a launch never mixes directions, and each matrix serves its requests in
+    arrival order."""
+    mats = {0: 24, 1: 36}
+    ex, sch = make(mats)
+    reqs = poisson_requests(mats, rate=5000.0, count=150, seed=6, adjoint_frac=0.4)
+    assert 20 < sum(q.adjoint for q in reqs) < 130
+    launched = []
+    orig = ex.launch
+
+    def spy(mid, slot, xs, adjoint=False):
+        launched.append((mid, adjoint, [id(x) for x in xs]))
+        return orig(mid, slot, xs, adjoint=adjoint)
+
+    ex.launch = spy
+    done = sch.run(reqs, clock=FakeClock(ex))
+    assert len(done) == 150
+    by_x = {id(q.x): q for q in reqs}
+    for mid, adjoint, xs in launched:
+        assert all(by_x[x].adjoint == adjoint and by_x[x].mid == mid for x in xs)
+    for q in done:
+        a = ex.A[q.mid].T if q.adjoint else ex.A[q.mid]
+        assert np.allclose(q.y, a @ q.x, rtol=1e-12, atol=1e-12)
+    for mid in mats:
+        order = [by_x[x].rid for (m, _, xs) in launched if m == mid for x in xs]
+        assert order == sorted(order)
 
 
 def test_rejects_bad_requests():
