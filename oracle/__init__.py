@@ -18,7 +18,7 @@ Modules
   nested   -- shared (UH, Sec. 2.3) and nested (H^2, Sec. 2.4) cluster bases
   compress -- direct and VALR compression of a built matrix (Sec. 4.1-4.2)
   matvec   -- Alg. 1, Alg. 4 + 5, Alg. 6 + 7, with Alg. 8 decompression
-  hlu      -- H-LU factors on the block tree and their triangular solves (Sec. 6 outlook)
+  hlu      -- H-LU factors on the block tree and their triangular solves (Sec. 5, Conclusion)
   baseline -- the timed CPU run used as the benchmark's CPU baseline
 
 Parity status: every function is pinned by ``tests/test_oracle_*.py`` except

@@ -1,4 +1,4 @@
-"""Triangular vector solves with H-LU factors (Sec. 6: the outlook names
+"""Triangular vector solves with H-LU factors (Sec. 5, Conclusion: the outlook names
 triangular solves for H-LU factorisations as the next operation that reads the
 same compressed blocks as the product).
 
