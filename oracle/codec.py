@@ -21,7 +21,9 @@ Plain FP64 / integer definitions.  A code is an unsigned integer of 8*B bits
   dynamic range, as e_dr), at least 1; m' is the smallest value >= m with
   1 + m' + e a multiple of 8.  Layout: sign | f | mantissa, most significant
   first.  Decoding is v = +-fl(fl(s - 1) * vmin).  If 1 + m' + e > 56 (or
-  m' > 52) the raw FP64 bits are stored (B = 8).  An all-zero array uses
+  m' > 52), or if s leaves the FP64 range (vmax/vmin + 1 overflows, or rounding
+  carries s to 2^1024, where no f reproduces the value), the raw FP64 bits are
+  stored (B = 8).  An all-zero array uses
   B = 1, e = 1, m' = 6, vmin = 1.  Parity unpinned: the paper does not print
   the AFLP bit layout, so only its stated properties are pinned.
 """
@@ -173,18 +175,22 @@ def aflp_compress(v: np.ndarray, m: int) -> dict:
                 "codes": sign << U64(7)}
     vmin = float(a[nz].min())
     vmax = float(a[nz].max())
-    s = np.where(nz, (a / vmin) + 1.0, 2.0)            # two FP64 RN operations
+    raw = {"codec": "aflp", "B": 8, "e": 0, "mp": 52, "vmin": vmin, "raw": True, "codes": bits.copy()}
     smax = (vmax / vmin) + 1.0
+    if not np.isfinite(smax):                          # s beyond FP64: no exponent f reproduces v
+        return raw
+    s = np.where(nz, (a / vmin) + 1.0, 2.0)            # two FP64 RN operations
     f0 = (int(f64_bits(np.array([smax]))[0]) >> 52) - 1023
     e = max(1, bitlen(f0))
     for _ in range(2):
         mp = _aflp_mprime(m, e)
         if 1 + mp + e > 56 or mp > 52:
-            return {"codec": "aflp", "B": 8, "e": 0, "mp": 52, "vmin": vmin, "raw": True,
-                    "codes": bits.copy()}
+            return raw
         sr = round_mag_bits(f64_bits(s), 52 - mp)
         f = ((sr >> U64(52)).astype(np.int64) - 1023)
         fmax = int(f[nz].max())
+        if fmax > 1023:                                # rounding carried s to 2^1024
+            return raw
         if bitlen(fmax) <= e:
             break
         e = bitlen(fmax)

@@ -12,7 +12,9 @@
 // AFLP: s = fl(fl(|v|/vmin) + 1) in [2, ...) is rounded to m' mantissa bits,
 // its exponent f >= 1 stored in e bits (f = 0 encodes zero), e the bit length
 // of the largest f (at least 1), m' >= m the smallest with 1+m'+e = 8B.
-// Code layout: sign | f | mantissa.  If 1+m'+e > 56 or m' > 52, raw FP64.
+// Code layout: sign | f | mantissa.  If 1+m'+e > 56 or m' > 52, raw FP64; raw
+// FP64 as well when s leaves the FP64 range (vmax/vmin + 1 overflows, or the
+// rounded s reaches 2^1024), since no f then reproduces the value.
 // Decoding: v = +-fl(fl(s - 1) * vmin).
 //
 // Compile with -ffp-contract=off: the divisions and additions must round as
@@ -162,22 +164,24 @@ bool encode_values(const double* v, int64_t n, int64_t inc, int codec, int key, 
     for (int64_t i = 0; i < n; ++i) codes[i] = (dbits(v[i * inc]) >> 63) << 7;
     return true;
   }
+  auto raw = [&]() {
+    h.B = 8;
+    h.fmt = FMT_RAW;
+    h.e = 0;
+    h.m = 52;
+    h.vmin = vmin;
+    for (int64_t i = 0; i < n; ++i) codes[i] = dbits(v[i * inc]);
+    return true;
+  };
   double smax = (vmax / vmin) + 1.0;
+  if (!std::isfinite(smax)) return raw();
   int f0 = (int)(dbits(smax) >> 52) - 1023;
   int e = bit_length((uint64_t)f0);
   if (e < 1) e = 1;
   int mp = 0;
   for (int it = 0; it < 2; ++it) {
     mp = aflp_mprime(m, e);
-    if (1 + mp + e > 56 || mp > 52) {
-      h.B = 8;
-      h.fmt = FMT_RAW;
-      h.e = 0;
-      h.m = 52;
-      h.vmin = vmin;
-      for (int64_t i = 0; i < n; ++i) codes[i] = dbits(v[i * inc]);
-      return true;
-    }
+    if (1 + mp + e > 56 || mp > 52) return raw();
     int fmax = 0;
     for (int64_t i = 0; i < n; ++i) {
       double a = std::fabs(v[i * inc]);
@@ -187,6 +191,7 @@ bool encode_values(const double* v, int64_t n, int64_t inc, int codec, int key, 
       int f = (int)(sr >> 52) - 1023;
       if (f > fmax) fmax = f;
     }
+    if (fmax > 1023) return raw();
     if (bit_length((uint64_t)fmax) <= e) break;
     e = bit_length((uint64_t)fmax);
     if (it == 1) return false;

@@ -217,6 +217,19 @@ def test_aflp_rounding_carry_raises_exponent_bits():
     assert cd.decompress(c)[1] == 15.0
 
 
+@pytest.mark.parametrize("v", [
+    np.array([1e-300, 1e-200, 5e-324, -7.0]),            # |v|/vmin + 1 overflows
+    np.array([1.0, -np.finfo(np.float64).max]),           # finite s rounds up to 2^1024
+])
+def test_aflp_beyond_fp64_range_stays_exact(v):
+    # no exponent f of s = |v|/vmin + 1 fits FP64: the array is kept as raw FP64
+    for m in (1, 7, 20, 30):
+        c = cd.aflp_compress(v, m)
+        d = cd.decompress(c)
+        assert np.all(np.isfinite(d))
+        assert c["raw"] and np.array_equal(d.view(np.uint64), v.view(np.uint64))
+
+
 def test_valr_key_brute_force():
     rng = np.random.default_rng(9)
     for _ in range(3000):
