@@ -14,7 +14,8 @@ Plain FP64 / integer definitions.  A code is an unsigned integer of 8*B bits
 * FPX e8 rows: the value is rounded once, from FP64, to m mantissa bits; if any
   value of the array then lies outside the FP32 normal range (or is an FP32
   subnormal), the whole array moves to the e11 row with the smallest m that is
-  at least the requested one.
+  at least the requested one.  An array with a value that an e11 row rounds to
+  infinity (beyond the FP64 maximum) moves to the exact row e11 m52.
 * AFLP (Sec. 4.1, m_eps and e_dr formulas): s = fl(fl(|v|/vmin) + 1) >= 2 is
   rounded to m' mantissa bits; its binary exponent f >= 1 is stored in e bits,
   f = 0 is reserved for zero.  e is the bit length of the largest f (the data's
@@ -110,7 +111,8 @@ def fpx_bytes(e: int, m: int) -> int:
 
 
 def fpx_encode(v: np.ndarray, e: int, m: int):
-    """FPX codes of v in format (e, m), or None if an e8 value is out of range."""
+    """FPX codes of v in format (e, m), or None if a value is out of the format's
+    range (e8: outside the FP32 normal range; e11: rounded to infinity)."""
     v = np.asarray(v, dtype=np.float64)
     if not np.all(np.isfinite(v)):
         raise ValueError("FPX needs finite values")
@@ -119,6 +121,8 @@ def fpx_encode(v: np.ndarray, e: int, m: int):
     sign = bits >> U64(63)
     mag = round_mag_bits(bits & U64(0x7FFFFFFFFFFFFFFF), 52 - m)
     if e == 11:
+        if np.any((mag >> U64(52)) == U64(2047)):     # rounded past the FP64 maximum
+            return None
         full = (sign << U64(63)) | mag
         return full >> U64(64 - 8 * nb)
     assert e == 8
@@ -146,8 +150,11 @@ def fpx_compress(v: np.ndarray, key: int) -> dict:
     """Direct FPX compression of an array for accuracy key (table + promotion)."""
     e, m = fpx_format(key)
     codes = fpx_encode(v, e, m)
-    if codes is None:                      # e8 out of range: smallest e11 row (m = 28 > 23)
+    if codes is None and e == 8:           # e8 out of range: smallest e11 row (m = 28 > 23)
         e, m = 11, 28
+        codes = fpx_encode(v, e, m)
+    if codes is None:                      # rounded past the FP64 maximum: the exact row
+        e, m = 11, 52
         codes = fpx_encode(v, e, m)
     return {"codec": "fpx", "B": fpx_bytes(e, m), "e": e, "m": m, "codes": codes}
 

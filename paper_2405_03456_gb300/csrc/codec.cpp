@@ -4,7 +4,8 @@
 // FPX (Fig. tab:fpx): a value is rounded once, to nearest with ties to even,
 // from FP64 to the row's m mantissa bits (bit-pattern rounding carries into the
 // exponent); e8 rows keep the FP32 exponent range and an array with any value
-// outside the FP32 normal range moves to the e11 m28 row.  The code is the top
+// outside the FP32 normal range moves to the e11 m28 row; an array with a value
+// that rounds past the FP64 maximum moves to the exact e11 m52 row.  The code is the top
 // B bytes of the FP32 (e8) or FP64 (e11) pattern.  The first table row (keys
 // 0..10 -> e8m7) covers keys 0..8; keys 9 and 10 use e8m15 so that the
 // rounding error 2^-(m+1) never exceeds 2^-key, as for every other row.
@@ -102,6 +103,7 @@ bool fpx_try(const double* v, int64_t n, int64_t inc, int e, int m, uint64_t* co
     uint64_t sign = b >> 63;
     uint64_t mag = round_bits(b & 0x7FFFFFFFFFFFFFFFull, 52 - m);
     if (e == 11) {
+      if ((mag >> 52) == 0x7FF) return false;     // rounded to infinity
       codes[i] = ((sign << 63) | mag) >> (64 - 8 * B);
       continue;
     }
@@ -131,9 +133,15 @@ bool encode_values(const double* v, int64_t n, int64_t inc, int codec, int key, 
   if (codec == HM_CODEC_FPX) {
     int e, m;
     fpx_format(key, e, m);
-    if (!fpx_try(v, n, inc, e, m, codes)) {
+    bool ok = fpx_try(v, n, inc, e, m, codes);
+    if (!ok && e == 8) {          // out of the FP32 normal range
       e = 11;
       m = 28;
+      ok = fpx_try(v, n, inc, e, m, codes);
+    }
+    if (!ok) {                    // rounded past the FP64 maximum
+      e = 11;
+      m = 52;
       fpx_try(v, n, inc, e, m, codes);
     }
     h.B = (1 + e + m) / 8;

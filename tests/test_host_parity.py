@@ -75,7 +75,7 @@ def _cases():
     out.append(np.array([1.0, 16.0 - 2.0 ** -20]))
     out.append(np.array([1.0, 3e40, -2.0]))                 # forces FPX e11 promotion
     out.append(np.array([1e-300, 1e-200, 5e-324, -7.0]))    # AFLP s overflows: raw FP64
-    out.append(np.array([1.0, -np.finfo(np.float64).max]))   # AFLP s rounds to 2^1024: raw FP64
+    out.append(np.array([1.0, -np.finfo(np.float64).max]))   # AFLP s / FPX e11 round to 2^1024
     return out
 
 

@@ -230,6 +230,18 @@ def test_aflp_beyond_fp64_range_stays_exact(v):
         assert c["raw"] and np.array_equal(d.view(np.uint64), v.view(np.uint64))
 
 
+def test_fpx_beyond_fp64_maximum_moves_to_exact_row():
+    big = np.finfo(np.float64).max
+    v = np.array([1.0, -big, 3.0])
+    for key in (5, 20, 24, 30, 40):
+        c = cd.fpx_compress(v, key)
+        assert (c["e"], c["m"]) == (11, 52)
+        assert np.array_equal(cd.decompress(c), v)
+    w = np.array([1.0, -2.0 ** 1023 * 1.5])                 # exact in e11m28: no promotion
+    c = cd.fpx_compress(w, 24)
+    assert (c["e"], c["m"]) == (11, 28) and np.array_equal(cd.decompress(c), w)
+
+
 def test_valr_key_brute_force():
     rng = np.random.default_rng(9)
     for _ in range(3000):
