@@ -1,0 +1,471 @@
+// Host check of the launch program of a compressed matrix: the packed layout
+// the product kernels stream, and the FP64 meaning of its launches.  Test code,
+// built by tests/test_program_layout.py against the library's host objects; it
+// runs no GPU code.
+//
+// For every launch shape of the program it checks
+//  * copy descriptors: 16-byte aligned, inside the payload, at most one stage,
+//    and of the size their inline header describes;
+//  * every vector index a launch reads or writes (inputs and their 16-byte
+//    padded copies, multipliers, outputs, partials, fix-up slots, fan-out
+//    slots) inside the buffer the library allocates for it;
+//  * warp ranges in order and covering their launch;
+//  * within one launch, no vector entry both read as a multiplier or input and
+//    written as an output (the launch's warps run concurrently);
+// then it replays the launches in program order in FP64 (Alg. 8: each code
+// decoded, then Alg. 1 / 4-7 as the program orders them).  The replay must give
+// the same y bit for bit on a second pass (no state left between products), and
+// its distance from the FP64 product of the matrix as the host stores it (H
+// blocks, or bases and couplings) is printed.
+//
+// usage: program_check <points+x file> n format eps codec leaf nsm adm kernel
+//   file: n*3 doubles (points, row-major) then n doubles (x, original order)
+//   format 0 H, 1 UH, 2 H2, 3 UH with separate couplings; codec 0 none,
+//   1 AFLP, 2 FPX; adm 0 standard, 1 HODLR, 2 BLR; kernel 0 Laplace, 1 Matern
+// prints one line per shape and "ok" or "FAILED <count>"; exit status 0 iff ok.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+#include "program.h"
+
+using namespace hm;
+
+namespace {
+
+int g_fails = 0;
+
+#define CHECK(cond, ...)                                  \
+  do {                                                    \
+    if (!(cond)) {                                        \
+      if (g_fails < 20) {                                 \
+        std::printf("FAIL line %d: ", __LINE__);          \
+        std::printf(__VA_ARGS__);                         \
+        std::printf("\n");                                \
+      }                                                   \
+      ++g_fails;                                          \
+    }                                                     \
+  } while (0)
+
+// Value of one code given the 16-bit format B | fmt << 4 | e << 6 | m << 10
+// (fmt 0 FPX e8, 1 FPX e11, 2 AFLP as (s - 1) with s = 2^f (1 + mant 2^-m),
+// its vmin applied by the scale the program attaches, 3 raw FP64).
+double decode(uint64_t code, uint16_t f16) {
+  const int B = f16 & 15, fmt = (f16 >> 4) & 3, e = (f16 >> 6) & 15, m = f16 >> 10;
+  if (fmt == 0) {
+    const uint32_t w = (uint32_t)(code << (32 - 8 * B));
+    float f;
+    std::memcpy(&f, &w, 4);
+    return f;
+  }
+  if (fmt == 1 || fmt == 3) {
+    const uint64_t w = code << (64 - 8 * B);
+    double d;
+    std::memcpy(&d, &w, 8);
+    return d;
+  }
+  const uint64_t sign = (code >> (8 * B - 1)) & 1, f = (code >> m) & ((1ull << e) - 1),
+                 mant = code & ((1ull << m) - 1);
+  const double v = f ? std::ldexp(1.0 + std::ldexp((double)mant, -m), (int)f) - 1.0 : 0.0;
+  return sign ? -v : v;
+}
+
+uint64_t load_code(const uint8_t* p, int B) {
+  uint64_t c = 0;
+  for (int b = 0; b < B; ++b) c |= (uint64_t)p[b] << (8 * b);
+  return c;
+}
+
+uint16_t format16(int B, int fmt, uint16_t em) {
+  return (uint16_t)(B | (fmt << 4) | ((em & 0xff) << 6) | ((em >> 8) << 10));
+}
+
+double ff(const F2& v) { return (double)v.hi + (double)v.lo; }
+
+// Entries of a 16-byte aligned copy of `count` 8-byte entries starting at i.
+int64_t padded_entries(int64_t i, int64_t count) { return ((i - (i & ~1LL) + count) * 8 + 15) / 16 * 2; }
+
+struct Replay {
+  const HostMatrix& H;
+  const Program& P;
+  int shape;
+  double alpha;
+  int64_t NV;                 // vector entries allocated (nvec + 16)
+  int64_t nfix;               // fix-up slots of this shape
+  std::vector<double> v, part, fix, y;
+  std::vector<int> cnt;
+
+  Replay(const HostMatrix& h, const Program& p, int cf, double a)
+      : H(h), P(p), shape(cf), alpha(a), NV(p.nvec + 16), nfix(cf == MR_SHAPE ? p.nfix_mr : p.nfix) {
+    v.assign(P.nvec, NAN);
+    part.assign(std::max<int64_t>(P.npartial, 1), NAN);
+    fix.assign((size_t)std::max<int64_t>(nfix, 1) * CHUNK_ROWS, NAN);
+    cnt.assign(P.splits.size(), 0);
+  }
+
+  void ranges(const Launch& L) {
+    const int nw = L.nw[shape];
+    if (nw == 0) return;
+    CHECK(L.woff[shape] + nw < (int64_t)P.wbeg.size(), "range list past its end");
+    const int32_t* wb = P.wbeg.data() + L.woff[shape];
+    CHECK(wb[0] == L.off && wb[nw] == L.off + L.n, "ranges do not cover the launch");
+    for (int w = 0; w < nw; ++w) CHECK(wb[w] <= wb[w + 1], "ranges out of order");
+  }
+
+  void column_dots(const Launch& L, std::vector<char>& read, std::vector<char>& written) {
+    const auto& pay = P.pk.pay;
+    for (int64_t it = L.off; it < L.off + L.n; ++it) {
+      const ItemCopy& c = P.items[it];
+      const uint64_t off = (uint64_t)c.off16 * 16;
+      CHECK(off + ((c.bytes + 15) & ~15u) <= pay.size(), "item %ld outside the payload", (long)it);
+      CHECK(c.bytes <= (uint32_t)STAGE_BYTES, "item %ld larger than a stage", (long)it);
+      if (off + 16 > pay.size()) continue;
+      CPieceHdr h;
+      std::memcpy(&h, &pay[off], sizeof h);
+      CHECK(h.vin == c.vin && h.nrows == c.nrows, "item %ld: descriptor and header differ", (long)it);
+      CHECK(h.nrows >= 1 && h.nrows <= SEG_ROWS && h.ncols >= 1 && h.ncols <= CPIECE_MAX_COLS,
+            "item %ld: header out of range", (long)it);
+      const int64_t x0 = c.vin & ~1;
+      CHECK(x0 >= 0 && x0 + padded_entries(c.vin, c.nrows) <= NV, "item %ld: input copy outside v", (long)it);
+      CHECK(padded_entries(c.vin, c.nrows) * 8 <= SEG_ROWS * 8 + 16, "item %ld: input copy too long", (long)it);
+      const bool final = h.flags & ITEM_FINAL;
+      const int B = h.fb & 15, fmt = (h.fb >> 4) & 3;
+      const size_t rows16 = (h.nrows + 15) & ~15, stride = rows16 * B;
+      const size_t cb = off + 16 + (final ? 16 : 8) * (size_t)h.ncols;
+      CHECK(cb + stride * h.ncols - off == c.bytes, "item %ld: %zu bytes described, %u copied", (long)it,
+            cb + stride * h.ncols - off, c.bytes);
+      if (cb + stride * h.ncols > pay.size()) continue;
+      for (int64_t r = 0; r < h.nrows; ++r)
+        if (h.vin + r >= 0 && h.vin + r < P.nvec) read[h.vin + r] = 1;
+      const CColMeta* cm = reinterpret_cast<const CColMeta*>(&pay[off + 16]);
+      const F2* sc = reinterpret_cast<const F2*>(&pay[off + 16 + 8 * (size_t)h.ncols]);
+      for (int j = 0; j < h.ncols; ++j) {
+        const uint16_t f16 = format16(B, fmt, cm[j].em);
+        double s = 0;
+        for (size_t r = 0; r < rows16; ++r) {
+          const double d = decode(load_code(&pay[cb + j * stride + r * B], B), f16);
+          if (r >= (size_t)h.nrows)
+            CHECK(d == 0.0, "item %ld: padding row not zero", (long)it);
+          else
+            s += d * v[h.vin + r];
+        }
+        if (final) {
+          CHECK(cm[j].out >= 0 && cm[j].out < P.nvec, "item %ld: output outside v", (long)it);
+          if (cm[j].out < 0 || cm[j].out >= P.nvec) continue;
+          s *= ff(sc[j]);
+          if (h.flags & ITEM_ALPHA) s *= alpha;
+          v[cm[j].out] = s;
+          written[cm[j].out] = 1;
+        } else {
+          CHECK(cm[j].out >= 0 && cm[j].out < P.npartial, "item %ld: partial outside its array", (long)it);
+          if (cm[j].out >= 0 && cm[j].out < P.npartial) part[cm[j].out] = s;
+        }
+      }
+    }
+  }
+
+  void segment_sums(const Launch& L) {
+    for (int64_t i = L.off; i < L.off + L.n; ++i) {
+      const GsumOut& o = P.gouts[i];
+      double s = 0;
+      for (int p = o.p0; p < o.p1; ++p) {
+        CHECK(p >= 0 && p < P.npartial, "segment sum %ld: partial outside its array", (long)i);
+        if (p < 0 || p >= P.npartial) continue;
+        CHECK(!std::isnan(part[p]), "segment sum %ld: partial %d never written", (long)i, p);
+        double w = 1.0;
+        if (o.flags & 2) {
+          const int64_t q = o.ps + (p - o.p0);
+          CHECK(q >= 0 && q < (int64_t)P.pscale.size(), "segment sum %ld: weight outside its array", (long)i);
+          if (q >= 0 && q < (int64_t)P.pscale.size()) w = ff(P.pscale[q]);
+        }
+        s += part[p] * w;
+      }
+      s *= ff(o.scale);
+      if (o.flags & 1) s *= alpha;
+      CHECK(o.out >= 0 && o.out < P.nvec, "segment sum %ld: output outside v", (long)i);
+      if (o.out >= 0 && o.out < P.nvec) v[o.out] = s;
+    }
+    std::fill(part.begin(), part.end(), NAN);   // partials are consumed by the launch
+  }
+
+  void fan_out(const Launch& L) {
+    CHECK(L.off >= 0 && L.off + L.n <= (int64_t)P.fan_src.size(), "fan-out range outside its list");
+    for (int64_t i = L.off; i < L.off + L.n && i < (int64_t)P.fan_src.size(); ++i) {
+      const int32_t s = P.fan_src[i];
+      CHECK(s >= 0 && s < P.fan_base, "fan-out %ld reads outside the coefficients", (long)i);
+      CHECK(P.fan_base + i < P.nvec, "fan-out slot %ld outside v", (long)i);
+      if (s >= 0 && s < P.fan_base && P.fan_base + i < P.nvec) v[P.fan_base + i] = v[s];
+    }
+  }
+
+  void row_chunks(const Launch& L, std::vector<char>& read, std::vector<char>& written) {
+    const auto& pay = P.pk.pay;
+    const std::vector<double> vin = v;   // multipliers: values before the launch
+    CHECK((int64_t)P.pdesc[shape].size() == P.npieces, "descriptor list size");
+    const int nw = L.nw[shape];
+    const int32_t* wb = P.wbeg.data() + L.woff[shape];
+    for (int w = 0; w < nw; ++w) {
+      std::vector<double> acc(CHUNK_ROWS, 0.0);
+      for (int32_t pi = wb[w]; pi < wb[w + 1]; ++pi) {
+        const PieceCopy& c = P.pdesc[shape][pi];
+        const uint64_t off = (uint64_t)c.off16 * 16;
+        const uint32_t bytes = c.bytes_flags & 0xffff, rflags = (c.bytes_flags >> 16) & 0xff,
+                       ncols = c.bytes_flags >> 24;
+        CHECK(off + ((bytes + 15) & ~15u) <= pay.size(), "piece %d outside the payload", pi);
+        CHECK(bytes <= (uint32_t)STAGE_BYTES, "piece %d larger than a stage", pi);
+        if (off + sizeof(PieceHdr) > pay.size()) continue;
+        PieceHdr h;
+        std::memcpy(&h, &pay[off], sizeof h);
+        const int B = h.fb & 15, fmt = (h.fb >> 4) & 3;
+        // (a piece without columns only emits its chunk: e.g. coefficients that
+        // receive nothing at one level of the H2 down-sweep)
+        CHECK(h.nrows >= 1 && h.nrows <= CHUNK_ROWS && h.ncols <= PIECE_MAX_COLS, "piece %d: header out of range",
+              pi);
+        CHECK(ncols == h.ncols, "piece %d: descriptor and header differ", pi);
+        const bool tile = h.flags & PH_TILE;
+        if (tile) CHECK(c.moff == h.vin0, "piece %d: tile multipliers differ", pi);
+        CHECK(c.moff >= 0 && c.moff + h.ncols <= P.nvec, "piece %d: multipliers outside v", pi);
+        CHECK((c.moff & ~1) + padded_entries(c.moff, h.ncols) <= NV, "piece %d: multiplier copy outside v", pi);
+        CHECK(padded_entries(c.moff, h.ncols) * 8 <= PIECE_MAX_COLS * 8 + 16, "piece %d: multiplier copy too long",
+              pi);
+        const size_t stride = ((size_t)h.nrows * B + 7) & ~(size_t)7;
+        const size_t cb = off + 40 + (tile ? 0 : ((2 * (size_t)h.ncols + 7) & ~(size_t)7));
+        CHECK(cb + stride * h.ncols - off == bytes, "piece %d: %zu bytes described, %u copied", pi,
+              cb + stride * h.ncols - off, bytes);
+        if (cb + stride * h.ncols > pay.size() || c.moff < 0 || c.moff + h.ncols > P.nvec) continue;
+        if (rflags & PD_FIRST) std::fill(acc.begin(), acc.end(), 0.0);
+        const uint16_t* em = reinterpret_cast<const uint16_t*>(&pay[off + 40]);
+        for (int j = 0; j < h.ncols; ++j) {
+          const int32_t vi = c.moff + j;
+          read[vi] = 1;
+          const uint16_t f16 = format16(B, fmt, tile ? h.em : em[j]);
+          double mult = vin[vi];
+          if (tile) {
+            mult *= ff(h.scale);
+            if (h.flags & PH_TALPHA) mult *= alpha;
+          }
+          for (int r = 0; r < h.nrows; ++r)
+            acc[r] += decode(load_code(&pay[cb + j * stride + (size_t)r * B], B), f16) * mult;
+        }
+        if (rflags & PD_LAST) emit(L, h, c, acc, written, pi);
+      }
+    }
+  }
+
+  void emit(const Launch& L, const PieceHdr& h, const PieceCopy& c, const std::vector<double>& acc,
+            std::vector<char>& written, int pi) {
+    std::vector<double> out(acc.begin(), acc.begin() + h.nrows);
+    if ((c.bytes_flags >> 16) & PD_SPLIT) {
+      const int split = c.split_part >> 8, pidx = c.split_part & 0xff;
+      CHECK(split >= 0 && split < (int)P.splits.size(), "piece %d: split outside its list", pi);
+      if (split < 0 || split >= (int)P.splits.size()) return;
+      const Split& sp = P.splits[split];
+      CHECK(sp.nparts >= 2 && sp.nparts <= 256 && pidx < sp.nparts, "piece %d: part outside its split", pi);
+      CHECK(sp.slot0 >= 0 && sp.slot0 + sp.nparts <= nfix, "piece %d: fix-up slots outside their array", pi);
+      if (pidx >= sp.nparts || sp.slot0 < 0 || sp.slot0 + sp.nparts > nfix) return;
+      for (int r = 0; r < h.nrows; ++r) fix[(size_t)(sp.slot0 + pidx) * CHUNK_ROWS + r] = acc[r];
+      if (++cnt[split] != sp.nparts) return;
+      cnt[split] = 0;   // the last part resets the counter for the next product
+      for (int r = 0; r < h.nrows; ++r) {
+        double s = 0;
+        for (int k = 0; k < sp.nparts; ++k) s += fix[(size_t)(sp.slot0 + k) * CHUNK_ROWS + r];
+        out[r] = s;
+      }
+    }
+    for (int r = 0; r < h.nrows; ++r) {
+      const int64_t g = h.row0 + r;
+      if (L.mode == MODE_Y) {
+        CHECK(g >= 0 && g < H.n, "piece %d: row outside y", pi);
+        if (g >= 0 && g < H.n) y[H.ct.perm[g]] = out[r];
+        continue;
+      }
+      CHECK(g >= 0 && g < P.nvec, "piece %d: coefficient outside v", pi);
+      if (g < 0 || g >= P.nvec) continue;
+      double val = out[r];
+      if (L.mode == MODE_VEC_ADD) val += v[g];
+      if (L.use_rowscale) val *= P.rowscale[g];
+      if (h.flags & PH_CALPHA) val *= alpha;
+      v[g] = val;
+      written[g] = 1;
+    }
+  }
+
+  void run(const std::vector<double>& x) {
+    y.assign(H.n, NAN);
+    for (const Launch& L : P.launches) {
+      std::vector<char> read(P.nvec, 0), written(P.nvec, 0);
+      switch (L.kind) {
+        case Launch::GATHER:
+          for (int64_t i = 0; i < H.n; ++i) v[i] = x[H.ct.perm[i]];
+          break;
+        case Launch::FANOUT:
+          fan_out(L);
+          break;
+        case Launch::GSUM:
+          segment_sums(L);
+          break;
+        case Launch::CDOT:
+          ranges(L);
+          column_dots(L, read, written);
+          break;
+        case Launch::RGEMV:
+          ranges(L);
+          row_chunks(L, read, written);
+          break;
+      }
+      int64_t both = 0;
+      for (int64_t i = 0; i < P.nvec; ++i) both += read[i] && written[i];
+      CHECK(both == 0, "a launch reads and writes %ld vector entries", (long)both);
+    }
+    for (size_t s = 0; s < cnt.size(); ++s) CHECK(cnt[s] == 0, "split %zu: counter left at %d", s, cnt[s]);
+  }
+};
+
+// Explicit basis of cluster c (n_c x k_c, column-major): stored for UH and for
+// H2 leaves; an inner H2 cluster stacks its sons' bases times their transfer
+// matrices (rows of son s: W_s E_s, E_s of size k_s x k_c).
+std::vector<double> explicit_basis(const HostMatrix& H, const Bases& b, int c) {
+  const Cluster& cl = H.ct.cl[c];
+  if (H.prm.format != HM_FMT_H2 || cl.leaf()) return b.B[c];
+  const int64_t nc = cl.end - cl.start;
+  const int kc = b.k[c];
+  std::vector<double> w((size_t)nc * kc, 0.0);
+  for (int q = 0; q < cl.nsons; ++q) {
+    const int s = cl.son[q];
+    const Cluster& sc = H.ct.cl[s];
+    const int64_t ns = sc.end - sc.start, r0 = sc.start - cl.start;
+    const int ks = b.k[s];
+    const std::vector<double> ws = explicit_basis(H, b, s);
+    for (int j = 0; j < kc; ++j)
+      for (int l = 0; l < ks; ++l) {
+        const double e = b.E[s][l + (size_t)j * ks];
+        for (int64_t i = 0; i < ns; ++i) w[(r0 + i) + (size_t)j * nc] += ws[i + (size_t)l * ns] * e;
+      }
+  }
+  return w;
+}
+
+// alpha * M x in FP64 (original order) for the matrix as the host stores it in
+// the chosen format: H blocks W diag(s) X^T; UH and H2 blocks W_t S X_s^T with
+// the coupling S (separate couplings: S = Sr Sc^T); dense blocks D.
+std::vector<double> host_product(const HostMatrix& H, const std::vector<double>& x, double alpha) {
+  const int format = H.prm.format;
+  std::vector<std::vector<double>> wb(H.ct.cl.size()), xb(H.ct.cl.size());
+  if (format != HM_FMT_H)
+    for (size_t c = 0; c < H.ct.cl.size(); ++c) {
+      wb[c] = explicit_basis(H, H.rowb, (int)c);
+      xb[c] = explicit_basis(H, H.colb, (int)c);
+    }
+  std::vector<double> y(H.n, 0.0);
+  for (size_t b = 0; b < H.blocks.size(); ++b) {
+    const BlockLeaf& bl = H.blocks[b];
+    const Cluster& t = H.ct.cl[bl.row];
+    const Cluster& s = H.ct.cl[bl.col];
+    const int64_t nt = t.end - t.start, ns = s.end - s.start;
+    std::vector<double> xs(ns), ys(nt, 0.0);
+    for (int64_t j = 0; j < ns; ++j) xs[j] = x[H.ct.perm[s.start + j]];
+    if (!bl.adm) {
+      const auto& D = H.dn[H.slot[b]].D;
+      for (int64_t j = 0; j < ns; ++j)
+        for (int64_t i = 0; i < nt; ++i) ys[i] += D[j * nt + i] * xs[j];
+    } else if (format == HM_FMT_H) {
+      const LowRankBlock& L = H.lr[H.slot[b]];
+      for (int k = 0; k < L.k; ++k) {
+        double tk = 0;
+        for (int64_t j = 0; j < ns; ++j) tk += L.X[k * ns + j] * xs[j];
+        tk *= L.s[k];
+        for (int64_t i = 0; i < nt; ++i) ys[i] += L.W[k * nt + i] * tk;
+      }
+    } else {
+      const int kt = H.rowb.k[bl.row], ks = H.colb.k[bl.col];
+      std::vector<double> sv(ks, 0.0), tv(kt, 0.0);     // s = X_s^T x, t = S s
+      for (int l = 0; l < ks; ++l)
+        for (int64_t j = 0; j < ns; ++j) sv[l] += xb[bl.col][j + (size_t)l * ns] * xs[j];
+      if (format == HM_FMT_UH_SEP) {
+        const auto& R = H.coupling_r[H.slot[b]];
+        const auto& C = H.coupling_ct[H.slot[b]];
+        const int kb = H.lr[H.slot[b]].k;
+        std::vector<double> u(kb, 0.0);
+        for (int l = 0; l < kb; ++l)
+          for (int j = 0; j < ks; ++j) u[l] += C[l + (size_t)j * kb] * sv[j];
+        for (int i = 0; i < kt; ++i)
+          for (int l = 0; l < kb; ++l) tv[i] += R[i + (size_t)l * kt] * u[l];
+      } else {
+        const auto& S = H.coupling[H.slot[b]];
+        for (int i = 0; i < kt; ++i)
+          for (int j = 0; j < ks; ++j) tv[i] += S[i + (size_t)j * kt] * sv[j];
+      }
+      for (int l = 0; l < kt; ++l)
+        for (int64_t i = 0; i < nt; ++i) ys[i] += wb[bl.row][i + (size_t)l * nt] * tv[l];
+    }
+    for (int64_t i = 0; i < nt; ++i) y[H.ct.perm[t.start + i]] += alpha * ys[i];
+  }
+  return y;
+}
+
+}  // namespace
+
+int main(int argc, char** argv) {
+  if (argc != 10) {
+    std::fprintf(stderr, "usage: %s file n format eps codec leaf nsm adm kernel\n", argv[0]);
+    return 2;
+  }
+  const int64_t n = std::atoll(argv[2]);
+  const int format = std::atoi(argv[3]), codec = std::atoi(argv[5]), leaf = std::atoi(argv[6]),
+            nsm = std::atoi(argv[7]), adm = std::atoi(argv[8]), kernel = std::atoi(argv[9]);
+  const double eps = std::atof(argv[4]);
+  std::vector<double> pts(3 * n), x(n);
+  FILE* f = std::fopen(argv[1], "rb");
+  if (!f || std::fread(pts.data(), 8, 3 * n, f) != (size_t)(3 * n) || std::fread(x.data(), 8, n, f) != (size_t)n) {
+    std::fprintf(stderr, "cannot read %s\n", argv[1]);
+    return 2;
+  }
+  std::fclose(f);
+
+  HostMatrix H;
+  H.prm.kernel = (hm_kernel)kernel;
+  H.prm.leaf_size = leaf;
+  H.prm.eta = 2.0;
+  H.prm.format = (hm_format)format;
+  H.prm.eps_build = eps;
+  H.prm.adm = (hm_adm)adm;
+  H.n = n;
+  H.kparam = kernel == HM_KERNEL_LAPLACE ? std::sqrt(4.0 * M_PI / (double)n) : 0.1;
+  H.pts = pts;
+  build_cluster_tree(H.pts.data(), n, leaf, H.ct);
+  build_block_tree(H.ct, 2.0, H.blocks, adm);
+  build_lowrank_blocks(H, 8);
+  if (format == HM_FMT_UH || format == HM_FMT_UH_SEP) build_uniform_bases(H, 8);
+  if (format == HM_FMT_H2) build_nested_bases(H, 8);
+  Program P;
+  if (!build_program(H, codec, eps, 1, nsm, P)) {
+    std::printf("build_program failed\n");
+    return 1;
+  }
+  const double alpha = 0.75;
+  const std::vector<double> yref = host_product(H, x, alpha);
+  double den = 0;
+  for (double t : yref) den += t * t;
+  for (int cf = 0; cf < NSHAPES; ++cf) {
+    Replay R(H, P, cf, alpha);
+    R.run(x);
+    const std::vector<double> first = R.y;
+    R.run(x);
+    double num = 0;
+    int64_t differ = 0;
+    for (int64_t i = 0; i < n; ++i) {
+      differ += !(R.y[i] == first[i]);
+      num += (R.y[i] - yref[i]) * (R.y[i] - yref[i]);
+    }
+    CHECK(differ == 0, "shape %d: second product differs in %ld entries", cf, (long)differ);
+    std::printf("shape %d rel_err %.6e\n", cf, std::sqrt(num / den));
+  }
+  if (g_fails) {
+    std::printf("FAILED %d\n", g_fails);
+    return 1;
+  }
+  std::printf("ok\n");
+  return 0;
+}

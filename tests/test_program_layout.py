@@ -1,0 +1,88 @@
+"""Host check of the launch program, for every launch shape, without a GPU.
+
+``tests/program_check.cpp`` is linked against the library's host objects.  It
+builds a matrix, packs it and builds its launch program, and checks the program
+in two ways.  First, every copy descriptor and every vector index the kernels
+would touch is checked against the buffers the library allocates.  Second, the
+launches are replayed in FP64, and the replay must give the same y on a second
+pass.  The replayed product is compared with the FP64 product of the matrix as
+the host stores it in its format (H blocks, or bases and couplings):
+
+* uncompressed: equal up to FP64 rounding (1e-13), which pins the program's
+  indices, scales and emit modes for every format;
+* compressed: within eps, the codecs' rounding only (measured at most 0.18 eps
+  over formats, codecs and eps 1e-4..1e-8).
+"""
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+import synth
+from paper_2405_03456_gb300 import build as hbuild
+
+HOST = ["trees.cpp", "linalg.cpp", "build.cpp", "codec.cpp", "program.cpp"]
+FORMATS = {"h": 0, "uh": 1, "h2": 2, "uh_sep": 3}
+CODECS = {"none": 0, "aflp": 1, "fpx": 2}
+ADMS = {"std": 0, "hodlr": 1, "blr": 2}
+
+# (points, n, format, eps, codec, leaf, nsm, adm)
+CASES = [("sphere", 3000, f, 1e-6, c, 32, 152, "std") for f in FORMATS for c in CODECS] + [
+    ("sphere", 2048, "h", 1e-8, "aflp", 32, 152, "std"),        # float-float tier
+    ("sphere", 2048, "h2", 1e-8, "fpx", 32, 152, "std"),
+    ("sphere", 3000, "uh_sep", 1e-8, "aflp", 64, 152, "std"),
+    ("sphere", 3000, "h", 1e-6, "aflp", 32, 7, "std"),          # few SMs: long ranges, shared chunks
+    ("sphere", 3000, "h2", 1e-6, "aflp", 32, 3, "std"),
+    ("sphere", 3000, "h", 1e-6, "aflp", 32, 152, "hodlr"),
+    ("sphere", 3000, "uh", 1e-6, "fpx", 32, 152, "blr"),
+    ("cube", 3000, "h2", 1e-4, "aflp", 32, 152, "std"),         # Matern
+    ("cube", 2048, "h", 1e-8, "fpx", 32, 152, "blr"),
+]
+
+
+@pytest.fixture(scope="module")
+def checker(tmp_path_factory):
+    if shutil.which("g++") is None:
+        pytest.skip("needs g++")
+    hbuild.build()
+    tmp = tmp_path_factory.mktemp("program_check")
+    exe = str(tmp / "program_check")
+    src = os.path.join(os.path.dirname(os.path.abspath(__file__)), "program_check.cpp")
+    inc = os.path.join(hbuild.HERE, "..", "include")
+    objs = [os.path.join(hbuild.OUT, f + ".o") for f in HOST]
+    subprocess.run(["g++", "-std=c++17", "-O2", "-fopenmp", "-ffp-contract=off", "-I", hbuild.CSRC, "-I", inc,
+                    src] + objs + ["-o", exe], check=True)
+    return exe, tmp
+
+
+def _run(checker, pts_kind, n, fmt, eps, codec, leaf, nsm, adm):
+    exe, tmp = checker
+    path = tmp / f"{pts_kind}{n}.bin"
+    if not path.exists():
+        pts = synth.sphere_points(n) if pts_kind == "sphere" else synth.cube_points(n)
+        x = synth.rhs(n)[:, 0]
+        path.write_bytes(np.ascontiguousarray(pts).tobytes() + np.ascontiguousarray(x).tobytes())
+    kernel = 0 if pts_kind == "sphere" else 1
+    return subprocess.run([exe, str(path), str(n), str(FORMATS[fmt]), repr(eps), str(CODECS[codec]), str(leaf),
+                           str(nsm), str(ADMS[adm]), str(kernel)],
+                          stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True, timeout=600)
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: "-".join(map(str, c)))
+def test_program_layout_and_replay(checker, case):
+    pts_kind, n, fmt, eps, codec, leaf, nsm, adm = case
+    r = _run(checker, *case)
+    assert r.returncode == 0 and r.stdout.rstrip().endswith("ok"), r.stdout[-2000:]
+    errs = [float(line.split()[-1]) for line in r.stdout.splitlines() if line.startswith("shape")]
+    assert len(errs) == 4                                  # three warp shapes and the multi-RHS shape
+    bound = 1e-13 if codec == "none" else eps
+    assert max(errs) <= bound, (errs, bound)
+
+
+def test_h2_hodlr_basis_rank_above_the_kernel_limit(checker):
+    # HODLR's top-level blocks need H2 bases of rank > 128: the program is not
+    # built (hm_compress reports HM_ERR_CAPACITY)
+    r = _run(checker, "sphere", 3000, "h2", 1e-6, "aflp", 32, 152, "hodlr")
+    assert r.returncode == 1 and "build_program failed" in r.stdout
