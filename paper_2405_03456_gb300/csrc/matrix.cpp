@@ -207,82 +207,6 @@ namespace {
 std::once_flag g_kinit;
 cudaError_t g_kinit_err = cudaSuccess;
 
-// Dependencies of the pieces of launches [first, last) run as the phases of one
-// persistent launch.  Coefficient chunks are the output rows [row0, row0 + nrows)
-// of the MODE_VEC / MODE_VEC_ADD chunks of the run; a chunk's version counts the
-// phases that have emitted it.  Each piece waits for the chunk holding its
-// multipliers at the version reached before its phase, and for its own chunk
-// at its current version (read-modify-write, or ordered overwrite).  Returns
-// false (run stays per launch) if a multiplier run straddles chunks, or a
-// chunk is written after a phase that reads it (a reader could see the later
-// value).  deps is sized to the pieces and filled for the run's pieces.
-bool seq_dependencies(const Program& P, size_t first, size_t last, std::vector<SeqDep>& deps, int& nchunks) {
-  const auto& Ls = P.launches;
-  const auto& pd = P.pdesc[SEQ_SHAPE];
-  auto hdr = [&](int64_t i, int32_t& row0, int& nrows) {
-    const uint8_t* h = P.pk.pay.data() + (size_t)pd[i].off16 * 16;
-    std::memcpy(&row0, h, 4);
-    uint16_t nr;
-    std::memcpy(&nr, h + 4, 2);
-    nrows = nr;
-  };
-  std::map<int32_t, std::pair<int, int>> chunk;   // row0 -> (id, nrows)
-  for (size_t k = first; k < last; ++k) {
-    if (Ls[k].mode == MODE_Y) continue;
-    for (int64_t i = Ls[k].off; i < Ls[k].off + Ls[k].n; ++i) {
-      int32_t r0;
-      int nr;
-      hdr(i, r0, nr);
-      if (!chunk.count(r0)) chunk[r0] = {(int)chunk.size(), nr};
-    }
-  }
-  nchunks = (int)chunk.size();
-  std::vector<int> ver(nchunks, 0), last_read(nchunks, -1);
-  auto find = [&](int64_t m0, int64_t nc) -> int {   // chunk holding [m0, m0 + nc), -1 none, -2 straddles
-    auto it = chunk.upper_bound((int32_t)m0);
-    if (it != chunk.begin()) {
-      --it;
-      if (m0 < (int64_t)it->first + it->second.second)
-        return m0 + nc <= (int64_t)it->first + it->second.second ? it->second.first : -2;
-    }
-    auto nx = chunk.lower_bound((int32_t)m0);
-    return (nx != chunk.end() && nx->first < m0 + nc) ? -2 : -1;
-  };
-  if (deps.size() < (size_t)P.npieces) deps.resize((size_t)P.npieces, SeqDep{-1, 0, -1, 0});
-  for (size_t k = first; k < last; ++k) {
-    const Launch& L = Ls[k];
-    std::vector<int> wrote;
-    for (int64_t i = L.off; i < L.off + L.n; ++i) {   // reads of this phase first
-      const int nc = (int)(pd[i].bytes_flags >> 24);
-      SeqDep d{-1, 0, -1, 0};
-      if (nc > 0) {
-        const int c = find(pd[i].moff, nc);
-        if (c == -2) return false;
-        if (c >= 0) {
-          if (ver[c] > 0) d = SeqDep{c, ver[c], -1, 0};
-          last_read[c] = (int)k;
-        }
-      }
-      deps[(size_t)i] = d;
-    }
-    for (int64_t i = L.off; i < L.off + L.n; ++i) {   // then its writes
-      if (L.mode == MODE_Y) continue;
-      int32_t r0;
-      int nr;
-      hdr(i, r0, nr);
-      const int c = chunk[r0].first;
-      if (last_read[c] >= 0) return false;   // read as multipliers in this or an earlier phase, now written
-      deps[(size_t)i].c1 = c;
-      deps[(size_t)i].v1 = ver[c];
-      wrote.push_back(c);
-    }
-    std::sort(wrote.begin(), wrote.end());
-    wrote.erase(std::unique(wrote.begin(), wrote.end()), wrote.end());
-    for (int c : wrote) ++ver[c];
-  }
-  return true;
-}
-
 // The transpose of an H / UH / H2 matrix on the host: every block (t, s)
 // becomes (s, t) with W and X swapped (low rank), D^T (dense), S^T (couplings),
 // and the row and column bases (with their transfer matrices) trade places.

@@ -111,4 +111,10 @@ constexpr int64_t EMIT_COST = 8192;     // finished row chunks
 // range is outside what the kernels decode.
 bool build_program(const HostMatrix& H, int codec, double eps, int valr, int nsm, Program& P);
 
+// Dependencies (SeqDep per piece of shape SEQ_SHAPE) of the row-chunk launches
+// [first, last) of P run as the phases of one persistent launch; nchunks is the
+// number of coefficient chunks they version.  Returns false if the launches
+// cannot run that way (they then run one launch each).
+bool seq_dependencies(const Program& P, size_t first, size_t last, std::vector<SeqDep>& deps, int& nchunks);
+
 }  // namespace hm

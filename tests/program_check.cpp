@@ -16,7 +16,11 @@
 // decoded, then Alg. 1 / 4-7 as the program orders them).  The replay must give
 // the same y bit for bit on a second pass (no state left between products), and
 // its distance from the FP64 product of the matrix as the host stores it (H
-// blocks, or bases and couplings) is printed.
+// blocks, or bases and couplings) is printed.  The runs of row-chunk launches
+// the library fuses into one persistent launch are also replayed as dataflow:
+// warps that step in random order, each piece waiting for the chunk versions
+// of its dependencies.  No such order may stall with work left (a hang on the
+// device) or change y by a single bit (a race).
 //
 // usage: program_check <points+x file> n format eps codec leaf nsm adm kernel
 //   file: n*3 doubles (points, row-major) then n doubles (x, original order)
@@ -27,6 +31,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <random>
 #include <vector>
 
 #include "program.h"
@@ -94,6 +99,7 @@ struct Replay {
   double alpha;
   int64_t NV;                 // vector entries allocated (nvec + 16)
   int64_t nfix;               // fix-up slots of this shape
+  int persistent_runs = 0;    // runs replayed as one persistent launch
   std::vector<double> v, part, fix, y;
   std::vector<int> cnt;
 
@@ -201,72 +207,72 @@ struct Replay {
   }
 
   void row_chunks(const Launch& L, std::vector<char>& read, std::vector<char>& written) {
-    const auto& pay = P.pk.pay;
-    const std::vector<double> vin = v;   // multipliers: values before the launch
     CHECK((int64_t)P.pdesc[shape].size() == P.npieces, "descriptor list size");
     const int nw = L.nw[shape];
     const int32_t* wb = P.wbeg.data() + L.woff[shape];
-    for (int w = 0; w < nw; ++w) {
-      std::vector<double> acc(CHUNK_ROWS, 0.0);
-      for (int32_t pi = wb[w]; pi < wb[w + 1]; ++pi) {
-        const PieceCopy& c = P.pdesc[shape][pi];
-        const uint64_t off = (uint64_t)c.off16 * 16;
-        const uint32_t bytes = c.bytes_flags & 0xffff, rflags = (c.bytes_flags >> 16) & 0xff,
-                       ncols = c.bytes_flags >> 24;
-        CHECK(off + ((bytes + 15) & ~15u) <= pay.size(), "piece %d outside the payload", pi);
-        CHECK(bytes <= (uint32_t)STAGE_BYTES, "piece %d larger than a stage", pi);
-        if (off + sizeof(PieceHdr) > pay.size()) continue;
-        PieceHdr h;
-        std::memcpy(&h, &pay[off], sizeof h);
-        const int B = h.fb & 15, fmt = (h.fb >> 4) & 3;
-        // (a piece without columns only emits its chunk: e.g. coefficients that
-        // receive nothing at one level of the H2 down-sweep)
-        CHECK(h.nrows >= 1 && h.nrows <= CHUNK_ROWS && h.ncols <= PIECE_MAX_COLS, "piece %d: header out of range",
-              pi);
-        CHECK(ncols == h.ncols, "piece %d: descriptor and header differ", pi);
-        const bool tile = h.flags & PH_TILE;
-        if (tile) CHECK(c.moff == h.vin0, "piece %d: tile multipliers differ", pi);
-        CHECK(c.moff >= 0 && c.moff + h.ncols <= P.nvec, "piece %d: multipliers outside v", pi);
-        CHECK((c.moff & ~1) + padded_entries(c.moff, h.ncols) <= NV, "piece %d: multiplier copy outside v", pi);
-        CHECK(padded_entries(c.moff, h.ncols) * 8 <= PIECE_MAX_COLS * 8 + 16, "piece %d: multiplier copy too long",
-              pi);
-        const size_t stride = ((size_t)h.nrows * B + 7) & ~(size_t)7;
-        const size_t cb = off + 40 + (tile ? 0 : ((2 * (size_t)h.ncols + 7) & ~(size_t)7));
-        CHECK(cb + stride * h.ncols - off == bytes, "piece %d: %zu bytes described, %u copied", pi,
-              cb + stride * h.ncols - off, bytes);
-        if (cb + stride * h.ncols > pay.size() || c.moff < 0 || c.moff + h.ncols > P.nvec) continue;
-        if (rflags & PD_FIRST) std::fill(acc.begin(), acc.end(), 0.0);
-        const uint16_t* em = reinterpret_cast<const uint16_t*>(&pay[off + 40]);
-        for (int j = 0; j < h.ncols; ++j) {
-          const int32_t vi = c.moff + j;
-          read[vi] = 1;
-          const uint16_t f16 = format16(B, fmt, tile ? h.em : em[j]);
-          double mult = vin[vi];
-          if (tile) {
-            mult *= ff(h.scale);
-            if (h.flags & PH_TALPHA) mult *= alpha;
-          }
-          for (int r = 0; r < h.nrows; ++r)
-            acc[r] += decode(load_code(&pay[cb + j * stride + (size_t)r * B], B), f16) * mult;
-        }
-        if (rflags & PD_LAST) emit(L, h, c, acc, written, pi);
-      }
-    }
+    std::vector<double> acc(CHUNK_ROWS, 0.0);
+    for (int w = 0; w < nw; ++w)
+      for (int32_t pi = wb[w]; pi < wb[w + 1]; ++pi) piece(L, pi, acc, read, written);
   }
 
-  void emit(const Launch& L, const PieceHdr& h, const PieceCopy& c, const std::vector<double>& acc,
+  // One row-chunk piece: its multipliers are read from v now (as a warp copies
+  // them when the piece starts); its last piece of a part emits.  Returns true
+  // if the piece emitted its chunk (a shared chunk: only its last part).
+  bool piece(const Launch& L, int32_t pi, std::vector<double>& acc, std::vector<char>& read,
+             std::vector<char>& written) {
+    const auto& pay = P.pk.pay;
+    const PieceCopy& c = P.pdesc[shape][pi];
+    const uint64_t off = (uint64_t)c.off16 * 16;
+    const uint32_t bytes = c.bytes_flags & 0xffff, rflags = (c.bytes_flags >> 16) & 0xff, ncols = c.bytes_flags >> 24;
+    CHECK(off + ((bytes + 15) & ~15u) <= pay.size(), "piece %d outside the payload", pi);
+    CHECK(bytes <= (uint32_t)STAGE_BYTES, "piece %d larger than a stage", pi);
+    if (off + sizeof(PieceHdr) > pay.size()) return false;
+    PieceHdr h;
+    std::memcpy(&h, &pay[off], sizeof h);
+    const int B = h.fb & 15, fmt = (h.fb >> 4) & 3;
+    // (a piece without columns only emits its chunk: e.g. coefficients that
+    // receive nothing at one level of the H2 down-sweep)
+    CHECK(h.nrows >= 1 && h.nrows <= CHUNK_ROWS && h.ncols <= PIECE_MAX_COLS, "piece %d: header out of range", pi);
+    CHECK(ncols == h.ncols, "piece %d: descriptor and header differ", pi);
+    const bool tile = h.flags & PH_TILE;
+    if (tile) CHECK(c.moff == h.vin0, "piece %d: tile multipliers differ", pi);
+    CHECK(c.moff >= 0 && c.moff + h.ncols <= P.nvec, "piece %d: multipliers outside v", pi);
+    CHECK((c.moff & ~1) + padded_entries(c.moff, h.ncols) <= NV, "piece %d: multiplier copy outside v", pi);
+    CHECK(padded_entries(c.moff, h.ncols) * 8 <= PIECE_MAX_COLS * 8 + 16, "piece %d: multiplier copy too long", pi);
+    const size_t stride = ((size_t)h.nrows * B + 7) & ~(size_t)7;
+    const size_t cb = off + 40 + (tile ? 0 : ((2 * (size_t)h.ncols + 7) & ~(size_t)7));
+    CHECK(cb + stride * h.ncols - off == bytes, "piece %d: %zu bytes described, %u copied", pi,
+          cb + stride * h.ncols - off, bytes);
+    if (cb + stride * h.ncols > pay.size() || c.moff < 0 || c.moff + h.ncols > P.nvec) return false;
+    if (rflags & PD_FIRST) std::fill(acc.begin(), acc.end(), 0.0);
+    const uint16_t* em = reinterpret_cast<const uint16_t*>(&pay[off + 40]);
+    for (int j = 0; j < h.ncols; ++j) {
+      const int32_t vi = c.moff + j;
+      read[vi] = 1;
+      const uint16_t f16 = format16(B, fmt, tile ? h.em : em[j]);
+      double mult = v[vi];
+      if (tile) {
+        mult *= ff(h.scale);
+        if (h.flags & PH_TALPHA) mult *= alpha;
+      }
+      for (int r = 0; r < h.nrows; ++r) acc[r] += decode(load_code(&pay[cb + j * stride + (size_t)r * B], B), f16) * mult;
+    }
+    return (rflags & PD_LAST) ? emit(L, h, c, acc, written, pi) : false;
+  }
+
+  bool emit(const Launch& L, const PieceHdr& h, const PieceCopy& c, const std::vector<double>& acc,
             std::vector<char>& written, int pi) {
     std::vector<double> out(acc.begin(), acc.begin() + h.nrows);
     if ((c.bytes_flags >> 16) & PD_SPLIT) {
       const int split = c.split_part >> 8, pidx = c.split_part & 0xff;
       CHECK(split >= 0 && split < (int)P.splits.size(), "piece %d: split outside its list", pi);
-      if (split < 0 || split >= (int)P.splits.size()) return;
+      if (split < 0 || split >= (int)P.splits.size()) return false;
       const Split& sp = P.splits[split];
       CHECK(sp.nparts >= 2 && sp.nparts <= 256 && pidx < sp.nparts, "piece %d: part outside its split", pi);
       CHECK(sp.slot0 >= 0 && sp.slot0 + sp.nparts <= nfix, "piece %d: fix-up slots outside their array", pi);
-      if (pidx >= sp.nparts || sp.slot0 < 0 || sp.slot0 + sp.nparts > nfix) return;
+      if (pidx >= sp.nparts || sp.slot0 < 0 || sp.slot0 + sp.nparts > nfix) return false;
       for (int r = 0; r < h.nrows; ++r) fix[(size_t)(sp.slot0 + pidx) * CHUNK_ROWS + r] = acc[r];
-      if (++cnt[split] != sp.nparts) return;
+      if (++cnt[split] != sp.nparts) return false;
       cnt[split] = 0;   // the last part resets the counter for the next product
       for (int r = 0; r < h.nrows; ++r) {
         double s = 0;
@@ -290,11 +296,85 @@ struct Replay {
       v[g] = val;
       written[g] = 1;
     }
+    return true;
   }
 
-  void run(const std::vector<double>& x) {
+  // Row-chunk launches [first, last) as the phases of one persistent launch:
+  // nwarps warps take the ranges of each phase in order (a warp without a range
+  // claims the next one, moving to the next phase when a phase has none left)
+  // and run them piece by piece.  A piece starts only when the chunk versions of
+  // its SeqDep are reached; an emit of a chunk raises its version.  The warp that
+  // steps next is drawn at random among those that can.  Work left with no warp
+  // able to step would be a hang of the launch.
+  void dataflow(size_t first, size_t last, const std::vector<SeqDep>& deps, int nchunks, int nwarps,
+                std::mt19937& rng) {
+    struct Warp {
+      size_t phase = 0;
+      int32_t next = 0, end = 0;
+      bool done = false;
+      std::vector<double> acc = std::vector<double>(CHUNK_ROWS, 0.0);
+    };
+    const size_t nph = last - first;
+    std::vector<int> ver(nchunks, 0), claim(nph, 0);
+    std::vector<Warp> warps(nwarps);
+    std::vector<char> read(P.nvec, 0), written(P.nvec, 0);   // phases read what earlier phases wrote
+    auto ready = [&](int32_t i) {
+      const SeqDep& d = deps[i];
+      return (d.c0 < 0 || ver[d.c0] >= d.v0) && (d.c1 < 0 || ver[d.c1] >= d.v1);
+    };
+    for (;;) {
+      std::vector<int> can;
+      bool left = false;
+      for (int w = 0; w < nwarps; ++w) {
+        Warp& a = warps[w];
+        while (!a.done && a.next == a.end) {
+          if (a.phase == nph) {
+            a.done = true;
+            break;
+          }
+          const Launch& L = P.launches[first + a.phase];
+          const int r = claim[a.phase]++;
+          if (r >= L.nw[shape]) {
+            ++a.phase;
+            continue;
+          }
+          const int32_t* wb = P.wbeg.data() + L.woff[shape];
+          a.next = wb[r];
+          a.end = wb[r + 1];
+        }
+        if (a.done) continue;
+        left = true;
+        if (ready(a.next)) can.push_back(w);
+      }
+      if (!left) break;
+      CHECK(!can.empty(), "persistent run from launch %zu: work left and no warp can step", first);
+      if (can.empty()) return;
+      Warp& a = warps[can[rng() % can.size()]];
+      const int32_t i = a.next++;
+      if (piece(P.launches[first + a.phase], i, a.acc, read, written) && deps[i].c1 >= 0) ++ver[deps[i].c1];
+    }
+  }
+
+  // One product.  nwarps > 0: runs of row-chunk launches that the library fuses
+  // into one persistent launch (SEQ_SHAPE) go through `dataflow`.
+  void run(const std::vector<double>& x, int nwarps = 0, uint32_t seed = 1) {
     y.assign(H.n, NAN);
-    for (const Launch& L : P.launches) {
+    std::mt19937 rng(seed);
+    for (size_t li = 0; li < P.launches.size(); ++li) {
+      const Launch& L = P.launches[li];
+      if (nwarps > 0 && shape == SEQ_SHAPE && L.kind == Launch::RGEMV) {
+        size_t j = li;
+        while (j < P.launches.size() && P.launches[j].kind == Launch::RGEMV) ++j;
+        std::vector<SeqDep> deps;
+        int nchunks = 0;
+        if (j - li >= 2 && seq_dependencies(P, li, j, deps, nchunks)) {
+          for (size_t k = li; k < j; ++k) ranges(P.launches[k]);
+          dataflow(li, j, deps, nchunks, nwarps, rng);
+          ++persistent_runs;
+          li = j - 1;
+          continue;
+        }
+      }
       std::vector<char> read(P.nvec, 0), written(P.nvec, 0);
       switch (L.kind) {
         case Launch::GATHER:
@@ -461,6 +541,18 @@ int main(int argc, char** argv) {
     }
     CHECK(differ == 0, "shape %d: second product differs in %ld entries", cf, (long)differ);
     std::printf("shape %d rel_err %.6e\n", cf, std::sqrt(num / den));
+    if (cf != SEQ_SHAPE) continue;
+    // the persistent launch: any order its waits allow must give the same y
+    const int warp_counts[] = {1, 2, 7, 64, 1000};
+    for (int nwarps : warp_counts)
+      for (uint32_t seed = 1; seed <= 3; ++seed) {
+        Replay D(H, P, cf, alpha);
+        D.run(x, nwarps, seed);
+        int64_t d = 0;
+        for (int64_t i = 0; i < n; ++i) d += !(D.y[i] == first[i]);
+        CHECK(d == 0, "persistent launch, %d warps, seed %u: %ld entries differ", nwarps, seed, (long)d);
+        if (nwarps == 1 && seed == 1) std::printf("persistent runs %d\n", D.persistent_runs);
+      }
   }
   if (g_fails) {
     std::printf("FAILED %d\n", g_fails);

@@ -12,6 +12,13 @@ the host stores it in its format (H blocks, or bases and couplings):
   indices, scales and emit modes for every format;
 * compressed: within eps, the codecs' rounding only (measured at most 0.18 eps
   over formats, codecs and eps 1e-4..1e-8).
+
+The runs of row-chunk launches that the library fuses into one persistent
+launch (the H2 sweeps, the two coupling stages of separate couplings) are also
+replayed as dataflow.  Warps step in random order with 1 to 1000 warps, and each
+piece waits for the chunk versions of its dependencies.  No order may stall with
+work left, which would be a hang, and none may change y by a bit, which would be
+a race.
 """
 import os
 import shutil
@@ -79,6 +86,10 @@ def test_program_layout_and_replay(checker, case):
     assert len(errs) == 4                                  # three warp shapes and the multi-RHS shape
     bound = 1e-13 if codec == "none" else eps
     assert max(errs) <= bound, (errs, bound)
+    runs = [int(line.split()[-1]) for line in r.stdout.splitlines() if line.startswith("persistent runs")]
+    assert len(runs) == 1
+    if fmt in ("h2", "uh_sep"):
+        assert runs[0] >= 1                                # the dataflow replay ran
 
 
 def test_h2_hodlr_basis_rank_above_the_kernel_limit(checker):
