@@ -506,4 +506,63 @@ void build_nested_bases(HostMatrix& hm, int nthreads) {
   }
 }
 
+// The transpose of an H / UH / H2 matrix on the host: every block (t, s)
+// becomes (s, t) with W and X swapped (low rank), D^T (dense), S^T (couplings),
+// and the row and column bases (with their transfer matrices) trade places.
+// Same cluster tree, same block numbering, same singular values: compressing it
+// gives the codes of the original blocks, rearranged.
+void transpose_host(const HostMatrix& H, HostMatrix& T) {
+  T.prm = H.prm;
+  T.n = H.n;
+  T.kparam = H.kparam;
+  T.pts = H.pts;
+  T.ct = H.ct;
+  T.blocks = H.blocks;
+  for (BlockLeaf& b : T.blocks) std::swap(b.row, b.col);
+  T.slot = H.slot;
+  T.lr = H.lr;
+  for (LowRankBlock& l : T.lr) std::swap(l.W, l.X);
+  T.dn.assign(H.dn.size(), DenseBlock());
+  T.coupling.assign(H.coupling.size(), std::vector<double>());
+  for (size_t b = 0; b < H.blocks.size(); ++b) {
+    const int64_t nt = H.ct.cl[H.blocks[b].row].size(), ns = H.ct.cl[H.blocks[b].col].size();
+    const int sl = H.slot[b];
+    if (!H.blocks[b].adm) {
+      const std::vector<double>& D = H.dn[sl].D;   // nt x ns
+      std::vector<double>& Dt = T.dn[sl].D;        // ns x nt
+      Dt.resize(D.size());
+      for (int64_t j = 0; j < ns; ++j)
+        for (int64_t i = 0; i < nt; ++i) Dt[(size_t)j + (size_t)i * ns] = D[(size_t)i + (size_t)j * nt];
+    } else if ((size_t)sl < H.coupling.size() && !H.coupling[sl].empty()) {
+      const int kt = H.rowb.k[H.blocks[b].row], ks = H.colb.k[H.blocks[b].col];
+      const std::vector<double>& S = H.coupling[sl];   // kt x ks
+      std::vector<double>& St = T.coupling[sl];        // ks x kt
+      St.resize(S.size());
+      for (int j = 0; j < ks; ++j)
+        for (int i = 0; i < kt; ++i) St[(size_t)j + (size_t)i * ks] = S[(size_t)i + (size_t)j * kt];
+    }
+  }
+  // UH_SEP: S^T = Sc Sr^T, so Sr' = (Sc^T)^T and Sc'^T = Sr^T
+  T.coupling_r.assign(H.coupling_ct.size(), std::vector<double>());
+  T.coupling_ct.assign(H.coupling_r.size(), std::vector<double>());
+  for (size_t b = 0; b < H.blocks.size(); ++b) {
+    const int sl = H.slot[b];
+    if (!H.blocks[b].adm || (size_t)sl >= H.coupling_r.size() || H.coupling_r[sl].empty()) continue;
+    const int kt = H.rowb.k[H.blocks[b].row], ks = H.colb.k[H.blocks[b].col];
+    const int kb = (int)(H.coupling_r[sl].size() / std::max(kt, 1));
+    const std::vector<double>& R = H.coupling_r[sl];    // kt x kb
+    const std::vector<double>& C = H.coupling_ct[sl];   // kb x ks
+    std::vector<double>& Rt = T.coupling_r[sl];         // ks x kb = C^T
+    std::vector<double>& Ct = T.coupling_ct[sl];        // kb x kt = R^T
+    Rt.resize(C.size());
+    Ct.resize(R.size());
+    for (int l = 0; l < kb; ++l) {
+      for (int j = 0; j < ks; ++j) Rt[(size_t)j + (size_t)l * ks] = C[(size_t)l + (size_t)j * kb];
+      for (int i = 0; i < kt; ++i) Ct[(size_t)l + (size_t)i * kb] = R[(size_t)i + (size_t)l * kt];
+    }
+  }
+  T.rowb = H.colb;
+  T.colb = H.rowb;
+}
+
 }  // namespace hm

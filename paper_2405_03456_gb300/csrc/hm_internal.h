@@ -93,6 +93,9 @@ struct HostMatrix {
 void build_lowrank_blocks(HostMatrix& hm, int nthreads);
 void build_uniform_bases(HostMatrix& hm, int nthreads);
 void build_nested_bases(HostMatrix& hm, int nthreads);
+// The transpose: blocks (t, s) -> (s, t) with W and X, row and column bases and
+// their transfer matrices swapped, dense blocks and couplings transposed.
+void transpose_host(const HostMatrix& H, HostMatrix& T);
 
 // ---------------------------------------------------------------- codecs (Sec. 4.1)
 enum { FMT_FPX8 = 0, FMT_FPX11 = 1, FMT_AFLP = 2, FMT_RAW = 3 };

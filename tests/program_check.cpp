@@ -22,8 +22,10 @@
 // of its dependencies.  No such order may stall with work left (a hang on the
 // device) or change y by a single bit (a race).
 //
-// usage: program_check <points+x file> n format eps codec leaf nsm adm kernel
+// usage: program_check <points+x file> n format eps codec leaf nsm adm kernel [adjoint]
 //   file: n*3 doubles (points, row-major) then n doubles (x, original order)
+//   adjoint 1: the program of the transposed matrix (transpose_host, as the
+//   adjoint product runs it), compared with M^T x from the original's blocks
 //   format 0 H, 1 UH, 2 H2, 3 UH with separate couplings; codec 0 none,
 //   1 AFLP, 2 FPX; adm 0 standard, 1 HODLR, 2 BLR; kernel 0 Laplace, 1 Matern
 // prints one line per shape and "ok" or "FAILED <count>"; exit status 0 iff ok.
@@ -427,10 +429,11 @@ std::vector<double> explicit_basis(const HostMatrix& H, const Bases& b, int c) {
   return w;
 }
 
-// alpha * M x in FP64 (original order) for the matrix as the host stores it in
-// the chosen format: H blocks W diag(s) X^T; UH and H2 blocks W_t S X_s^T with
-// the coupling S (separate couplings: S = Sr Sc^T); dense blocks D.
-std::vector<double> host_product(const HostMatrix& H, const std::vector<double>& x, double alpha) {
+// alpha * M x (transpose: alpha * M^T x) in FP64, original order, for the matrix
+// as the host stores it in its format: H blocks W diag(s) X^T; UH and H2 blocks
+// W_t S X_s^T with the coupling S (separate couplings: S = Sr Sc^T); dense
+// blocks D.  Each block maps its input cluster to its output cluster.
+std::vector<double> host_product(const HostMatrix& H, const std::vector<double>& x, double alpha, bool transpose) {
   const int format = H.prm.format;
   std::vector<std::vector<double>> wb(H.ct.cl.size()), xb(H.ct.cl.size());
   if (format != HM_FMT_H)
@@ -438,49 +441,51 @@ std::vector<double> host_product(const HostMatrix& H, const std::vector<double>&
       wb[c] = explicit_basis(H, H.rowb, (int)c);
       xb[c] = explicit_basis(H, H.colb, (int)c);
     }
+  // column-major a (m x k) times v: a v, or a^T v
+  auto apply = [](const std::vector<double>& a, int64_t m, int64_t k, const std::vector<double>& in, bool tr) {
+    std::vector<double> out(tr ? k : m, 0.0);
+    for (int64_t j = 0; j < k; ++j)
+      for (int64_t i = 0; i < m; ++i) {
+        if (tr)
+          out[j] += a[i + (size_t)j * m] * in[i];
+        else
+          out[i] += a[i + (size_t)j * m] * in[j];
+      }
+    return out;
+  };
   std::vector<double> y(H.n, 0.0);
   for (size_t b = 0; b < H.blocks.size(); ++b) {
     const BlockLeaf& bl = H.blocks[b];
     const Cluster& t = H.ct.cl[bl.row];
     const Cluster& s = H.ct.cl[bl.col];
     const int64_t nt = t.end - t.start, ns = s.end - s.start;
-    std::vector<double> xs(ns), ys(nt, 0.0);
-    for (int64_t j = 0; j < ns; ++j) xs[j] = x[H.ct.perm[s.start + j]];
+    const Cluster& in = transpose ? t : s;
+    const Cluster& out = transpose ? s : t;
+    std::vector<double> xi(in.end - in.start), yo;
+    for (int64_t j = 0; j < (int64_t)xi.size(); ++j) xi[j] = x[H.ct.perm[in.start + j]];
     if (!bl.adm) {
-      const auto& D = H.dn[H.slot[b]].D;
-      for (int64_t j = 0; j < ns; ++j)
-        for (int64_t i = 0; i < nt; ++i) ys[i] += D[j * nt + i] * xs[j];
+      yo = apply(H.dn[H.slot[b]].D, nt, ns, xi, transpose);
     } else if (format == HM_FMT_H) {
       const LowRankBlock& L = H.lr[H.slot[b]];
-      for (int k = 0; k < L.k; ++k) {
-        double tk = 0;
-        for (int64_t j = 0; j < ns; ++j) tk += L.X[k * ns + j] * xs[j];
-        tk *= L.s[k];
-        for (int64_t i = 0; i < nt; ++i) ys[i] += L.W[k * nt + i] * tk;
-      }
+      // W diag(s) X^T x, or X diag(s) W^T x
+      std::vector<double> c = transpose ? apply(L.W, nt, L.k, xi, true) : apply(L.X, ns, L.k, xi, true);
+      for (int k = 0; k < L.k; ++k) c[k] *= L.s[k];
+      yo = transpose ? apply(L.X, ns, L.k, c, false) : apply(L.W, nt, L.k, c, false);
     } else {
       const int kt = H.rowb.k[bl.row], ks = H.colb.k[bl.col];
-      std::vector<double> sv(ks, 0.0), tv(kt, 0.0);     // s = X_s^T x, t = S s
-      for (int l = 0; l < ks; ++l)
-        for (int64_t j = 0; j < ns; ++j) sv[l] += xb[bl.col][j + (size_t)l * ns] * xs[j];
-      if (format == HM_FMT_UH_SEP) {
+      std::vector<double> c = transpose ? apply(wb[bl.row], nt, kt, xi, true) : apply(xb[bl.col], ns, ks, xi, true);
+      if (format == HM_FMT_UH_SEP) {   // S = R C with R (kt x kb), C (kb x ks)
         const auto& R = H.coupling_r[H.slot[b]];
         const auto& C = H.coupling_ct[H.slot[b]];
         const int kb = H.lr[H.slot[b]].k;
-        std::vector<double> u(kb, 0.0);
-        for (int l = 0; l < kb; ++l)
-          for (int j = 0; j < ks; ++j) u[l] += C[l + (size_t)j * kb] * sv[j];
-        for (int i = 0; i < kt; ++i)
-          for (int l = 0; l < kb; ++l) tv[i] += R[i + (size_t)l * kt] * u[l];
+        c = transpose ? apply(C, kb, ks, apply(R, kt, kb, c, true), true)
+                      : apply(R, kt, kb, apply(C, kb, ks, c, false), false);
       } else {
-        const auto& S = H.coupling[H.slot[b]];
-        for (int i = 0; i < kt; ++i)
-          for (int j = 0; j < ks; ++j) tv[i] += S[i + (size_t)j * kt] * sv[j];
+        c = apply(H.coupling[H.slot[b]], kt, ks, c, transpose);
       }
-      for (int l = 0; l < kt; ++l)
-        for (int64_t i = 0; i < nt; ++i) ys[i] += wb[bl.row][i + (size_t)l * nt] * tv[l];
+      yo = transpose ? apply(xb[bl.col], ns, ks, c, false) : apply(wb[bl.row], nt, kt, c, false);
     }
-    for (int64_t i = 0; i < nt; ++i) y[H.ct.perm[t.start + i]] += alpha * ys[i];
+    for (int64_t i = 0; i < (int64_t)yo.size(); ++i) y[H.ct.perm[out.start + i]] += alpha * yo[i];
   }
   return y;
 }
@@ -488,10 +493,11 @@ std::vector<double> host_product(const HostMatrix& H, const std::vector<double>&
 }  // namespace
 
 int main(int argc, char** argv) {
-  if (argc != 10) {
-    std::fprintf(stderr, "usage: %s file n format eps codec leaf nsm adm kernel\n", argv[0]);
+  if (argc != 10 && argc != 11) {
+    std::fprintf(stderr, "usage: %s file n format eps codec leaf nsm adm kernel [adjoint]\n", argv[0]);
     return 2;
   }
+  const bool adjoint = argc == 11 && std::atoi(argv[10]) != 0;
   const int64_t n = std::atoll(argv[2]);
   const int format = std::atoi(argv[3]), codec = std::atoi(argv[5]), leaf = std::atoi(argv[6]),
             nsm = std::atoi(argv[7]), adm = std::atoi(argv[8]), kernel = std::atoi(argv[9]);
@@ -519,17 +525,20 @@ int main(int argc, char** argv) {
   build_lowrank_blocks(H, 8);
   if (format == HM_FMT_UH || format == HM_FMT_UH_SEP) build_uniform_bases(H, 8);
   if (format == HM_FMT_H2) build_nested_bases(H, 8);
+  HostMatrix T;   // adjoint: the program of the transposed matrix, as hm_matvec_adjoint runs it
+  if (adjoint) transpose_host(H, T);
+  const HostMatrix& M = adjoint ? T : H;
   Program P;
-  if (!build_program(H, codec, eps, 1, nsm, P)) {
+  if (!build_program(M, codec, eps, 1, nsm, P)) {
     std::printf("build_program failed\n");
     return 1;
   }
   const double alpha = 0.75;
-  const std::vector<double> yref = host_product(H, x, alpha);
+  const std::vector<double> yref = host_product(H, x, alpha, adjoint);
   double den = 0;
   for (double t : yref) den += t * t;
   for (int cf = 0; cf < NSHAPES; ++cf) {
-    Replay R(H, P, cf, alpha);
+    Replay R(M, P, cf, alpha);
     R.run(x);
     const std::vector<double> first = R.y;
     R.run(x);
@@ -546,7 +555,7 @@ int main(int argc, char** argv) {
     const int warp_counts[] = {1, 2, 7, 64, 1000};
     for (int nwarps : warp_counts)
       for (uint32_t seed = 1; seed <= 3; ++seed) {
-        Replay D(H, P, cf, alpha);
+        Replay D(M, P, cf, alpha);
         D.run(x, nwarps, seed);
         int64_t d = 0;
         for (int64_t i = 0; i < n; ++i) d += !(D.y[i] == first[i]);

@@ -13,6 +13,10 @@ the host stores it in its format (H blocks, or bases and couplings):
 * compressed: within eps, the codecs' rounding only (measured at most 0.18 eps
   over formats, codecs and eps 1e-4..1e-8).
 
+The program of the transposed matrix, which the adjoint product runs, is
+checked the same way.  Its replay is compared with M^T x, computed from the
+original matrix's blocks.
+
 The runs of row-chunk launches that the library fuses into one persistent
 launch (the H2 sweeps, the two coupling stages of separate couplings) are also
 replayed as dataflow.  Warps step in random order with 1 to 1000 warps, and each
@@ -64,7 +68,7 @@ def checker(tmp_path_factory):
     return exe, tmp
 
 
-def _run(checker, pts_kind, n, fmt, eps, codec, leaf, nsm, adm):
+def _run(checker, pts_kind, n, fmt, eps, codec, leaf, nsm, adm, adjoint=False):
     exe, tmp = checker
     path = tmp / f"{pts_kind}{n}.bin"
     if not path.exists():
@@ -73,7 +77,7 @@ def _run(checker, pts_kind, n, fmt, eps, codec, leaf, nsm, adm):
         path.write_bytes(np.ascontiguousarray(pts).tobytes() + np.ascontiguousarray(x).tobytes())
     kernel = 0 if pts_kind == "sphere" else 1
     return subprocess.run([exe, str(path), str(n), str(FORMATS[fmt]), repr(eps), str(CODECS[codec]), str(leaf),
-                           str(nsm), str(ADMS[adm]), str(kernel)],
+                           str(nsm), str(ADMS[adm]), str(kernel), str(int(adjoint))],
                           stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True, timeout=600)
 
 
@@ -90,6 +94,18 @@ def test_program_layout_and_replay(checker, case):
     assert len(runs) == 1
     if fmt in ("h2", "uh_sep"):
         assert runs[0] >= 1                                # the dataflow replay ran
+
+
+@pytest.mark.parametrize("fmt", list(FORMATS))
+@pytest.mark.parametrize("codec", ["none", "fpx"])
+def test_adjoint_program(checker, fmt, codec):
+    # the adjoint product runs the program of the transposed matrix: its replay
+    # must give M^T x computed from the original matrix's blocks
+    eps = 1e-6
+    r = _run(checker, "sphere", 3000, fmt, eps, codec, 32, 152, "std", adjoint=True)
+    assert r.returncode == 0 and r.stdout.rstrip().endswith("ok"), r.stdout[-2000:]
+    errs = [float(line.split()[-1]) for line in r.stdout.splitlines() if line.startswith("shape")]
+    assert len(errs) == 4 and max(errs) <= (1e-13 if codec == "none" else eps), errs
 
 
 def test_h2_hodlr_basis_rank_above_the_kernel_limit(checker):
