@@ -24,10 +24,10 @@
 //
 // usage: program_check <points+x file> n format eps codec leaf nsm adm kernel [adjoint]
 //   file: n*3 doubles (points, row-major) then n doubles (x, original order)
-//   adjoint 1: the program of the transposed matrix (transpose_host, as the
-//   adjoint product runs it), compared with M^T x from the original's blocks
 //   format 0 H, 1 UH, 2 H2, 3 UH with separate couplings; codec 0 none,
 //   1 AFLP, 2 FPX; adm 0 standard, 1 HODLR, 2 BLR; kernel 0 Laplace, 1 Matern
+//   adjoint 1: the program of the transposed matrix (transpose_host, as the
+//   adjoint product runs it), compared with M^T x from the original's blocks
 // prints one line per shape and "ok" or "FAILED <count>"; exit status 0 iff ok.
 #include <cmath>
 #include <cstdio>
