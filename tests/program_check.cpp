@@ -12,6 +12,8 @@
 //  * warp ranges in order and covering their launch;
 //  * within one launch, no vector entry both read as a multiplier or input and
 //    written as an output (the launch's warps run concurrently);
+//  * in the FP32 tier, every decoded value equal to the sum of the BF16 limbs
+//    the multi-RHS path keeps for its piece (the `limbs` header field);
 // then it replays the launches in program order in FP64 (Alg. 8: each code
 // decoded, then Alg. 1 / 4-7 as the program orders them).  The replay must give
 // the same y bit for bit on a second pass (no state left between products), and
@@ -91,6 +93,30 @@ uint16_t format16(int B, int fmt, uint16_t em) {
 
 double ff(const F2& v) { return (double)v.hi + (double)v.lo; }
 
+// Round an FP32 value to BF16, to nearest with ties to even, as its FP32 value.
+float bf16_rn(float a) {
+  uint32_t b;
+  std::memcpy(&b, &a, 4);
+  b = (b + 0x7fffu + ((b >> 16) & 1u)) & 0xffff0000u;
+  float r;
+  std::memcpy(&r, &b, 4);
+  return r;
+}
+
+// The multi-RHS path splits each decoded value a (FP32) into BF16 limbs,
+// a = l0 + l1 + l2 with l0 = bf16(a), l1 = bf16(a - l0), l2 = bf16(a - l0 - l1),
+// and multiplies only the first `limbs` of them: true if those are exactly a.
+// Three limbs hold every FP32 value; a piece that keeps fewer must hold values
+// of at most 8 * limbs significant bits, exact in FP32.
+bool limbs_exact(double v, int limbs) {
+  if (limbs >= 3) return true;
+  const float a = (float)v;
+  if ((double)a != v) return false;
+  const float l0 = bf16_rn(a), r1 = a - l0, l1 = bf16_rn(r1), r2 = r1 - l1, l2 = bf16_rn(r2);
+  const double sum = limbs == 1 ? (double)l0 : limbs == 2 ? (double)l0 + l1 : ((double)l0 + l1) + l2;
+  return sum == v;
+}
+
 // Entries of a 16-byte aligned copy of `count` 8-byte entries starting at i.
 int64_t padded_entries(int64_t i, int64_t count) { return ((i - (i & ~1LL) + count) * 8 + 15) / 16 * 2; }
 
@@ -158,6 +184,8 @@ struct Replay {
             CHECK(d == 0.0, "item %ld: padding row not zero", (long)it);
           else
             s += d * v[h.vin + r];
+          if (P.tier == TIER_F32)
+            CHECK(limbs_exact(d, h.limbs), "item %ld: a value needs more than %d BF16 limbs", (long)it, h.limbs);
         }
         if (final) {
           CHECK(cm[j].out >= 0 && cm[j].out < P.nvec, "item %ld: output outside v", (long)it);
@@ -257,7 +285,12 @@ struct Replay {
         mult *= ff(h.scale);
         if (h.flags & PH_TALPHA) mult *= alpha;
       }
-      for (int r = 0; r < h.nrows; ++r) acc[r] += decode(load_code(&pay[cb + j * stride + (size_t)r * B], B), f16) * mult;
+      for (int r = 0; r < h.nrows; ++r) {
+        const double d = decode(load_code(&pay[cb + j * stride + (size_t)r * B], B), f16);
+        if (P.tier == TIER_F32)
+          CHECK(limbs_exact(d, h.limbs), "piece %d: a value needs more than %d BF16 limbs", pi, h.limbs);
+        acc[r] += d * mult;
+      }
     }
     return (rflags & PD_LAST) ? emit(L, h, c, acc, written, pi) : false;
   }
