@@ -60,6 +60,7 @@ class MatrixSlot:
     resident_bytes: int
     queue: list = field(default_factory=list)
     busy: bool = False
+    adjoint: bool = False         # serves M^H x requests (its transposed copy is resident too)
 
 
 class Scheduler:
@@ -81,14 +82,16 @@ class Scheduler:
         self.rhs_launched = 0
 
     # -------------------------------------------------------------- matrices
-    def add_matrix(self, mid: int, n: int, resident_bytes: int) -> None:
-        """Register a resident matrix; refuses it if the budget would be exceeded."""
-        need = resident_bytes + self.ex.staging_bytes(n, self.max_rhs)
+    def add_matrix(self, mid: int, n: int, resident_bytes: int, adjoint: bool = False) -> None:
+        """Register a resident matrix; refuses it if the budget would be exceeded.
+        adjoint: the matrix also serves M^H x requests, which run on its transposed
+        copy (the same codes rearranged), counted as a second resident_bytes."""
+        need = resident_bytes * (2 if adjoint else 1) + self.ex.staging_bytes(n, self.max_rhs)
         if self.used + need > self.budget:
             raise MemoryError(f"matrix {mid}: {need} bytes exceed the remaining budget "
                               f"{self.budget - self.used}")
         self.used += need
-        self.mats[mid] = MatrixSlot(mid, n, resident_bytes)
+        self.mats[mid] = MatrixSlot(mid, n, resident_bytes, adjoint=adjoint)
 
     # -------------------------------------------------------------- requests
     def _req_bytes(self, req: Request) -> int:
@@ -98,6 +101,8 @@ class Scheduler:
         """Admit a request if its data fits next to what is queued, else keep it in the backlog."""
         if req.r < 1 or req.r > self.max_rhs or req.mid not in self.mats:
             raise ValueError(f"request {req.rid}: bad matrix or RHS count")
+        if req.adjoint and not self.mats[req.mid].adjoint:
+            raise ValueError(f"request {req.rid}: matrix {req.mid} was registered without adjoint support")
         if self.backlog or self.used + self.queued_bytes + self._req_bytes(req) > self.budget:
             self.backlog.append(req)
             return

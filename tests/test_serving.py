@@ -54,11 +54,11 @@ class FakeClock:
             ex.now = max(ex.now, min(cand))
 
 
-def make(mats, budget=10**12, nslots=2):
+def make(mats, budget=10**12, nslots=2, adjoint=False):
     ex = FakeExecutor(mats)
     sch = Scheduler(ex, budget, nslots=nslots)
     for mid, n in mats.items():
-        sch.add_matrix(mid, n, resident_bytes=1000)
+        sch.add_matrix(mid, n, resident_bytes=1000, adjoint=adjoint)
     return ex, sch
 
 
@@ -106,7 +106,7 @@ def test_adjoint_requests_one_direction_per_launch():
     a launch never mixes directions, and each matrix serves its requests in
     arrival order."""
     mats = {0: 24, 1: 36}
-    ex, sch = make(mats)
+    ex, sch = make(mats, adjoint=True)
     reqs = poisson_requests(mats, rate=5000.0, count=150, seed=6, adjoint_frac=0.4)
     assert 20 < sum(q.adjoint for q in reqs) < 130
     launched = []
@@ -136,6 +136,20 @@ def test_rejects_bad_requests():
         sch.submit(Request(0, 5, np.zeros((8, 1)), 0.0), 0.0)
     with pytest.raises(ValueError):
         sch.submit(Request(1, 0, np.zeros((8, MAX_BATCH_RHS + 1)), 0.0), 0.0)
+    with pytest.raises(ValueError):                          # registered without adjoint support
+        sch.submit(Request(2, 0, np.zeros((8, 1)), 0.0, adjoint=True), 0.0)
+
+
+def test_adjoint_support_counts_the_transposed_copy():
+    ex = FakeExecutor({0: 8, 1: 8})
+    stage = ex.staging_bytes(8, MAX_BATCH_RHS)
+    sch = Scheduler(ex, budget_bytes=3000 + 2 * stage, nslots=2)
+    sch.add_matrix(0, 8, resident_bytes=1000, adjoint=True)     # 2000 + staging
+    assert sch.used == 2000 + stage
+    with pytest.raises(MemoryError):
+        sch.add_matrix(1, 8, resident_bytes=1000, adjoint=True)
+    sch.add_matrix(1, 8, resident_bytes=1000)                    # fits without its transpose
+    assert sch.used == 3000 + 2 * stage
 
 
 @pytest.mark.gpu
