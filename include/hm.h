@@ -219,6 +219,10 @@ typedef struct { int32_t B, fmt, e, m; double vmin; } hm_codec_header;
  * hm_codec_encode -- host: compress n FP64 values (host, contiguous) with
  * `codec` (AFLP or FPX) at accuracy key (AFLP: m requested mantissa bits;
  * FPX: table row of the key).  out: host, capacity cap bytes (>= 8n suffices).
+ * The header reports the format actually used: AFLP stores raw FP64 when
+ * 1 + m' + e > 56 or when s = |v|/vmin + 1 leaves the FP64 range; an FPX e8
+ * row moves to e11 m28 when a value lies outside the FP32 normal range, and an
+ * e11 row to the exact e11 m52 when a value rounds past the FP64 maximum.
  * Errors: HM_ERR_ARG (null, n < 0, key outside 0..60, cap too small, NaN/Inf).
  */
 hm_status hm_codec_encode(const double* v, int64_t n, int32_t codec, int32_t key, uint8_t* out,
