@@ -108,6 +108,15 @@ def test_adjoint_program(checker, fmt, codec):
     assert len(errs) == 4 and max(errs) <= (1e-13 if codec == "none" else eps), errs
 
 
+@pytest.mark.parametrize("fmt,adm,codec", [("h", "hodlr", "aflp"), ("uh", "blr", "aflp"), ("h2", "blr", "none")])
+def test_adjoint_program_other_admissibility(checker, fmt, adm, codec):
+    eps = 1e-6
+    r = _run(checker, "sphere", 3000, fmt, eps, codec, 32, 152, adm, adjoint=True)
+    assert r.returncode == 0 and r.stdout.rstrip().endswith("ok"), r.stdout[-2000:]
+    errs = [float(line.split()[-1]) for line in r.stdout.splitlines() if line.startswith("shape")]
+    assert len(errs) == 4 and max(errs) <= (1e-13 if codec == "none" else eps), errs
+
+
 def test_h2_hodlr_basis_rank_above_the_kernel_limit(checker):
     # HODLR's top-level blocks need H2 bases of rank > 128: the program is not
     # built (hm_compress reports HM_ERR_CAPACITY)
