@@ -117,6 +117,24 @@ def test_adjoint_program_other_admissibility(checker, fmt, adm, codec):
     assert len(errs) == 4 and max(errs) <= (1e-13 if codec == "none" else eps), errs
 
 
+HEADLINE = [(131072, f, eps, c, adj) for (f, eps, c, adj) in [
+    ("h", 1e-6, "aflp", False), ("uh", 1e-6, "aflp", False), ("h2", 1e-6, "aflp", False),
+    ("uh_sep", 1e-6, "aflp", False), ("h", 1e-8, "aflp", False), ("h", 1e-4, "fpx", False),
+    ("h", 1e-6, "none", False), ("h", 1e-6, "aflp", True)]]
+
+
+@pytest.mark.skipif(os.environ.get("HM_CHECK_FULL") != "1", reason="full-size check: set HM_CHECK_FULL=1 "
+                    "(about 2 minutes and 6 GB of host memory per case)")
+@pytest.mark.parametrize("case", HEADLINE, ids=lambda c: "-".join(map(str, c)))
+def test_program_layout_headline_size(checker, case):
+    # the sphere workload the benchmark times: N = 131072, leaf 64
+    n, fmt, eps, codec, adjoint = case
+    r = _run(checker, "sphere", n, fmt, eps, codec, 64, 152, "std", adjoint=adjoint)
+    assert r.returncode == 0 and r.stdout.rstrip().endswith("ok"), r.stdout[-2000:]
+    errs = [float(line.split()[-1]) for line in r.stdout.splitlines() if line.startswith("shape")]
+    assert len(errs) == 4 and max(errs) <= (1e-13 if codec == "none" else eps), errs
+
+
 def test_h2_hodlr_basis_rank_above_the_kernel_limit(checker):
     # HODLR's top-level blocks need H2 bases of rank > 128: the program is not
     # built (hm_compress reports HM_ERR_CAPACITY)
