@@ -59,3 +59,27 @@ def test_argument_errors_without_gpu(lib):
         hm.hm_build(bad)
     assert lib.hm_matvec(None, 1.0, None, 1, 0.0, None, 1, 1, None) == 1
     assert lib.hm_free(None) == 0
+
+
+def test_newer_entry_points_check_arguments_and_order(lib):
+    """Adjoint, persistent launches and the admissibility / format enums reject bad
+    input before any device work."""
+    import ctypes as C
+
+    from paper_2405_03456_gb300 import hm
+    pts = np.random.default_rng(3).uniform(-1, 1, (64, 3))
+    for bad in ({"adm": 3}, {"fmt": 4}):
+        p = hm.hm_build_params(0, 0.0, 16, 2.0, bad.get("fmt", 0), 1e-6, 1, bad.get("adm", 0))
+        h = C.c_void_p()
+        assert lib.hm_build(C.byref(p), pts.ctypes.data, 64, C.byref(h)) == 1
+    assert lib.hm_matvec_adjoint(None, 1.0, None, 1, 0.0, None, 1, 1, None) == 1
+    assert lib.hm_persistent(None, 1) == 1
+    h = hm.hm_build(pts, leaf_size=16, nthreads=1)
+    try:
+        buf = np.zeros(64)
+        # built but not compressed: call order violated, nothing reaches the device
+        assert lib.hm_matvec_adjoint(h, 1.0, buf.ctypes.data, 64, 0.0, buf.ctypes.data, 64, 1, None) == 4
+        assert lib.hm_matvec_adjoint(h, 1.0, buf.ctypes.data, 64, 0.0, buf.ctypes.data, 64, 65, None) == 1
+        assert lib.hm_persistent(h, 0) == 0 and lib.hm_persistent(h, 1) == 0
+    finally:
+        assert lib.hm_free(h) == 0
