@@ -45,6 +45,22 @@ def test_kernel_entries_closed_form():
     assert b[0, 1] == pytest.approx((1 + t) * np.exp(-t))
     assert b[2, 2] == 1.0
     assert kernels.default_param("laplace", 100) == pytest.approx(np.sqrt(4 * np.pi / 100))
+    # general positions (every coordinate differs) against scipy's pairwise distances
+    from scipy.spatial.distance import cdist
+    rng = np.random.default_rng(11)
+    q = rng.uniform(-1, 1, (7, 3))
+    idx = np.arange(7)
+    r = cdist(q, q)
+    off = ~np.eye(7, dtype=bool)
+    a = kernels.entries("laplace", q, idx, idx, 0.5)
+    assert np.allclose(a[off], 1 / (4 * np.pi * r[off]), rtol=1e-14, atol=0)
+    b = kernels.entries("matern", q, idx, idx, 0.1)
+    t = np.sqrt(3) * r / 0.1
+    assert np.allclose(b, (1 + t) * np.exp(-t), rtol=1e-13, atol=1e-300)
+    # one pair by hand: |(0.1, 0.2, 0.3) - (0.4, -0.5, 0.9)|^2 = 0.09 + 0.49 + 0.36
+    h = np.array([[0.1, 0.2, 0.3], [0.4, -0.5, 0.9]])
+    assert kernels.entries("laplace", h, np.arange(2), np.arange(2), 0.5)[0, 1] == pytest.approx(
+        1 / (4 * np.pi * np.sqrt(0.94)), rel=1e-15)
 
 
 def test_cluster_tree_definition(sphere512):
