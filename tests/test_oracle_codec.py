@@ -105,7 +105,15 @@ def test_unit_roundoff_matches_paper_table():
         assert rel <= u
         assert rel > 0.9 * u          # the bound is attained closely on random data
         assert abs(u - ur[name]) / ur[name] < 5e-3
+        key = {23: 20, 7: 5}[m]                 # table rows e8m23 and e8m7
+        assert cd.unit_error(cd.fpx_compress(v, key)) == u
     assert abs(2.0 ** -53 - ur["FP64"]) / ur["FP64"] < 5e-3
+    # AFLP: the stated per-value relative bound 2^-m' of its mantissa width
+    c = cd.aflp_compress(v, 20)
+    assert not c["raw"] and cd.unit_error(c) == 2.0 ** -c["mp"]
+    d = cd.decompress(c)
+    rel = np.max(np.abs(d - v) / np.abs(v))
+    assert 2.0 ** -(c["mp"] + 2) < rel <= cd.unit_error(c)
 
 
 def _fpx_cases():

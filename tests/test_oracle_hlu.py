@@ -58,6 +58,12 @@ def test_factor_blocks(factors):
     Ld, Ud = hlu.dense_factor(f.L), hlu.dense_factor(f.U)
     assert np.array_equal(np.triu(Ld, 1), np.zeros_like(Ld)) and np.array_equal(np.diag(Ld), np.ones(N))
     assert np.array_equal(np.tril(Ud, -1), np.zeros_like(Ud))
+    # the expanded factors approximate the exact ones blockwise at eps (spectral), so
+    # in the Frobenius norm within eps times the number of blocks
+    nb = len(f.L.blocks) + len(f.U.blocks)
+    assert np.linalg.norm(Ld - lx) <= eps * nb * np.linalg.norm(lx)
+    assert np.linalg.norm(Ud - ux) <= eps * nb * np.linalg.norm(ux)
+    assert np.linalg.norm(Ld - lx) > 0                      # low-rank blocks were truncated
     for m, ex in ((f.L, lx), (f.U, ux)):
         for b, d in zip(m.blocks, m.data):
             t, s = rows(b), cols(b)
@@ -83,6 +89,9 @@ def test_block_substitution_equals_dense_triangular_solves(factors, codec):
     assert np.abs(x[perm] - z).max() <= 1e-12 * np.abs(z).max()
     x0 = hlu.hlu_solve(cL, cU, b[:, 1])
     assert np.abs(x0 - x[:, 1]).max() <= 1e-13 * np.abs(x[:, 1]).max()
+    if codec == "none":                                     # the FP64 factors themselves
+        xf = hlu.hlu_solve(f.L, f.U, b)
+        assert np.abs(xf - x).max() <= 1e-13 * np.abs(x).max()
 
 
 @pytest.mark.parametrize("codec", ["none", "aflp", "fpx"])
