@@ -28,7 +28,7 @@ def _oracle_structure(pts, leaf, eta):
     return ct.perm, cl, b
 
 
-@pytest.mark.parametrize("case", ["sphere2048", "sphere5000", "cube3000", "dupes"])
+@pytest.mark.parametrize("case", ["sphere2048", "sphere5000", "cube3000", "dupes", "lattice"])
 def test_trees_bit_exact(hm, case):
     if case == "sphere2048":
         pts, leaf, kern = synth.sphere_points(2048), 32, "laplace"
@@ -36,6 +36,10 @@ def test_trees_bit_exact(hm, case):
         pts, leaf, kern = synth.sphere_points(5000), 64, "laplace"
     elif case == "cube3000":
         pts, leaf, kern = synth.cube_points(3000), 64, "matern"
+    elif case == "lattice":                 # 9 x 9 x 9 grid: points lie on the bisection midpoints
+        g = np.arange(9, dtype=np.float64) / 8.0
+        pts = np.ascontiguousarray(np.stack(np.meshgrid(g, g, g, indexing="ij"), axis=-1).reshape(-1, 3))
+        leaf, kern = 8, "matern"
     else:                                   # repeated points force the degenerate split
         base = synth.cube_points(50)
         pts, leaf, kern = np.ascontiguousarray(np.repeat(base, 7, axis=0)), 4, "matern"

@@ -250,6 +250,31 @@ def test_fpx_beyond_fp64_maximum_moves_to_exact_row():
     assert (c["e"], c["m"]) == (11, 28) and np.array_equal(cd.decompress(c), w)
 
 
+def test_fpx_e8_range_boundaries():
+    # the FP32 normal range is [2^-126, 2^128): its ends stay in the e8 rows
+    lo, hi = 2.0 ** -126, 1.5 * 2.0 ** 127
+    c = cd.fpx_compress(np.array([lo, -hi, 1.0]), 20)
+    assert (c["e"], c["m"]) == (8, 23)
+    assert np.array_equal(cd.decompress(c), np.array([lo, -hi, 1.0]))
+    for out in (2.0 ** -127, (2.0 - 2.0 ** -30) * 2.0 ** 127):   # subnormal; rounds up to 2^128
+        c = cd.fpx_compress(np.array([out, 1.0]), 20)
+        assert (c["e"], c["m"]) == (11, 28)
+
+
+def test_aflp_largest_exponent_fits():
+    # s just below 2^1024 (f = 1023) is still an AFLP code; the next carry is raw
+    v = np.array([1.0, 1.5 * 2.0 ** 1023])
+    c = cd.aflp_compress(v, 20)
+    assert not c["raw"] and c["e"] == 10
+    assert np.all(np.abs(cd.decompress(c) - v) <= cd.unit_error(c) * np.abs(v))
+
+
+def test_ceil_log2_rejects_nonpositive():
+    for r in (0.0, -1.0, float("inf"), float("nan")):
+        with pytest.raises(ValueError):
+            cd.ceil_log2(r)
+
+
 def test_valr_key_brute_force():
     rng = np.random.default_rng(9)
     for _ in range(3000):

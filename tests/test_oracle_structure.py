@@ -297,3 +297,42 @@ def test_uh_separate_couplings(sphere2048, codec):
     lhs = float(y @ matvec.uhsep_mvm(m, 1.0, x[:, 0], 0.0))
     rhs = float(matvec.uhsep_mvm(m, 1.0, y, 0.0, adjoint=True) @ x[:, 0])
     assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+
+
+def test_uncompressed_codec_and_payload_counts(sphere512):
+    """codec "none" keeps FP64 values: the compressed-form products equal the FP64
+    products, and the payload is 8 bytes per stored value, counted from the
+    structure (dense entries, k (n_t + n_s) per low-rank block, basis, coupling
+    and transfer entries)."""
+    pts, h = sphere512
+    x = synth.rhs(512, 2)
+    cl = h.ct.clusters
+    ch = compress.compress_h(h, "none")
+    assert np.linalg.norm(matvec.h_mvm(ch, 1.0, x) - matvec.h_mvm(h, 1.0, x)) <= 1e-14 * np.linalg.norm(x)
+    vals = sum(d.size if not b.adm else d.rank * (cl[b.row].size + cl[b.col].size)
+               for b, d in zip(h.blocks, h.data))
+    assert compress.payload_bytes(ch) == 8 * vals
+    u = nested.build_uniform(h)
+    cu = compress.compress_uh(u, "none")
+    yu = matvec.uh_mvm(u, 1.0, x)
+    assert np.linalg.norm(matvec.uh_mvm(cu, 1.0, x) - yu) <= 1e-13 * np.linalg.norm(yu)
+    vals = sum(w.size for w in u.W) + sum(w.size for w in u.X) + sum(s.size for s in u.S)
+    assert compress.payload_bytes(cu) == 8 * vals
+    m2 = nested.build_h2(h)
+    c2 = compress.compress_h2(m2, "none")
+    y2 = matvec.h2_mvm(m2, 1.0, x)
+    assert np.linalg.norm(matvec.h2_mvm(c2, 1.0, x) - y2) <= 1e-13 * np.linalg.norm(y2)
+    vals = (sum(w.size for w in m2.Wleaf.values()) + sum(w.size for w in m2.Xleaf.values())
+            + sum(e.size for e in m2.EW.values()) + sum(e.size for e in m2.EX.values())
+            + sum(s.size for s in m2.S))
+    assert compress.payload_bytes(c2) == 8 * vals
+
+
+def test_bisection_point_on_the_midpoint_goes_to_the_second_son():
+    # points at 0, 0.5, 1 on the x axis: mid = 0.5 exactly, "< mid" forms the first son
+    p = np.array([[0.0, 0, 0], [0.5, 0, 0], [1.0, 0, 0]])
+    ct = trees.build_cluster_tree(p, 1)
+    root = ct.root
+    s0, s1 = (ct.clusters[i] for i in root.sons)
+    assert (s0.size, s1.size) == (1, 2)
+    assert ct.perm[s0.start] == 0 and sorted(ct.perm[s1.start:s1.end].tolist()) == [1, 2]
