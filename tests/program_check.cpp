@@ -12,6 +12,8 @@
 //  * warp ranges in order and covering their launch;
 //  * within one launch, no vector entry both read as a multiplier or input and
 //    written as an output (the launch's warps run concurrently);
+//  * each launch's algorithmic byte count (the roofline numerator) equal to the
+//    count from its units' headers by the per-unit definition;
 //  * in the FP32 tier, every decoded value equal to the sum of the BF16 limbs
 //    the multi-RHS path keeps for its piece (the `limbs` header field);
 // then it replays the launches in program order in FP64 (Alg. 8: each code
@@ -390,6 +392,51 @@ struct Replay {
     }
   }
 
+  // Algorithmic bytes of a launch, counted from its units' inline headers by the
+  // per-unit definition the benchmark's roofline uses: gather and fan-out 20 per
+  // entry (index, value read, value write); a column-dot piece rows * B per column
+  // + 16 (header) + 16 per column (metadata, output) + 8 per column (scale, one-
+  // segment sets) + 8 * rows (input segment) + 16 (descriptor); a segment sum 8
+  // per partial (16 with weights) + 40; a row-chunk piece rows * B per column + 40
+  // (header) + 10 per column (8 for tiles: decode parameters, multiplier) + 16
+  // (descriptor), and at a chunk's last piece per row 20 (y) or 8 / 16 (plain /
+  // accumulated coefficients) + 8 with row scales.
+  int64_t alg_bytes(const Launch& L) const {
+    const auto& pay = P.pk.pay;
+    int64_t b = 0;
+    switch (L.kind) {
+      case Launch::GATHER:
+      case Launch::FANOUT:
+        return L.n * 20;
+      case Launch::GSUM:
+        for (int64_t i = L.off; i < L.off + L.n; ++i) {
+          const GsumOut& o = P.gouts[i];
+          b += (int64_t)(o.p1 - o.p0) * ((o.flags & 2) ? 16 : 8) + 40;
+        }
+        return b;
+      case Launch::CDOT:
+        for (int64_t it = L.off; it < L.off + L.n; ++it) {
+          CPieceHdr h;
+          std::memcpy(&h, &pay[(uint64_t)P.items[it].off16 * 16], sizeof h);
+          const int64_t R = h.nrows, nc = h.ncols, B = h.fb & 15;
+          b += R * B * nc + 16 + 16 * nc + ((h.flags & ITEM_FINAL) ? 8 * nc : 0) + 8 * R + 16;
+        }
+        return b;
+      case Launch::RGEMV:
+        for (int64_t i = L.off; i < L.off + L.n; ++i) {
+          PieceHdr h, nx{};
+          std::memcpy(&h, &pay[(uint64_t)P.pdesc[0][i].off16 * 16], sizeof h);
+          if (i + 1 < L.off + L.n) std::memcpy(&nx, &pay[(uint64_t)P.pdesc[0][i + 1].off16 * 16], sizeof nx);
+          const int64_t R = h.nrows, nc = h.ncols, B = h.fb & 15;
+          b += R * B * nc + 40 + ((h.flags & PH_TILE) ? 8 : 10) * nc + 16;
+          if (i + 1 == L.off + L.n || nx.row0 != h.row0)
+            b += R * (L.mode == MODE_Y ? 20 : (L.mode == MODE_VEC_ADD ? 16 : 8) + (L.use_rowscale ? 8 : 0));
+        }
+        return b;
+    }
+    return -1;
+  }
+
   // One product.  nwarps > 0: runs of row-chunk launches that the library fuses
   // into one persistent launch (SEQ_SHAPE) go through `dataflow`.
   void run(const std::vector<double>& x, int nwarps = 0, uint32_t seed = 1) {
@@ -572,6 +619,16 @@ int main(int argc, char** argv) {
   for (double t : yref) den += t * t;
   for (int cf = 0; cf < NSHAPES; ++cf) {
     Replay R(M, P, cf, alpha);
+    if (cf == 0) {   // the launches' algorithmic byte counts (shape independent)
+      int64_t tot = 0;
+      for (size_t li = 0; li < P.launches.size(); ++li) {
+        const int64_t a = R.alg_bytes(P.launches[li]);
+        CHECK(a == P.launches[li].bytes, "launch %zu: %ld algorithmic bytes counted, %ld recorded", li, (long)a,
+              (long)P.launches[li].bytes);
+        tot += a;
+      }
+      std::printf("algorithmic bytes %ld\n", (long)tot);
+    }
     R.run(x);
     const std::vector<double> first = R.y;
     R.run(x);
