@@ -625,6 +625,9 @@ int main(int argc, char** argv) {
         const int64_t a = R.alg_bytes(P.launches[li]);
         CHECK(a == P.launches[li].bytes, "launch %zu: %ld algorithmic bytes counted, %ld recorded", li, (long)a,
               (long)P.launches[li].bytes);
+        static const char* kinds[] = {"gather", "cdot", "gsum", "rgemv", "fanout"};
+        std::printf("launch %zu %s units %ld algorithmic bytes %ld\n", li, kinds[P.launches[li].kind],
+                    (long)P.launches[li].n, (long)a);
         tot += a;
       }
       std::printf("algorithmic bytes %ld\n", (long)tot);
