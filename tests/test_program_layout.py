@@ -135,6 +135,20 @@ def test_program_layout_headline_size(checker, case):
     assert len(errs) == 4 and max(errs) <= (1e-13 if codec == "none" else eps), errs
 
 
+def test_persistent_dependency_analysis_on_hand_built_programs(checker):
+    # seq_dependencies on small programs: which chunk a multiplier run reads, the
+    # versions it waits for, and the cases that must keep the launches separate
+    exe, tmp = checker
+    src = os.path.join(os.path.dirname(os.path.abspath(__file__)), "seqdeps_check.cpp")
+    inc = os.path.join(hbuild.HERE, "..", "include")
+    objs = [os.path.join(hbuild.OUT, f + ".o") for f in HOST]
+    sd = str(tmp / "seqdeps_check")
+    subprocess.run(["g++", "-std=c++17", "-O2", "-fopenmp", "-I", hbuild.CSRC, "-I", inc, src] + objs + ["-o", sd],
+                   check=True)
+    r = subprocess.run([sd], stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True, timeout=60)
+    assert r.returncode == 0 and r.stdout.strip() == "ok", r.stdout
+
+
 def test_h2_hodlr_basis_rank_above_the_kernel_limit(checker):
     # HODLR's top-level blocks need H2 bases of rank > 128: the program is not
     # built (hm_compress reports HM_ERR_CAPACITY)
