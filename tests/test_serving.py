@@ -152,6 +152,76 @@ def test_adjoint_support_counts_the_transposed_copy():
     assert sch.used == 3000 + 2 * stage
 
 
+def test_stats_by_hand():
+    # one matrix, one slot; products take 1 ms + 0.1 ms per RHS of fake time
+    ex = FakeExecutor({0: 8})
+    sch = Scheduler(ex, budget_bytes=10**9, nslots=1)
+    sch.add_matrix(0, 8, 1000)
+    x = lambda r: np.asfortranarray(np.ones((8, r)))
+    ex.now = 0.5                                      # the stream starts at 0.5 s
+    reqs = [Request(0, 0, x(2), 0.5), Request(1, 0, x(3), 0.5), Request(2, 0, x(1), 0.51)]
+    sch.run(reqs, clock=FakeClock(ex))
+    # requests 0 and 1 share one launch ending 1.5 ms later; request 2 runs alone, 0.51 s .. 0.5111 s
+    st = sch.stats()
+    assert (st["requests"], st["rhs"], st["launches"]) == (3, 6, 2)
+    assert st["mean_batch_rhs"] == 3.0
+    assert st["p50_ms"] == pytest.approx(1.5) and st["max_ms"] == pytest.approx(1.5)
+    assert st["p99_ms"] == pytest.approx(1.5)
+    assert st["seconds"] == pytest.approx(0.0111)
+    assert st["requests_per_s"] == pytest.approx(3 / 0.0111) and st["rhs_per_s"] == pytest.approx(6 / 0.0111)
+
+
+def test_oldest_waiting_request_goes_first():
+    # the slot is busy with matrix 2; meanwhile matrix 1 gets a request before matrix 0
+    ex = FakeExecutor({0: 8, 1: 8, 2: 8})
+    sch = Scheduler(ex, budget_bytes=10**9, nslots=1)
+    for mid in (0, 1, 2):
+        sch.add_matrix(mid, 8, 1000)
+    x = np.asfortranarray(np.ones((8, 1)))
+    sch.run([Request(0, 2, x, 0.0), Request(1, 1, x, 1e-4), Request(2, 0, x, 2e-4)], clock=FakeClock(ex))
+    assert [mid for (mid, _, _, _) in ex.log] == [2, 1, 0]
+
+
+def test_batch_fills_exactly_max_rhs():
+    ex = FakeExecutor({0: 8})
+    sch = Scheduler(ex, budget_bytes=10**9, nslots=1)
+    sch.add_matrix(0, 8, 1000)
+    x = lambda r: np.asfortranarray(np.ones((8, r)))
+    reqs = [Request(0, 0, x(1), 0.0), Request(1, 0, x(MAX_BATCH_RHS - 8), 1e-4), Request(2, 0, x(8), 1e-4),
+            Request(3, 0, x(1), 1e-4)]
+    sch.run(reqs, clock=FakeClock(ex))
+    assert [r for (_, _, _, r) in ex.log] == [1, MAX_BATCH_RHS, 1]
+
+
+def test_admission_at_the_exact_budget():
+    ex = FakeExecutor({0: 8})
+    need = 1000 + FakeExecutor.staging_bytes(8, MAX_BATCH_RHS)
+    sch = Scheduler(ex, need + 16 * 8 * MAX_BATCH_RHS, nslots=1)
+    sch.add_matrix(0, 8, 1000)
+    sch.submit(Request(0, 0, np.zeros((8, MAX_BATCH_RHS)), 0.0), 0.0)   # the largest request, exactly fitting
+    assert not sch.backlog and sch.queued_bytes == 16 * 8 * MAX_BATCH_RHS
+    sch.submit(Request(1, 0, np.zeros((8, 1)), 0.0), 0.0)                # one more RHS does not fit
+    assert [q.rid for q in sch.backlog] == [1]
+    # two requests that each fill the budget: the second leaves the backlog once the first is done
+    sch = Scheduler(ex, need + 16 * 8 * MAX_BATCH_RHS, nslots=1)
+    sch.add_matrix(0, 8, 1000)
+    x = np.asfortranarray(np.ones((8, MAX_BATCH_RHS)))
+    done = sch.run([Request(0, 0, x, 0.0), Request(1, 0, x, 0.0)], clock=FakeClock(ex))
+    assert [q.rid for q in done] == [0, 1]
+
+
+def test_poisson_request_ranges():
+    reqs = poisson_requests({0: 8, 1: 8}, rate=1000.0, count=2000, seed=3, rhs_max=4, adjoint_frac=0.5)
+    rs = sorted({q.r for q in reqs})
+    assert rs == [1, 2, 3, 4]
+    assert sorted({q.mid for q in reqs}) == [0, 1]
+    arr = np.array([q.arrival for q in reqs])
+    assert np.all(np.diff(arr) > 0) and 1.5 < arr[-1] < 2.5          # 2000 arrivals at 1000 per second
+    assert 800 < sum(q.adjoint for q in reqs) < 1200
+    assert not any(q.adjoint for q in poisson_requests({0: 8}, 1000.0, 200, seed=3))
+    assert all(q.adjoint for q in poisson_requests({0: 8}, 1000.0, 200, seed=3, adjoint_frac=1.0))
+
+
 @pytest.mark.gpu
 def test_gpu_serving_alone_equals_mix():
     torch = pytest.importorskip("torch")
