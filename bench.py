@@ -12,11 +12,14 @@ A step is one product y := M x + y (gather / decode / low-rank forward /
 row-chunk accumulation / scatter: every kernel of the path), timed with CUDA
 events on the launching stream.  The packed matrix (> 0.5 GB) is larger than
 the 129 MB L2, so no flush is needed between steps.  ``value`` is the
-algorithmic bytes one product moves (packed values, format words, descriptors,
-vector reads and writes) divided by the median step time, summed over ranks.
+method's algorithmic bytes per product (packed codes and their inline metadata,
+24 N for x and y, 16 per coefficient of the coefficient vectors) divided by
+the median step time, summed over ranks; the layout's intermediate traffic is
+reported beside it, not counted in it.
 
 ``--impl reference`` times the CPU oracle (Alg. 1 with Alg. 8 decompression)
-on a bounded random block sample of the same workload.
+on all host cores (one process per core) over a bounded random block sample of
+the same workload; ``cpu_baseline`` in the GPU line is the same measurement.
 """
 from __future__ import annotations
 
@@ -96,34 +99,97 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ CPU baseline (oracle)
-def cpu_baseline_child(budget_mb: float, passes: int, warmup: int) -> dict:
-    """Runs in a child process with one BLAS thread: the oracle as it stands."""
-    import numpy as np
-    from oracle import baseline
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else platform)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.strip().lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for ln in open("/proc/cpuinfo"):
+            if ln.lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def _cpu_worker(p, nw, budget_bytes, passes, warmup, barrier, q):
+    """One oracle process (one BLAS thread): builds its share of the block
+    sample, then times Alg. 1 + Alg. 8 passes over it in step with the others."""
+    for k in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[k] = "1"
+    try:
+        import synth
+        from oracle import baseline
+        h, ch, nblocks = baseline.sample_h(N_DEFAULT, HEADLINE[0], HEADLINE[1], budget_bytes, part=(p, nw))
+        ab = baseline.alg_bytes(ch)
+        xp = synth.rhs(N_DEFAULT)[:, 0][ch.h.ct.perm]
+        import numpy as np
+        yp = np.zeros(N_DEFAULT)
+        for _ in range(warmup):
+            baseline.run_pass(ch, xp, yp)
+        ts = []
+        for _ in range(passes):
+            barrier.wait(timeout=900)
+            t0 = time.perf_counter()
+            baseline.run_pass(ch, xp, yp)
+            ts.append(time.perf_counter() - t0)
+        q.put((p, ab, len(h.blocks), nblocks, ts, None))
+    except Exception as e:  # noqa: BLE001
+        try:
+            barrier.abort()
+        except Exception:  # noqa: BLE001
+            pass
+        q.put((p, 0, 0, 0, [], repr(e)[:300]))
+
+
+def cpu_baseline_parallel(budget_mb_per_worker: float, passes: int, warmup: int, workers: int = 0,
+                          timeout: float = 1200.0) -> dict:
+    """The oracle as it stands on all host cores: nw spawned processes (one per
+    core), each timing Alg. 1 + Alg. 8 over a disjoint share of one random
+    block sample of the headline workload; a pass is timed from a common
+    barrier to the slowest process's end.  value = the sample's algorithmic
+    bytes / the median pass time."""
+    import multiprocessing as mp
+    nproc = os.cpu_count() or 1
+    nw = workers or nproc
+    ctx = mp.get_context("spawn")   # fresh interpreters: no CUDA state is inherited
+    barrier = ctx.Barrier(nw)
+    q = ctx.Queue()
+    budget = budget_mb_per_worker * 1e6 * nw
+    procs = [ctx.Process(target=_cpu_worker, args=(p, nw, budget, passes, warmup, barrier, q), daemon=True)
+             for p in range(nw)]
     t0 = time.perf_counter()
-    h, ch, nblocks = baseline.sample_h(N_DEFAULT, HEADLINE[0], HEADLINE[1], budget_mb * 1e6)
-    build_s = time.perf_counter() - t0
-    ab = baseline.alg_bytes(ch)
-    ts = baseline.time_passes(ch, passes, warmup)
-    med = float(np.median(ts))
-    return {"value": ab / med / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
-            "sample": (f"{len(h.blocks)} of {nblocks} leaf blocks (<= 2^20 entries, random, seed 3) of the "
-                       f"N={N_DEFAULT} sphere H-matrix at eps=1e-6, AFLP VALR; Alg. 1 + Alg. 8 decode, "
-                       f"{passes} passes, {ab / 1e6:.2f} MB algorithmic per pass"),
-            "pass_s": ts.tolist(), "build_s": build_s, "alg_bytes": ab}
-
-
-def run_cpu_child(budget_mb, passes, warmup, timeout=600):
-    env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1",
-               PYTHONPATH=ROOT)
-    code = ("import json,bench;print('CPUJSON'+json.dumps(bench.cpu_baseline_child(%r,%d,%d)))"
-            % (budget_mb, passes, warmup))
-    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True,
-                       timeout=timeout)
-    for ln in r.stdout.splitlines():
-        if ln.startswith("CPUJSON"):
-            return json.loads(ln[7:])
-    raise RuntimeError("cpu baseline failed: " + r.stderr[-2000:])
+    for pr in procs:
+        pr.start()
+    res = []
+    try:
+        for _ in range(nw):
+            res.append(q.get(timeout=timeout))
+    finally:
+        for pr in procs:
+            pr.join(timeout=10)
+            if pr.is_alive():
+                pr.terminate()
+    errs = [r[5] for r in res if r[5]]
+    if errs:
+        raise RuntimeError("oracle worker failed: " + errs[0])
+    ab = sum(r[1] for r in res)
+    nb = sum(r[2] for r in res)
+    per_pass = [max(r[4][k] for r in res) for k in range(passes)]
+    med = statistics.median(per_pass)
+    return {"value": ab / med / 1e9, "unit": "GB/s", "cores": nw, "nproc": nproc, "cpu_model": cpu_model(),
+            "kind": "oracle",
+            "sample": (f"{nb} of {res[0][3]} leaf blocks (<= 2^20 entries, random, seed 3) of the N={N_DEFAULT} "
+                       f"sphere H-matrix at eps=1e-6, AFLP VALR, split over {nw} processes (one per core, one "
+                       f"BLAS thread each); Alg. 1 + Alg. 8 decode in FP64, {passes} passes from a common "
+                       f"barrier, {ab / 1e6:.2f} MB algorithmic per pass"),
+            "pass_s_median": med, "wall_s": round(time.perf_counter() - t0, 1), "alg_bytes": ab}
 
 
 # ------------------------------------------------------------------ GPU arm
@@ -259,14 +325,15 @@ def gpu_arm(args, rank, world):
                 M.autotune(5, stream.cuda_stream)
             M.graph(not args.no_graph)
             info = M.info()
-            ab = M.alg_bytes()
+            ab = info["bytes_alg"]          # the method's bytes (codes, their metadata, vectors)
+            lb = M.alg_bytes()              # what the launches move, intermediates included
             if not clocks_started:
                 clocks.start()
                 clocks_started = True
             per, total = time_variant(torch, M, x, y, args.steps, args.warmup, stream, world)
             med = statistics.median(per)
             r = {"ms_p50": med, "ms_p99": pct(per, 0.99), "ms_mean": total / args.steps,
-                 "gbs": ab / (med * 1e-3) / 1e9, "matvecs_per_s": 1e3 / med, "alg_bytes": ab,
+                 "gbs": ab / (med * 1e-3) / 1e9, "matvecs_per_s": 1e3 / med, "alg_bytes": ab, "layout_bytes": lb,
                  "payload_bytes": info["bytes_payload"], "value_bytes": info["bytes_values"],
                  "fp64_bytes": info["bytes_fp64"], "tier": info["tier"], "launches": info["nlaunches"],
                  "shapes": [s for s in M.launch_shapes() if s >= 0]}
@@ -320,7 +387,7 @@ def gpu_arm(args, rank, world):
                 M.autotune(5, stream.cuda_stream)
             M.graph(not args.no_graph)
             info = M.info()
-            ab = M.alg_bytes()
+            ab = info["bytes_alg"]
             per, total = time_variant(torch, M, x, y, args.steps, args.warmup, stream, world)
             med = statistics.median(per)
             fmt_results[(fmt, codec)] = {"ms_p50": med, "ms_p99": pct(per, 0.99), "gbs": ab / (med * 1e-3) / 1e9,
@@ -343,7 +410,7 @@ def gpu_arm(args, rank, world):
         ym = torch.zeros_like(xm)
         reps = max(5, min(50, args.steps))
         per, _ = time_variant(torch, M, xm, ym, reps, 3, stream, world)
-        ab = M.alg_bytes()
+        ab = info["bytes_alg"]
         single = {"ms_p50": round(statistics.median(per), 4), "gbs": round(ab / (statistics.median(per) * 1e-3) / 1e9, 1),
                   "hbm_frac": round(ab / (statistics.median(per) * 1e-3) / 1e9 / hbm_peak, 3)}
         matern = {"workload": f"matern-1.5 l=0.1 N={nm} uniform unit cube, leaf=64 eta=2 H eps=1e-6 AFLP VALR",
@@ -374,7 +441,7 @@ def gpu_arm(args, rank, world):
                 M.autotune(3, stream.cuda_stream)
             M.graph(not args.no_graph)
             info = M.info()
-            ab = M.alg_bytes()
+            ab = info["bytes_alg"]
             per, _ = time_variant(torch, M, xa, ya, max(20, min(args.steps, 200)), 3, stream, world)
             med = statistics.median(per)
             adm_legs[adm] = {"ms_p50": round(med, 4), "gbs": round(ab / (med * 1e-3) / 1e9, 1),
@@ -401,12 +468,17 @@ def gpu_arm(args, rank, world):
     by_eps = {}
     for (eps, codec), r in results.items():
         base = results.get((eps, "none"))
+        # the uncompressed FP64 product at the HBM roof: its bytes at the measured peak
+        roof_ms = base["alg_bytes"] / (hbm_peak * 1e9) * 1e3 if base else None
         by_eps.setdefault(f"{eps:g}", {})[codec] = {
             "gbs": round(r["gbs"], 1), "matvecs_per_s": round(r["matvecs_per_s"], 1),
             "ms_p50": round(r["ms_p50"], 4), "ms_p99": round(r["ms_p99"], 4),
+            "alg_mb": round(r["alg_bytes"] / 1e6, 1),
+            "intermediate_mb": round((r["layout_bytes"] - r["alg_bytes"]) / 1e6, 1),
             "payload_mb": round(r["payload_bytes"] / 1e6, 1), "fp64_mb": round(r["fp64_bytes"] / 1e6, 1),
             "compression_ratio": round(r["fp64_bytes"] / max(r["value_bytes"], 1), 3),
             "speedup_vs_fp64": round(base["ms_p50"] / r["ms_p50"], 3) if base else None,
+            "speedup_vs_fp64_at_roof": round(roof_ms / r["ms_p50"], 3) if base else None,
             "hbm_frac": round(r["gbs"] / hbm_peak, 3), "tier": "ff" if r["tier"] else "f32",
             "launch_shapes": r["shapes"]}
     line = {
@@ -414,13 +486,18 @@ def gpu_arm(args, rank, world):
         "warmup": args.warmup, "ms_per_step": round(med, 5), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32/ff decode of AFLP codes, f64 y",
         "data": "synthetic (seeded jittered Fibonacci sphere, x ~ U(-1,1))",
-        "config": {"workload": workload_name(n), "n": n, "eps": HEADLINE[0], "codec": "aflp-valr",
-                   "format": "H", "nrhs": 1, "parallelism": "replicas" if world > 1 else "single-gpu",
-                   "cuda_graph": not args.no_graph,
-                   "l2": "inputs larger than L2 (packed matrix %.0f MB vs 129 MB L2), no flush"
-                         % (headline["payload_bytes"] / 1e6)},
+        "config": config_of(n, world),
         "matvecs_per_s": round(1e3 / med * world, 1), "ms_p50": round(med, 5),
         "ms_p99": round(headline["ms_p99"], 5),
+        "hbm_frac": round(value / world / hbm_peak, 4),
+        "bytes": {"alg_per_step": ab, "intermediate_per_step": headline["layout_bytes"] - ab,
+                  "payload": headline["payload_bytes"], "codes": headline["value_bytes"],
+                  "definition": "value = alg_per_step / median step time: packed codes + their inline metadata "
+                                "(unit headers, per-column decode parameters and scales) + 24 N (x read, y read "
+                                "and written) + 16 per coefficient (t_b written once and read once); "
+                                "intermediate_per_step = the layout's extra traffic (copy descriptors, per-piece "
+                                "input segments and multiplier runs, segment partials, fan-out slots), counted in "
+                                "the per-kernel figures only"},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": hbm_peak,
                      "unit": "GB/s", "frac": round(achieved / hbm_peak, 4), "traffic": profiled_traffic(dom, n),
                      "alg_bytes_per_launch": int(per_launch_bytes),
@@ -451,38 +528,38 @@ def gpu_arm(args, rank, world):
         line["hodlr_blr"] = adm_legs
     if not args.no_cpu:
         try:
-            line["cpu_baseline"] = run_cpu_child(args.cpu_budget_mb, args.cpu_passes, 1)
-            line["cpu_baseline"].pop("pass_s", None)
+            line["cpu_baseline"] = cpu_baseline_parallel(args.cpu_budget_mb, args.cpu_passes, 1)
         except Exception as e:  # noqa: BLE001
-            line["cpu_baseline"] = {"value": None, "unit": "GB/s", "cores": 1, "kind": "oracle",
+            line["cpu_baseline"] = {"value": None, "unit": "GB/s", "cores": os.cpu_count(), "kind": "oracle",
                                     "sample": f"failed: {e}"[:300]}
     return line
 
 
 # ------------------------------------------------------------------ reference arm
+def config_of(n, world):
+    """The workload's config (both arms report the same one)."""
+    return {"workload": workload_name(n), "n": n, "eps": HEADLINE[0], "codec": "aflp-valr", "format": "H",
+            "nrhs": 1, "parallelism": "replicas" if world > 1 else "single-gpu",
+            "l2": "inputs larger than L2 (packed matrix ~0.96 GB vs 129 MB L2), no flush"}
+
+
 def reference_arm(args, rank, world):
+    """The oracle (the paper's Alg. 1 with Alg. 8 decode, FP64) on all host
+    cores; each step is one pass over a bounded block sample of the workload."""
     if rank != 0:
         return None
-    import numpy as np
-    from oracle import baseline
     # size the per-step sample so that the whole run stays within a few minutes
-    budget_mb = max(0.5, min(20.0, 150.0 / max(args.steps + args.warmup, 1)))
-    t0 = time.perf_counter()
-    h, ch, nblocks = baseline.sample_h(N_DEFAULT, HEADLINE[0], HEADLINE[1], budget_mb * 1e6)
-    ab = baseline.alg_bytes(ch)
-    ts = baseline.time_passes(ch, args.steps, args.warmup)
-    med = float(np.median(ts))
-    value = ab / med / 1e9
-    sample = (f"{len(h.blocks)} of {nblocks} leaf blocks (<= 2^20 entries, random) of the N={N_DEFAULT} sphere "
-              f"H-matrix, eps=1e-6 AFLP VALR, one pass per step")
+    budget_mb = max(0.5, min(8.0, 200.0 / max(args.steps + args.warmup, 1)))
+    cb = cpu_baseline_parallel(budget_mb, args.steps, args.warmup)
+    value = cb["value"]
     return {"impl": "reference", "metric": METRIC, "value": round(value, 5), "unit": "GB/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(med * 1e3, 3),
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(cb["pass_s_median"] * 1e3, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic (seeded)", "config": {"workload": workload_name(N_DEFAULT), "n": N_DEFAULT,
-                                                     "eps": HEADLINE[0], "codec": "aflp-valr", "format": "H"},
-            "cpu_baseline": {"value": round(value, 5), "unit": "GB/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "data": "synthetic (seeded jittered Fibonacci sphere, x ~ U(-1,1))", "config": config_of(N_DEFAULT, world),
+            "cpu_baseline": {"value": round(value, 5), "unit": "GB/s", "cores": cb["cores"], "nproc": cb["nproc"],
+                             "cpu_model": cb["cpu_model"], "kind": "oracle", "sample": cb["sample"]},
             "e2e": {"value": round(value, 5), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-            "build_s": round(time.perf_counter() - t0 - float(np.sum(ts)), 2)}
+            "wall_s": cb["wall_s"]}
 
 
 def main():
@@ -503,8 +580,8 @@ def main():
                     help="also time HODLR and BLR H-matrices of the sphere problem at this N (opt-in)")
     ap.add_argument("--matern", type=int, default=0,
                     help="also time multi-RHS products on the Matern cube with this many points (slow to build)")
-    ap.add_argument("--cpu-budget-mb", type=float, default=20.0)
-    ap.add_argument("--cpu-passes", type=int, default=30)
+    ap.add_argument("--cpu-budget-mb", type=float, default=8.0, help="oracle sample per host core (MB of FP64)")
+    ap.add_argument("--cpu-passes", type=int, default=10)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

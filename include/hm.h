@@ -181,6 +181,12 @@ typedef struct {
   int64_t bytes_dense_fp64;   /* FP64 bytes of dense leaves */
   int64_t nlaunches;        /* kernels launched by one hm_matvec with nrhs = 1 */
   int32_t tier;             /* 0: FP32 arithmetic, 1: float-float (eps <= 2^-22 or NONE) */
+  int64_t nunits;           /* packed units (column-dot pieces, then row-chunk pieces) */
+  int64_t bytes_inline_meta; /* per-unit headers and per-column decode parameters in the payload */
+  int64_t bytes_alg;        /* algorithmic bytes of one product per right-hand side: packed codes
+                               (bytes_values) + bytes_inline_meta + 24 n (x read, y read and
+                               written, FP64) + 16 per coefficient of the coefficient vectors
+                               (t_b / s / t, written once and read once) */
 } hm_info_t;
 
 /* hm_info -- sizes and counts of m.  Errors: HM_ERR_ARG. */
@@ -274,9 +280,42 @@ typedef struct { double ms; int64_t launches; int64_t bytes; } hm_kernel_stat;
 hm_status hm_profile(hm_matrix* m, int32_t enable);
 hm_status hm_profile_read(hm_matrix* m, hm_kernel_stat* out, int32_t nout);
 
-/* hm_alg_bytes -- algorithmic bytes one hm_matvec moves per right-hand side
- * (the sum over its launches of the bytes hm_profile_read reports). */
+/* hm_alg_bytes -- bytes the launches of one hm_matvec move per right-hand side
+ * (the sum over its launches of the bytes hm_profile_read reports): the
+ * method's bytes (hm_info_t.bytes_alg) plus the traffic of this layout's
+ * intermediate steps (copy descriptors, per-piece input segments and multiplier
+ * runs, segment partials, fan-out slots). */
 hm_status hm_alg_bytes(const hm_matrix* m, int64_t* bytes);
+
+/*
+ * hm_decompress_debug -- decode packed values of m's resident payload on the
+ * GPU with the decoders the product kernels run (Sec. 4.1, Alg. 8), for the
+ * bit-exact check of decompression against the CPU oracle.
+ *   tier : 0 = the FP32-tier decoders (column dots, row chunks and the
+ *          multi-RHS kernels of matrices compressed at eps > 2^-22): head = the
+ *          stored value rounded to nearest FP32 (ties to even), tail = 0;
+ *          1 = the float-float-tier decoders (eps <= 2^-22 and HM_CODEC_NONE):
+ *          head + tail = the stored value (exact for every AFLP code with
+ *          m' <= 47 and f <= 46 and every FPX code up to e11 m44; a raw FP64
+ *          value keeps its low 29 mantissa bits rounded to 24).
+ *          Either tier may be asked for on any matrix.
+ *   u0, u1 : units [u0, u1) (column-dot pieces 0 .. nitems-1, then row-chunk
+ *          pieces; hm_info_t.nunits in all); u1 is clamped to nunits.
+ *   Values come in payload order: unit by unit, column by column, row by row.
+ *   AFLP values are +-(s - 1) with s = 2^f (1 + mant 2^-m'): the array's vmin
+ *   is not applied (the kernels fold it into the coefficient and tile scales).
+ *   head, tail : host float[cap]; code : host uint64[cap], each value's code
+ *   (8 B bits, little-endian bytes of the payload); fmt : host uint16[cap], its
+ *   format B | fmt << 4 | e << 6 | m << 10 (fmt 0 FPX e8, 1 FPX e11, 2 AFLP,
+ *   3 raw FP64; m = m' for AFLP).  count : receives the number of values.
+ *   With head == NULL only *count is set (no GPU work).
+ * Allocates device memory for the call, synchronises `stream`.
+ * Errors: HM_ERR_ARG (null count, bad tier or range, cap < count),
+ * HM_ERR_STATE (not compressed), HM_ERR_OOM, HM_ERR_CUDA; an unknown decode
+ * class latches HM_ERR_DEVICE (hm_sync_status).
+ */
+hm_status hm_decompress_debug(hm_matrix* m, int32_t tier, int64_t u0, int64_t u1, int64_t cap, float* head,
+                              float* tail, uint64_t* code, uint16_t* fmt, int64_t* count, void* stream);
 
 /*
  * hm_matvec_host_noalloc -- hm_matvec_host for callers that cannot let the
@@ -292,11 +331,18 @@ hm_status hm_alg_bytes(const hm_matrix* m, int64_t* bytes);
  *   x, y : host FP64 (n x nrhs, ld n, column-major); y is overwritten with
  *          alpha*M*x + beta*y.  Synchronises `stream` before returning.
  * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  All calls share the one array: calls whose GPU
+ * (cudaGetSymbolAddress) with that device current and keeps it for the life of
+ * the process; make that first call before any stream capture.  The kept
+ * address belongs to the device's primary context: after cudaDeviceReset (a new
+ * primary context) it is stale, so do not call this entry point on a device
+ * that was reset.  With lazy module loading (the CUDA default) the array's
+ * memory is committed when the library's device code first loads on the
+ * device, by the CUDA runtime, not by a cudaMalloc of this call.  All calls
+ * share the one array, which keeps the last call's contents: calls whose GPU
  * work overlaps (other host threads, other streams) race and must be
- * serialised by the caller.  x and y are copied in whole on every call, so no
- * earlier contents are read and nothing needs clearing.
+ * serialised by the caller.  x is copied in whole on every call, and y too when
+ * beta != 0; with beta == 0 the product writes every entry of y without
+ * reading it, so no earlier contents are read and nothing needs clearing.
  * Errors: HM_ERR_ARG, HM_ERR_STATE (not compressed), HM_ERR_CAPACITY if
  * n * nrhs > HM_NOALLOC_MAX_ENTRIES, HM_ERR_CUDA.
  */

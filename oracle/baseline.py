@@ -25,8 +25,12 @@ from .trees import build_block_tree, build_cluster_tree
 
 
 def sample_h(n: int, eps: float, codec: str, budget_bytes: float, seed: int = 3,
-             leaf: int = 64, eta: float = 2.0):
-    """Oracle-built compressed H-matrix restricted to a random block sample."""
+             leaf: int = 64, eta: float = 2.0, part: tuple[int, int] = (0, 1)):
+    """Oracle-built compressed H-matrix restricted to a random block sample.
+
+    part = (p, P): only every P-th block of the sample, starting at the p-th
+    (in block-tree order), so that P processes each build and time a disjoint
+    share of the same sample."""
     pts = synth.sphere_points(n)
     param = kernels.default_param("laplace", n)
     ct = build_cluster_tree(pts, leaf)
@@ -45,6 +49,7 @@ def sample_h(n: int, eps: float, codec: str, budget_bytes: float, seed: int = 3,
         if tot >= budget_bytes:
             break
     chosen.sort()
+    chosen = chosen[part[0]::part[1]]
     sub = [blocks[i] for i in chosen]
     data = []
     for b in sub:

@@ -189,6 +189,18 @@ struct GsumOut {
   int32_t pad;
 };
 
+// Decoder check (hm_decompress_debug): 8 consecutive codes of one packed
+// column at payload byte offset `off` (8-byte aligned), decode class
+// fb = fmt << 4 | B and em = e | m << 8 packed as fb | em << 16; values
+// out .. out + nr - 1 of the result take the first nr of them.
+struct DbgTask {
+  uint64_t off;
+  uint32_t fbem;
+  int32_t out;
+  int32_t nr;
+  int32_t pad;
+};
+
 enum { MODE_Y = 0, MODE_VEC = 1, MODE_VEC_ADD = 2 };
 enum { TIER_F32 = 0, TIER_FF = 1 };
 

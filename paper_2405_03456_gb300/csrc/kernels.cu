@@ -918,6 +918,68 @@ __global__ void k_decode(const uint8_t* __restrict__ p, int64_t n, int B, int fm
   out[i] = v;
 }
 
+// ---------------------------------------------------------------- decoder check over the resident payload
+// One task: 8 consecutive codes of one packed column (a lane's share in the
+// product kernels), decoded by the same template instances the product kernels
+// run -- decode8p (FP32 tier: column dots, row chunks, multi-RHS) or
+// decode8s<TIER_FF> (float-float tier) -- from a per-thread shared-memory copy
+// of the 8 B bytes, exactly as the kernels read them from their stages.
+template <int TIER>
+__global__ void k_decode_debug(const DbgTask* __restrict__ tasks, int64_t ntask, const uint8_t* __restrict__ pay,
+                               float2* __restrict__ out, int* err) {
+  __shared__ __align__(16) uint64_t buf[256 * 8];
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= ntask) return;
+  const DbgTask T = tasks[t];
+  const int fb = (int)(T.fbem & 0xffu), B = fb & 15;
+  const int e = (int)((T.fbem >> 16) & 0xffu), m = (int)(T.fbem >> 24);
+  const uint64_t* src = reinterpret_cast<const uint64_t*>(pay + T.off);
+  uint64_t* dst = buf + threadIdx.x * 8;
+  for (int i = 0; i < B && i < 8; ++i) dst[i] = src[i];
+  const uint32_t a = smem_u32(dst);
+  float h[8], l[8];
+#pragma unroll
+  for (int u = 0; u < 8; ++u) {
+    h[u] = 0.f;
+    l[u] = 0.f;
+  }
+  bool ok = true;
+  if constexpr (TIER == TIER_F32) {
+    float2 h2[4];
+    switch (fb) {
+#define HM_DD(FF_, BB_) \
+  case ((FF_) << 4) | (BB_): decode8p<FF_, BB_>(a, e, m, h2); break;
+      HM_FORMATS(HM_DD)
+#undef HM_DD
+      default:
+        ok = false;
+    }
+    if (ok) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        h[2 * k] = h2[k].x;
+        h[2 * k + 1] = h2[k].y;
+      }
+    }
+  } else {
+    switch (fb) {
+#define HM_DD(FF_, BB_) \
+  case ((FF_) << 4) | (BB_): decode8s<TIER_FF, FF_, BB_>(a, e, m, h, l); break;
+      HM_FORMATS(HM_DD)
+#undef HM_DD
+      default:
+        ok = false;
+    }
+  }
+  if (!ok) {
+    latch_error(err, 1);
+    return;
+  }
+#pragma unroll
+  for (int u = 0; u < 8; ++u)
+    if (u < T.nr) out[T.out + u] = make_float2(h[u], l[u]);
+}
+
 // ---------------------------------------------------------------- launchers
 // Launch with programmatic stream serialization (see pdl_trigger / pdl_wait).
 template <typename... KArgs, typename... Args>
@@ -1117,6 +1179,17 @@ cudaError_t launch_decode(const uint8_t* p, int64_t n, int B, int fmt, int e, in
                           double* out, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   k_decode<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(p, n, B, fmt, e, m, vmin, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_decode_debug(int tier, const DbgTask* tasks, int64_t ntask, const uint8_t* pay, float2* out,
+                                int* err, cudaStream_t st) {
+  if (ntask <= 0) return cudaSuccess;
+  const unsigned grid = (unsigned)((ntask + 255) / 256);
+  if (tier == TIER_F32)
+    k_decode_debug<TIER_F32><<<grid, 256, 0, st>>>(tasks, ntask, pay, out, err);
+  else
+    k_decode_debug<TIER_FF><<<grid, 256, 0, st>>>(tasks, ntask, pay, out, err);
   return cudaGetLastError();
 }
 

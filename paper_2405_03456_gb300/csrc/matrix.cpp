@@ -46,6 +46,8 @@ cudaError_t launch_rgemv_mr(int mode, const PieceCopy* pieces, const int32_t* wb
                             const Split* splits, int* err, cudaStream_t st);
 cudaError_t launch_decode(const uint8_t* p, int64_t n, int B, int fmt, int e, int m, double vmin,
                           double* out, cudaStream_t st);
+cudaError_t launch_decode_debug(int tier, const DbgTask* tasks, int64_t ntask, const uint8_t* pay, float2* out,
+                                int* err, cudaStream_t st);
 }  // namespace hm
 
 using namespace hm;
@@ -294,6 +296,57 @@ hm_status upload(hm_matrix* M) {
     }
   }
   return HM_OK;
+}
+
+}  // namespace
+
+namespace {
+
+// One packed column of a unit of the payload: byte offset of its first code,
+// rows, decode class fb = fmt << 4 | B and em = e | m << 8.
+struct PackedCol {
+  uint64_t off;
+  int32_t rows;
+  uint16_t fb, em;
+};
+
+// The packed columns of units [u0, u1) in payload order: column-dot pieces
+// (P.items) first, then row-chunk pieces (in program order), each read from its
+// inline header exactly as the kernels read it.
+void packed_columns(const Program& P, int64_t u0, int64_t u1, std::vector<PackedCol>& cols) {
+  const uint8_t* pay = P.pk.pay.data();
+  const int64_t ni = (int64_t)P.items.size();
+  for (int64_t u = u0; u < u1; ++u) {
+    if (u < ni) {
+      const uint64_t off = (uint64_t)P.items[u].off16 * 16u;
+      CPieceHdr h;
+      std::memcpy(&h, pay + off, sizeof h);
+      const int B = h.fb & 15, nc = h.ncols, R = h.nrows;
+      const bool fin = (h.flags & ITEM_FINAL) != 0;
+      const uint64_t cm = off + sizeof(CPieceHdr);
+      const uint64_t cb = cm + (uint64_t)(fin ? 16 : 8) * nc;
+      const uint64_t stride = (uint64_t)((R + 15) & ~15) * B;
+      for (int j = 0; j < nc; ++j) {
+        CColMeta c;
+        std::memcpy(&c, pay + cm + 8u * j, sizeof c);
+        cols.push_back(PackedCol{cb + j * stride, R, h.fb, c.em});
+      }
+    } else {
+      const uint64_t off = (uint64_t)P.pdesc[0][u - ni].off16 * 16u;
+      PieceHdr h;
+      std::memcpy(&h, pay + off, sizeof h);
+      const int B = h.fb & 15, nc = h.ncols, R = h.nrows;
+      const bool tile = (h.flags & PH_TILE) != 0;
+      const uint64_t cm = off + sizeof(PieceHdr);
+      const uint64_t cb = cm + (tile ? 0 : (uint64_t)((2 * nc + 7) & ~7));
+      const uint64_t stride = (uint64_t)((R * B + 7) & ~7);
+      for (int j = 0; j < nc; ++j) {
+        uint16_t em = h.em;
+        if (!tile) std::memcpy(&em, pay + cm + 2u * j, 2);
+        cols.push_back(PackedCol{cb + j * stride, R, h.fb, em});
+      }
+    }
+  }
 }
 
 }  // namespace
@@ -783,6 +836,9 @@ hm_status hm_info(const hm_matrix* M, hm_info_t* o) {
     o->bytes_workspace += ((P.nvec + SEG_ROWS) + P.npartial) * RP * 4 + P.nfix_mr * CHUNK_ROWS * RP * 8;
   o->nlaunches = (int64_t)P.launches.size();
   o->tier = P.tier;
+  o->nunits = (int64_t)P.items.size() + P.npieces;
+  o->bytes_inline_meta = P.pk.meta_bytes;
+  o->bytes_alg = M->compressed ? P.pk.value_bytes + P.pk.meta_bytes + 24 * H.n + 16 * (P.fan_base - H.n) : 0;
   return HM_OK;
 }
 
@@ -835,6 +891,72 @@ hm_status hm_codec_decode(const uint8_t* packed, int64_t n, const hm_codec_heade
   if (h->fmt == FMT_AFLP && (h->e < 1 || h->m < 1 || 1 + h->e + h->m != 8 * h->B)) return HM_ERR_ARG;
   cudaError_t e = launch_decode(packed, n, h->B, h->fmt, h->e, h->m, h->vmin, out, (cudaStream_t)stream);
   return e == cudaSuccess ? HM_OK : HM_ERR_CUDA;
+}
+
+hm_status hm_decompress_debug(hm_matrix* M, int32_t tier, int64_t u0, int64_t u1, int64_t cap, float* head,
+                              float* tail, uint64_t* code, uint16_t* fmt, int64_t* count, void* stream) {
+  if (!M || !count || (tier != TIER_F32 && tier != TIER_FF) || u0 < 0 || u1 < u0) return HM_ERR_ARG;
+  if (!M->compressed) return HM_ERR_STATE;
+  const Program& P = M->prog;
+  const int64_t nunits = (int64_t)P.items.size() + P.npieces;
+  u1 = std::min(u1, nunits);
+  u0 = std::min(u0, u1);
+  std::vector<PackedCol> cols;
+  try {
+    packed_columns(P, u0, u1, cols);
+  } catch (const std::bad_alloc&) {
+    return HM_ERR_OOM;
+  }
+  int64_t nv = 0;
+  for (const PackedCol& c : cols) nv += c.rows;
+  *count = nv;
+  if (!head) return HM_OK;
+  if (!tail || !code || !fmt || cap < nv) return HM_ERR_ARG;
+  if (nv == 0) return HM_OK;
+  std::vector<DbgTask> tasks;
+  const uint8_t* pay = P.pk.pay.data();
+  int64_t v = 0;
+  for (const PackedCol& c : cols) {
+    const int B = c.fb & 15;
+    const uint16_t f16 = (uint16_t)(B | (((c.fb >> 4) & 3) << 4) | ((c.em & 0xf) << 6) | (((c.em >> 8) & 0x3f) << 10));
+    for (int r = 0; r < c.rows; ++r) {
+      uint64_t cv = 0;
+      for (int b = 0; b < B; ++b) cv |= (uint64_t)pay[c.off + (uint64_t)r * B + b] << (8 * b);
+      code[v + r] = cv;
+      fmt[v + r] = f16;
+    }
+    for (int q = 0; q * RPL < c.rows; ++q)
+      tasks.push_back(DbgTask{c.off + (uint64_t)q * RPL * B, (uint32_t)c.fb | ((uint32_t)c.em << 16),
+                              (int32_t)(v + q * RPL), std::min(RPL, c.rows - q * RPL), 0});
+    v += c.rows;
+  }
+  if (nv > (int64_t)INT32_MAX) return HM_ERR_CAPACITY;
+  cudaStream_t st = (cudaStream_t)stream;
+  DbgTask* dt = nullptr;
+  float2* dout = nullptr;
+  hm_status out = HM_OK;
+  if (cudaMalloc(&dt, tasks.size() * sizeof(DbgTask)) != cudaSuccess ||
+      cudaMalloc(&dout, (size_t)nv * sizeof(float2)) != cudaSuccess) {
+    out = HM_ERR_OOM;
+  } else if (cudaMemcpyAsync(dt, tasks.data(), tasks.size() * sizeof(DbgTask), cudaMemcpyHostToDevice, st) !=
+                 cudaSuccess ||
+             launch_decode_debug(tier, dt, (int64_t)tasks.size(), M->d_pay.p, dout, M->d_err, st) != cudaSuccess) {
+    out = HM_ERR_CUDA;
+  } else {
+    std::vector<float2> hv((size_t)nv);
+    if (cudaMemcpyAsync(hv.data(), dout, (size_t)nv * sizeof(float2), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+      out = HM_ERR_CUDA;
+    } else {
+      for (int64_t i = 0; i < nv; ++i) {
+        head[i] = hv[i].x;
+        tail[i] = hv[i].y;
+      }
+    }
+  }
+  if (dt) cudaFree(dt);
+  if (dout) cudaFree(dout);
+  return out;
 }
 
 }  // extern "C"

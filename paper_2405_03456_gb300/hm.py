@@ -25,7 +25,8 @@ KERNELS = {"laplace": HM_KERNEL_LAPLACE, "matern": HM_KERNEL_MATERN15}
 DECLARED = ["hm_build", "hm_compress", "hm_matvec", "hm_matvec_host", "hm_free", "hm_info",
             "hm_status_str", "hm_sync_status", "hm_structure", "hm_codec_encode", "hm_codec_decode",
             "hm_profile", "hm_profile_read", "hm_alg_bytes", "hm_matvec_host_noalloc", "hm_graph",
-            "hm_autotune", "hm_launch_shapes", "hm_set_launch_shapes", "hm_persistent", "hm_matvec_adjoint"]
+            "hm_autotune", "hm_launch_shapes", "hm_set_launch_shapes", "hm_persistent", "hm_matvec_adjoint",
+            "hm_decompress_debug"]
 NSHAPES = 3
 HM_NOALLOC_MAX_ENTRIES = 1 << 20
 KERNEL_KINDS = ["gather", "cdot", "gsum", "rgemv", "fanout"]
@@ -44,7 +45,8 @@ class hm_info_t(C.Structure):
                 ("depth", C.c_int32), ("max_rank", C.c_int32), ("bytes_fp64", C.c_int64),
                 ("bytes_payload", C.c_int64), ("bytes_values", C.c_int64), ("bytes_meta", C.c_int64),
                 ("bytes_workspace", C.c_int64), ("bytes_lowrank_fp64", C.c_int64),
-                ("bytes_dense_fp64", C.c_int64), ("nlaunches", C.c_int64), ("tier", C.c_int32)]
+                ("bytes_dense_fp64", C.c_int64), ("nlaunches", C.c_int64), ("tier", C.c_int32),
+                ("nunits", C.c_int64), ("bytes_inline_meta", C.c_int64), ("bytes_alg", C.c_int64)]
 
 
 class hm_codec_header(C.Structure):
@@ -99,6 +101,7 @@ def load(path: str | None = None) -> C.CDLL:
         "hm_autotune": ([vp, i32, vp], i32),
         "hm_launch_shapes": ([vp, vp, i32, C.POINTER(i32)], i32),
         "hm_set_launch_shapes": ([vp, i32], i32),
+        "hm_decompress_debug": ([vp, i32, i64, i64, i64, vp, vp, vp, vp, C.POINTER(i64), vp], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -244,6 +247,24 @@ def hm_alg_bytes(h: int) -> int:
     b = C.c_int64()
     check(load().hm_alg_bytes(h, C.byref(b)), "hm_alg_bytes")
     return b.value
+
+
+def hm_decompress_debug(h: int, tier: int, u0: int = 0, u1: int = 1 << 62, stream: int = 0) -> dict:
+    """Decode units [u0, u1) of the resident payload with the product kernels'
+    decoders of `tier` (0 FP32, 1 float-float): per value its code, format word,
+    and the GPU's head and tail (numpy arrays, payload order)."""
+    L = load()
+    n = C.c_int64()
+    check(L.hm_decompress_debug(h, tier, u0, u1, 0, None, None, None, None, C.byref(n), stream),
+          "hm_decompress_debug")
+    cnt = n.value
+    head = np.zeros(max(cnt, 1), dtype=np.float32)
+    tail = np.zeros(max(cnt, 1), dtype=np.float32)
+    code = np.zeros(max(cnt, 1), dtype=np.uint64)
+    fmt = np.zeros(max(cnt, 1), dtype=np.uint16)
+    check(L.hm_decompress_debug(h, tier, u0, u1, cnt, _ptr(head), _ptr(tail), _ptr(code), _ptr(fmt), C.byref(n),
+                                stream), "hm_decompress_debug")
+    return {"head": head[:cnt], "tail": tail[:cnt], "code": code[:cnt], "fmt": fmt[:cnt]}
 
 
 # ---------------------------------------------------------------- convenience object

@@ -1,0 +1,177 @@
+"""Bit-exact decompression of the RESIDENT payload by the product kernels' own decoders.
+
+``hm_decompress_debug`` runs, over the packed units of a compressed matrix as
+they sit in device memory, the decoder template instances the product kernels
+run: ``decode8p`` (FP32 tier: column dots, row chunks, multi-RHS panels) and
+``decode8s<TIER_FF>`` (float-float tier).  Each value is compared with the CPU
+oracle's decoder (Sec. 4.1, Alg. 8: ``oracle.codec.aflp_decode`` /
+``fpx_decode``) applied to the same code:
+
+* float-float tier: head + tail (summed in FP64) equals the oracle's value bit
+  for bit.  AFLP values are compared as +-(s - 1), i.e. the oracle's decode with
+  vmin = 1 (the kernels fold each array's vmin into the coefficient and tile
+  scales).  The stated exceptions (raw FP64 and FPX e11 m52, whose low 29
+  mantissa bits the tail keeps rounded to 24; AFLP codes with m' >= 48 or
+  f > 46) are held to 2^-48 relative instead, and counted.
+* FP32 tier: head equals the oracle's value rounded to nearest FP32 (ties to
+  even, numpy's float64 -> float32 cast), bit for bit, and the tail is zero.
+
+Matrices: every format (H, UH, H^2, UH with separate couplings) at N = 2048,
+AFLP and FPX at eps = 1e-4 .. 1e-14 and uncompressed; together they hold every
+decode class the kernels instantiate (FPX e8 B = 2..4, e11 B = 5..8, AFLP
+B = 1..7, raw FP64), zero codes and both signs (checked at the end).
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import codec as ocd
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+ALL_CLASSES = {(0, 2), (0, 3), (0, 4), (1, 5), (1, 6), (1, 7), (1, 8),
+               (2, 1), (2, 2), (2, 3), (2, 4), (2, 5), (2, 6), (2, 7), (3, 8)}
+SEEN = {"classes": set(), "zero": 0, "neg": 0, "pos": 0, "cases": 0}
+NCASES = 4 * 3 + 3
+
+
+@pytest.fixture(scope="module")
+def hm():
+    from paper_2405_03456_gb300 import build, hm as _hm
+    build.build()
+    _hm.load()
+    return _hm
+
+
+def fields(fmt):
+    fmt = fmt.astype(np.int64)
+    return fmt & 15, (fmt >> 4) & 3, (fmt >> 6) & 15, fmt >> 10
+
+
+def oracle_values(code, fmt):
+    """The oracle's FP64 value of every code (AFLP: vmin = 1, i.e. +-fl(s - 1))."""
+    B, F, E, Mb = fields(fmt)
+    out = np.empty(code.size)
+    keys = np.stack([B, F, E, Mb], axis=1)
+    for b, f, e, m in np.unique(keys, axis=0):
+        sel = (B == b) & (F == f) & (E == e) & (Mb == m)
+        c = code[sel]
+        if f == 0:
+            out[sel] = ocd.fpx_decode(c, 8, 8 * int(b) - 9)
+        elif f == 1:
+            out[sel] = ocd.fpx_decode(c, 11, 8 * int(b) - 12)
+        elif f == 2:
+            out[sel] = ocd.aflp_decode(c, int(b), int(e), int(m), 1.0, False)
+        else:
+            out[sel] = ocd.bits_f64(c)
+    return out
+
+
+def aflp_f(code, fmt):
+    B, F, E, Mb = fields(fmt)
+    f = np.zeros(code.size, dtype=np.int64)
+    a = F == 2
+    f[a] = ((code[a] >> Mb[a].astype(np.uint64)) & ((np.uint64(1) << E[a].astype(np.uint64)) - np.uint64(1))
+            ).astype(np.int64)
+    return f
+
+
+def check_resident(hm, M, record=True):
+    """Both tiers over every unit of M's payload; returns the counts of values
+    held to the stated bound instead of bit equality (FF tier)."""
+    info = M.info()
+    d_ff = hm.hm_decompress_debug(M.h, 1, 0, info["nunits"])
+    d_32 = hm.hm_decompress_debug(M.h, 0, 0, info["nunits"])
+    assert M.sync_status() == 0
+    code, fmt = d_ff["code"], d_ff["fmt"]
+    assert np.array_equal(code, d_32["code"]) and np.array_equal(fmt, d_32["fmt"])
+    assert code.size > 0
+    v = oracle_values(code, fmt)
+    B, F, E, Mb = fields(fmt)
+    f = aflp_f(code, fmt)
+    wide = ((F == 3) | ((F == 1) & (B == 8)) | ((F == 2) & ((Mb >= 48) | (f > 46))))
+    tiny = np.abs(v) < 2.0 ** -74
+    exact = ~(wide | tiny)
+    # float-float tier: head + tail == value
+    got = d_ff["head"].astype(np.float64) + d_ff["tail"].astype(np.float64)
+    assert np.array_equal(got[exact].view(np.uint64), v[exact].view(np.uint64)), \
+        np.flatnonzero(got[exact] != v[exact])[:5]
+    rest = wide & ~tiny
+    assert np.all(np.abs(got[rest] - v[rest]) <= 2.0 ** -48 * np.abs(v[rest]))
+    small = tiny & (np.abs(v) >= 2.0 ** -126)      # FP64 entries whose tail falls below 2^-126: head only
+    assert np.all(np.abs(got[small] - v[small]) <= 2.0 ** -23 * np.abs(v[small]))
+    # FP32 tier: head == RN32(value), tail == 0
+    want32 = v.astype(np.float32)
+    ok32 = ~(((F == 2) & ((Mb >= 48) | (f > 46))) | (np.abs(v) < 2.0 ** -126))
+    assert np.array_equal(d_32["head"][ok32].view(np.uint32), want32[ok32].view(np.uint32)), \
+        np.flatnonzero(d_32["head"][ok32] != want32[ok32])[:5]
+    assert not np.any(d_32["tail"])
+    if record:
+        SEEN["classes"] |= {(int(a), int(b)) for a, b in np.unique(np.stack([F, B], 1), axis=0)}
+        SEEN["zero"] += int(np.count_nonzero(v == 0))
+        SEEN["neg"] += int(np.count_nonzero(v < 0))
+        SEEN["pos"] += int(np.count_nonzero(v > 0))
+    return int(np.count_nonzero(~exact & ~tiny & ~(F == 3) & ~((F == 1) & (B == 8))))
+
+
+N = 2048
+
+
+@pytest.fixture(scope="module")
+def pts():
+    return synth.sphere_points(N)
+
+
+@pytest.mark.parametrize("fmt", ["h", "uh", "h2", "uh_sep"])
+@pytest.mark.parametrize("eps", [1e-4, 1e-6, 1e-8])
+def test_resident_decode_bit_exact(hm, pts, fmt, eps):
+    M = hm.HMatrix(pts, "laplace", 32, 2.0, fmt, eps)
+    try:
+        for codec in ("aflp", "fpx", "none"):
+            M.compress(eps, codec, True)
+            assert check_resident(hm, M) == 0, (fmt, eps, codec)
+        SEEN["cases"] += 1
+    finally:
+        M.close()
+
+
+@pytest.mark.parametrize("eps", [1e-10, 1e-12, 1e-14])
+def test_resident_decode_wide_codes(hm, pts, eps):
+    """Tight accuracies reach the wide classes: AFLP B = 5..7, FPX e11 B = 6..8, raw."""
+    M = hm.HMatrix(pts, "laplace", 32, 2.0, "h", eps)
+    try:
+        for codec in ("aflp", "fpx"):
+            M.compress(eps, codec, True)
+            check_resident(hm, M)
+        SEEN["cases"] += 1
+    finally:
+        M.close()
+
+
+def test_resident_decode_partial_ranges(hm, pts):
+    """Unit ranges concatenate to the whole payload; an empty range gives nothing."""
+    M = hm.HMatrix(pts, "laplace", 32, 2.0, "h", 1e-6)
+    try:
+        M.compress(1e-6, "aflp", True)
+        nu = M.info()["nunits"]
+        whole = hm.hm_decompress_debug(M.h, 0, 0, nu)
+        cut = nu // 3
+        a = hm.hm_decompress_debug(M.h, 0, 0, cut)
+        b = hm.hm_decompress_debug(M.h, 0, cut, nu + 5)
+        for k in ("code", "fmt", "head"):
+            assert np.array_equal(np.concatenate([a[k], b[k]]), whole[k])
+        assert hm.hm_decompress_debug(M.h, 1, cut, cut)["code"].size == 0
+    finally:
+        M.close()
+
+
+def test_zz_every_decode_class_seen():
+    """The matrices above exercised every decode class, zero codes and both signs."""
+    if SEEN["cases"] < NCASES:
+        pytest.skip("needs every matrix case of this module in the same run")
+    assert SEEN["classes"] >= ALL_CLASSES, sorted(ALL_CLASSES - SEEN["classes"])
+    assert SEEN["zero"] > 0 and SEEN["neg"] > 0 and SEEN["pos"] > 0
