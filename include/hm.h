@@ -56,11 +56,18 @@ typedef enum { HM_FMT_H = 0, HM_FMT_UH = 1, HM_FMT_H2 = 2, HM_FMT_UH_SEP = 3 } h
  * standard condition, larger blocks are always subdivided). */
 typedef enum { HM_ADM_STANDARD = 0, HM_ADM_HODLR = 1, HM_ADM_BLR = 2 } hm_adm;
 typedef enum { HM_CODEC_NONE = 0, HM_CODEC_AFLP = 1, HM_CODEC_FPX = 2 } hm_codec;
-typedef enum { HM_KERNEL_LAPLACE = 0, HM_KERNEL_MATERN15 = 1 } hm_kernel;
+/* Matrix entries of the model problems (point-kernel stand-ins for the
+ * Galerkin single-layer matrix of Sec. 2.1):
+ *   LAPLACE   a_ij = 1 / (4 pi |p_i - p_j|), a_ii = 1 / (4 pi h);
+ *   MATERN15  a_ij = (1 + sqrt3 r / l) exp(-sqrt3 r / l), r = |p_i - p_j|, a_ii = 1;
+ *   LAPLACE_W w_i times the LAPLACE entry, w_i = 1 + x_i / 2 (x_i the first
+ *             coordinate of point i): diag(w) A, a non-symmetric matrix for
+ *             checks of the adjoint product. */
+typedef enum { HM_KERNEL_LAPLACE = 0, HM_KERNEL_MATERN15 = 1, HM_KERNEL_LAPLACE_W = 2 } hm_kernel;
 
 typedef struct {
   int32_t kernel;      /* hm_kernel */
-  double kparam;       /* Laplace: diagonal spacing h (<= 0: sqrt(4 pi / n));
+  double kparam;       /* Laplace (and LAPLACE_W): diagonal spacing h (<= 0: sqrt(4 pi / n));
                           Matern: length scale (<= 0: 0.1) */
   int32_t leaf_size;   /* cluster tree leaf size (Def. Cluster Tree), 1..128 */
   double eta;          /* standard admissibility parameter, > 0 */

@@ -9,6 +9,9 @@ unit sphere (Sec. 2.1, eqn. slp / matcoeff).  Point-kernel stand-ins are used:
   h = sqrt(4 pi / N) the mean spacing of N points on the unit sphere.
 * Matern nu = 3/2: a_ij = (1 + sqrt3 r / l) exp(-sqrt3 r / l), r = |p_i - p_j|,
   l the length scale (diagonal 1).
+* Row-weighted Laplace (a non-symmetric matrix diag(w) A for the adjoint
+  product, remark after Alg. 3): w_i times the Laplace entry, w_i = 1 + x_i / 2
+  with x_i the first coordinate of point i.
 """
 from __future__ import annotations
 
@@ -16,6 +19,7 @@ import numpy as np
 
 LAPLACE = "laplace"
 MATERN = "matern"
+LAPLACE_W = "laplace_w"
 
 
 def _dist(p: np.ndarray, q: np.ndarray) -> np.ndarray:
@@ -31,6 +35,9 @@ def entries(kind: str, pts: np.ndarray, rows: np.ndarray, cols: np.ndarray,
 
     ``param`` is the diagonal spacing h for Laplace and the length scale for Matern.
     """
+    if kind == LAPLACE_W:
+        w = 1.0 + 0.5 * pts[rows, 0]
+        return w[:, None] * entries(LAPLACE, pts, rows, cols, param)
     r = _dist(pts[rows], pts[cols])
     same = rows[:, None] == cols[None, :]
     if kind == LAPLACE:
@@ -48,6 +55,6 @@ def entries(kind: str, pts: np.ndarray, rows: np.ndarray, cols: np.ndarray,
 
 def default_param(kind: str, n: int) -> float:
     """Laplace: the mean spacing sqrt(4 pi / N); Matern: length scale 0.1."""
-    if kind == LAPLACE:
+    if kind in (LAPLACE, LAPLACE_W):
         return float(np.sqrt(4.0 * np.pi / n))
     return 0.1

@@ -29,8 +29,10 @@
 namespace hm {
 
 double KernelFn::operator()(int64_t i, int64_t j) const {
-  if (i == j) return kind == HM_KERNEL_LAPLACE ? 1.0 / (4.0 * M_PI * param) : 1.0;
   const double* p = pts + 3 * i;
+  if (kind == HM_KERNEL_LAPLACE_W)   // row weight w_i = 1 + x_i / 2 times the Laplace entry
+    return (1.0 + 0.5 * p[0]) * KernelFn{HM_KERNEL_LAPLACE, param, pts}(i, j);
+  if (i == j) return kind == HM_KERNEL_LAPLACE ? 1.0 / (4.0 * M_PI * param) : 1.0;
   const double* q = pts + 3 * j;
   double d0 = p[0] - q[0], d1 = p[1] - q[1], d2 = p[2] - q[2];
   double r = std::sqrt((d0 * d0 + d1 * d1) + d2 * d2);

@@ -375,7 +375,8 @@ hm_status hm_build(const hm_build_params* prm, const double* pts, int64_t n, hm_
   if (prm->leaf_size < 1 || prm->leaf_size > 128) return HM_ERR_ARG;
   if (!(prm->eta > 0) || !(prm->eps_build > 0 && prm->eps_build < 1)) return HM_ERR_ARG;
   if (prm->format < HM_FMT_H || prm->format > HM_FMT_UH_SEP) return HM_ERR_ARG;
-  if (prm->kernel != HM_KERNEL_LAPLACE && prm->kernel != HM_KERNEL_MATERN15) return HM_ERR_ARG;
+  if (prm->kernel != HM_KERNEL_LAPLACE && prm->kernel != HM_KERNEL_MATERN15 && prm->kernel != HM_KERNEL_LAPLACE_W)
+    return HM_ERR_ARG;
   if (prm->adm < HM_ADM_STANDARD || prm->adm > HM_ADM_BLR) return HM_ERR_ARG;
   for (int64_t i = 0; i < 3 * n; ++i)
     if (!std::isfinite(pts[i])) return HM_ERR_ARG;
@@ -386,7 +387,7 @@ hm_status hm_build(const hm_build_params* prm, const double* pts, int64_t n, hm_
     H.prm = *prm;
     H.n = n;
     H.kparam = prm->kparam > 0 ? prm->kparam
-                               : (prm->kernel == HM_KERNEL_LAPLACE ? std::sqrt(4.0 * M_PI / (double)n) : 0.1);
+                               : (prm->kernel != HM_KERNEL_MATERN15 ? std::sqrt(4.0 * M_PI / (double)n) : 0.1);
     H.pts.assign(pts, pts + 3 * n);
     int nth = prm->nthreads > 0 ? prm->nthreads : (int)std::max(1u, std::thread::hardware_concurrency());
     build_cluster_tree(H.pts.data(), n, prm->leaf_size, H.ct);

@@ -17,10 +17,10 @@ from . import build as _build
 
 HM_FMT_H, HM_FMT_UH, HM_FMT_H2, HM_FMT_UH_SEP = 0, 1, 2, 3
 HM_CODEC_NONE, HM_CODEC_AFLP, HM_CODEC_FPX = 0, 1, 2
-HM_KERNEL_LAPLACE, HM_KERNEL_MATERN15 = 0, 1
+HM_KERNEL_LAPLACE, HM_KERNEL_MATERN15, HM_KERNEL_LAPLACE_W = 0, 1, 2
 FORMATS = {"h": HM_FMT_H, "uh": HM_FMT_UH, "h2": HM_FMT_H2, "uh_sep": HM_FMT_UH_SEP}
 CODECS = {"none": HM_CODEC_NONE, "aflp": HM_CODEC_AFLP, "fpx": HM_CODEC_FPX}
-KERNELS = {"laplace": HM_KERNEL_LAPLACE, "matern": HM_KERNEL_MATERN15}
+KERNELS = {"laplace": HM_KERNEL_LAPLACE, "matern": HM_KERNEL_MATERN15, "laplace_w": HM_KERNEL_LAPLACE_W}
 
 DECLARED = ["hm_build", "hm_compress", "hm_matvec", "hm_matvec_host", "hm_free", "hm_info",
             "hm_status_str", "hm_sync_status", "hm_structure", "hm_codec_encode", "hm_codec_decode",

@@ -8,7 +8,11 @@ Alg. 3), through the C ABI.
 * the adjoint identity <y, M x> = <M^H y, x> between the GPU's own forward and
   adjoint products in the float-float tier, where the products are accurate to
   about 1e-13: the Laplace matrix is symmetric up to its approximation error, so
-  only this identity tells M^T x from M x.
+  only this identity tells M^T x from M x there;
+* the row-weighted Laplace matrix diag(w) A (far from symmetric: M^T x and M x
+  differ by far more than 4 eps), every format and both tiers: within 4 eps of
+  the oracle's adjoint, which pins the adjoint product itself in the FP32 tier
+  as well.
 """
 import numpy as np
 import pytest
@@ -141,3 +145,39 @@ def test_recompress_rebuilds_the_adjoint(hm):
     assert np.array_equal(outs[0].view(np.uint64), outs[1].view(np.uint64))
     ref = oracle_adj(pts, "h", 1e-6, x.cpu().numpy(), 1.0, np.zeros(N), 0.0)
     assert rel(outs[0], ref) <= 4 * 1e-6
+
+
+_wcache = {}
+
+
+@pytest.mark.parametrize("fmt", ["h", "uh", "h2", "uh_sep"])
+@pytest.mark.parametrize("eps", [1e-6, 1e-8])
+def test_adjoint_non_symmetric(hm, fmt, eps):
+    pts = synth.sphere_points(N)
+    if eps not in _wcache:
+        h = hmatrix.build_h(pts, "laplace_w", 32, 2.0, eps)
+        _wcache[eps] = {"h": h, "uh": nested.build_uniform(h), "h2": nested.build_h2(h)}
+    om = _wcache[eps]["uh" if fmt == "uh_sep" else fmt]
+    fa = {"h": matvec.h_mvm_adjoint, "uh": matvec.uh_mvm_adjoint, "h2": matvec.h2_mvm_adjoint,
+          "uh_sep": matvec.uh_mvm_adjoint}[fmt]
+    fw = {"h": matvec.h_mvm, "uh": matvec.uh_mvm, "h2": matvec.h2_mvm, "uh_sep": matvec.uh_mvm}[fmt]
+    x = synth.rhs(N, 1, seed=61)[:, 0]
+    y0 = synth.rhs(N, 1, seed=62)[:, 0]
+    ref = fa(om, 0.75, x, -0.5, y0)
+    fwd = fw(om, 0.75, x, -0.5, y0)
+    assert rel(fwd, ref) > 100 * eps                     # the check tells M^T x from M x
+    M = hm.HMatrix(pts, "laplace_w", 32, 2.0, fmt, eps)
+    try:
+        M.compress(eps, "aflp", True)
+        xd = torch.from_numpy(x.copy()).cuda()
+        yd = torch.from_numpy(y0.copy()).cuda()
+        M.matvec(0.75, xd, -0.5, yd, adjoint=True)
+        torch.cuda.synchronize()
+        assert M.sync_status() == 0
+        assert rel(yd.cpu().numpy(), ref) <= 4 * eps
+        yf = torch.from_numpy(y0.copy()).cuda()
+        M.matvec(0.75, xd, -0.5, yf)
+        torch.cuda.synchronize()
+        assert rel(yf.cpu().numpy(), fwd) <= 4 * eps
+    finally:
+        M.close()

@@ -63,3 +63,29 @@ def test_adjoint_columns_and_scalars(mats, fmt):
         one = fa(m, 1.0, x[:, k], 0.0)
         ref = -1.25 * one + 0.5 * y0[:, k]
         assert np.allclose(full[:, k], ref, rtol=1e-13, atol=1e-13 * np.linalg.norm(ref))
+
+
+@pytest.fixture(scope="module")
+def weighted():
+    """The row-weighted Laplace matrix diag(w) A: far from symmetric."""
+    pts = synth.sphere_points(N)
+    h = hmatrix.build_h(pts, "laplace_w", 32, 2.0, 1e-6)
+    return h, nested.build_uniform(h), nested.build_h2(h)
+
+
+def test_adjoint_of_a_non_symmetric_matrix(weighted):
+    """H: adjoint = dense transpose (to 1e-13) and far from the forward product;
+    UH, H^2: the adjoint identity and the same distance from the forward product."""
+    h, u, h2 = weighted
+    a = hmatrix.dense_matrix(h)
+    x = synth.rhs(N, 1, seed=51)[:, 0]
+    y = synth.rhs(N, 1, seed=52)[:, 0]
+    at = matvec.h_mvm_adjoint(h, 1.0, x, 0.0)
+    assert np.linalg.norm(at - a.T @ x) <= 1e-13 * np.linalg.norm(a.T @ x)
+    fwd = matvec.h_mvm(h, 1.0, x, 0.0)
+    assert np.linalg.norm(at - fwd) > 1e-2 * np.linalg.norm(fwd)
+    for m, f, fa in ((u, matvec.uh_mvm, matvec.uh_mvm_adjoint), (h2, matvec.h2_mvm, matvec.h2_mvm_adjoint)):
+        mx, mty = f(m, 1.0, x, 0.0), fa(m, 1.0, y, 0.0)
+        assert abs(float(y @ mx) - float(mty @ x)) <= 1e-11 * np.linalg.norm(y) * np.linalg.norm(mx)
+        adj = fa(m, 1.0, x, 0.0)
+        assert np.linalg.norm(adj - a.T @ x) <= 4e-6 * np.linalg.norm(a.T @ x)

@@ -63,6 +63,27 @@ def test_kernel_entries_closed_form():
         1 / (4 * np.pi * np.sqrt(0.94)), rel=1e-15)
 
 
+def test_row_weighted_kernel_is_diag_w_times_laplace():
+    """laplace_w = diag(1 + x_i / 2) A: rows scaled by the weight of their own
+    point (not the column's), so the matrix is not symmetric."""
+    from scipy.spatial.distance import cdist
+    rng = np.random.default_rng(12)
+    q = rng.uniform(-1, 1, (6, 3))
+    idx = np.arange(6)
+    r = cdist(q, q)
+    off = ~np.eye(6, dtype=bool)
+    w = 1 + q[:, 0] / 2
+    a = kernels.entries("laplace_w", q, idx, idx, 0.5)
+    want = w[:, None] / (4 * np.pi * np.where(off, r, 1.0))
+    want[~off] = w / (4 * np.pi * 0.5)
+    assert np.allclose(a, want, rtol=1e-14, atol=0)
+    assert not np.allclose(a, a.T, rtol=1e-3)
+    # a sub-block is the same rows and columns of the whole matrix
+    sub = kernels.entries("laplace_w", q, np.array([4, 1]), np.array([0, 5, 2]), 0.5)
+    assert np.array_equal(sub, a[np.ix_([4, 1], [0, 5, 2])])
+    assert kernels.default_param("laplace_w", 100) == kernels.default_param("laplace", 100)
+
+
 def test_cluster_tree_definition(sphere512):
     pts, h = sphere512
     ct = h.ct
