@@ -287,6 +287,83 @@ def pct(v, q):
     return v[i]
 
 
+def serving_draw(nmin: int, nmax: int, count: int = 8, seed: int = 5, budget_gb: float = 120.0):
+    """Seeded draw of the resident matrices of the serving workload: kernel
+    alternating Laplace sphere / Matern cube, N log-uniform in [nmin, nmax]
+    (rounded to 1024), eps uniform in {1e-4, 1e-6, 1e-8}."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        n = int(round(2.0 ** rng.uniform(np.log2(nmin), np.log2(nmax)) / 1024.0)) * 1024
+        eps = float(rng.choice([1e-4, 1e-6, 1e-8]))
+        out.append(("laplace" if i % 2 == 0 else "matern", max(n, 1024), eps))
+    return out
+
+
+def serving_leg(torch, hm, nmin, nmax, reqs_per_point):
+    """Continuous batching of a seeded Poisson stream of 1..32-RHS requests on 8
+    resident compressed H-matrices (hm_matvec panels on 4 slot streams, admitted
+    by an HBM budget): closed-loop capacity, then offered loads of 25..120 % of it;
+    throughput and p50/p99 latency per load."""
+    import numpy as np
+    import synth
+    from paper_2405_03456_gb300.serving import GpuExecutor, Request, Scheduler
+    draw = serving_draw(nmin, nmax)
+    ex = GpuExecutor(nslots=4, max_rhs=64)
+    sch_budget = int(120e9)
+    Ms, mats, X = {}, {}, {}
+    t0 = time.perf_counter()
+    resident = 0
+    for mid, (kern, n, eps) in enumerate(draw):
+        pts = synth.sphere_points(n) if kern == "laplace" else synth.cube_points(n)
+        M = hm.HMatrix(pts, kern, 64, 2.0, "h", eps).compress(eps, "aflp", True)
+        M.graph(False)
+        info = M.info()
+        Ms[mid] = M
+        mats[mid] = {"kernel": kern, "n": n, "eps": eps, "payload_mb": round(info["bytes_payload"] / 1e6, 1)}
+        resident += info["bytes_payload"] + info["bytes_meta"] + info["bytes_workspace"]
+        ex.add(mid, M)
+        X[mid] = np.asfortranarray(np.random.default_rng(100 + mid).uniform(-1.0, 1.0, (n, 32)))
+    build_s = time.perf_counter() - t0
+
+    def stream_of(rate, count, seed):
+        rng = np.random.default_rng(seed)
+        t, out = 0.0, []
+        for k in range(count):
+            t += rng.exponential(1.0 / rate) if rate > 0 else 0.0
+            mid = int(rng.integers(len(draw)))
+            r = int(rng.integers(1, 33))
+            out.append(Request(k, mid, X[mid][:, :r], t))
+        return out
+
+    def run(rate, seed):
+        sch = Scheduler(ex, budget_bytes=sch_budget, nslots=4, max_batch_rhs=64)
+        for mid, M in Ms.items():
+            info = M.info()
+            sch.add_matrix(mid, mats[mid]["n"], info["bytes_payload"] + info["bytes_meta"] + info["bytes_workspace"])
+        sch.run(stream_of(rate, reqs_per_point, seed))
+        st = sch.stats()
+        return {k: (round(v, 3) if isinstance(v, float) else v) for k, v in st.items()}
+
+    run(0.0, 1)                                    # warm-up (graphs off: first launches, staging)
+    cap = run(0.0, 2)                              # closed loop: every request at t = 0
+    sat = cap["requests_per_s"]
+    points = []
+    for frac in (0.25, 0.5, 0.75, 0.9, 1.0, 1.2):
+        st = run(frac * sat, 10 + int(frac * 100))
+        st["offered_requests_per_s"] = round(frac * sat, 1)
+        points.append(st)
+    for M in Ms.values():
+        M.close()
+    return {"workload": (f"8 resident H-matrices (Laplace sphere / Matern cube alternating, N log-uniform in "
+                         f"[{nmin}, {nmax}], eps in {{1e-4, 1e-6, 1e-8}}, AFLP VALR, seed 5), Poisson "
+                         f"requests of U{{1..32}} FP64 right-hand sides, host buffers (copies included), "
+                         f"4 slot streams, batches of <= 64 RHS, HBM budget 120 GB"),
+            "matrices": mats, "resident_gb": round(resident / 1e9, 2), "build_s": round(build_s, 1),
+            "requests_per_point": reqs_per_point, "closed_loop": cap, "by_load": points}
+
+
 def gpu_arm(args, rank, world):
     import numpy as np
     import torch
@@ -450,6 +527,10 @@ def gpu_arm(args, rank, world):
                              "nblocks": info["nblocks"], "build_s": round(build_s, 1)}
             M.close()
         adm_legs["workload"] = f"laplace sphere N={na}, leaf 64, H eps=1e-6 AFLP VALR; HODLR and BLR block trees"
+    serving = None
+    if args.serving:
+        lo, hi = (16384, 1048576) if args.serving == "full" else (16384, 131072)
+        serving = serving_leg(torch, hm, lo, hi, args.serving_requests)
     clk = clocks.stop()
 
     # ------------------------------------------------------------ multi-rank reduction
@@ -524,6 +605,8 @@ def gpu_arm(args, rank, world):
     }
     if matern is not None:
         line["matern_multi_rhs"] = matern
+    if serving is not None:
+        line["serving"] = serving
     if adm_legs is not None:
         line["hodlr_blr"] = adm_legs
     if not args.no_cpu:
@@ -578,6 +661,10 @@ def main():
     ap.add_argument("--no-multi-rhs", action="store_true", help="skip the multi-RHS timings")
     ap.add_argument("--adm-legs", type=int, default=0,
                     help="also time HODLR and BLR H-matrices of the sphere problem at this N (opt-in)")
+    ap.add_argument("--serving", default="small", choices=["", "small", "full"],
+                    help="serving leg: small = N in [16384, 131072] (default), full = [16384, 1048576] (slow to "
+                         "build), '' = none")
+    ap.add_argument("--serving-requests", type=int, default=200)
     ap.add_argument("--matern", type=int, default=0,
                     help="also time multi-RHS products on the Matern cube with this many points (slow to build)")
     ap.add_argument("--cpu-budget-mb", type=float, default=8.0, help="oracle sample per host core (MB of FP64)")

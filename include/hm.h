@@ -170,6 +170,28 @@ hm_status hm_graph(hm_matrix* m, int32_t enable);
  */
 hm_status hm_persistent(hm_matrix* m, int32_t enable);
 
+/*
+ * hm_save -- write m to the file `path`: the built matrix (cluster tree, block
+ * tree, dense leaves, low-rank factors, cluster bases, couplings and transfer
+ * matrices, FP64, as hm_build made them) and, if m is compressed, the eps /
+ * codec / valr of its last hm_compress.  The packed device form is not written
+ * (its layout depends on the GPU); hm_load rebuilds it.  Host only, no sync.
+ * The format is little-endian with a magic and a version number.
+ * Errors: HM_ERR_ARG (null), HM_ERR_IO (the file cannot be written).
+ */
+hm_status hm_save(const hm_matrix* m, const char* path);
+
+/*
+ * hm_load -- read a matrix written by hm_save into a new hm_matrix (*out).  If
+ * the saved matrix was compressed, hm_compress runs with the saved settings on
+ * the current device, so that the loaded matrix gives the saved one's product
+ * bit for bit on the same GPU; an uncompressed one needs no GPU.
+ * Errors: HM_ERR_ARG (null), HM_ERR_IO (cannot be read, wrong magic or
+ * version, truncated, trailing bytes, or indices out of range), HM_ERR_OOM,
+ * and the errors of hm_compress.
+ */
+hm_status hm_load(const char* path, hm_matrix** out);
+
 /* hm_free -- release host and device memory of m (NULL is accepted). */
 hm_status hm_free(hm_matrix* m);
 
@@ -304,7 +326,8 @@ hm_status hm_alg_bytes(const hm_matrix* m, int64_t* bytes);
  *          1 = the float-float-tier decoders (eps <= 2^-22 and HM_CODEC_NONE):
  *          head + tail = the stored value (exact for every AFLP code with
  *          m' <= 47 and f <= 46 and every FPX code up to e11 m44; a raw FP64
- *          value keeps its low 29 mantissa bits rounded to 24).
+ *          value keeps its low 29 mantissa bits rounded to 24, within 2^-48
+ *          relative; AFLP codes beyond those limits within 2^-46 relative).
  *          Either tier may be asked for on any matrix.
  *   u0, u1 : units [u0, u1) (column-dot pieces 0 .. nitems-1, then row-chunk
  *          pieces; hm_info_t.nunits in all); u1 is clamped to nunits.

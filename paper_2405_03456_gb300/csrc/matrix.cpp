@@ -204,6 +204,18 @@ struct hm_matrix {
   }
 };
 
+namespace hm {
+// Access for persist.cpp (hm_save / hm_load).
+HostMatrix& host_of(hm_matrix* m) { return m->H; }
+bool compressed_state(const hm_matrix* m, double& eps, int& codec, int& valr) {
+  eps = m->eps;
+  codec = m->codec;
+  valr = m->valr;
+  return m->compressed;
+}
+hm_matrix* new_matrix() { return new hm_matrix(); }
+}  // namespace hm
+
 namespace {
 
 std::once_flag g_kinit;

@@ -26,7 +26,7 @@ DECLARED = ["hm_build", "hm_compress", "hm_matvec", "hm_matvec_host", "hm_free",
             "hm_status_str", "hm_sync_status", "hm_structure", "hm_codec_encode", "hm_codec_decode",
             "hm_profile", "hm_profile_read", "hm_alg_bytes", "hm_matvec_host_noalloc", "hm_graph",
             "hm_autotune", "hm_launch_shapes", "hm_set_launch_shapes", "hm_persistent", "hm_matvec_adjoint",
-            "hm_decompress_debug"]
+            "hm_decompress_debug", "hm_save", "hm_load"]
 NSHAPES = 3
 HM_NOALLOC_MAX_ENTRIES = 1 << 20
 KERNEL_KINDS = ["gather", "cdot", "gsum", "rgemv", "fanout"]
@@ -102,6 +102,8 @@ def load(path: str | None = None) -> C.CDLL:
         "hm_launch_shapes": ([vp, vp, i32, C.POINTER(i32)], i32),
         "hm_set_launch_shapes": ([vp, i32], i32),
         "hm_decompress_debug": ([vp, i32, i64, i64, i64, vp, vp, vp, vp, C.POINTER(i64), vp], i32),
+        "hm_save": ([vp, C.c_char_p], i32),
+        "hm_load": ([C.c_char_p, C.POINTER(vp)], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -267,6 +269,16 @@ def hm_decompress_debug(h: int, tier: int, u0: int = 0, u1: int = 1 << 62, strea
     return {"head": head[:cnt], "tail": tail[:cnt], "code": code[:cnt], "fmt": fmt[:cnt]}
 
 
+def hm_save(h: int, path: str) -> None:
+    check(load().hm_save(h, os.fsencode(path)), "hm_save")
+
+
+def hm_load(path: str) -> int:
+    h = C.c_void_p()
+    check(load().hm_load(os.fsencode(path), C.byref(h)), "hm_load")
+    return h.value
+
+
 # ---------------------------------------------------------------- convenience object
 class HMatrix:
     """Owns one hm_matrix handle; products take CUDA tensors (torch) or host arrays."""
@@ -275,6 +287,17 @@ class HMatrix:
                  kparam=0.0, nthreads=0, adm="std"):
         self.h = hm_build(pts, kernel, leaf_size, eta, fmt, eps_build, kparam, nthreads, adm)
         self.n = pts.shape[0]
+
+    @classmethod
+    def load(cls, path):
+        """A matrix written by save() (compressed again on the current device if it was)."""
+        self = cls.__new__(cls)
+        self.h = hm_load(path)
+        self.n = hm_info(self.h)["n"]
+        return self
+
+    def save(self, path):
+        hm_save(self.h, path)
 
     def compress(self, eps, codec="aflp", valr=True):
         hm_compress(self.h, eps, codec, valr)

@@ -224,31 +224,56 @@ def test_poisson_request_ranges():
 
 @pytest.mark.gpu
 def test_gpu_serving_alone_equals_mix():
+    """Four resident matrices of every format (H, UH, H^2, UH with separate
+    couplings; AFLP and FPX; eps 1e-4 .. 1e-8), a Poisson stream with 30 %
+    adjoint requests: products of different matrices -- the UH / H^2 / UH_SEP
+    ones as persistent cooperative launches -- run concurrently on three slot
+    streams.  Every result must lie within 4 eps of the same request computed
+    alone (one product of just its columns, on the default stream) and within
+    4 eps of the CPU oracle's product of the uncompressed matrix."""
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         pytest.skip("needs a CUDA GPU")
+    from oracle import hmatrix, matvec, nested
     from paper_2405_03456_gb300 import build, hm
     from paper_2405_03456_gb300.serving import GpuExecutor
     build.build()
-    specs = {0: ("laplace", 2048, 1e-6), 1: ("matern", 3000, 1e-4), 2: ("laplace", 4096, 1e-8)}
+    specs = {0: ("laplace", 2048, 1e-6, "h", "aflp"), 1: ("matern", 3000, 1e-4, "uh", "fpx"),
+             2: ("laplace", 4096, 1e-8, "h2", "aflp"), 3: ("laplace", 2048, 1e-6, "uh_sep", "fpx")}
     ex = GpuExecutor(nslots=3)
     sch = Scheduler(ex, budget_bytes=8 << 30, nslots=3)
-    Ms = {}
-    for mid, (kern, n, eps) in specs.items():
+    Ms, oracles = {}, {}
+    for mid, (kern, n, eps, fmt, codec) in specs.items():
         pts = synth.sphere_points(n) if kern == "laplace" else synth.cube_points(n)
-        M = hm.HMatrix(pts, kern, 64, 2.0, "h", eps).compress(eps, "aflp")
+        M = hm.HMatrix(pts, kern, 64, 2.0, fmt, eps).compress(eps, codec)
         Ms[mid] = M
         info = M.info()
-        sch.add_matrix(mid, n, info["bytes_payload"] + info["bytes_meta"] + info["bytes_workspace"])
-        ex.add(mid, M)
-    reqs = poisson_requests({m: s[1] for m, s in specs.items()}, rate=20000.0, count=60, seed=8)
+        sch.add_matrix(mid, n, info["bytes_payload"] + info["bytes_meta"] + info["bytes_workspace"], adjoint=True)
+        ex.add(mid, M, prepare_adjoint=True)
+        h = hmatrix.build_h(pts, kern, 64, 2.0, eps)
+        if fmt == "h":
+            oracles[mid] = (h, matvec.h_mvm, matvec.h_mvm_adjoint)
+        elif fmt == "h2":
+            oracles[mid] = (nested.build_h2(h), matvec.h2_mvm, matvec.h2_mvm_adjoint)
+        else:   # separate couplings: the same product as single couplings (uncompressed, to 1e-13)
+            oracles[mid] = (nested.build_uniform(h), matvec.uh_mvm, matvec.uh_mvm_adjoint)
+    reqs = poisson_requests({m: s[1] for m, s in specs.items()}, rate=20000.0, count=80, seed=8, adjoint_frac=0.3)
     done = sch.run(reqs)
-    assert len(done) == 60
-    assert sch.stats()["mean_batch_rhs"] > 1
+    assert len(done) == 80
+    st = sch.stats()
+    assert st["mean_batch_rhs"] > 1 and any(q.adjoint for q in done) and not all(q.adjoint for q in done)
     for q in done:
-        alone = np.asfortranarray(np.zeros_like(q.x))
-        Ms[q.mid].matvec_host(1.0, q.x, 0.0, alone)
         eps = specs[q.mid][2]
-        assert np.linalg.norm(q.y - alone) <= 4 * eps * np.linalg.norm(alone)
+        n = specs[q.mid][1]
+        xd = torch.from_numpy(np.asfortranarray(q.x.reshape(n, -1))).cuda().t().contiguous().t()
+        yd = torch.zeros_like(xd)
+        Ms[q.mid].matvec(1.0, xd, 0.0, yd, adjoint=q.adjoint)
+        torch.cuda.synchronize()
+        alone = yd.cpu().numpy().reshape(q.y.shape)
+        m, f, fa = oracles[q.mid]
+        ref = (fa if q.adjoint else f)(m, 1.0, q.x, 0.0)
+        assert np.linalg.norm(q.y - alone) <= 4 * eps * np.linalg.norm(alone), (q.mid, q.adjoint)
+        assert np.linalg.norm(q.y - ref) <= 4 * eps * np.linalg.norm(ref), (q.mid, q.adjoint)
     for M in Ms.values():
+        assert M.sync_status() == 0
         M.close()
