@@ -348,6 +348,51 @@ hm_status hm_decompress_debug(hm_matrix* m, int32_t tier, int64_t u0, int64_t u1
                               float* tail, uint64_t* code, uint16_t* fmt, int64_t* count, void* stream);
 
 /*
+ * Triangular solves with H-LU factors (Sec. 5, Conclusion: the triangular
+ * solves of an H-LU factorisation read the same compressed blocks as the
+ * product, with sequential dependencies).  x := U^-1 L^-1 b for A = L U without
+ * pivoting (L unit lower, U upper triangular, cluster order): meant for
+ * matrices whose unpivoted elimination is stable, such as the SPD Matern
+ * covariance matrix.
+ *
+ * hm_lu_build -- host: dense elimination of the kernel matrix of prm on pts
+ *   (cluster tree and block tree as hm_build; prm->format is not used), then
+ *   the factors cut along A's block tree: a leaf block (t, s) with t after s
+ *   goes to L, t before s to U, a diagonal leaf (t, t) holds the unit lower
+ *   triangle of L_tt and the upper triangle of U_tt; admissible blocks are
+ *   truncated at sigma_k <= prm->eps_build sigma_0 (eqn. epsilon), the others
+ *   stay exact.  The dense array limits n to 8192.
+ *   Errors: HM_ERR_ARG, HM_ERR_CAPACITY (n > 8192), HM_ERR_OOM,
+ *   HM_ERR_UNSUPPORTED (a pivot vanished).
+ * hm_lu_compress -- pack both factors as H-matrices (Sec. 4.1-4.2: direct
+ *   compression of dense blocks and triangles, VALR columns of low-rank
+ *   blocks) with eps / codec / valr as hm_compress, and upload them with the
+ *   work list of the solve.  Synchronises the device.
+ *   Errors: HM_ERR_ARG, HM_ERR_OOM, HM_ERR_CUDA, HM_ERR_UNSUPPORTED.
+ * hm_lu_solve -- x := U^-1 L^-1 b for nrhs columns (device FP64, original
+ *   point order, column-major, leading dimensions ldb, ldx >= n; x must not
+ *   overlap b), stream-ordered, no sync.  Each column is one persistent
+ *   cooperative launch: warps take the leaf solves (forward over the leaves,
+ *   then backward) and the coefficient products t_b = S X^T z of the low-rank
+ *   factor blocks in a dependency order, each waiting (bounded) for what it
+ *   reads; values are decoded exactly (head + tail) and the arithmetic is FP64.
+ *   A wait that runs out latches HM_ERR_TIMEOUT (hm_lu_sync_status).
+ *   Errors: HM_ERR_ARG, HM_ERR_STATE (not compressed), HM_ERR_CUDA.
+ * hm_lu_sync_status -- as hm_sync_status, for the solve's error word.
+ * hm_lu_info -- stats[0 .. min(nstats, 7)) = n, packed payload bytes, packed
+ *   code bytes, FP64 bytes of the same factors, work items, leaves, low-rank
+ *   blocks.  Errors: HM_ERR_ARG.
+ * hm_lu_free -- release host and device memory (NULL accepted).
+ */
+typedef struct hm_lu hm_lu;
+hm_status hm_lu_build(const hm_build_params* prm, const double* pts, int64_t n, hm_lu** out);
+hm_status hm_lu_compress(hm_lu* f, double eps, int32_t codec, int32_t valr);
+hm_status hm_lu_solve(hm_lu* f, const double* b, int64_t ldb, double* x, int64_t ldx, int64_t nrhs, void* stream);
+hm_status hm_lu_sync_status(hm_lu* f, void* stream);
+hm_status hm_lu_info(const hm_lu* f, int64_t* stats, int32_t nstats);
+hm_status hm_lu_free(hm_lu* f);
+
+/*
  * hm_matvec_host_noalloc -- hm_matvec_host for callers that cannot let the
  * library allocate device memory.  (The paper has no counterpart: this is a
  * deployment aid.)  A serving process that has committed its whole HBM budget

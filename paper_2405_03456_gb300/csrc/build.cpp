@@ -44,7 +44,9 @@ double KernelFn::operator()(int64_t i, int64_t j) const {
 namespace {
 
 // ACA with partial pivoting; returns U (m x k), V (n x k), A ~ U V^T.
-int aca(const KernelFn& f, const int64_t* rows, int64_t m, const int64_t* cols, int64_t n,
+// f(i, j): entry of row rows[i], column cols[j] (a kernel function, or a dense array).
+template <class Fn>
+int aca(const Fn& f, const int64_t* rows, int64_t m, const int64_t* cols, int64_t n,
         double eps, std::vector<double>& U, std::vector<double>& V) {
   const int64_t kmax = std::min(m, n);
   U.clear();
@@ -163,7 +165,8 @@ void gemm_nn(int64_t m, int64_t p, int64_t q, const double* A, int64_t lda, cons
   }
 }
 
-void lowrank_block(const KernelFn& f, const int64_t* rows, int64_t m, const int64_t* cols, int64_t n,
+template <class Fn>
+void lowrank_block(const Fn& f, const int64_t* rows, int64_t m, const int64_t* cols, int64_t n,
                    double eps, LowRankBlock& out) {
   std::vector<double> U, V;
   int k = aca(f, rows, m, cols, n, eps * 0.1, U, V);
@@ -211,6 +214,14 @@ void svd_basis(int64_t m, int64_t K, const std::vector<double>& R, double thr, s
 }
 
 }  // namespace
+
+void lowrank_dense(const double* A, int64_t lda, int64_t m, int64_t n, double eps, LowRankBlock& out) {
+  std::vector<int64_t> ri(m), ci(n);
+  std::iota(ri.begin(), ri.end(), 0);
+  std::iota(ci.begin(), ci.end(), 0);
+  auto f = [A, lda](int64_t i, int64_t j) { return A[i + j * lda]; };
+  lowrank_block(f, ri.data(), m, ci.data(), n, eps, out);
+}
 
 void build_lowrank_blocks(HostMatrix& hm, int nthreads) {
   KernelFn f;

@@ -201,6 +201,44 @@ struct DbgTask {
   int32_t pad;
 };
 
+// ---------------------------------------------------------------- H-LU triangular solves
+// One packed column of a factor, restricted to the rows an item reads: a
+// column of a dense leaf block or of a diagonal triangle (direct compression,
+// one format per block), a column of W_b restricted to a leaf's rows, or a
+// whole column of X_b (VALR, one format per column).
+constexpr int32_t LC_COEF = 1;   // the multiplier is a coefficient t_b[j] (else the solved vector)
+struct LuCol {
+  uint64_t off;     // payload byte offset of the first row's code (8-byte aligned)
+  double scale;     // value scale: AFLP vmin of a direct block, or the coefficient scale (column items)
+  int32_t rows;
+  int32_t mult;     // multiplier index (row items) / coefficient index (column items)
+  uint16_t fb, em;  // decode class fmt << 4 | B; e | m << 8
+  int32_t flags;
+};
+static_assert(sizeof(LuCol) == 32, "LuCol layout");
+
+// Work items of the solve, in an order in which every item depends only on
+// earlier ones.  Row items solve one leaf cluster's rows: forward (L, unit
+// lower triangle) or backward (U, upper triangle); column items form the
+// coefficients t_b = X_b^T z_sigma of the low-rank factor blocks once z_sigma
+// is final.
+enum { LU_ROW_L = 0, LU_COL_L = 1, LU_ROW_U = 2, LU_COL_U = 3 };
+struct LuItem {
+  int32_t kind;
+  int32_t r0, nr;   // row items: the leaf's rows [r0, r0 + nr); column items: sigma's first row, rows
+  int32_t c0, c1;   // column table range: contributions (row items) / X_b columns (column items)
+  int32_t tri;      // row items: the first of nr columns of the diagonal triangle
+  int32_t d0, d1;   // dependency range
+  int32_t flag;     // row items: the done flag it sets; column items: the counter it adds to
+  int32_t pad[3];
+};
+static_assert(sizeof(LuItem) == 48, "LuItem layout");
+
+// A dependency: flags[flag] must reach target (done flags 1, coefficient counters k_b).
+struct LuDep {
+  int32_t flag, target;
+};
+
 enum { MODE_Y = 0, MODE_VEC = 1, MODE_VEC_ADD = 2 };
 enum { TIER_F32 = 0, TIER_FF = 1 };
 

@@ -91,6 +91,9 @@ struct HostMatrix {
 };
 
 void build_lowrank_blocks(HostMatrix& hm, int nthreads);
+// Low-rank approximation of a dense m x n block (column-major, leading dimension
+// lda) by ACA, QR and SVD recompression, truncated at sigma_k <= eps sigma_0.
+void lowrank_dense(const double* A, int64_t lda, int64_t m, int64_t n, double eps, LowRankBlock& out);
 void build_uniform_bases(HostMatrix& hm, int nthreads);
 void build_nested_bases(HostMatrix& hm, int nthreads);
 // The transpose: blocks (t, s) -> (s, t) with W and X, row and column bases and

@@ -1165,4 +1165,155 @@ bool seq_dependencies(const Program& P, size_t first, size_t last, std::vector<S
   return true;
 }
 
+// ---------------------------------------------------------------- H-LU triangular solves
+// Work list of x = U^-1 L^-1 b (block forward substitution with L, then block
+// backward substitution with U, leaf by leaf).  For a leaf c the forward row
+// item computes
+//   w_c = L_cc^-1 (b_c - sum_{(t, s) in L, t >= c} L_ts|_c z_s)
+// where a dense block contributes its rows of c times the solved entries of s,
+// and a low-rank block W S X^T contributes W|_c t_b with t_b = S X^T w_s, formed
+// by the block's column items once every leaf of s is solved.  The backward
+// pass is the same with U, leaves in reverse order, the upper triangle U_cc.
+bool build_lu_program(const HostMatrix& Lf, const HostMatrix& Uf, int codec, double eps, int valr,
+                      LuProgram& P) {
+  P = LuProgram();
+  const ClusterTree& ct = Lf.ct;
+  const auto lv = leaves_under(ct);
+  const std::vector<int>& leaves = lv[0];
+  const int64_t nl = (int64_t)leaves.size();
+  P.nleaves = nl;
+  std::vector<int> leaf_of(ct.cl.size(), -1);
+  for (int64_t i = 0; i < nl; ++i) leaf_of[leaves[i]] = (int)i;
+  auto first_leaf = [&](int c) { return leaf_of[lv[c].front()]; };
+  auto last_leaf = [&](int c) { return leaf_of[lv[c].back()]; };
+  const int64_t fwd0 = 0, bwd0 = nl;
+  int64_t ncounter = 0;
+  for (int f = 0; f < 2; ++f) {
+    const HostMatrix& H = f == 0 ? Lf : Uf;
+    Program dummy;
+    Ctx cx{H, dummy, codec, eps, valr ? 1 : 0, m_eps(eps), 1, {}};
+    const int64_t nb = (int64_t)H.blocks.size();
+    std::vector<ColSet> csd(nb), csw(nb), csx(nb);
+    std::atomic<bool> ok{true};
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t b = 0; b < nb; ++b) {
+      const BlockLeaf& B = H.blocks[b];
+      const int64_t m = ct.cl[B.row].size(), n = ct.cl[B.col].size();
+      if (!B.adm) {
+        if (!make_direct(cx, H.dn[H.slot[b]].D.data(), m, (int)n, csd[b])) ok = false;
+        continue;
+      }
+      const LowRankBlock& R = H.lr[H.slot[b]];
+      if (R.k == 0) continue;
+      const auto keys = keys_lowrank(cx, R.s);
+      if (!make_cols(cx, R.W.data(), m, R.k, keys, csw[b]) || !make_cols(cx, R.X.data(), n, R.k, keys, csx[b]))
+        ok = false;
+    }
+    if (!ok) return false;
+    // per leaf: the blocks whose row cluster contains it; per block: coefficient base and counter
+    std::vector<std::vector<int64_t>> rowblocks(nl);
+    std::vector<int64_t> cbase(nb, -1), cnt(nb, -1), diag(nl, -1);
+    for (int64_t b = 0; b < nb; ++b) {
+      const BlockLeaf& B = H.blocks[b];
+      if (B.row == B.col) {
+        diag[leaf_of[B.row]] = b;
+        continue;
+      }
+      if (B.adm && H.lr[H.slot[b]].k == 0) continue;
+      for (int c : lv[B.row]) rowblocks[leaf_of[c]].push_back(b);
+      if (B.adm) {
+        cbase[b] = P.ncoef;
+        P.ncoef += H.lr[H.slot[b]].k;
+        cnt[b] = 2 * nl + ncounter++;
+      }
+      P.bytes_fp64 += 8 * (B.adm ? (ct.cl[B.row].size() + ct.cl[B.col].size()) * H.lr[H.slot[b]].k
+                                 : ct.cl[B.row].size() * ct.cl[B.col].size());
+    }
+    auto put_col = [&](const ColSet& cs, int j, int64_t r0, int64_t R, double scale, int32_t mult, int32_t flags) {
+      const int B = cs.B(j);
+      const uint64_t off = P.pk.put(cs.col(j) + r0, R, B);
+      const uint32_t fw = cs.fw(j);
+      P.cols.push_back(LuCol{off, scale, (int32_t)R, mult, class_of(fw), em_of(fw), flags});
+    };
+    auto add_deps = [&](std::vector<LuDep>& d, int s, int64_t base) {
+      for (int c : lv[s]) d.push_back(LuDep{(int32_t)(base + leaf_of[c]), 1});
+    };
+    // column items of the low-rank blocks whose column cluster ends (forward) or
+    // starts (backward) with a given leaf
+    std::vector<std::vector<int64_t>> colitems(nl);
+    for (int64_t b = 0; b < nb; ++b)
+      if (cbase[b] >= 0) colitems[f == 0 ? last_leaf(H.blocks[b].col) : first_leaf(H.blocks[b].col)].push_back(b);
+    const int64_t done0 = f == 0 ? fwd0 : bwd0;
+    for (int64_t k = 0; k < nl; ++k) {
+      const int64_t i = f == 0 ? k : nl - 1 - k;
+      const Cluster& c = ct.cl[leaves[i]];
+      const int64_t R = c.size();
+      if (diag[i] < 0) return false;   // every leaf has its diagonal block
+      LuItem it{};
+      it.kind = f == 0 ? LU_ROW_L : LU_ROW_U;
+      it.r0 = (int32_t)c.start;
+      it.nr = (int32_t)R;
+      it.c0 = (int32_t)P.cols.size();
+      std::vector<LuDep> d;
+      if (f == 1) d.push_back(LuDep{(int32_t)(fwd0 + i), 1});   // the forward result of this leaf
+      for (int64_t b : rowblocks[i]) {
+        const BlockLeaf& B = H.blocks[b];
+        const Cluster& t = ct.cl[B.row];
+        const Cluster& s = ct.cl[B.col];
+        const int64_t r0 = c.start - t.start;
+        if (!B.adm) {
+          for (int j = 0; j < csd[b].n; ++j)
+            put_col(csd[b], j, r0, R, csd[b].scale(0), (int32_t)(s.start + j), 0);
+          add_deps(d, B.col, done0);
+        } else {
+          for (int j = 0; j < csw[b].n; ++j) put_col(csw[b], j, r0, R, 1.0, (int32_t)(cbase[b] + j), LC_COEF);
+          d.push_back(LuDep{(int32_t)cnt[b], H.lr[H.slot[b]].k});
+        }
+      }
+      it.c1 = (int32_t)P.cols.size();
+      it.tri = (int32_t)P.cols.size();
+      const ColSet& dt = csd[diag[i]];
+      for (int j = 0; j < dt.n; ++j) put_col(dt, j, 0, R, dt.scale(0), 0, 0);
+      std::sort(d.begin(), d.end(), [](const LuDep& a, const LuDep& b) {
+        return a.flag != b.flag ? a.flag < b.flag : a.target < b.target;
+      });
+      d.erase(std::unique(d.begin(), d.end(), [](const LuDep& a, const LuDep& b) { return a.flag == b.flag; }),
+              d.end());
+      it.d0 = (int32_t)P.deps.size();
+      P.deps.insert(P.deps.end(), d.begin(), d.end());
+      it.d1 = (int32_t)P.deps.size();
+      it.flag = (int32_t)(done0 + i);
+      P.items.push_back(it);
+      for (int64_t b : colitems[i]) {
+        const BlockLeaf& B = H.blocks[b];
+        const Cluster& s = ct.cl[B.col];
+        const LowRankBlock& Rb = H.lr[H.slot[b]];
+        std::vector<LuDep> dc;
+        add_deps(dc, B.col, done0);
+        for (int j0 = 0; j0 < Rb.k; j0 += 4) {   // a few columns per item: long columns in parallel
+          LuItem ci{};
+          ci.kind = f == 0 ? LU_COL_L : LU_COL_U;
+          ci.r0 = (int32_t)s.start;
+          ci.nr = (int32_t)s.size();
+          ci.c0 = (int32_t)P.cols.size();
+          for (int j = j0; j < std::min(Rb.k, j0 + 4); ++j)
+            put_col(csx[b], j, 0, s.size(), Rb.s[j] * csx[b].scale(j) * csw[b].scale(j), (int32_t)(cbase[b] + j), 0);
+          ci.c1 = (int32_t)P.cols.size();
+          ci.tri = -1;
+          ci.d0 = (int32_t)P.deps.size();
+          P.deps.insert(P.deps.end(), dc.begin(), dc.end());
+          ci.d1 = (int32_t)P.deps.size();
+          ci.flag = (int32_t)cnt[b];
+          P.items.push_back(ci);
+        }
+      }
+    }
+  }
+  P.nflags = 2 * nl + ncounter;
+  P.pk.align(16);
+  P.pk.pay.resize(P.pk.pay.size() + 256, 0);   // 8-code groups of a column's last rows read past its end
+  if (P.pk.pay.size() >= (1ull << 40) || P.ncoef >= INT32_MAX || P.cols.size() >= (size_t)INT32_MAX) return false;
+  return true;
+}
+
 }  // namespace hm

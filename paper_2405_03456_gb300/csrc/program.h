@@ -117,4 +117,27 @@ bool build_program(const HostMatrix& H, int codec, double eps, int valr, int nsm
 // cannot run that way (they then run one launch each).
 bool seq_dependencies(const Program& P, size_t first, size_t last, std::vector<SeqDep>& deps, int& nchunks);
 
+// Packed factors and work list of the H-LU triangular solves x = U^-1 L^-1 b
+// (Sec. 5, Conclusion).  L and U hold the factor blocks on the block tree of A
+// (L: blocks after the diagonal and the unit lower diagonal triangles; U:
+// blocks before it and the upper diagonal triangles).
+struct LuProgram {
+  int tier = TIER_FF;
+  Packer pk;
+  std::vector<LuCol> cols;
+  std::vector<LuItem> items;
+  std::vector<LuDep> deps;
+  int64_t nflags = 0;       // done flags (2 per leaf) and coefficient counters
+  int64_t ncoef = 0;        // coefficients of the low-rank blocks of both factors
+  int64_t nleaves = 0;
+  int64_t bytes_fp64 = 0;   // FP64 bytes of the same factors
+};
+bool build_lu_program(const HostMatrix& L, const HostMatrix& U, int codec, double eps, int valr, LuProgram& P);
+
+// Dense unpivoted A = L U of the kernel matrix of prm on pts (cluster order),
+// cut along A's block tree into the factor blocks of L and U (lu_factor.cpp).
+// False if a pivot vanishes.  The dense array bounds n (LU_MAX_DENSE).
+constexpr int64_t LU_MAX_DENSE = 8192;
+bool lu_factor_host(const hm_build_params& prm, const double* pts, int64_t n, HostMatrix& L, HostMatrix& U);
+
 }  // namespace hm

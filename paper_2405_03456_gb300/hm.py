@@ -26,7 +26,8 @@ DECLARED = ["hm_build", "hm_compress", "hm_matvec", "hm_matvec_host", "hm_free",
             "hm_status_str", "hm_sync_status", "hm_structure", "hm_codec_encode", "hm_codec_decode",
             "hm_profile", "hm_profile_read", "hm_alg_bytes", "hm_matvec_host_noalloc", "hm_graph",
             "hm_autotune", "hm_launch_shapes", "hm_set_launch_shapes", "hm_persistent", "hm_matvec_adjoint",
-            "hm_decompress_debug", "hm_save", "hm_load"]
+            "hm_decompress_debug", "hm_save", "hm_load", "hm_lu_build", "hm_lu_compress", "hm_lu_solve",
+            "hm_lu_sync_status", "hm_lu_info", "hm_lu_free"]
 NSHAPES = 3
 HM_NOALLOC_MAX_ENTRIES = 1 << 20
 KERNEL_KINDS = ["gather", "cdot", "gsum", "rgemv", "fanout"]
@@ -103,6 +104,12 @@ def load(path: str | None = None) -> C.CDLL:
         "hm_set_launch_shapes": ([vp, i32], i32),
         "hm_decompress_debug": ([vp, i32, i64, i64, i64, vp, vp, vp, vp, C.POINTER(i64), vp], i32),
         "hm_save": ([vp, C.c_char_p], i32),
+        "hm_lu_build": ([C.POINTER(hm_build_params), vp, i64, C.POINTER(vp)], i32),
+        "hm_lu_compress": ([vp, dbl, i32, i32], i32),
+        "hm_lu_solve": ([vp, vp, i64, vp, i64, i64, vp], i32),
+        "hm_lu_sync_status": ([vp, vp], i32),
+        "hm_lu_info": ([vp, vp, i32], i32),
+        "hm_lu_free": ([vp], i32),
         "hm_load": ([C.c_char_p, C.POINTER(vp)], i32),
     }
     for name, (args, res) in sig.items():
@@ -277,6 +284,55 @@ def hm_load(path: str) -> int:
     h = C.c_void_p()
     check(load().hm_load(os.fsencode(path), C.byref(h)), "hm_load")
     return h.value
+
+
+class HLU:
+    """Owns one hm_lu handle: H-LU factors of a kernel matrix and their triangular solves."""
+
+    INFO = ["n", "bytes_payload", "bytes_values", "bytes_fp64", "items", "leaves", "lowrank_blocks"]
+
+    def __init__(self, pts, kernel="matern", leaf_size=32, eta=2.0, eps_build=1e-6, kparam=0.0, nthreads=0,
+                 adm="std"):
+        p = hm_build_params(KERNELS[kernel], kparam, leaf_size, eta, 0, eps_build, nthreads, ADMS[adm])
+        pts = np.ascontiguousarray(pts, dtype=np.float64)
+        h = C.c_void_p()
+        check(load().hm_lu_build(C.byref(p), _ptr(pts), pts.shape[0], C.byref(h)), "hm_lu_build")
+        self.h = h.value
+        self.n = pts.shape[0]
+
+    def compress(self, eps, codec="aflp", valr=True):
+        check(load().hm_lu_compress(self.h, eps, CODECS[codec], 1 if valr else 0), "hm_lu_compress")
+        return self
+
+    def solve(self, b, x, stream=None):
+        """x := U^-1 L^-1 b for CUDA FP64 tensors of shape (n,) or (n, r), column-major."""
+        import torch
+        if stream is None:
+            stream = torch.cuda.current_stream().cuda_stream
+        nrhs = 1 if b.dim() == 1 else b.shape[1]
+        ldb = b.shape[0] if nrhs == 1 else b.stride(1)
+        ldx = x.shape[0] if nrhs == 1 else x.stride(1)
+        check(load().hm_lu_solve(self.h, b.data_ptr(), ldb, x.data_ptr(), ldx, nrhs, stream), "hm_lu_solve")
+        return x
+
+    def sync_status(self, stream=0):
+        return load().hm_lu_sync_status(self.h, stream)
+
+    def info(self):
+        out = np.zeros(7, dtype=np.int64)
+        check(load().hm_lu_info(self.h, _ptr(out), 7), "hm_lu_info")
+        return dict(zip(self.INFO, out.tolist()))
+
+    def close(self):
+        if self.h:
+            load().hm_lu_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # ---------------------------------------------------------------- convenience object
