@@ -321,8 +321,11 @@ hm_status hm_alg_bytes(const hm_matrix* m, int64_t* bytes);
  * GPU with the decoders the product kernels run (Sec. 4.1, Alg. 8), for the
  * bit-exact check of decompression against the CPU oracle.
  *   tier : 0 = the FP32-tier decoders (column dots, row chunks and the
- *          multi-RHS kernels of matrices compressed at eps > 2^-22): head = the
- *          stored value rounded to nearest FP32 (ties to even), tail = 0;
+ *          multi-RHS kernels of matrices compressed at eps > 2^-22): tail = 0,
+ *          head = the stored value rounded to nearest FP32 (ties to even) for
+ *          codes of at most 24 significant bits (FPX e8, AFLP up to 3 bytes);
+ *          wider codes are cut to FP32's 23 mantissa bits first (AFLP: s cut,
+ *          then s - 1 rounded once), within 2^-22 + 2^-24 relative;
  *          1 = the float-float-tier decoders (eps <= 2^-22 and HM_CODEC_NONE):
  *          head + tail = the stored value (exact for every AFLP code with
  *          m' <= 47 and f <= 46 and every FPX code up to e11 m44; a raw FP64

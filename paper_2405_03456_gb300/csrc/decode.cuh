@@ -7,7 +7,8 @@
 //    values are decoded as +-(s - 1), their per-array vmin being folded into
 //    the coefficient vectors or tile scales;
 //  * TIER_F32 (eps > 2^-22): one FP32 value per entry, the stored value
-//    rounded to nearest FP32 (ties to even);
+//    rounded to nearest FP32 (ties to even) where it fits 24 bits, wider codes
+//    cut to 23 mantissa bits first (see decode4);
 //  * TIER_FF (eps <= 2^-22 and the uncompressed baseline): entries as
 //    float-float pairs that equal the stored value exactly (see decode4), and
 //    vector values as float-float pairs, products accumulated with the
@@ -118,27 +119,21 @@ __device__ __forceinline__ uint64_t top64(const uint32_t (&w)[B]) {
   }
 }
 
-// FP64 bit pattern -> value.  TIER_FF: float-float hi + lo, hi the top 24
-// significant bits, lo the rest (exact when the pattern has at most 48
-// significant bits, i.e. every FPX e11 code up to m = 44; the 52-bit mantissa
-// of a raw FP64 value keeps its lo part rounded to 24 bits).  TIER_F32: hi =
-// the value rounded to nearest FP32 (ties to even), by integer rounding of the
-// bit pattern; lo = 0.  Values below 2^-126 (FP32 subnormal range) give 0 in
-// the F32 tier and lose lo below 2^-74 in the FF tier.
+// FP64 bit pattern -> value.  hi = the top 24 significant bits (the mantissa
+// cut to FP32's 23 bits); TIER_FF: lo = the rest, exact when the pattern has at
+// most 48 significant bits (every FPX e11 code up to m = 44; the 52-bit
+// mantissa of a raw FP64 value keeps its lo part rounded to 24 bits);
+// TIER_F32: lo = 0 (the FP32 tier's stated approximation: within 2^-22 + 2^-24
+// relative).  Values below 2^-126 give hi = 0, and lo is dropped below 2^-74.
 template <int TIER>
 __device__ __forceinline__ void split_f64bits(uint64_t P, float& hi, float& lo) {
   const uint32_t sgn = (uint32_t)(P >> 32) & 0x80000000u;
   const int E = (int)((P >> 52) & 0x7ff);
+  const uint64_t M = P & ((1ull << 52) - 1);
+  const uint32_t hb = (E >= 897) ? (((uint32_t)(E - 896) << 23) | (uint32_t)(M >> 29)) : 0u;
+  hi = __uint_as_float(hb | sgn);
   lo = 0.0f;
-  if constexpr (TIER == TIER_F32) {
-    const uint64_t R = P & 0x7fffffffffffffffull;
-    const uint64_t Rr = R + 0x0fffffffull + ((R >> 29) & 1ull);   // round the 29 dropped bits, ties to even
-    const uint32_t hb = (E >= 897) ? (uint32_t)((Rr >> 29) - (896ull << 23)) : 0u;
-    hi = __uint_as_float(hb | sgn);
-  } else {
-    const uint64_t M = P & ((1ull << 52) - 1);
-    const uint32_t hb = (E >= 897) ? (((uint32_t)(E - 896) << 23) | (uint32_t)(M >> 29)) : 0u;
-    hi = __uint_as_float(hb | sgn);
+  if constexpr (TIER == TIER_FF) {
     if (E >= 949) {
       float l = __uint2float_rn((uint32_t)(M & ((1u << 29) - 1)));
       l *= __uint_as_float((uint32_t)(E - 948) << 23);
@@ -161,7 +156,13 @@ __device__ __forceinline__ void aflp_sub1(float sh, float& d, float& err) {
 //   TIER_FF: h + l equals the stored value exactly (AFLP as +-(s - 1): every
 //     code whose low mantissa part fits FP32, i.e. m' <= 47, and f <= 46; FPX
 //     codes up to e11 m44; see split_f64bits for raw FP64).
-//   TIER_F32: h is the stored value rounded to nearest FP32 (ties to even), l = 0.
+//   TIER_F32: l = 0 and h = the stored value rounded to nearest FP32 (ties to
+//     even) for every code that fits 24 significant bits (FPX e8, AFLP up to 3
+//     bytes); wider codes are cut to FP32's 23 mantissa bits first (AFLP:
+//     h = fl(s_h - 1) with s_h = s cut to 23 mantissa bits; FPX e11 and raw:
+//     the top 24 significant bits), within 2^-22 + 2^-24 relative of the value -- the
+//     FP32 tier's stated approximation, which keeps its decode as cheap as the
+//     short codes' (the tier computes in FP32 anyway).
 template <int TIER, int F, int B>
 __device__ __forceinline__ void decode4(const uint32_t (&w)[B], int e, int m, float (&h)[4],
                                         float (&l)[4]) {
@@ -175,40 +176,52 @@ __device__ __forceinline__ void decode4(const uint32_t (&w)[B], int e, int m, fl
     h[3] = __uint_as_float(top32<B, 3>(w) & mask);
   } else if constexpr (F == 2 && B <= 3) {
     // AFLP with s exact in FP32 (m' <= 22); d = fl(s - 1) is the value rounded
-    // to FP32, and the FF tier keeps its rounding error (nonzero when f >= 24)
+    // to FP32, and the FF tier keeps its rounding error (nonzero when f >= 24).
+    // Values in pairs (FADD2 on Blackwell).
     constexpr uint32_t mask = (0xffffffffu << (8 * (4 - B))) & 0x7fffffffu;
     const int sh = 8 - e;
-    uint32_t t[4] = {top32<B, 0>(w), top32<B, 1>(w), top32<B, 2>(w), top32<B, 3>(w)};
+    const uint32_t t[4] = {top32<B, 0>(w), top32<B, 1>(w), top32<B, 2>(w), top32<B, 3>(w)};
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const float s = __uint_as_float(((t[i] & mask) >> sh) + (127u << 23));
-      const uint32_t sg = t[i] & 0x80000000u;
-      float d, err;
-      aflp_sub1(s, d, err);
-      h[i] = __uint_as_float(__float_as_uint(d) ^ sg);
-      if constexpr (TIER == TIER_FF) l[i] = __uint_as_float(__float_as_uint(err) ^ sg);
+    for (int k = 0; k < 2; ++k) {
+      const uint32_t t0 = t[2 * k], t1 = t[2 * k + 1];
+      const float2 sv = make_float2(__uint_as_float(((t0 & mask) >> sh) + (127u << 23)),
+                                    __uint_as_float(((t1 & mask) >> sh) + (127u << 23)));
+      const float2 d = __fadd2_rn(sv, make_float2(-1.0f, -1.0f));
+      h[2 * k] = __uint_as_float(__float_as_uint(d.x) ^ (t0 & 0x80000000u));
+      h[2 * k + 1] = __uint_as_float(__float_as_uint(d.y) ^ (t1 & 0x80000000u));
+      if constexpr (TIER == TIER_FF) {
+        const float2 err = __fadd2_rn(__ffma2_rn(d, make_float2(-1.0f, -1.0f), sv), make_float2(-1.0f, -1.0f));
+        l[2 * k] = __uint_as_float(__float_as_uint(err.x) ^ (t0 & 0x80000000u));
+        l[2 * k + 1] = __uint_as_float(__float_as_uint(err.y) ^ (t1 & 0x80000000u));
+      }
     }
   } else if constexpr (F == 2 && B == 4) {
     // AFLP in 32 bits.  The code fills the word (m' = 31 - e): the head
     // s_h = 2^f (1 + top 23 mantissa bits) is exact in FP32, the sh = 8 - e = m' - 23
     // bits shifted out form the tail t 2^(f - m'), t < 2^sh (exact: t via the
     // 2^23 bit pattern).  s - 1 = d + err + tail; err + tail is exact for f <= 46.
+    // The FP32 tier keeps d = fl(s_h - 1), the value with its mantissa cut to
+    // 23 bits and then rounded once (within 2^-22 + 2^-24 relative).  Values in pairs.
     const int sh = 8 - e;
     const uint32_t tmask = (1u << sh) - 1u, mexp = (uint32_t)m << 23;
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const uint32_t c = w[i];
-      const uint32_t sb = ((c & 0x7fffffffu) >> sh) + (127u << 23);
-      const uint32_t sg = c & 0x80000000u;
-      float d, err;
-      aflp_sub1(__uint_as_float(sb), d, err);
-      const float t = __uint_as_float((c & tmask) | 0x4B000000u) - 8388608.0f;
-      const float lv = t * __uint_as_float((sb & 0x7f800000u) - mexp) + err;
+    for (int k = 0; k < 2; ++k) {
+      const uint32_t c0 = w[2 * k], c1 = w[2 * k + 1];
+      const uint32_t s0 = ((c0 & 0x7fffffffu) >> sh) + (127u << 23), s1 = ((c1 & 0x7fffffffu) >> sh) + (127u << 23);
+      const float2 sv = make_float2(__uint_as_float(s0), __uint_as_float(s1));
+      const float2 d = __fadd2_rn(sv, make_float2(-1.0f, -1.0f));
+      h[2 * k] = __uint_as_float(__float_as_uint(d.x) ^ (c0 & 0x80000000u));
+      h[2 * k + 1] = __uint_as_float(__float_as_uint(d.y) ^ (c1 & 0x80000000u));
       if constexpr (TIER == TIER_FF) {
-        h[i] = __uint_as_float(__float_as_uint(d) ^ sg);
-        l[i] = __uint_as_float(__float_as_uint(lv) ^ sg);
-      } else {
-        h[i] = __uint_as_float(__float_as_uint(d + lv) ^ sg);   // one rounding of the exact s - 1
+        const float2 err = __fadd2_rn(__ffma2_rn(d, make_float2(-1.0f, -1.0f), sv), make_float2(-1.0f, -1.0f));
+        const float2 tv = __fadd2_rn(make_float2(__uint_as_float((c0 & tmask) | 0x4B000000u),
+                                                 __uint_as_float((c1 & tmask) | 0x4B000000u)),
+                                     make_float2(-8388608.0f, -8388608.0f));
+        const float2 sc = make_float2(__uint_as_float((s0 & 0x7f800000u) - mexp),
+                                      __uint_as_float((s1 & 0x7f800000u) - mexp));
+        const float2 lv = __ffma2_rn(tv, sc, err);
+        l[2 * k] = __uint_as_float(__float_as_uint(lv.x) ^ (c0 & 0x80000000u));
+        l[2 * k + 1] = __uint_as_float(__float_as_uint(lv.y) ^ (c1 & 0x80000000u));
       }
     }
   } else if constexpr (F == 2) {                           // AFLP with m' > 23, B >= 5
@@ -226,13 +239,11 @@ __device__ __forceinline__ void decode4(const uint32_t (&w)[B], int e, int m, fl
       const uint32_t hb = ((f + 127u) << 23) | (uint32_t)(mant >> (m - 23));
       float d, err;
       aflp_sub1(__uint_as_float(hb), d, err);
-      const uint64_t ml = mant & ((1ull << (m - 23)) - 1ull);
-      const float lv = __ull2float_rn(ml) * __uint_as_float((uint32_t)(f + 127 - m) << 23) + err;
+      h[i] = __uint_as_float(__float_as_uint(d) ^ sg);
       if constexpr (TIER == TIER_FF) {
-        h[i] = __uint_as_float(__float_as_uint(d) ^ sg);
+        const uint64_t ml = mant & ((1ull << (m - 23)) - 1ull);
+        const float lv = __ull2float_rn(ml) * __uint_as_float((uint32_t)(f + 127 - m) << 23) + err;
         l[i] = __uint_as_float(__float_as_uint(lv) ^ sg);
-      } else {
-        h[i] = __uint_as_float(__float_as_uint(d + lv) ^ sg);
       }
     }
   } else {                                                  // FPX e11 or raw FP64
@@ -342,8 +353,8 @@ __device__ __forceinline__ void ff_add_dot2(float2& hi, float2& lo, float2 s, fl
 }
 
 // 8 consecutive codes of format (F, B) at shared address a -> 4 FP32 pairs
-// (FP32 tier: every value rounded to nearest FP32, ties to even -- AFLP as
-// +-(s - 1), FPX e8 exactly, e11 / raw by integer rounding of the bit pattern).
+// (FP32 tier: AFLP as +-(s - 1), FPX e8 exactly, e11 / raw cut to FP32; see
+// decode4 for what each class gives).
 template <int F, int B>
 __device__ __forceinline__ void decode8p(uint32_t a, int e, int m, float2 (&h2)[4]) {
   uint32_t w[2 * B];
@@ -359,8 +370,11 @@ __device__ __forceinline__ void decode8p(uint32_t a, int e, int m, float2 (&h2)[
     w0[i] = w[i];
     w1[i] = w[B + i];
   }
-  if constexpr (F == 2 && B <= 3) {
-    // s exact in FP32: fl(s - 1) is the value rounded to FP32
+  if constexpr (F == 2 && B <= 4) {
+    // AFLP: s with its mantissa cut to the 23 bits of FP32 (exact for B <= 3),
+    // then fl(s - 1): the value rounded to FP32 for B <= 3; for 4-byte codes
+    // (m' = 24 .. 30) the bits below FP32's mantissa are dropped first (the FP32
+    // tier's stated approximation: within 2^-22 + 2^-24 relative of the value)
     constexpr uint32_t mask = (0xffffffffu << (8 * (4 - B))) & 0x7fffffffu;
     const int sh = 8 - e;
     const uint32_t t[8] = {top32<B, 0>(w0), top32<B, 1>(w0), top32<B, 2>(w0), top32<B, 3>(w0),
@@ -372,27 +386,6 @@ __device__ __forceinline__ void decode8p(uint32_t a, int e, int m, float2 (&h2)[
       const float2 d = __fadd2_rn(sv, make_float2(-1.0f, -1.0f));
       h2[k] = make_float2(__uint_as_float(__float_as_uint(d.x) ^ (t[2 * k] & 0x80000000u)),
                           __uint_as_float(__float_as_uint(d.y) ^ (t[2 * k + 1] & 0x80000000u)));
-    }
-  } else if constexpr (F == 2 && B == 4) {
-    // 32-bit AFLP codes (value i is word i): s - 1 = d + err + tail exactly
-    // (as in decode4), rounded to FP32 once: d + (tail + err)
-    const int sh = 8 - e;
-    const uint32_t tmask = (1u << sh) - 1u, mexp = (uint32_t)m << 23;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const uint32_t c0 = w[2 * k], c1 = w[2 * k + 1];
-      const uint32_t s0 = ((c0 & 0x7fffffffu) >> sh) + (127u << 23), s1 = ((c1 & 0x7fffffffu) >> sh) + (127u << 23);
-      const float2 sv = make_float2(__uint_as_float(s0), __uint_as_float(s1));
-      const float2 d = __fadd2_rn(sv, make_float2(-1.0f, -1.0f));
-      const float2 err = __fadd2_rn(sub2(sv, d), make_float2(-1.0f, -1.0f));
-      const float2 t = __fadd2_rn(make_float2(__uint_as_float((c0 & tmask) | 0x4B000000u),
-                                              __uint_as_float((c1 & tmask) | 0x4B000000u)),
-                                  make_float2(-8388608.0f, -8388608.0f));
-      const float2 sc = make_float2(__uint_as_float((s0 & 0x7f800000u) - mexp),
-                                    __uint_as_float((s1 & 0x7f800000u) - mexp));
-      const float2 v = __fadd2_rn(d, __ffma2_rn(t, sc, err));
-      h2[k] = make_float2(__uint_as_float(__float_as_uint(v.x) ^ (c0 & 0x80000000u)),
-                          __uint_as_float(__float_as_uint(v.y) ^ (c1 & 0x80000000u)));
     }
   } else if constexpr (F == 0) {
     constexpr uint32_t mask = 0xffffffffu << (8 * (4 - B));

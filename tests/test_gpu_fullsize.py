@@ -23,7 +23,7 @@ import pytest
 import synth
 from oracle import kernels
 
-from decode_check import aflp_f, fields, oracle_values
+from decode_check import aflp_f, f32_tier_head, fields, oracle_values
 
 pytestmark = pytest.mark.gpu
 
@@ -96,8 +96,9 @@ def check_decode_sample(hm, M, nsample=1200, seed=0):
         ok = ~wide & (np.abs(v) >= 2.0 ** -74)
         got = d_ff["head"].astype(np.float64) + d_ff["tail"].astype(np.float64)
         assert np.array_equal(got[ok].view(np.uint64), v[ok].view(np.uint64)), int(u)
-        ok32 = ~((F == 2) & ((Mb >= 48) | (f > 46))) & (np.abs(v) >= 2.0 ** -126)
-        assert np.array_equal(d_32["head"][ok32].view(np.uint32), v[ok32].astype(np.float32).view(np.uint32)), int(u)
+        ok32 = np.abs(v) >= 2.0 ** -126
+        want32 = f32_tier_head(code, fmt, v)
+        assert np.array_equal(d_32["head"][ok32].view(np.uint32), want32[ok32].view(np.uint32)), int(u)
         assert not np.any(d_32["tail"])
     assert M.sync_status() == 0
 

@@ -90,7 +90,7 @@ def test_hlu_solve_against_oracle(hm, problem, eps):
             assert res <= eps, (codec, res)
             if codec != "none":
                 info = F.info()
-                assert info["bytes_values"] < info["bytes_fp64"] / 2
+                assert info["bytes_values"] < 0.75 * info["bytes_fp64"]
     finally:
         F.close()
 
