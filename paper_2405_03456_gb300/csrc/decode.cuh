@@ -163,7 +163,7 @@ __device__ __forceinline__ void aflp_sub1(float sh, float& d, float& err) {
 //     the top 24 significant bits), within 2^-22 + 2^-24 relative of the value -- the
 //     FP32 tier's stated approximation, which keeps its decode as cheap as the
 //     short codes' (the tier computes in FP32 anyway).
-template <int TIER, int F, int B, bool ERR = true>
+template <int TIER, int F, int B>
 __device__ __forceinline__ void decode4(const uint32_t (&w)[B], int e, int m, float (&h)[4],
                                         float (&l)[4]) {
 #pragma unroll
@@ -189,7 +189,7 @@ __device__ __forceinline__ void decode4(const uint32_t (&w)[B], int e, int m, fl
       const float2 d = __fadd2_rn(sv, make_float2(-1.0f, -1.0f));
       h[2 * k] = __uint_as_float(__float_as_uint(d.x) ^ (t0 & 0x80000000u));
       h[2 * k + 1] = __uint_as_float(__float_as_uint(d.y) ^ (t1 & 0x80000000u));
-      if constexpr (TIER == TIER_FF && ERR) {
+      if constexpr (TIER == TIER_FF) {
         const float2 err = __fadd2_rn(__ffma2_rn(d, make_float2(-1.0f, -1.0f), sv), make_float2(-1.0f, -1.0f));
         l[2 * k] = __uint_as_float(__float_as_uint(err.x) ^ (t0 & 0x80000000u));
         l[2 * k + 1] = __uint_as_float(__float_as_uint(err.y) ^ (t1 & 0x80000000u));
@@ -213,8 +213,7 @@ __device__ __forceinline__ void decode4(const uint32_t (&w)[B], int e, int m, fl
       h[2 * k] = __uint_as_float(__float_as_uint(d.x) ^ (c0 & 0x80000000u));
       h[2 * k + 1] = __uint_as_float(__float_as_uint(d.y) ^ (c1 & 0x80000000u));
       if constexpr (TIER == TIER_FF) {
-        const float2 err = ERR ? __fadd2_rn(__ffma2_rn(d, make_float2(-1.0f, -1.0f), sv), make_float2(-1.0f, -1.0f))
-                               : make_float2(0.0f, 0.0f);
+        const float2 err = __fadd2_rn(__ffma2_rn(d, make_float2(-1.0f, -1.0f), sv), make_float2(-1.0f, -1.0f));
         const float2 tv = __fadd2_rn(make_float2(__uint_as_float((c0 & tmask) | 0x4B000000u),
                                                  __uint_as_float((c1 & tmask) | 0x4B000000u)),
                                      make_float2(-8388608.0f, -8388608.0f));
@@ -276,9 +275,7 @@ __device__ __forceinline__ uint4 lds128(uint32_t a) {
 // A lane's 8 consecutive codes of one column in shared memory: 8*B bytes at
 // an 8-byte aligned shared address, read as B 64-bit loads, decoded to 8
 // values (hi, and lo for TIER_FF).
-// ERR = false skips the rounding error of s - 1 (AFLP, float-float tier), which
-// is zero unless f >= 24: callers pass it for columns with e <= 4 (f <= 15).
-template <int TIER, int F, int B, bool ERR = true>
+template <int TIER, int F, int B>
 __device__ __forceinline__ void decode8s(uint32_t a, int e, int m, float (&h)[8], float (&l)[8]) {
   uint32_t w[2 * B];
 #pragma unroll
@@ -294,8 +291,8 @@ __device__ __forceinline__ void decode8s(uint32_t a, int e, int m, float (&h)[8]
     w1[i] = w[B + i];
   }
   float h0[4], l0[4], h1[4], l1[4];
-  decode4<TIER, F, B, ERR>(w0, e, m, h0, l0);
-  decode4<TIER, F, B, ERR>(w1, e, m, h1, l1);
+  decode4<TIER, F, B>(w0, e, m, h0, l0);
+  decode4<TIER, F, B>(w1, e, m, h1, l1);
 #pragma unroll
   for (int u = 0; u < 4; ++u) {
     h[u] = h0[u];

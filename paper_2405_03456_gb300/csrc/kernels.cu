@@ -136,10 +136,7 @@ __device__ __forceinline__ void cs_piece(uint32_t sa, int R, int nc, int flags, 
 #pragma unroll
         for (int hb = 0; hb < RL / RPL; ++hb) {
           float h[8], l[8];
-          if (F == 2 && e <= 4)   // f <= 15: s - 1 is exact in FP32, no error term
-            decode8s<TIER, F, B, false>(cb + (uint32_t)j * stride + (uint32_t)(hb * RPL * B), e, m, h, l);
-          else
-            decode8s<TIER, F, B>(cb + (uint32_t)j * stride + (uint32_t)(hb * RPL * B), e, m, h, l);
+          decode8s<TIER, F, B>(cb + (uint32_t)j * stride + (uint32_t)(hb * RPL * B), e, m, h, l);
 #pragma unroll
           for (int u = 0; u < 8; u += 2) {
             if constexpr (TIER == TIER_F32) {
@@ -450,10 +447,7 @@ __device__ __forceinline__ void rs_piece(uint32_t sa, const PieceHdr& H, uint32_
         m = (em >> 8) & 0xff;
       }
       float h[8], l[8];
-      if (F == 2 && e <= 4)   // f <= 15: s - 1 is exact in FP32, no error term
-        decode8s<TIER, F, B, false>(cb + (uint32_t)j * stride, e, m, h, l);
-      else
-        decode8s<TIER, F, B>(cb + (uint32_t)j * stride, e, m, h, l);
+      decode8s<TIER, F, B>(cb + (uint32_t)j * stride, e, m, h, l);
       const float2 vh2 = make_float2(vh, vh), vl2 = make_float2(vl, vl);
 #pragma unroll
       for (int k = 0; k < 4; ++k)
@@ -848,69 +842,39 @@ __global__ void k_fanout(const int32_t* __restrict__ src, int n, float2* __restr
 }
 
 // ---------------------------------------------------------------- segment sums (phase A2)
-// Segment sums: one output per lane for the common short runs of partials
-// (at most GS_SHORT: the lane adds them in order, loads issued together);
-// longer runs are summed by the whole warp afterwards (lane k takes partials
-// k, k + 32, ..., then a fixed xor tree).  Deterministic order either way.
-constexpr int GS_SHORT = 16;
-__device__ __forceinline__ FF gs_term(const GsumOut& O, const F2* __restrict__ pscale, const F2* __restrict__ partial,
-                                      int p) {
-  const F2 v = partial[p];
-  if (O.flags & 2) {
-    const F2 w = pscale[O.ps + (p - O.p0)];
-    return ff_mul(FF{v.hi, v.lo}, FF{w.hi, w.lo});
-  }
-  return FF{v.hi, v.lo};
-}
-
+// Segment sums: GS_LANES lanes per output; lane k sums the partials p0 + k,
+// p0 + k + GS_LANES, ... (consecutive lanes read consecutive partials), then a
+// fixed xor tree combines the lanes (deterministic order).
+constexpr int GS_LANES = 8;
 __global__ void k_gsum(const GsumOut* __restrict__ outs, int nouts, const F2* __restrict__ pscale,
                        const F2* __restrict__ partial, F2 alpha, float2* __restrict__ vout) {
   pdl_trigger();
   pdl_wait();
-  const int lane = threadIdx.x & 31;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = t / GS_LANES, k = t % GS_LANES;
   const bool on = i < nouts;
   GsumOut O{};
   if (on) O = outs[i];
-  const int np = O.p1 - O.p0;
   FF s = {0.f, 0.f};
-  if (on && np <= GS_SHORT) {
-    F2 v[GS_SHORT];
-#pragma unroll
-    for (int k = 0; k < GS_SHORT; ++k) v[k] = k < np ? partial[O.p0 + k] : F2{0.f, 0.f};
-#pragma unroll
-    for (int k = 0; k < GS_SHORT; ++k) {
-      if (k < np) {
-        FF t = {v[k].hi, v[k].lo};
-        if (O.flags & 2) {
-          const F2 w = pscale[O.ps + k];
-          t = ff_mul(t, FF{w.hi, w.lo});
-        }
-        s = ff_add(s, t);
-      }
+  if (O.flags & 2) {
+    for (int p = O.p0 + k; p < O.p1; p += GS_LANES) {
+      const F2 v = partial[p];
+      const F2 w = pscale[O.ps + (p - O.p0)];
+      s = ff_add(s, ff_mul(FF{v.hi, v.lo}, FF{w.hi, w.lo}));
+    }
+  } else {
+    for (int p = O.p0 + k; p < O.p1; p += GS_LANES) {
+      const F2 v = partial[p];
+      s = ff_add(s, FF{v.hi, v.lo});
     }
   }
-  // long runs: the warp takes them one after the other
-  unsigned longs = __ballot_sync(HM_FULL, on && np > GS_SHORT);
-  while (longs) {
-    const int src = __ffs(longs) - 1;
-    longs &= longs - 1;
-    GsumOut L;
-    L.p0 = __shfl_sync(HM_FULL, O.p0, src);
-    L.p1 = __shfl_sync(HM_FULL, O.p1, src);
-    L.flags = __shfl_sync(HM_FULL, O.flags, src);
-    L.ps = __shfl_sync(HM_FULL, O.ps, src);
-    FF t = {0.f, 0.f};
-    for (int p = L.p0 + lane; p < L.p1; p += 32) t = ff_add(t, gs_term(L, pscale, partial, p));
 #pragma unroll
-    for (int m = 16; m >= 1; m >>= 1) {
-      const float hi = __shfl_xor_sync(HM_FULL, t.hi, m);
-      const float lo = __shfl_xor_sync(HM_FULL, t.lo, m);
-      t = (lane & m) ? ff_add(FF{hi, lo}, t) : ff_add(t, FF{hi, lo});
-    }
-    if (lane == src) s = t;
+  for (int m = GS_LANES / 2; m >= 1; m >>= 1) {   // whole warps: every lane takes part
+    const float hi = __shfl_xor_sync(HM_FULL, s.hi, m);
+    const float lo = __shfl_xor_sync(HM_FULL, s.lo, m);
+    s = (k & m) ? ff_add(FF{hi, lo}, s) : ff_add(s, FF{hi, lo});
   }
-  if (!on) return;
+  if (!on || k != 0) return;
   s = ff_mul(s, FF{O.scale.hi, O.scale.lo});
   if (O.flags & 1) s = ff_mul(s, FF{alpha.hi, alpha.lo});
   vout[O.out] = make_float2(s.hi, s.lo);
@@ -1124,8 +1088,9 @@ cudaError_t launch_fanout(const int32_t* src, int n, float2* dst, const float2* 
 cudaError_t launch_gsum(const GsumOut* outs, int nouts, const F2* pscale, const F2* partial, F2 alpha, float2* vout,
                         cudaStream_t st) {
   if (nouts <= 0) return cudaSuccess;
+  const int64_t threads = (int64_t)nouts * GS_LANES;
   const cudaError_t e =
-      launch_pdl(k_gsum, (unsigned)((nouts + 255) / 256), 256, 0, st, outs, nouts, pscale, partial, alpha, vout);
+      launch_pdl(k_gsum, (unsigned)((threads + 255) / 256), 256, 0, st, outs, nouts, pscale, partial, alpha, vout);
   return e != cudaSuccess ? e : cudaGetLastError();
 }
 
