@@ -842,62 +842,42 @@ __global__ void k_fanout(const int32_t* __restrict__ src, int n, float2* __restr
 }
 
 // ---------------------------------------------------------------- segment sums (phase A2)
-// Segment sums: a group of GS_LANES lanes takes GS_OUTS consecutive outputs;
-// lane k sums the partials p0 + k, p0 + k + GS_LANES, ... of each (consecutive
-// lanes read consecutive partials; the loads of the group's outputs are in
-// flight together), then a fixed xor tree combines the lanes (deterministic
-// order).
+// Segment sums: GS_LANES lanes per output; lane k sums the partials p0 + k,
+// p0 + k + GS_LANES, ... (consecutive lanes read consecutive partials), then a
+// fixed xor tree combines the lanes (deterministic order).
 constexpr int GS_LANES = 8;
-constexpr int GS_OUTS = 4;
 __global__ void k_gsum(const GsumOut* __restrict__ outs, int nouts, const F2* __restrict__ pscale,
                        const F2* __restrict__ partial, F2 alpha, float2* __restrict__ vout) {
   pdl_trigger();
   pdl_wait();
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  const int g = t / GS_LANES, k = t % GS_LANES;
-  GsumOut O[GS_OUTS];
-  FF s[GS_OUTS];
-#pragma unroll
-  for (int q = 0; q < GS_OUTS; ++q) {
-    const int i = g * GS_OUTS + q;
-    O[q] = i < nouts ? outs[i] : GsumOut{0, 0, 0, 0, F2{0.f, 0.f}, 0, 0};
-    s[q] = FF{0.f, 0.f};
-  }
-  for (int r = 0;; r += GS_LANES) {
-    bool any = false;
-#pragma unroll
-    for (int q = 0; q < GS_OUTS; ++q) {
-      const int p = O[q].p0 + k + r;
-      if (p < O[q].p1) {
-        any = true;
-        const F2 v = partial[p];
-        FF tv = {v.hi, v.lo};
-        if (O[q].flags & 2) {
-          const F2 w = pscale[O[q].ps + (p - O[q].p0)];
-          tv = ff_mul(tv, FF{w.hi, w.lo});
-        }
-        s[q] = ff_add(s[q], tv);
-      }
+  const int i = t / GS_LANES, k = t % GS_LANES;
+  const bool on = i < nouts;
+  GsumOut O{};
+  if (on) O = outs[i];
+  FF s = {0.f, 0.f};
+  if (O.flags & 2) {
+    for (int p = O.p0 + k; p < O.p1; p += GS_LANES) {
+      const F2 v = partial[p];
+      const F2 w = pscale[O.ps + (p - O.p0)];
+      s = ff_add(s, ff_mul(FF{v.hi, v.lo}, FF{w.hi, w.lo}));
     }
-    if (!any) break;
-  }
-#pragma unroll
-  for (int q = 0; q < GS_OUTS; ++q) {
-#pragma unroll
-    for (int m = GS_LANES / 2; m >= 1; m >>= 1) {   // whole warps: every lane takes part
-      const float hi = __shfl_xor_sync(HM_FULL, s[q].hi, m);
-      const float lo = __shfl_xor_sync(HM_FULL, s[q].lo, m);
-      s[q] = (k & m) ? ff_add(FF{hi, lo}, s[q]) : ff_add(s[q], FF{hi, lo});
+  } else {
+    for (int p = O.p0 + k; p < O.p1; p += GS_LANES) {
+      const F2 v = partial[p];
+      s = ff_add(s, FF{v.hi, v.lo});
     }
   }
 #pragma unroll
-  for (int q = 0; q < GS_OUTS; ++q) {
-    const int i = g * GS_OUTS + q;
-    if (k != q || i >= nouts) continue;
-    FF v = ff_mul(s[q], FF{O[q].scale.hi, O[q].scale.lo});
-    if (O[q].flags & 1) v = ff_mul(v, FF{alpha.hi, alpha.lo});
-    vout[O[q].out] = make_float2(v.hi, v.lo);
+  for (int m = GS_LANES / 2; m >= 1; m >>= 1) {   // whole warps: every lane takes part
+    const float hi = __shfl_xor_sync(HM_FULL, s.hi, m);
+    const float lo = __shfl_xor_sync(HM_FULL, s.lo, m);
+    s = (k & m) ? ff_add(FF{hi, lo}, s) : ff_add(s, FF{hi, lo});
   }
+  if (!on || k != 0) return;
+  s = ff_mul(s, FF{O.scale.hi, O.scale.lo});
+  if (O.flags & 1) s = ff_mul(s, FF{alpha.hi, alpha.lo});
+  vout[O.out] = make_float2(s.hi, s.lo);
 }
 
 // ---------------------------------------------------------------- gather x
@@ -1108,7 +1088,7 @@ cudaError_t launch_fanout(const int32_t* src, int n, float2* dst, const float2* 
 cudaError_t launch_gsum(const GsumOut* outs, int nouts, const F2* pscale, const F2* partial, F2 alpha, float2* vout,
                         cudaStream_t st) {
   if (nouts <= 0) return cudaSuccess;
-  const int64_t threads = (int64_t)((nouts + GS_OUTS - 1) / GS_OUTS) * GS_LANES;
+  const int64_t threads = (int64_t)nouts * GS_LANES;
   const cudaError_t e =
       launch_pdl(k_gsum, (unsigned)((threads + 255) / 256), 256, 0, st, outs, nouts, pscale, partial, alpha, vout);
   return e != cudaSuccess ? e : cudaGetLastError();
