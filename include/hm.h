@@ -157,16 +157,22 @@ hm_status hm_matvec_host(hm_matrix* m, double alpha, const double* x, double bet
 hm_status hm_graph(hm_matrix* m, int32_t enable);
 
 /*
- * hm_persistent -- enable (nonzero, the default) or disable persistent
- * launches.  When enabled, every run of two or more consecutive row-chunk
- * launches (the row-chunk form of Alg. 3 / 5 / 7 and the sweeps of Alg. 6 / 7,
- * one launch per tree level) and the multiplier fan-outs between them execute
- * as the phases of ONE cooperative launch with one block per SM: the blocks
- * meet at a grid barrier between phases (bounded wait; a barrier that does not
- * complete latches HM_ERR_TIMEOUT, read by hm_sync_status).  The phases use the
- * warp ranges of launch shape 0 whatever hm_autotune chose.  Results equal the
- * per-launch path with all shapes 0 bit for bit.  Profiling (hm_profile)
- * always uses the per-launch path.  Errors: HM_ERR_ARG.
+ * hm_persistent -- how the launches of one product run (the batching form).
+ *   0: one kernel launch per step (gather, column dots, segment sums, fan-outs,
+ *      row chunks), chained on the stream;
+ *   1 (the default): as 0, but every run of two or more consecutive row-chunk
+ *      launches (the row-chunk form of Alg. 3 / 5 / 7 and the sweeps of Alg. 6 /
+ *      7, one launch per tree level) executes as the phases of ONE cooperative
+ *      launch with one block per SM, each piece waiting (bounded) only for the
+ *      coefficient chunks it reads;
+ *   2: the whole product -- every step of a1-a10, forward, coupling and backward
+ *      passes included -- as ONE cooperative launch with one block per SM: the
+ *      steps are its phases, separated by grid barriers (bounded waits), the
+ *      runs of row-chunk steps as in 1.
+ * A wait that runs out latches HM_ERR_TIMEOUT (hm_sync_status).  Modes 1 and 2
+ * use the warp ranges of launch shape 0 whatever hm_autotune chose, and their
+ * results equal mode 0 with all shapes 0 bit for bit.  Profiling (hm_profile)
+ * always runs mode 0.  Errors: HM_ERR_ARG (enable outside 0..2).
  */
 hm_status hm_persistent(hm_matrix* m, int32_t enable);
 

@@ -69,6 +69,21 @@ struct SeqPhase {
   int32_t rowscale;  // 1: scale the rows by the row-scale vector
 };
 
+// One phase of the whole-product persistent launch (hm_persistent mode 2):
+// the launches of one product run as the phases of ONE cooperative launch,
+// phases separated by grid barriers, runs of row-chunk launches as dataflow.
+enum { PP_GATHER = 0, PP_CDOT = 1, PP_GSUM = 2, PP_FANOUT = 3, PP_RGEMV = 4, PP_RUN = 5 };
+struct ProgPhase {
+  int32_t kind;
+  int32_t off, n;     // GATHER: n entries; CDOT / RGEMV: ranges wbeg[off .. off + n]; GSUM / FANOUT:
+                      // outputs / slots [off, off + n); RUN: SeqPhase entries [off, off + n)
+  int32_t mode;       // RGEMV: output mode; RUN: the run's index
+  int32_t rowscale;   // RGEMV: rows scaled by the row-scale vector
+  int32_t aux;        // FANOUT: vector index of slot 0; RUN: offset of its state (versions, abort, claims)
+  int32_t nchunks;    // RUN: versioned coefficient chunks
+  int32_t pad;
+};
+
 // Dependencies of one piece of a persistent launch, as versions of coefficient
 // chunks (a version counts the emits of the chunk so far in the launch): the
 // piece's multipliers are final once ver[c0] >= v0 (c0 < 0: written before the

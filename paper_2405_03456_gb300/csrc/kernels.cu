@@ -254,6 +254,122 @@ __device__ __forceinline__ void cs_piece_f32(uint32_t sa, int R, int nc, int fla
   }
 }
 
+// Arguments of the column-dot products shared by every range of a launch.
+struct CsArgs {
+  const ItemCopy* cps;
+  const uint8_t* pay;
+  const float2* vec;
+  F2 alpha;
+  F2* partial;
+  float2* vout;
+  int* err;
+};
+
+// One warp's range of column-dot pieces [p0, p0 + n): a ring of NS shared-memory
+// stages (SSTR bytes apart) filled by bulk copies (piece + its input segment
+// when it changes), decoded and reduced.  it counts the stages this warp has
+// used before (their mbarrier phases) and is advanced.  Returns false if a
+// copy did not arrive in time (error latched).
+template <int TIER, int NS, int SSTR>
+__device__ __forceinline__ bool cs_range(const CsArgs& A, int p0, int n, uint8_t* ring, uint64_t* bars, int lane,
+                                         uint32_t& it) {
+  const uint32_t sring = smem_u32(ring);
+  const uint32_t it0 = it;
+  // copy descriptors, 32 per batch: lane l holds entry dbase + l (dc) and dbase + 32 + l (dn)
+  const ItemCopy zero{0, 0, -1, 0};
+  ItemCopy dc = lane < n ? A.cps[p0 + lane] : zero;
+  ItemCopy dn = 32 + lane < n ? A.cps[p0 + 32 + lane] : zero;
+  int dbase = 0, issued = 0;
+  const uint64_t pol = policy_evict_first();
+  int32_t last_vin = -1, last_rows = -1;   // input segment of the last issued piece
+  auto issue = [&](int i) {   // all lanes; copies piece i (and its input segment if new) into stage (it0 + i) % NS
+    if (i - dbase >= 32) {
+      dc = dn;
+      dbase += 32;
+      dn = dbase + 32 + lane < n ? A.cps[p0 + dbase + 32 + lane] : zero;
+    }
+    const int sl = i - dbase;
+    const uint32_t off16 = __shfl_sync(HM_FULL, dc.off16, sl);
+    const uint32_t bytes = __shfl_sync(HM_FULL, dc.bytes, sl);
+    const int32_t vin = __shfl_sync(HM_FULL, dc.vin, sl);
+    const int32_t nrows = __shfl_sync(HM_FULL, dc.nrows, sl);
+    const bool newx = vin != last_vin || nrows != last_rows;
+    last_vin = vin;
+    last_rows = nrows;
+    if (lane == 0) {
+      const uint32_t st_i = (it0 + (uint32_t)i) % NS;
+      uint8_t* st = ring + st_i * SSTR;
+      uint64_t* bar = &bars[st_i];
+      const uint32_t pb = pad16u(bytes);
+      const int64_t x0 = (int64_t)vin & ~int64_t(1);
+      const uint32_t xb = newx ? pad16u((uint32_t)((vin - x0) + nrows) * 8u) : 0u;
+      fence_proxy_async();
+      mbar_expect_tx(bar, pb + xb);
+      bulk_g2s_hint(st, A.pay + (uint64_t)off16 * 16u, pb, bar, pol);
+      if (newx) bulk_g2s(st + A_XOFF, A.vec + x0, xb, bar);
+    }
+    issued = i + 1;
+  };
+  for (int i = 0; i < NS && i < n; ++i) issue(i);
+  constexpr int RL = RPL;   // rows per lane
+  float xh[RL], xl[RL];
+  int32_t xv = -1, xr = -1;
+  for (int i = 0; i < n; ++i) {
+    const uint32_t u = it0 + (uint32_t)i;
+    const uint32_t s = u % NS;
+    if (!mbar_wait(&bars[s], (u / NS) & 1u)) {
+      latch_error(A.err, 99);
+      drain<NS>(bars, i + 1, issued, it0);
+      it = it0 + (uint32_t)issued;
+      return false;
+    }
+    const uint32_t sa = sring + s * (uint32_t)SSTR;
+    const uint4 hw = lds128(sa);                       // CPieceHdr
+    const int32_t hvin = (int32_t)hw.x;
+    const int R = (int)(hw.y & 0xffffu), nc = (int)(hw.y >> 16);
+    const uint32_t fb = hw.z & 0xffffu, flags = hw.z >> 16;
+    if (hvin != xv || R != xr) {   // a new input segment came with this piece
+      const uint32_t xa = sa + A_XOFF + 8u * (uint32_t)(hvin & 1);
+      const int q = lane % (SEG_ROWS / RL);
+#pragma unroll
+      for (int k = 0; k < RL; ++k) {
+        const int r = RL * q + k;
+        uint2 v = make_uint2(0u, 0u);
+        if (r < R) v = lds64(xa + 8u * r);
+        xh[k] = __uint_as_float(v.x);
+        xl[k] = __uint_as_float(v.y);
+      }
+      xv = hvin;
+      xr = R;
+    }
+    if constexpr (TIER == TIER_F32) {
+      const float2 x2[4] = {make_float2(xh[0], xh[1]), make_float2(xh[2], xh[3]), make_float2(xh[4], xh[5]),
+                            make_float2(xh[6], xh[7])};
+      switch (fb) {
+#define HM_CS(FF_, BB_) \
+  case ((FF_) << 4) | (BB_): cs_piece_f32<FF_, BB_>(sa, R, nc, (int)flags, x2, lane, A.alpha, A.partial, A.vout); break;
+        HM_FORMATS(HM_CS)
+#undef HM_CS
+        default:
+          latch_error(A.err, 1);
+      }
+    } else {
+      switch (fb) {
+#define HM_CS(FF_, BB_) \
+  case ((FF_) << 4) | (BB_): cs_piece<TIER, FF_, BB_, RL>(sa, R, nc, (int)flags, xh, xl, lane, A.alpha, A.partial, A.vout); break;
+        HM_FORMATS(HM_CS)
+#undef HM_CS
+        default:
+          latch_error(A.err, 1);
+      }
+    }
+    __syncwarp();
+    if (issued < n) issue(issued);
+  }
+  it = it0 + (uint32_t)n;
+  return true;
+}
+
 template <int TIER, int NW, int NS>
 __global__ void __launch_bounds__(NW * 32, 1)
     k_cstream(const ItemCopy* __restrict__ cps, const int32_t* __restrict__ wbeg, int nwt,
@@ -267,102 +383,16 @@ __global__ void __launch_bounds__(NW * 32, 1)
   const int p0 = wbeg[gw], n = wbeg[gw + 1] - p0;
   if (n <= 0) return;
   uint8_t* ring = smem + (size_t)warp * NS * A_STAGE;
-  const uint32_t sring = smem_u32(ring);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + (size_t)NW * NS * A_STAGE) + warp * NS;
   if (lane == 0) {
     for (int s = 0; s < NS; ++s) mbar_init(&bars[s], 1);
     mbar_init_fence();
   }
   __syncwarp();
-  // copy descriptors, 32 per batch: lane l holds entry dbase + l (dc) and dbase + 32 + l (dn)
-  const ItemCopy zero{0, 0, -1, 0};
-  ItemCopy dc = lane < n ? cps[p0 + lane] : zero;
-  ItemCopy dn = 32 + lane < n ? cps[p0 + 32 + lane] : zero;
-  int dbase = 0, issued = 0;
-  const uint64_t pol = policy_evict_first();
-  int32_t last_vin = -1, last_rows = -1;   // input segment of the last issued piece
-  auto issue = [&](int i) {   // all lanes; copies piece i (and its input segment if new) into stage i % NS
-    if (i - dbase >= 32) {
-      dc = dn;
-      dbase += 32;
-      dn = dbase + 32 + lane < n ? cps[p0 + dbase + 32 + lane] : zero;
-    }
-    const int sl = i - dbase;
-    const uint32_t off16 = __shfl_sync(HM_FULL, dc.off16, sl);
-    const uint32_t bytes = __shfl_sync(HM_FULL, dc.bytes, sl);
-    const int32_t vin = __shfl_sync(HM_FULL, dc.vin, sl);
-    const int32_t nrows = __shfl_sync(HM_FULL, dc.nrows, sl);
-    const bool newx = vin != last_vin || nrows != last_rows;
-    last_vin = vin;
-    last_rows = nrows;
-    if (lane == 0) {
-      uint8_t* st = ring + (i % NS) * A_STAGE;
-      uint64_t* bar = &bars[i % NS];
-      const uint32_t pb = pad16u(bytes);
-      const int64_t x0 = (int64_t)vin & ~int64_t(1);
-      const uint32_t xb = newx ? pad16u((uint32_t)((vin - x0) + nrows) * 8u) : 0u;
-      fence_proxy_async();
-      mbar_expect_tx(bar, pb + xb);
-      bulk_g2s_hint(st, pay + (uint64_t)off16 * 16u, pb, bar, pol);
-      if (newx) bulk_g2s(st + A_XOFF, vec + x0, xb, bar);
-    }
-    issued = i + 1;
-  };
   pdl_wait();   // the input segments come from the previous kernel
-  for (int i = 0; i < NS && i < n; ++i) issue(i);
-  constexpr int RL = RPL;   // rows per lane
-  float xh[RL], xl[RL];
-  int32_t xv = -1, xr = -1;
-  for (int i = 0; i < n; ++i) {
-    const int s = i % NS;
-    if (!mbar_wait(&bars[s], (uint32_t)((i / NS) & 1))) {
-      latch_error(err, 99);
-      drain<NS>(bars, i + 1, issued);
-      return;
-    }
-    const uint32_t sa = sring + (uint32_t)(s * A_STAGE);
-    const uint4 hw = lds128(sa);                       // CPieceHdr
-    const int32_t hvin = (int32_t)hw.x;
-    const int R = (int)(hw.y & 0xffffu), nc = (int)(hw.y >> 16);
-    const uint32_t fb = hw.z & 0xffffu, flags = hw.z >> 16;
-    if (hvin != xv || R != xr) {   // a new input segment came with this piece
-      const uint32_t xa = sa + A_XOFF + 8u * (uint32_t)(hvin & 1);
-      const int q = lane % (SEG_ROWS / RL);
-#pragma unroll
-      for (int u = 0; u < RL; ++u) {
-        const int r = RL * q + u;
-        uint2 v = make_uint2(0u, 0u);
-        if (r < R) v = lds64(xa + 8u * r);
-        xh[u] = __uint_as_float(v.x);
-        xl[u] = __uint_as_float(v.y);
-      }
-      xv = hvin;
-      xr = R;
-    }
-    if constexpr (TIER == TIER_F32) {
-      const float2 x2[4] = {make_float2(xh[0], xh[1]), make_float2(xh[2], xh[3]), make_float2(xh[4], xh[5]),
-                            make_float2(xh[6], xh[7])};
-      switch (fb) {
-#define HM_CS(FF_, BB_) \
-  case ((FF_) << 4) | (BB_): cs_piece_f32<FF_, BB_>(sa, R, nc, (int)flags, x2, lane, alpha, partial, vout); break;
-        HM_FORMATS(HM_CS)
-#undef HM_CS
-        default:
-          latch_error(err, 1);
-      }
-    } else {
-    switch (fb) {
-#define HM_CS(FF_, BB_) \
-  case ((FF_) << 4) | (BB_): cs_piece<TIER, FF_, BB_, RL>(sa, R, nc, (int)flags, xh, xl, lane, alpha, partial, vout); break;
-      HM_FORMATS(HM_CS)
-#undef HM_CS
-      default:
-        latch_error(err, 1);
-    }
-    }
-    __syncwarp();
-    if (issued < n) issue(issued);
-  }
+  const CsArgs A{cps, pay, vec, alpha, partial, vout, err};
+  uint32_t it = 0;
+  cs_range<TIER, NS, A_STAGE>(A, p0, n, ring, bars, lane, it);
 }
 
 // ---------------------------------------------------------------- row chunks (phase C)
@@ -822,15 +852,13 @@ __global__ void __launch_bounds__(NW * 32, 1)
 // FAN_PER slots per thread, all index loads, then all gathers, then all stores
 // (few waves of threads, several loads in flight per thread).
 constexpr int FAN_PER = 4;
-__global__ void k_fanout(const int32_t* __restrict__ src, int n, float2* __restrict__ dst,
-                         const float2* __restrict__ vec) {
-  pdl_trigger();
-  pdl_wait();
-  const int base = blockIdx.x * blockDim.x * FAN_PER + threadIdx.x;
+// Slots [base, base + FAN_PER * stride) of thread `base`: the fan-out work of one thread.
+__device__ __forceinline__ void fanout_one(const int32_t* __restrict__ src, int n, float2* __restrict__ dst,
+                                           const float2* __restrict__ vec, int base, int stride) {
   int ix[FAN_PER];
 #pragma unroll
   for (int k = 0; k < FAN_PER; ++k) {
-    const int i = base + k * blockDim.x;
+    const int i = base + k * stride;
     ix[k] = i < n ? __ldg(src + i) : -1;
   }
   float2 v[FAN_PER];
@@ -838,7 +866,14 @@ __global__ void k_fanout(const int32_t* __restrict__ src, int n, float2* __restr
   for (int k = 0; k < FAN_PER; ++k) v[k] = ix[k] >= 0 ? vec[ix[k]] : make_float2(0.f, 0.f);
 #pragma unroll
   for (int k = 0; k < FAN_PER; ++k)
-    if (ix[k] >= 0) dst[base + k * blockDim.x] = v[k];
+    if (ix[k] >= 0) dst[base + k * stride] = v[k];
+}
+
+__global__ void k_fanout(const int32_t* __restrict__ src, int n, float2* __restrict__ dst,
+                         const float2* __restrict__ vec) {
+  pdl_trigger();
+  pdl_wait();
+  fanout_one(src, n, dst, vec, blockIdx.x * blockDim.x * FAN_PER + threadIdx.x, blockDim.x);
 }
 
 // ---------------------------------------------------------------- segment sums (phase A2)
@@ -846,12 +881,12 @@ __global__ void k_fanout(const int32_t* __restrict__ src, int n, float2* __restr
 // p0 + k + GS_LANES, ... (consecutive lanes read consecutive partials), then a
 // fixed xor tree combines the lanes (deterministic order).
 constexpr int GS_LANES = 8;
-__global__ void k_gsum(const GsumOut* __restrict__ outs, int nouts, const F2* __restrict__ pscale,
-                       const F2* __restrict__ partial, F2 alpha, float2* __restrict__ vout) {
-  pdl_trigger();
-  pdl_wait();
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  const int i = t / GS_LANES, k = t % GS_LANES;
+// Output t / GS_LANES, lane t % GS_LANES of its group (whole warps call this).
+__device__ __forceinline__ void gsum_one(const GsumOut* __restrict__ outs, int nouts, const F2* __restrict__ pscale,
+                                         const F2* __restrict__ partial, F2 alpha, float2* __restrict__ vout,
+                                         int64_t t) {
+  const int64_t i = t / GS_LANES;
+  const int k = (int)(t % GS_LANES);
   const bool on = i < nouts;
   GsumOut O{};
   if (on) O = outs[i];
@@ -880,6 +915,13 @@ __global__ void k_gsum(const GsumOut* __restrict__ outs, int nouts, const F2* __
   vout[O.out] = make_float2(s.hi, s.lo);
 }
 
+__global__ void k_gsum(const GsumOut* __restrict__ outs, int nouts, const F2* __restrict__ pscale,
+                       const F2* __restrict__ partial, F2 alpha, float2* __restrict__ vout) {
+  pdl_trigger();
+  pdl_wait();
+  gsum_one(outs, nouts, pscale, partial, alpha, vout, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+}
+
 // ---------------------------------------------------------------- gather x
 __global__ void k_gather(const double* __restrict__ x, const int32_t* __restrict__ perm, int n,
                          float2* __restrict__ xo) {
@@ -888,6 +930,171 @@ __global__ void k_gather(const double* __restrict__ x, const int32_t* __restrict
   if (i >= n) return;
   FF f = ff_from_d(x[perm[i]]);
   xo[i] = make_float2(f.hi, f.lo);
+}
+
+constexpr int SEQ_NW = RS_CFG_WARPS[SEQ_SHAPE], SEQ_NS = RS_CFG_STAGES[SEQ_SHAPE];   // persistent phases
+
+// ---------------------------------------------------------------- the whole product as one launch
+// All launches of a product (gather, column dots, segment sums, fan-outs, row
+// chunks) as the phases of ONE cooperative launch of SEQ_NW warps per block,
+// one block per SM.  Phases follow each other at grid barriers (every warp of
+// every block takes part in each barrier, also after an error, so none can be
+// left waiting); a run of row-chunk launches is one dataflow phase as in
+// k_rseq.  The column-dot and row-chunk phases use the warp ranges of launch
+// shape 0, so the result equals the per-launch path with shape 0 bit for bit.
+struct ProgArgs {
+  const ProgPhase* phases;
+  int nphases;
+  const double* x;
+  const ItemCopy* items;
+  const GsumOut* gouts;
+  const F2* pscale;
+  F2* partial;
+  const int32_t* fan;
+  const int32_t* wbeg;
+  const SeqPhase* seqph;
+  const SeqDep* deps;
+  unsigned* state;     // [0]: barrier counter, [1]: abort word, then the runs' versions / abort / claims
+  const F2* rowscale;
+};
+
+// Grid barrier number b (0, 1, ...): the block's warps meet, thread 0 publishes
+// the block's writes (gpu-scope fence) and waits (bounded) until every block
+// has arrived; the warps then see every block's writes.  False after a timeout
+// or an abort elsewhere (the abort word is set, every later wait gives up).
+__device__ bool prog_barrier(unsigned* state, unsigned target) {
+  __shared__ int ok_s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    __threadfence();
+    atomicAdd(state, 1u);
+    for (uint32_t i = 0;; ++i) {
+      unsigned v;
+      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(state) : "memory");
+      if (v >= target) break;
+      if (*(volatile int*)(state + 1) || i >= (1u << 22)) {   // about 2 s of L2 round trips
+        atomicExch(reinterpret_cast<int*>(state + 1), 1);
+        ok = 0;
+        break;
+      }
+    }
+    asm volatile("fence.proxy.async.global;" ::: "memory");   // later bulk copies read what other SMs wrote
+    ok_s = ok;
+  }
+  __syncthreads();
+  return ok_s != 0;
+}
+
+// The range loops of the phases, out of line: each keeps the register
+// allocation it has in its own kernel instead of sharing one across all phases.
+template <int TIER>
+__device__ __noinline__ bool prog_cs(const CsArgs& C, int p0, int n, uint8_t* ring, uint64_t* bars, int lane,
+                                     uint32_t& it) {
+  return cs_range<TIER, SEQ_NS, C_STAGE>(C, p0, n, ring, bars, lane, it);
+}
+
+template <int TIER, int MODE, bool DF>
+__device__ __noinline__ bool prog_rs(const RsArgs& B, int p0, int n, uint8_t* ring, int4* info, uint64_t* bars,
+                                     int lane, uint32_t& it, const DfArgs* D) {
+  return rs_range<TIER, MODE, SEQ_NS, DF>(B, p0, n, ring, info, bars, lane, it, D);
+}
+
+template <int TIER>
+__global__ void __launch_bounds__(SEQ_NW * 32, 1) k_prog(RsArgs A, ProgArgs P) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int gw = blockIdx.x * SEQ_NW + warp, nwarps = gridDim.x * SEQ_NW;
+  const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, nthreads = (int64_t)gridDim.x * blockDim.x;
+  uint8_t* ring;
+  int4* info;
+  uint64_t* bars;
+  rs_ring_init<SEQ_NW, SEQ_NS>(ring, info, bars, warp, lane);
+  uint32_t it = 0;
+  bool good = true;        // this warp has not hit a timeout
+  unsigned nbar = 0;
+  const CsArgs C{P.items, A.pay, A.vec, A.alpha_ff, P.partial, A.vout, A.err};
+  for (int p = 0; p < P.nphases; ++p) {
+    const ProgPhase Ph = P.phases[p];
+    if (good && !*(volatile int*)(P.state + 1)) {
+      switch (Ph.kind) {
+        case PP_GATHER:
+          for (int64_t i = gtid; i < Ph.n; i += nthreads) {
+            const FF f = ff_from_d(P.x[A.perm[i]]);
+            A.vout[i] = make_float2(f.hi, f.lo);
+          }
+          break;
+        case PP_CDOT:
+          for (int r = gw; r < Ph.n; r += nwarps) {
+            const int p0 = P.wbeg[Ph.off + r], n = P.wbeg[Ph.off + r + 1] - p0;
+            if (n > 0 && !prog_cs<TIER>(C, p0, n, ring, bars, lane, it)) good = false;
+          }
+          break;
+        case PP_GSUM: {
+          const int64_t total = (int64_t)Ph.n * GS_LANES;
+          for (int64_t t0 = (int64_t)gw * 32; t0 < total; t0 += (int64_t)nwarps * 32)
+            gsum_one(P.gouts + Ph.off, Ph.n, P.pscale, P.partial, A.alpha_ff, A.vout, t0 + lane);
+          break;
+        }
+        case PP_FANOUT: {
+          const int64_t per = (int64_t)blockDim.x * FAN_PER;
+          for (int64_t c = blockIdx.x; c * per < Ph.n; c += gridDim.x)
+            fanout_one(P.fan + Ph.off, Ph.n, A.vout + Ph.aux + Ph.off, A.vec, (int)(c * per) + threadIdx.x,
+                       blockDim.x);
+          break;
+        }
+        case PP_RGEMV: {
+          RsArgs B = A;
+          B.rowscale = Ph.rowscale ? P.rowscale : nullptr;
+          for (int r = gw; r < Ph.n && good; r += nwarps) {
+            const int p0 = P.wbeg[Ph.off + r], n = P.wbeg[Ph.off + r + 1] - p0;
+            if (n <= 0) continue;
+            bool ok;
+            if (Ph.mode == MODE_Y)
+              ok = prog_rs<TIER, MODE_Y, false>(B, p0, n, ring, info, bars, lane, it, nullptr);
+            else if (Ph.mode == MODE_VEC)
+              ok = prog_rs<TIER, MODE_VEC, false>(B, p0, n, ring, info, bars, lane, it, nullptr);
+            else
+              ok = prog_rs<TIER, MODE_VEC_ADD, false>(B, p0, n, ring, info, bars, lane, it, nullptr);
+            good = good && ok;
+          }
+          break;
+        }
+        case PP_RUN: {
+          unsigned* st = P.state + Ph.aux;
+          const DfArgs D{P.deps, st, reinterpret_cast<int*>(st + Ph.nchunks), st + Ph.nchunks + 1};
+          for (int q = 0; q < Ph.n && good; ++q) {
+            const SeqPhase S = P.seqph[Ph.off + q];
+            RsArgs B = A;
+            B.rowscale = S.rowscale ? P.rowscale : nullptr;
+            for (;;) {   // ranges of this phase are handed out in order to whichever warp is free
+              int r = 0;
+              if (lane == 0) r = (int)atomicAdd(D.claim + q, 1u);
+              r = __shfl_sync(HM_FULL, r, 0);
+              if (r >= S.nw) break;
+              const int p0 = P.wbeg[S.woff + r], n = P.wbeg[S.woff + r + 1] - p0;
+              if (n <= 0) continue;
+              bool ok;
+              if (S.mode == MODE_Y)
+                ok = prog_rs<TIER, MODE_Y, true>(B, p0, n, ring, info, bars, lane, it, &D);
+              else if (S.mode == MODE_VEC)
+                ok = prog_rs<TIER, MODE_VEC, true>(B, p0, n, ring, info, bars, lane, it, &D);
+              else
+                ok = prog_rs<TIER, MODE_VEC_ADD, true>(B, p0, n, ring, info, bars, lane, it, &D);
+              if (!ok) {
+                good = false;
+                break;
+              }
+            }
+          }
+          break;
+        }
+        default:
+          latch_error(A.err, 2);
+      }
+    }
+    if (!good && lane == 0) atomicExch(reinterpret_cast<int*>(P.state + 1), 1);
+    if (p + 1 < P.nphases && !prog_barrier(P.state, ++nbar * gridDim.x)) good = false;
+  }
 }
 
 // ---------------------------------------------------------------- K0: bit-exact decode to FP64
@@ -1007,7 +1214,6 @@ constexpr size_t rs_smem() {
 }
 #define HM_CS_CFGS(X) X(0, 16, 2) X(1, 10, 3) X(2, 7, 4)
 #define HM_RS_CFGS(X) X(0, 16, 2) X(1, 11, 3) X(2, 8, 4)
-constexpr int SEQ_NW = RS_CFG_WARPS[SEQ_SHAPE], SEQ_NS = RS_CFG_STAGES[SEQ_SHAPE];   // persistent phases
 #define HM_CHK_CS(I, NW, NS)                                                                      \
   static_assert(CS_CFG_WARPS[I] == NW && CS_CFG_STAGES[I] == NS, "column-dot launch shapes");     \
   static_assert(cs_smem<NW, NS>() <= 227 * 1024, "shared memory per block");
@@ -1037,6 +1243,8 @@ cudaError_t kernels_init() {
   HM_RS_CFGS(HM_INIT)
   HM_ATTR((k_rseq<TIER_F32, SEQ_NW, SEQ_NS>), (rs_smem<SEQ_NW, SEQ_NS>()))
   HM_ATTR((k_rseq<TIER_FF, SEQ_NW, SEQ_NS>), (rs_smem<SEQ_NW, SEQ_NS>()))
+  HM_ATTR((k_prog<TIER_F32>), (rs_smem<SEQ_NW, SEQ_NS>()))
+  HM_ATTR((k_prog<TIER_FF>), (rs_smem<SEQ_NW, SEQ_NS>()))
 #undef HM_INIT_CS
 #undef HM_INIT
 #undef HM_ATTR
@@ -1162,6 +1370,47 @@ cudaError_t launch_rseq(int tier, int nblk, const SeqPhase* phases, int nph, con
   else
     e = cudaLaunchKernelEx(&cfg, k_rseq<TIER_FF, SEQ_NW, SEQ_NS>, A, phases, nph, wbeg, rowscale, D);
   return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+// The whole product as one cooperative launch of nblk blocks (one per SM); the
+// barrier counter, abort word and the runs' state (nstate words) are zeroed first.
+cudaError_t launch_prog(int tier, int nblk, const ProgPhase* phases, int nphases, const double* x,
+                        const ItemCopy* items, const GsumOut* gouts, const F2* pscale, F2* partial,
+                        const int32_t* fan, const PieceCopy* pieces, const int32_t* wbeg, const SeqPhase* seqph,
+                        const SeqDep* deps, unsigned* state, int nstate, const uint8_t* pay, float2* vec,
+                        double alpha, double beta, double* y, const int32_t* perm, const F2* rowscale, F2* fix,
+                        int32_t* fixcnt, const Split* splits, int* err, cudaStream_t st) {
+  if (nphases <= 0 || nblk <= 0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(state, 0, (size_t)nstate * sizeof(unsigned), st);
+  if (e != cudaSuccess) return e;
+  const F2 aff{(float)alpha, (float)(alpha - (double)(float)alpha)};
+  const RsArgs A{pieces, pay, vec, alpha, aff, beta, y, perm, vec, nullptr, fix, fixcnt, splits, err};
+  const ProgArgs P{phases, nphases, x, items, gouts, pscale, partial, fan, wbeg, seqph, deps, state, rowscale};
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)nblk);
+  cfg.blockDim = dim3(SEQ_NW * 32);
+  cfg.dynamicSmemBytes = rs_smem<SEQ_NW, SEQ_NS>();
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeCooperative;
+  at[0].val.cooperative = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  if (tier == TIER_F32)
+    e = cudaLaunchKernelEx(&cfg, k_prog<TIER_F32>, A, P);
+  else
+    e = cudaLaunchKernelEx(&cfg, k_prog<TIER_FF>, A, P);
+  return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+int prog_max_blocks() {
+  int per_sm = 0, dev = 0, nsm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_prog<TIER_F32>, SEQ_NW * 32,
+                                                    rs_smem<SEQ_NW, SEQ_NS>()) != cudaSuccess)
+    return 0;
+  return per_sm * nsm;
 }
 
 // Blocks of the persistent launch that fit on the device at once (0 if none).

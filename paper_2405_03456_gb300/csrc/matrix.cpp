@@ -32,6 +32,13 @@ cudaError_t launch_rseq(int tier, int nblk, const SeqPhase* phases, int nph, con
                         const Split* splits, const SeqDep* deps, unsigned* ver, int nchunks, int* err,
                         cudaStream_t st);
 int rseq_max_blocks();
+cudaError_t launch_prog(int tier, int nblk, const ProgPhase* phases, int nphases, const double* x,
+                        const ItemCopy* items, const GsumOut* gouts, const F2* pscale, F2* partial,
+                        const int32_t* fan, const PieceCopy* pieces, const int32_t* wbeg, const SeqPhase* seqph,
+                        const SeqDep* deps, unsigned* state, int nstate, const uint8_t* pay, float2* vec,
+                        double alpha, double beta, double* y, const int32_t* perm, const F2* rowscale, F2* fix,
+                        int32_t* fixcnt, const Split* splits, int* err, cudaStream_t st);
+int prog_max_blocks();
 cudaError_t mr_init();
 cudaError_t launch_gather_mr(const double* x, int64_t ldx, int r, const int32_t* perm, int n, float* v,
                              cudaStream_t st);
@@ -113,7 +120,10 @@ struct hm_matrix {
   int nsm = 0;
   // persistent launches: runs [first, last) of consecutive row-chunk launches
   // executed as the phases of one cooperative launch (dataflow between phases)
-  bool fuse = true;
+  int fuse = 1;                // 0 per launch, 1 runs of row-chunk launches fused, 2 the whole product
+  DevArr<ProgPhase> d_prog;    // phases of the whole-product launch
+  unsigned* d_pstate = nullptr;  // its barrier counter, abort word and the runs' state
+  int pstate_n = 0;
   struct Run {
     size_t first, last;
     int64_t ph0;   // first phase in d_phases
@@ -177,6 +187,10 @@ struct hm_matrix {
     d_rowscale_ff.release();
     d_phases.release();
     d_deps.release();
+    d_prog.release();
+    if (d_pstate) cudaFree(d_pstate);
+    d_pstate = nullptr;
+    pstate_n = 0;
     runs.clear();
     if (d_ver) cudaFree(d_ver);
     d_ver = nullptr;
@@ -305,6 +319,51 @@ hm_status upload(hm_matrix* M) {
       for (const hm_matrix::Run& R : M->runs) maxph = std::max(maxph, (int)(R.last - R.first));
       if ((e = cudaMalloc(&M->d_ver, (size_t)(maxchunks + 1 + maxph) * sizeof(unsigned))) != cudaSuccess)
         return cuda_status(e);
+    }
+  }
+  // the whole product as one launch (hm_persistent mode 2): one phase per
+  // launch, one per run of row-chunk launches; state = barrier counter, abort
+  // word, then per run its versions, abort word and range counters
+  if (prog_max_blocks() >= M->nsm && M->nsm > 0) {
+    std::vector<ProgPhase> pp;
+    int64_t nstate = 2;
+    const auto& Ls = P.launches;
+    size_t ri = 0;
+    for (size_t li = 0; li < Ls.size();) {
+      const Launch& L = Ls[li];
+      ProgPhase ph{};
+      if (ri < M->runs.size() && M->runs[ri].first == li) {
+        const hm_matrix::Run& R = M->runs[ri];
+        ph.kind = PP_RUN;
+        ph.off = (int32_t)R.ph0;
+        ph.n = (int32_t)(R.last - R.first);
+        ph.mode = (int32_t)ri;
+        ph.aux = (int32_t)nstate;
+        ph.nchunks = R.nchunks;
+        nstate += R.nchunks + 1 + ph.n;
+        pp.push_back(ph);
+        li = R.last;
+        ++ri;
+        continue;
+      }
+      switch (L.kind) {
+        case Launch::GATHER: ph = ProgPhase{PP_GATHER, 0, (int32_t)L.n, 0, 0, 0, 0, 0}; break;
+        case Launch::CDOT: ph = ProgPhase{PP_CDOT, (int32_t)L.woff[0], L.nw[0], 0, 0, 0, 0, 0}; break;
+        case Launch::GSUM: ph = ProgPhase{PP_GSUM, (int32_t)L.off, (int32_t)L.n, 0, 0, 0, 0, 0}; break;
+        case Launch::FANOUT:
+          ph = ProgPhase{PP_FANOUT, (int32_t)L.off, (int32_t)L.n, 0, 0, (int32_t)P.fan_base, 0, 0};
+          break;
+        case Launch::RGEMV:
+          ph = ProgPhase{PP_RGEMV, (int32_t)L.woff[SEQ_SHAPE], L.nw[SEQ_SHAPE], L.mode, L.use_rowscale ? 1 : 0, 0, 0, 0};
+          break;
+      }
+      pp.push_back(ph);
+      ++li;
+    }
+    if (!pp.empty() && nstate < INT32_MAX) {
+      if ((e = M->d_prog.upload(pp)) != cudaSuccess) return cuda_status(e);
+      if ((e = cudaMalloc(&M->d_pstate, (size_t)nstate * sizeof(unsigned))) != cudaSuccess) return cuda_status(e);
+      M->pstate_n = (int)nstate;
     }
   }
   return HM_OK;
@@ -540,6 +599,16 @@ static hm_status run_all(hm_matrix* M, double alpha, const double* x, int64_t ld
 static hm_status run_program(hm_matrix* M, double alpha, const double* x, double beta, double* y,
                              cudaStream_t st) {
   const auto& Ls = M->prog.launches;
+  if (M->fuse == 2 && !M->prof && M->d_pstate) {   // the whole product as one launch
+    Program& P = M->prog;
+    return launch_prog(P.tier, M->nsm, M->d_prog.p, (int)M->d_prog.n, x, M->d_items.p, M->d_gout.p, M->d_pscale.p,
+                       M->d_part, M->d_fan.p, M->d_pieces.p + (size_t)SEQ_SHAPE * P.npieces, M->d_wbeg.p,
+                       M->d_phases.p, M->d_deps.p, M->d_pstate, M->pstate_n, M->d_pay.p, M->d_vec, alpha, beta, y,
+                       M->d_perm.p, M->d_rowscale_ff.p, M->d_fix, M->d_fixcnt, M->d_splits.p, M->d_err,
+                       st) == cudaSuccess
+               ? HM_OK
+               : HM_ERR_CUDA;
+  }
   size_t ri = 0;
   for (size_t li = 0; li < Ls.size(); ++li) {
     const Launch& L = Ls[li];
@@ -619,7 +688,8 @@ hm_status hm_graph(hm_matrix* M, int32_t enable) {
 hm_status hm_persistent(hm_matrix* M, int32_t enable) {
   if (!M) return HM_ERR_ARG;
   std::lock_guard<std::mutex> g(M->mu);
-  M->fuse = enable != 0;
+  if (enable < 0 || enable > 2) return HM_ERR_ARG;
+  M->fuse = enable;
   M->drop_graph();
   return HM_OK;
 }

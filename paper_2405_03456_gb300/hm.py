@@ -220,8 +220,8 @@ def hm_graph(h: int, enable: bool) -> None:
     check(load().hm_graph(h, 1 if enable else 0), "hm_graph")
 
 
-def hm_persistent(h: int, enable: bool) -> None:
-    check(load().hm_persistent(h, 1 if enable else 0), "hm_persistent")
+def hm_persistent(h: int, mode: int) -> None:
+    check(load().hm_persistent(h, int(mode)), "hm_persistent")
 
 
 def hm_autotune(h: int, reps: int = 5, stream: int = 0) -> None:
@@ -391,7 +391,9 @@ class HMatrix:
         return self
 
     def persistent(self, enable=True):
-        hm_persistent(self.h, enable)
+        """0 / False: one launch per step; 1 / True: runs of row-chunk steps fused
+        (the default); 2: the whole product as one persistent launch."""
+        hm_persistent(self.h, int(enable))
         return self
 
     def autotune(self, reps=5, stream=0):

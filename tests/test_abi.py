@@ -80,6 +80,7 @@ def test_newer_entry_points_check_arguments_and_order(lib):
         # built but not compressed: call order violated, nothing reaches the device
         assert lib.hm_matvec_adjoint(h, 1.0, buf.ctypes.data, 64, 0.0, buf.ctypes.data, 64, 1, None) == 4
         assert lib.hm_matvec_adjoint(h, 1.0, buf.ctypes.data, 64, 0.0, buf.ctypes.data, 64, 65, None) == 1
-        assert lib.hm_persistent(h, 0) == 0 and lib.hm_persistent(h, 1) == 0
+        assert lib.hm_persistent(h, 0) == 0 and lib.hm_persistent(h, 1) == 0 and lib.hm_persistent(h, 2) == 0
+        assert lib.hm_persistent(h, 3) == 1 and lib.hm_persistent(h, -1) == 1
     finally:
         assert lib.hm_free(h) == 0

@@ -223,22 +223,25 @@ def test_launch_shapes_and_autotune(hm, problem, fmt):
         M.close()
 
 
-@pytest.mark.parametrize("fmt", ["h", "uh", "h2"])
+@pytest.mark.parametrize("fmt", ["h", "uh", "h2", "uh_sep"])
 @pytest.mark.parametrize("eps", [1e-6, 1e-8])
 def test_persistent_launch_equals_per_launch(hm, problem, fmt, eps):
-    """The persistent form (runs of row-chunk launches and fan-outs as phases of
-    one cooperative launch with grid barriers) gives the per-launch result bit
-    for bit (same warp ranges of shape 0, same order of every sum), within 4 eps
-    of the oracle, also replayed from a CUDA graph."""
+    """The persistent forms -- runs of row-chunk launches as one dataflow launch
+    (mode 1), and the whole product, forward, coupling and backward passes
+    included, as ONE cooperative launch with grid barriers between its phases
+    (mode 2) -- give the per-launch result bit for bit (same warp ranges of
+    shape 0, same order of every sum), within 4 eps of the oracle, also
+    replayed from a CUDA graph."""
     pts, x, y0 = problem
-    ref = oracle_ref(pts, fmt, eps, x[:, 0], 0.75, y0[:, 0], -0.5)
+    ref = oracle_ref(pts, "uh" if fmt == "uh_sep" else fmt, eps, x[:, 0], 0.75, y0[:, 0], -0.5)
     M = hm.HMatrix(pts, "laplace", 32, 2.0, fmt, eps)
     try:
         M.compress(eps, "aflp")
         M.set_launch_shapes(0)
         xd = torch.from_numpy(x[:, 0].copy()).cuda()
         outs = []
-        for persistent, graph in ((False, False), (True, False), (True, True), (True, True)):
+        for persistent, graph in ((0, False), (1, False), (1, True), (1, True), (2, False), (2, True), (2, True),
+                                  (0, False)):
             M.persistent(persistent)
             M.graph(graph)
             yd = torch.from_numpy(y0[:, 0].copy()).cuda()
