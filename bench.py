@@ -467,9 +467,16 @@ def gpu_arm(args, rank, world):
             ab = info["bytes_alg"]
             per, total = time_variant(torch, M, x, y, args.steps, args.warmup, stream, world)
             med = statistics.median(per)
+            mode = M.persistent_mode()
             fmt_results[(fmt, codec)] = {"ms_p50": med, "ms_p99": pct(per, 0.99), "gbs": ab / (med * 1e-3) / 1e9,
                                          "payload_bytes": info["bytes_payload"], "value_bytes": info["bytes_values"],
-                                         "fp64_bytes": info["bytes_fp64"], "launches": info["nlaunches"]}
+                                         "fp64_bytes": info["bytes_fp64"], "launches": info["nlaunches"],
+                                         "persistent_mode": mode}
+            if codec != "none":   # the whole product as ONE persistent launch (forward, coupling, backward)
+                M.persistent(2)
+                per2, _ = time_variant(torch, M, x, y, max(20, min(args.steps, 200)), 3, stream, world)
+                fmt_results[(fmt, codec)]["one_launch_ms_p50"] = statistics.median(per2)
+                M.persistent(mode)
         M.close()
     matern = None
     if args.matern:   # Matern nu = 1.5 covariance on the unit cube: multi-RHS products
@@ -528,7 +535,7 @@ def gpu_arm(args, rank, world):
             M.close()
         adm_legs["workload"] = f"laplace sphere N={na}, leaf 64, H eps=1e-6 AFLP VALR; HODLR and BLR block trees"
     serving = None
-    if args.serving:
+    if args.serving != "none":
         lo, hi = (16384, 1048576) if args.serving == "full" else (16384, 131072)
         serving = serving_leg(torch, hm, lo, hi, args.serving_requests)
     clk = clocks.stop()
@@ -600,6 +607,9 @@ def gpu_arm(args, rank, world):
                                    "ms_p99": round(r["ms_p99"], 4), "payload_mb": round(r["payload_bytes"] / 1e6, 1),
                                    "compression_ratio": round(r["fp64_bytes"] / max(r["value_bytes"], 1), 3),
                                    "hbm_frac": round(r["gbs"] / hbm_peak, 3), "launches": r["launches"],
+                                   "persistent_mode": r["persistent_mode"],
+                                   "one_launch_ms_p50": (round(r["one_launch_ms_p50"], 4)
+                                                         if "one_launch_ms_p50" in r else None),
                                    "speedup_vs_fp64": round(fmt_results[(f, "none")]["ms_p50"] / r["ms_p50"], 3)}
                       for (f, c), r in fmt_results.items()},
     }
@@ -661,12 +671,13 @@ def main():
     ap.add_argument("--no-multi-rhs", action="store_true", help="skip the multi-RHS timings")
     ap.add_argument("--adm-legs", type=int, default=0,
                     help="also time HODLR and BLR H-matrices of the sphere problem at this N (opt-in)")
-    ap.add_argument("--serving", default="small", choices=["", "small", "full"],
+    ap.add_argument("--serving", default="small", choices=["none", "small", "full"],
                     help="serving leg: small = N in [16384, 131072] (default), full = [16384, 1048576] (slow to "
-                         "build), '' = none")
+                         "build), none")
     ap.add_argument("--serving-requests", type=int, default=200)
-    ap.add_argument("--matern", type=int, default=0,
-                    help="also time multi-RHS products on the Matern cube with this many points (slow to build)")
+    ap.add_argument("--matern", type=int, default=524288,
+                    help="Matern cube leg (single and multi-RHS products) with this many points; 0 skips it "
+                         "(the host build takes minutes)")
     ap.add_argument("--cpu-budget-mb", type=float, default=8.0, help="oracle sample per host core (MB of FP64)")
     ap.add_argument("--cpu-passes", type=int, default=10)
     args = ap.parse_args()

@@ -175,6 +175,8 @@ hm_status hm_graph(hm_matrix* m, int32_t enable);
  * always runs mode 0.  Errors: HM_ERR_ARG (enable outside 0..2).
  */
 hm_status hm_persistent(hm_matrix* m, int32_t enable);
+/* hm_persistent_mode -- the mode in use (0, 1 or 2; hm_autotune may change it). */
+hm_status hm_persistent_mode(const hm_matrix* m, int32_t* mode);
 
 /*
  * hm_save -- write m to the file `path`: the built matrix (cluster tree, block
@@ -285,7 +287,8 @@ hm_status hm_codec_decode(const uint8_t* packed, int64_t n, const hm_codec_heade
  * block per SM); which shape a launch uses does not change its result beyond
  * the order of summation inside a chunk.
  * hm_autotune -- time every shape of every such launch `reps` times on
- *   `stream` (on internal zero vectors) and keep the fastest per launch.
+ *   `stream` (on internal zero vectors) and keep the fastest per launch; then
+ *   time the whole product in each hm_persistent mode and keep the fastest.
  *   Allocates two n-vectors for the duration of the call, synchronises the
  *   stream, and discards a captured graph.  Errors: HM_ERR_ARG (reps outside
  *   1..1000), HM_ERR_STATE (not compressed), HM_ERR_CUDA.

@@ -794,6 +794,31 @@ hm_status hm_autotune(hm_matrix* M, int32_t reps, void* stream) {
     }
     L.cfg = bestc;
   }
+  // then how the launches run: one launch per step (with the tuned shapes),
+  // fused runs of row-chunk steps, or the whole product as one launch --
+  // whole products timed, the fastest kept
+  {
+    float best = 0.f;
+    int bestm = M->fuse;
+    for (int mode = 0; mode <= 2 && out == HM_OK; ++mode) {
+      if (mode == 2 && !M->d_pstate) continue;
+      if (mode == 1 && M->runs.empty()) continue;   // same launches as mode 0
+      M->fuse = mode;
+      if (run_program(M, 1.0, x, 0.0, y, st) != HM_OK) out = HM_ERR_CUDA;
+      cudaEventRecord(e0, st);
+      for (int r = 0; r < reps && out == HM_OK; ++r)
+        if (run_program(M, 1.0, x, 0.0, y, st) != HM_OK) out = HM_ERR_CUDA;
+      cudaEventRecord(e1, st);
+      float ms = 0.f;
+      if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+        out = HM_ERR_CUDA;
+      if (mode == 0 || ms < best) {
+        best = ms;
+        bestm = mode;
+      }
+    }
+    M->fuse = bestm;
+  }
   if (cudaStreamSynchronize(st) != cudaSuccess && out == HM_OK) out = HM_ERR_CUDA;
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
@@ -809,6 +834,12 @@ hm_status hm_launch_shapes(const hm_matrix* M, int32_t* shapes, int32_t cap, int
   *count = (int32_t)Ls.size();
   for (int32_t i = 0; i < cap && i < (int32_t)Ls.size(); ++i)
     shapes[i] = (Ls[i].kind == Launch::CDOT || Ls[i].kind == Launch::RGEMV) ? Ls[i].cfg : -1;
+  return HM_OK;
+}
+
+hm_status hm_persistent_mode(const hm_matrix* M, int32_t* mode) {
+  if (!M || !mode) return HM_ERR_ARG;
+  *mode = M->fuse;
   return HM_OK;
 }
 
