@@ -118,7 +118,7 @@ def cpu_model() -> str:
     return platform.processor() or platform.machine()
 
 
-def _cpu_worker(p, nw, budget_bytes, passes, warmup, barrier, q):
+def _cpu_worker(p, nw, budget_bytes, passes, warmup, barrier, q, n=N_DEFAULT, kind="laplace"):
     """One oracle process (one BLAS thread): builds its share of the block
     sample, then times Alg. 1 + Alg. 8 passes over it in step with the others."""
     for k in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
@@ -126,11 +126,11 @@ def _cpu_worker(p, nw, budget_bytes, passes, warmup, barrier, q):
     try:
         import synth
         from oracle import baseline
-        h, ch, nblocks = baseline.sample_h(N_DEFAULT, HEADLINE[0], HEADLINE[1], budget_bytes, part=(p, nw))
+        h, ch, nblocks = baseline.sample_h(n, HEADLINE[0], HEADLINE[1], budget_bytes, part=(p, nw), kind=kind)
         ab = baseline.alg_bytes(ch)
-        xp = synth.rhs(N_DEFAULT)[:, 0][ch.h.ct.perm]
+        xp = synth.rhs(n)[:, 0][ch.h.ct.perm]
         import numpy as np
-        yp = np.zeros(N_DEFAULT)
+        yp = np.zeros(n)
         for _ in range(warmup):
             baseline.run_pass(ch, xp, yp)
         ts = []
@@ -149,7 +149,7 @@ def _cpu_worker(p, nw, budget_bytes, passes, warmup, barrier, q):
 
 
 def cpu_baseline_parallel(budget_mb_per_worker: float, passes: int, warmup: int, workers: int = 0,
-                          timeout: float = 1200.0) -> dict:
+                          timeout: float = 1200.0, n: int = N_DEFAULT, kind: str = "laplace") -> dict:
     """The oracle as it stands on all host cores: nw spawned processes (one per
     core), each timing Alg. 1 + Alg. 8 over a disjoint share of one random
     block sample of the headline workload; a pass is timed from a common
@@ -162,7 +162,7 @@ def cpu_baseline_parallel(budget_mb_per_worker: float, passes: int, warmup: int,
     barrier = ctx.Barrier(nw)
     q = ctx.Queue()
     budget = budget_mb_per_worker * 1e6 * nw
-    procs = [ctx.Process(target=_cpu_worker, args=(p, nw, budget, passes, warmup, barrier, q), daemon=True)
+    procs = [ctx.Process(target=_cpu_worker, args=(p, nw, budget, passes, warmup, barrier, q, n, kind), daemon=True)
              for p in range(nw)]
     t0 = time.perf_counter()
     for pr in procs:
@@ -185,8 +185,9 @@ def cpu_baseline_parallel(budget_mb_per_worker: float, passes: int, warmup: int,
     med = statistics.median(per_pass)
     return {"value": ab / med / 1e9, "unit": "GB/s", "cores": nw, "nproc": nproc, "cpu_model": cpu_model(),
             "kind": "oracle",
-            "sample": (f"{nb} of {res[0][3]} leaf blocks (<= 2^20 entries, random, seed 3) of the N={N_DEFAULT} "
-                       f"sphere H-matrix at eps=1e-6, AFLP VALR, split over {nw} processes (one per core, one "
+            "sample": (f"{nb} of {res[0][3]} leaf blocks (<= 2^20 entries, random, seed 3) of the N={n} "
+                       f"{'sphere Laplace' if kind == 'laplace' else 'cube Matern'} H-matrix at eps=1e-6, AFLP "
+                       f"VALR, split over {nw} processes (one per core, one "
                        f"BLAS thread each); Alg. 1 + Alg. 8 decode in FP64, {passes} passes from a common "
                        f"barrier, {ab / 1e6:.2f} MB algorithmic per pass"),
             "pass_s_median": med, "wall_s": round(time.perf_counter() - t0, 1), "alg_bytes": ab}
@@ -507,6 +508,12 @@ def gpu_arm(args, rank, world):
             M.autotune(3, stream.cuda_stream)
         per, _ = time_variant(torch, M, xm, ym, reps, 3, stream, world)
         matern["fp64_ms_p50"] = round(statistics.median(per), 4)
+        if not args.no_cpu:   # the oracle on the host cores, a block sample of the same matrix
+            try:
+                cb = cpu_baseline_parallel(args.cpu_budget_mb, args.cpu_passes, 1, n=nm, kind="matern")
+                matern["cpu_baseline"] = {k: (round(v, 5) if isinstance(v, float) else v) for k, v in cb.items()}
+            except Exception as e:  # noqa: BLE001
+                matern["cpu_baseline"] = {"value": None, "sample": f"failed: {e}"[:300]}
         matern["speedup_vs_fp64"] = round(statistics.median(per) / single["ms_p50"], 3)
         M.close()
     adm_legs = None

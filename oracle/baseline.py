@@ -25,14 +25,15 @@ from .trees import build_block_tree, build_cluster_tree
 
 
 def sample_h(n: int, eps: float, codec: str, budget_bytes: float, seed: int = 3,
-             leaf: int = 64, eta: float = 2.0, part: tuple[int, int] = (0, 1)):
+             leaf: int = 64, eta: float = 2.0, part: tuple[int, int] = (0, 1), kind: str = "laplace"):
     """Oracle-built compressed H-matrix restricted to a random block sample.
 
+    kind: "laplace" (sphere points) or "matern" (unit-cube points).
     part = (p, P): only every P-th block of the sample, starting at the p-th
     (in block-tree order), so that P processes each build and time a disjoint
     share of the same sample."""
-    pts = synth.sphere_points(n)
-    param = kernels.default_param("laplace", n)
+    pts = synth.sphere_points(n) if kind == "laplace" else synth.cube_points(n)
+    param = kernels.default_param(kind, n)
     ct = build_cluster_tree(pts, leaf)
     blocks = build_block_tree(ct, eta)
     cl = ct.clusters
@@ -55,14 +56,14 @@ def sample_h(n: int, eps: float, codec: str, budget_bytes: float, seed: int = 3,
     for b in sub:
         r = ct.perm[cl[b.row].start:cl[b.row].end]
         c = ct.perm[cl[b.col].start:cl[b.col].end]
-        a = kernels.entries("laplace", pts, r, c, param)
+        a = kernels.entries(kind, pts, r, c, param)
         if not b.adm:
             data.append(a)
             continue
         u, s, vt = np.linalg.svd(a, full_matrices=False)
         k = truncate_rank(s, eps)
         data.append(LowRank(np.asfortranarray(u[:, :k]), s[:k].copy(), np.asfortranarray(vt[:k].T)))
-    h = HMatrix("laplace", param, eps, ct, sub, data, pts)
+    h = HMatrix(kind, param, eps, ct, sub, data, pts)
     ch = compress.compress_h(h, codec)
     return h, ch, len(blocks)
 
