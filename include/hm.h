@@ -224,6 +224,7 @@ typedef struct {
                                (bytes_values) + bytes_inline_meta + 24 n (x read, y read and
                                written, FP64) + 16 per coefficient of the coefficient vectors
                                (t_b / s / t, written once and read once) */
+  int64_t bytes_by_width[8]; /* packed code bytes by code width B = 1 .. 8 (VALR and direct widths) */
 } hm_info_t;
 
 /* hm_info -- sizes and counts of m.  Errors: HM_ERR_ARG. */

@@ -120,6 +120,7 @@ struct hm_matrix {
   int nsm = 0;
   // persistent launches: runs [first, last) of consecutive row-chunk launches
   // executed as the phases of one cooperative launch (dataflow between phases)
+  int64_t width_bytes[8] = {};  // packed code bytes by code width B (set at compress time)
   int fuse = 1;                // 0 per launch, 1 runs of row-chunk launches fused, 2 the whole product
   DevArr<ProgPhase> d_prog;    // phases of the whole-product launch
   unsigned* d_pstate = nullptr;  // its barrier counter, abort word and the runs' state
@@ -504,6 +505,19 @@ hm_status hm_compress(hm_matrix* M, double eps, int32_t codec, int32_t valr) {
   M->valr = valr ? 1 : 0;
   M->eps = eps;
   M->compressed = true;
+  {   // code bytes by width, from the units' inline headers (in slices: bounded memory)
+    std::fill(M->width_bytes, M->width_bytes + 8, 0);
+    const int64_t nu = (int64_t)M->prog.items.size() + M->prog.npieces;
+    std::vector<PackedCol> cols;
+    for (int64_t u0 = 0; u0 < nu; u0 += 4096) {
+      cols.clear();
+      packed_columns(M->prog, u0, std::min(nu, u0 + 4096), cols);
+      for (const PackedCol& c : cols) {
+        const int B = c.fb & 15;
+        if (B >= 1 && B <= 8) M->width_bytes[B - 1] += (int64_t)c.rows * B;
+      }
+    }
+  }
   return HM_OK;
 }
 
@@ -953,6 +967,7 @@ hm_status hm_info(const hm_matrix* M, hm_info_t* o) {
   o->nunits = (int64_t)P.items.size() + P.npieces;
   o->bytes_inline_meta = P.pk.meta_bytes;
   o->bytes_alg = M->compressed ? P.pk.value_bytes + P.pk.meta_bytes + 24 * H.n + 16 * (P.fan_base - H.n) : 0;
+  for (int b = 0; b < 8; ++b) o->bytes_by_width[b] = M->width_bytes[b];
   return HM_OK;
 }
 

@@ -47,7 +47,8 @@ class hm_info_t(C.Structure):
                 ("bytes_payload", C.c_int64), ("bytes_values", C.c_int64), ("bytes_meta", C.c_int64),
                 ("bytes_workspace", C.c_int64), ("bytes_lowrank_fp64", C.c_int64),
                 ("bytes_dense_fp64", C.c_int64), ("nlaunches", C.c_int64), ("tier", C.c_int32),
-                ("nunits", C.c_int64), ("bytes_inline_meta", C.c_int64), ("bytes_alg", C.c_int64)]
+                ("nunits", C.c_int64), ("bytes_inline_meta", C.c_int64), ("bytes_alg", C.c_int64),
+                ("bytes_by_width", C.c_int64 * 8)]
 
 
 class hm_codec_header(C.Structure):
@@ -182,7 +183,9 @@ def hm_free(h: int) -> None:
 def hm_info(h: int) -> dict:
     o = hm_info_t()
     check(load().hm_info(h, C.byref(o)), "hm_info")
-    return {f: getattr(o, f) for f, _ in hm_info_t._fields_}
+    out = {f: getattr(o, f) for f, _ in hm_info_t._fields_}
+    out["bytes_by_width"] = list(o.bytes_by_width)
+    return out
 
 
 def hm_sync_status(h: int, stream: int = 0) -> int:

@@ -67,6 +67,9 @@ def check_resident(hm, M, record=True):
     code, fmt = d_ff["code"], d_ff["fmt"]
     assert np.array_equal(code, d_32["code"]) and np.array_equal(fmt, d_32["fmt"])
     assert code.size > 0
+    # hm_info's code bytes by width are the resident codes' widths
+    widths = np.bincount((fmt.astype(np.int64) & 15), minlength=9)[1:9] * np.arange(1, 9)
+    assert list(widths) == info["bytes_by_width"] and int(widths.sum()) == info["bytes_values"]
     v = oracle_values(code, fmt)
     B, F, E, Mb = fields(fmt)
     f = aflp_f(code, fmt)
