@@ -42,7 +42,6 @@ int prog_max_blocks();
 cudaError_t mr_init();
 cudaError_t launch_gather_mr(const double* x, int64_t ldx, int r, const int32_t* perm, int n, float* v,
                              cudaStream_t st);
-cudaError_t launch_fanout_mr(const int32_t* src, int n, float* dst, const float* v, cudaStream_t st);
 cudaError_t launch_gsum_mr(const GsumOut* outs, int nouts, const F2* pscale, const float* partial, F2 alpha, float* v,
                            cudaStream_t st);
 cudaError_t launch_cdot_mr(const ItemCopy* items, const int32_t* wbeg, int nblk, const uint8_t* pay, const float* vec,
@@ -50,7 +49,7 @@ cudaError_t launch_cdot_mr(const ItemCopy* items, const int32_t* wbeg, int nblk,
 cudaError_t launch_rgemv_mr(int mode, const PieceCopy* pieces, const int32_t* wbeg, int nblk, const uint8_t* pay,
                             const float* vec, double alpha, F2 alpha_ff, double beta, double* y, int64_t ldy, int r,
                             const int32_t* perm, float* vout, const F2* rowscale, F2* fix, int32_t* fixcnt,
-                            const Split* splits, int* err, cudaStream_t st);
+                            const Split* splits, const int32_t* fan, int32_t fan_base, int* err, cudaStream_t st);
 cudaError_t launch_decode(const uint8_t* p, int64_t n, int B, int fmt, int e, int m, double vmin,
                           double* out, cudaStream_t st);
 cudaError_t launch_decode_debug(int tier, const DbgTask* tasks, int64_t ntask, const uint8_t* pay, float2* out,
@@ -279,8 +278,8 @@ hm_status upload(hm_matrix* M) {
   const size_t ncnt = std::max<size_t>(P.splits.size(), 1) * sizeof(int32_t);
   if ((e = cudaMalloc(&M->d_fixcnt, ncnt)) != cudaSuccess) return cuda_status(e);
   if ((e = cudaMemset(M->d_fixcnt, 0, ncnt)) != cudaSuccess) return cuda_status(e);
-  if (P.tier == TIER_F32) {   // multi-RHS workspace (panels of RP right-hand sides)
-    const size_t nv = (size_t)(std::max<int64_t>(P.nvec, 1) + SEG_ROWS) * RP * sizeof(float);
+  if (P.tier == TIER_F32) {   // multi-RHS workspace (panels of RP right-hand sides; no fan-out slots)
+    const size_t nv = (size_t)(std::max<int64_t>(P.fan_base, 1) + SEG_ROWS) * RP * sizeof(float);
     if ((e = cudaMalloc(&M->d_vmr, nv)) != cudaSuccess) return cuda_status(e);
     if ((e = cudaMemset(M->d_vmr, 0, nv)) != cudaSuccess) return cuda_status(e);
     if ((e = cudaMalloc(&M->d_pmr, (size_t)std::max<int64_t>(P.npartial, 1) * RP * sizeof(float))) != cudaSuccess)
@@ -559,14 +558,13 @@ static cudaError_t run_launch_mr(hm_matrix* M, const Launch& L, double alpha, co
                             M->d_pmr, M->d_vmr, M->d_err, st);
     case Launch::GSUM:
       return launch_gsum_mr(M->d_gout.p + L.off, (int)L.n, M->d_pscale.p, M->d_pmr, aff, M->d_vmr, st);
-    case Launch::FANOUT:
-      return launch_fanout_mr(M->d_fan.p + L.off, (int)L.n, M->d_vmr + (size_t)(P.fan_base + L.off) * RP, M->d_vmr,
-                              st);
+    case Launch::FANOUT:   // the multi-RHS row-chunk kernel copies each multiplier row from its coefficient
+      return cudaSuccess;
     case Launch::RGEMV:
       return launch_rgemv_mr(L.mode, M->d_pieces.p + (size_t)MR_SHAPE * P.npieces, M->d_wbeg.p + L.woff[MR_SHAPE],
                              L.nw[MR_SHAPE], M->d_pay.p, M->d_vmr, alpha, aff, beta, y, ldy, r, M->d_perm.p,
                              M->d_vmr, L.use_rowscale ? M->d_rowscale_ff.p : nullptr, M->d_fixmr, M->d_fixcnt,
-                             M->d_splits.p, M->d_err, st);
+                             M->d_splits.p, M->d_fan.p, (int32_t)P.fan_base, M->d_err, st);
   }
   return cudaErrorInvalidValue;
 }
@@ -961,7 +959,7 @@ hm_status hm_info(const hm_matrix* M, hm_info_t* o) {
                   H.n * 4;
   o->bytes_workspace = P.nvec * 8 + P.npartial * 8 + P.nfix * CHUNK_ROWS * 8;
   if (M->d_vmr)
-    o->bytes_workspace += ((P.nvec + SEG_ROWS) + P.npartial) * RP * 4 + P.nfix_mr * CHUNK_ROWS * RP * 8;
+    o->bytes_workspace += ((P.fan_base + SEG_ROWS) + P.npartial) * RP * 4 + P.nfix_mr * CHUNK_ROWS * RP * 8;
   o->nlaunches = (int64_t)P.launches.size();
   o->tier = P.tier;
   o->nunits = (int64_t)P.items.size() + P.npieces;

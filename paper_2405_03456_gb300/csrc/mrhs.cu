@@ -40,7 +40,7 @@ __device__ __forceinline__ void mr_decode8(uint32_t a, int e, int m, float (&v)[
 // holds for the decode tasks of a piece (t < 64 G, G <= 16).
 __constant__ uint16_t c_div16384[17] = {0, 16384, 8192, 5462, 4096, 3277, 2731, 2341, 2048, 1821, 1639, 1490, 1366, 1261, 1171, 1093, 1024};
 
-// ---------------------------------------------------------------- gather, fan-out, segment sums
+// ---------------------------------------------------------------- gather, segment sums
 // v[i * RP + k] = x[perm[i] + k * ldx] (FP32 hi part), k < r; zero for k >= r.
 __global__ void k_gather_mr(const double* __restrict__ x, int64_t ldx, int r, const int32_t* __restrict__ perm, int n,
                             float* __restrict__ v) {
@@ -48,14 +48,6 @@ __global__ void k_gather_mr(const double* __restrict__ x, int64_t ldx, int r, co
   if (t >= (int64_t)n * RP) return;
   const int i = (int)(t / RP), k = (int)(t % RP);
   v[t] = k < r ? (float)x[(int64_t)perm[i] + k * ldx] : 0.0f;
-}
-
-__global__ void k_fanout_mr(const int32_t* __restrict__ src, int n, float* __restrict__ dst,
-                            const float* __restrict__ v) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (int64_t)n * RP) return;
-  const int i = (int)(t / RP), k = (int)(t % RP);
-  dst[t] = v[(int64_t)src[i] * RP + k];
 }
 
 __global__ void k_gsum_mr(const GsumOut* __restrict__ outs, int nouts, const F2* __restrict__ pscale,
@@ -116,7 +108,8 @@ constexpr int CB = RP + 8;                // 24 halves = 48 bytes
 constexpr int MR_LIMB_A = PIECE_MAX_COLS * CT * 2;   // bytes of one A limb tile (row chunks; column dots use less)
 constexpr int MR_LIMB_B = SEG_ROWS * CB * 2;         // bytes of one B limb tile (64 x RP)
 constexpr int NT = RP / 8;                           // 8-wide right-hand-side tiles of a panel
-constexpr int MR_PAIRS = (CHUNK_ROWS / 16) * NT / 8; // (row tile, rhs tile) pairs per warp in a row chunk
+constexpr int MR_PAIRS = NT;                         // (row tile, rhs tile) pairs per warp in a row chunk
+static_assert(CHUNK_ROWS / 16 == MR_THREADS / 32, "one 16-row tile of a row chunk per warp");
 constexpr int MR_TILES = 3 * MR_LIMB_A + 3 * MR_LIMB_B;
 
 // 8 FP32 values -> their first `limbs` BF16 limbs, 16 bytes per limb at dst + l * lstride
@@ -222,44 +215,47 @@ __device__ __forceinline__ void mr_cdot_mma(uint32_t sa, uint32_t xa, uint32_t t
   }
   __syncthreads();
   const int w = t >> 5, L = t & 31;
-  // (column tile, rhs tile) pairs p = w + 8 s: columns 16 (p / NT) .., rhs 8 (p % NT) ..
-  for (int p = w; p < (ncp / 16) * NT; p += 8) {
-    const int mt = p / NT, nt = p % NT;
-    float dd[3][4] = {};
+  // (column tile, pair of rhs tiles) q = w + 8 s: columns 16 (q / (NT / 2)) ..,
+  // rhs 16 (q % (NT / 2)) ..; one ldmatrix.x4.trans per limb feeds both rhs tiles
+  const int g = L >> 2, tq = L & 3;
+  for (int q = w; q < (ncp / 16) * (NT / 2); q += 8) {
+    const int mt = q / (NT / 2), h = q % (NT / 2);
+    float dd[2][3][4] = {};
     for (int k0 = 0; k0 < Rp; k0 += 16) {
       uint32_t af[3][4], bf[3][4];
       const uint32_t aad = ta + (uint32_t)((16 * mt + (L & 15)) * CA + k0 + (L >> 4) * 8) * 2u;
-      const uint32_t bad =
-          xl + (uint32_t)((k0 + (L & 7) + ((L >> 3) & 1) * 8) * CB + 16 * (nt >> 1) + (L >> 4) * 8) * 2u;
+      const uint32_t bad = xl + (uint32_t)((k0 + (L & 7) + ((L >> 3) & 1) * 8) * CB + 16 * h + (L >> 4) * 8) * 2u;
 #pragma unroll
       for (int l = 0; l < 3; ++l) {
         if (l < limbs) ldsm_x4(aad + l * MR_LIMB_A, af[l]);
         ldsm_x4_t(bad + l * MR_LIMB_B, bf[l]);
       }
-      const bool hi = (nt & 1) != 0;
-      const uint32_t b0[3] = {hi ? bf[0][2] : bf[0][0], hi ? bf[1][2] : bf[1][0], hi ? bf[2][2] : bf[2][0]};
-      const uint32_t b1[3] = {hi ? bf[0][3] : bf[0][1], hi ? bf[1][3] : bf[1][1], hi ? bf[2][3] : bf[2][1]};
-      mma_limbs(dd, af, b0, b1, limbs);
+      const uint32_t e0[3] = {bf[0][0], bf[1][0], bf[2][0]}, e1[3] = {bf[0][1], bf[1][1], bf[2][1]};
+      const uint32_t o0[3] = {bf[0][2], bf[1][2], bf[2][2]}, o1[3] = {bf[0][3], bf[1][3], bf[2][3]};
+      mma_limbs(dd[0], af, e0, e1, limbs);
+      mma_limbs(dd[1], af, o0, o1, limbs);
     }
-    float d[4];
-    mma_sum(dd, d);
-    // C fragment: d0 (col g, rhs 2t), d1 (g, 2t + 1), d2 (g + 8, 2t), d3 (g + 8, 2t + 1)
-    const int g = L >> 2, tq = L & 3;
 #pragma unroll
-    for (int hr = 0; hr < 2; ++hr) {
-      const int j = 16 * mt + g + 8 * hr;
-      if (j < nc) {
-        const int32_t out = (int32_t)lds32(cm + 8u * j + 4u);
-        const int k = 8 * nt + 2 * tq;
-        const float r0 = d[2 * hr], r1 = d[2 * hr + 1];
-        if (fin) {
-          const uint2 f = lds64(sc + 8u * j);
-          FF scl = {__uint_as_float(f.x), __uint_as_float(f.y)};
-          if (flags & ITEM_ALPHA) scl = ff_mul(scl, FF{alpha.hi, alpha.lo});
-          const FF v0 = ff_mul(FF{r0, 0.f}, scl), v1 = ff_mul(FF{r1, 0.f}, scl);
-          *reinterpret_cast<float2*>(vout + (int64_t)out * RP + k) = make_float2(v0.hi + v0.lo, v1.hi + v1.lo);
-        } else {
-          *reinterpret_cast<float2*>(partial + (int64_t)out * RP + k) = make_float2(r0, r1);
+    for (int u = 0; u < 2; ++u) {
+      float d[4];
+      mma_sum(dd[u], d);
+      // C fragment: d0 (col g, rhs 2tq), d1 (g, 2tq + 1), d2 (g + 8, 2tq), d3 (g + 8, 2tq + 1)
+#pragma unroll
+      for (int hr = 0; hr < 2; ++hr) {
+        const int j = 16 * mt + g + 8 * hr;
+        if (j < nc) {
+          const int32_t out = (int32_t)lds32(cm + 8u * j + 4u);
+          const int k = 8 * (2 * h + u) + 2 * tq;
+          const float r0 = d[2 * hr], r1 = d[2 * hr + 1];
+          if (fin) {
+            const uint2 f = lds64(sc + 8u * j);
+            FF scl = {__uint_as_float(f.x), __uint_as_float(f.y)};
+            if (flags & ITEM_ALPHA) scl = ff_mul(scl, FF{alpha.hi, alpha.lo});
+            const FF v0 = ff_mul(FF{r0, 0.f}, scl), v1 = ff_mul(FF{r1, 0.f}, scl);
+            *reinterpret_cast<float2*>(vout + (int64_t)out * RP + k) = make_float2(v0.hi + v0.lo, v1.hi + v1.lo);
+          } else {
+            *reinterpret_cast<float2*>(partial + (int64_t)out * RP + k) = make_float2(r0, r1);
+          }
         }
       }
     }
@@ -392,7 +388,8 @@ __global__ void __launch_bounds__(MR_THREADS, MR_BLOCKS_PER_SM)
                const uint8_t* __restrict__ pay, const float* __restrict__ vec, double alpha, F2 alpha_ff,
                double beta, double* __restrict__ y, int64_t ldy, int r, const int32_t* __restrict__ perm,
                float* __restrict__ vout, const F2* __restrict__ rowscale, F2* __restrict__ fix,
-               int32_t* __restrict__ fixcnt, const Split* __restrict__ splits, int* err) {
+               int32_t* __restrict__ fixcnt, const Split* __restrict__ splits, const int32_t* __restrict__ fan,
+               int32_t fan_base, int* err) {
   extern __shared__ __align__(128) uint8_t smem[];
   __shared__ int4 info[MR_STAGES];
   __shared__ int s_last;
@@ -420,15 +417,23 @@ __global__ void __launch_bounds__(MR_THREADS, MR_BLOCKS_PER_SM)
     const int sl = i - dbase;
     const uint32_t off16 = __shfl_sync(HM_FULL, dc.off16, sl), bf = __shfl_sync(HM_FULL, dc.bytes_flags, sl);
     const int32_t moff = __shfl_sync(HM_FULL, dc.moff, sl), sp = __shfl_sync(HM_FULL, dc.split_part, sl);
+    const int s = i % MR_STAGES;
+    const uint32_t nc = bf >> 24;
+    const bool fan_run = moff >= fan_base;   // multipliers scattered over the coefficient rows
     if (lane == 0) {
-      const int s = i % MR_STAGES;
-      const uint32_t nc = bf >> 24;
       const uint32_t pb = pad16m(bf & 0xffffu), mb = nc * RP * 4u;
       info[s] = make_int4((int)((bf >> 16) & 0xffu), sp, 0, 0);
       fence_proxy_async();
       mbar_expect_tx(&ring.bars[s], pb + mb);
       bulk_g2s_hint(ring.stage(s), pay + (uint64_t)off16 * 16u, pb, &ring.bars[s], pol);
-      if (mb) bulk_g2s(ring.stage(s) + STAGE_BYTES, vec + (int64_t)moff * RP, mb, &ring.bars[s]);
+      if (mb && !fan_run) bulk_g2s(ring.stage(s) + STAGE_BYTES, vec + (int64_t)moff * RP, mb, &ring.bars[s]);
+    }
+    if (fan_run) {   // row j of the run: the RP values of coefficient fan[moff - fan_base + j]
+      __syncwarp();
+      for (int j = lane; j < (int)nc; j += 32) {
+        const int32_t src = __ldg(fan + (moff - fan_base) + j);
+        bulk_g2s(ring.stage(s) + STAGE_BYTES + j * RP * 4, vec + (int64_t)src * RP, RP * 4u, &ring.bars[s]);
+      }
     }
   };
   if (threadIdx.x < 32) {
@@ -442,9 +447,9 @@ __global__ void __launch_bounds__(MR_THREADS, MR_BLOCKS_PER_SM)
   __syncthreads();
   const int w = threadIdx.x >> 5, L = threadIdx.x & 31;
   const int g = L >> 2, tq = L & 3;
-  // warp w owns the (row tile, rhs tile) pairs p = w + 8 s (rows 16 (p / NT) ..,
-  // right-hand sides 8 (p % NT) ..); accumulators per pair and C-fragment
-  // row half (row g / g + 8), float-float pairs over (rhs 2 tq, 2 tq + 1)
+  // warp w owns rows 16 w .. 16 w + 15 of the chunk and every right-hand side:
+  // pair sp2 = rhs tile 8 sp2 ..; accumulators per pair and C-fragment row half
+  // (row 16 w + g / + 8), float-float pairs over (rhs 8 sp2 + 2 tq, + 1)
   float2 ahi[MR_PAIRS][2], alo[MR_PAIRS][2];
 #pragma unroll
   for (int a = 0; a < MR_PAIRS; ++a)
@@ -490,33 +495,43 @@ __global__ void __launch_bounds__(MR_THREADS, MR_BLOCKS_PER_SM)
     }
     __syncthreads();
     const int R = H.nrows, ncp = (H.ncols + 15) & ~15, la = H.limbs;
-    // (row tile, rhs tile) pairs p = w + 8 s: rows 16 (p / NT) .., rhs 8 (p % NT) ..
+    // rows 16 w ..: A fragments once per k step (limbs l < la), B fragments of
+    // two rhs tiles per ldmatrix.x4.trans (registers 0, 1: tile 2 h; 2, 3: 2 h + 1)
+    if (16 * w < R) {
+      float dd[NT][3][4];
 #pragma unroll
-    for (int sp2 = 0; sp2 < MR_PAIRS; ++sp2) {
-      const int p = w + 8 * sp2, mt = p / NT, nt = p % NT;
-      if (16 * mt >= R) continue;
-      float dd[3][4] = {};
+      for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+        for (int l = 0; l < 3; ++l)
+#pragma unroll
+          for (int u = 0; u < 4; ++u) dd[nt][l][u] = 0.f;
       const uint32_t tl = tiles + 3u * MR_LIMB_A;
       for (int k0 = 0; k0 < ncp; k0 += 16) {
-        uint32_t af[3][4], bf[3][4];
+        uint32_t af[3][4];
         const uint32_t aad =
-            tiles + (uint32_t)((k0 + (L & 7) + ((L >> 4) << 3)) * CT + 16 * mt + ((L >> 3) & 1) * 8) * 2u;
-        const uint32_t bad =
-            tl + (uint32_t)((k0 + (L & 7) + ((L >> 3) & 1) * 8) * CB + 16 * (nt >> 1) + (L >> 4) * 8) * 2u;
+            tiles + (uint32_t)((k0 + (L & 7) + ((L >> 4) << 3)) * CT + 16 * w + ((L >> 3) & 1) * 8) * 2u;
 #pragma unroll
-        for (int l = 0; l < 3; ++l) {
+        for (int l = 0; l < 3; ++l)
           if (l < la) ldsm_x4_t(aad + l * MR_LIMB_A, af[l]);
-          ldsm_x4_t(bad + l * MR_LIMB_B, bf[l]);
+#pragma unroll
+        for (int h = 0; h < NT / 2; ++h) {
+          uint32_t bf[3][4];
+          const uint32_t bad = tl + (uint32_t)((k0 + (L & 7) + ((L >> 3) & 1) * 8) * CB + 16 * h + (L >> 4) * 8) * 2u;
+#pragma unroll
+          for (int l = 0; l < 3; ++l) ldsm_x4_t(bad + l * MR_LIMB_B, bf[l]);
+          const uint32_t e0[3] = {bf[0][0], bf[1][0], bf[2][0]}, e1[3] = {bf[0][1], bf[1][1], bf[2][1]};
+          const uint32_t o0[3] = {bf[0][2], bf[1][2], bf[2][2]}, o1[3] = {bf[0][3], bf[1][3], bf[2][3]};
+          mma_limbs(dd[2 * h], af, e0, e1, la);
+          mma_limbs(dd[2 * h + 1], af, o0, o1, la);
         }
-        const bool hi = (nt & 1) != 0;
-        const uint32_t b0[3] = {hi ? bf[0][2] : bf[0][0], hi ? bf[1][2] : bf[1][0], hi ? bf[2][2] : bf[2][0]};
-        const uint32_t b1[3] = {hi ? bf[0][3] : bf[0][1], hi ? bf[1][3] : bf[1][1], hi ? bf[2][3] : bf[2][1]};
-        mma_limbs(dd, af, b0, b1, la);
       }
-      float d[4];
-      mma_sum(dd, d);
-      ff_add_f2(ahi[sp2][0], alo[sp2][0], make_float2(d[0], d[1]));
-      ff_add_f2(ahi[sp2][1], alo[sp2][1], make_float2(d[2], d[3]));
+#pragma unroll
+      for (int nt = 0; nt < NT; ++nt) {
+        float d[4];
+        mma_sum(dd[nt], d);
+        ff_add_f2(ahi[nt][0], alo[nt][0], make_float2(d[0], d[1]));
+        ff_add_f2(ahi[nt][1], alo[nt][1], make_float2(d[2], d[3]));
+      }
     }
     if (rinfo.x & PD_LAST) {
       const bool calpha = (H.flags & PH_CALPHA) != 0;
@@ -528,8 +543,7 @@ __global__ void __launch_bounds__(MR_THREADS, MR_BLOCKS_PER_SM)
         for (int sp2 = 0; sp2 < MR_PAIRS; ++sp2)
 #pragma unroll
           for (int hr = 0; hr < 2; ++hr) {
-            const int p = w + 8 * sp2;
-            const int row = 16 * (p / NT) + g + 8 * hr, k = 8 * (p % NT) + 2 * tq;
+            const int row = 16 * w + g + 8 * hr, k = 8 * sp2 + 2 * tq;
             if (row < R) {
               mine[row * RP + k] = F2{ahi[sp2][hr].x, alo[sp2][hr].x};
               mine[row * RP + k + 1] = F2{ahi[sp2][hr].y, alo[sp2][hr].y};
@@ -544,17 +558,16 @@ __global__ void __launch_bounds__(MR_THREADS, MR_BLOCKS_PER_SM)
         emit = s_last != 0;
       }
       if (emit) {
-        // the thread's elements of pair sp2: rows 16 (p / NT) + g + 8 hr, right-hand
-        // sides 8 (p % NT) + 2 tq + c, held as (ahi, alo)[sp2][hr].{x, y}; per pair
+        // the thread's elements of pair sp2: rows 16 w + g + 8 hr, right-hand
+        // sides 8 sp2 + 2 tq + c, held as (ahi, alo)[sp2][hr].{x, y}; per pair
         // all global loads of a phase are issued before their values are used
 #pragma unroll
         for (int sp2 = 0; sp2 < MR_PAIRS; ++sp2) {
-          const int p = w + 8 * sp2;
-          const int k0 = 8 * (p % NT) + 2 * tq;
+          const int k0 = 8 * sp2 + 2 * tq;
           int row[2];
 #pragma unroll
-          for (int hr = 0; hr < 2; ++hr) row[hr] = 16 * (p / NT) + g + 8 * hr;
-          if (16 * (p / NT) >= R) continue;
+          for (int hr = 0; hr < 2; ++hr) row[hr] = 16 * w + g + 8 * hr;
+          if (16 * w >= R) continue;
           if (split) {   // the parts in part order
 #pragma unroll
             for (int hr = 0; hr < 2; ++hr) {
@@ -651,13 +664,6 @@ cudaError_t launch_gather_mr(const double* x, int64_t ldx, int r, const int32_t*
   return cudaGetLastError();
 }
 
-cudaError_t launch_fanout_mr(const int32_t* src, int n, float* dst, const float* v, cudaStream_t st) {
-  if (n <= 0) return cudaSuccess;
-  const int64_t tot = (int64_t)n * RP;
-  k_fanout_mr<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(src, n, dst, v);
-  return cudaGetLastError();
-}
-
 cudaError_t launch_gsum_mr(const GsumOut* outs, int nouts, const F2* pscale, const float* partial, F2 alpha, float* v,
                            cudaStream_t st) {
   if (nouts <= 0) return cudaSuccess;
@@ -676,11 +682,11 @@ cudaError_t launch_cdot_mr(const ItemCopy* items, const int32_t* wbeg, int nblk,
 cudaError_t launch_rgemv_mr(int mode, const PieceCopy* pieces, const int32_t* wbeg, int nblk, const uint8_t* pay,
                             const float* vec, double alpha, F2 alpha_ff, double beta, double* y, int64_t ldy, int r,
                             const int32_t* perm, float* vout, const F2* rowscale, F2* fix, int32_t* fixcnt,
-                            const Split* splits, int* err, cudaStream_t st) {
+                            const Split* splits, const int32_t* fan, int32_t fan_base, int* err, cudaStream_t st) {
   if (nblk <= 0) return cudaSuccess;
 #define HM_MRG(M)                                                                                           \
   k_rgemv_mr<M><<<nblk, MR_THREADS, MR_SMEM_R, st>>>(pieces, wbeg, nblk, pay, vec, alpha, alpha_ff, beta, y, ldy, r, \
-                                                     perm, vout, rowscale, fix, fixcnt, splits, err)
+                                                     perm, vout, rowscale, fix, fixcnt, splits, fan, fan_base, err)
   if (mode == MODE_Y)
     HM_MRG(MODE_Y);
   else if (mode == MODE_VEC)
