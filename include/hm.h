@@ -179,6 +179,22 @@ hm_status hm_persistent(hm_matrix* m, int32_t enable);
 hm_status hm_persistent_mode(const hm_matrix* m, int32_t* mode);
 
 /*
+ * hm_set_multi_rhs_engine -- how the row-chunk steps of multi-RHS panels (the
+ * precision / multi-RHS form, FP32 tier) multiply, for chunks of at most 64
+ * rows (wider chunks always take the shared-tile tensor-core kernel):
+ *   0: tensor cores -- each decoded value and multiplier cut into three exact
+ *      BF16 limbs, mma.sync products of limb order <= 2 in FP32;
+ *   1 (the default): FP32 pipes -- one FP32 FMA per product, as the single-RHS
+ *      kernels.
+ * Both sum per piece in FP32 and across pieces in float-float; results differ
+ * only in rounding.  hm_autotune times both on an RP-wide panel and keeps the
+ * faster.  Errors: HM_ERR_ARG (engine outside 0..1).
+ */
+hm_status hm_set_multi_rhs_engine(hm_matrix* m, int32_t engine);
+/* hm_multi_rhs_engine -- the engine in use (0 or 1). */
+hm_status hm_multi_rhs_engine(const hm_matrix* m, int32_t* engine);
+
+/*
  * hm_save -- write m to the file `path`: the built matrix (cluster tree, block
  * tree, dense leaves, low-rank factors, cluster bases, couplings and transfer
  * matrices, FP64, as hm_build made them) and, if m is compressed, the eps /
@@ -289,7 +305,10 @@ hm_status hm_codec_decode(const uint8_t* packed, int64_t n, const hm_codec_heade
  * the order of summation inside a chunk.
  * hm_autotune -- time every shape of every such launch `reps` times on
  *   `stream` (on internal zero vectors) and keep the fastest per launch; then
- *   time the whole product in each hm_persistent mode and keep the fastest.
+ *   time the whole product in each hm_persistent mode and keep the fastest;
+ *   in the FP32 tier also time an RP-wide multi-RHS panel with each
+ *   hm_set_multi_rhs_engine engine and keep the faster (two more n x RP
+ *   buffers for the call).
  *   Allocates two n-vectors for the duration of the call, synchronises the
  *   stream, and discards a captured graph.  Errors: HM_ERR_ARG (reps outside
  *   1..1000), HM_ERR_STATE (not compressed), HM_ERR_CUDA.

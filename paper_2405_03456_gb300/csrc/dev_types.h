@@ -56,6 +56,14 @@ constexpr int RS_CFG_STAGES[NCFG] = {2, 3, 4};
 // its descriptors are the extra launch shape index MR_SHAPE.
 constexpr int RP = 32;
 constexpr int MR_BLOCKS_PER_SM = 2;
+// Row-chunk launches of the multi-RHS shape are split into one range per warp
+// pair (MP_PAIRS pairs per SM); chunks of at most MP_ROWS rows run on the
+// register-fragment kernel, wider ones on the shared-tile kernel (one block per range).
+constexpr int MP_PAIRS = 4;
+constexpr int MP_ROWS = 64;
+// Column-dot launches of the multi-RHS shape: ranges per SM (one per warp of
+// the FP32-pipe kernel; the tensor-core kernel takes one per warp pair).
+constexpr int MR_CDOT_RANGES = 16;
 constexpr int MR_SHAPE = NCFG;
 constexpr int NSHAPES = NCFG + 1;
 constexpr int SEQ_SHAPE = 0;               // row-chunk shape of the persistent (multi-phase) launch

@@ -44,12 +44,13 @@ cudaError_t launch_gather_mr(const double* x, int64_t ldx, int r, const int32_t*
                              cudaStream_t st);
 cudaError_t launch_gsum_mr(const GsumOut* outs, int nouts, const F2* pscale, const float* partial, F2 alpha, float* v,
                            cudaStream_t st);
-cudaError_t launch_cdot_mr(const ItemCopy* items, const int32_t* wbeg, int nblk, const uint8_t* pay, const float* vec,
-                           F2 alpha, float* partial, float* vout, int* err, cudaStream_t st);
-cudaError_t launch_rgemv_mr(int mode, const PieceCopy* pieces, const int32_t* wbeg, int nblk, const uint8_t* pay,
-                            const float* vec, double alpha, F2 alpha_ff, double beta, double* y, int64_t ldy, int r,
-                            const int32_t* perm, float* vout, const F2* rowscale, F2* fix, int32_t* fixcnt,
-                            const Split* splits, const int32_t* fan, int32_t fan_base, int* err, cudaStream_t st);
+cudaError_t launch_cdot_mr(int engine, const ItemCopy* items, const int32_t* wbeg, int nblk, const uint8_t* pay,
+                           const float* vec, F2 alpha, float* partial, float* vout, int* err, cudaStream_t st);
+cudaError_t launch_rgemv_mr(int mode, int engine, const PieceCopy* pieces, const int32_t* wbeg, int nblk, int maxrows,
+                            const uint8_t* pay, const float* vec, double alpha, F2 alpha_ff, double beta, double* y,
+                            int64_t ldy, int r, const int32_t* perm, float* vout, const F2* rowscale, F2* fix,
+                            int32_t* fixcnt, const Split* splits, const int32_t* fan, int32_t fan_base, int* err,
+                            cudaStream_t st);
 cudaError_t launch_decode(const uint8_t* p, int64_t n, int B, int fmt, int e, int m, double vmin,
                           double* out, cudaStream_t st);
 cudaError_t launch_decode_debug(int tier, const DbgTask* tasks, int64_t ntask, const uint8_t* pay, float2* out,
@@ -121,6 +122,7 @@ struct hm_matrix {
   // executed as the phases of one cooperative launch (dataflow between phases)
   int64_t width_bytes[8] = {};  // packed code bytes by code width B (set at compress time)
   int fuse = 1;                // 0 per launch, 1 runs of row-chunk launches fused, 2 the whole product
+  int mr_engine = 1;           // multi-RHS row chunks: 0 tensor-core fragments, 1 FP32 pipes
   DevArr<ProgPhase> d_prog;    // phases of the whole-product launch
   unsigned* d_pstate = nullptr;  // its barrier counter, abort word and the runs' state
   int pstate_n = 0;
@@ -554,15 +556,15 @@ static cudaError_t run_launch_mr(hm_matrix* M, const Launch& L, double alpha, co
     case Launch::GATHER:
       return launch_gather_mr(x, ldx, r, M->d_perm.p, (int)L.n, M->d_vmr, st);
     case Launch::CDOT:
-      return launch_cdot_mr(M->d_items.p, M->d_wbeg.p + L.woff[MR_SHAPE], L.nw[MR_SHAPE], M->d_pay.p, M->d_vmr, aff,
+      return launch_cdot_mr(M->mr_engine, M->d_items.p, M->d_wbeg.p + L.woff[MR_SHAPE], L.nw[MR_SHAPE], M->d_pay.p, M->d_vmr, aff,
                             M->d_pmr, M->d_vmr, M->d_err, st);
     case Launch::GSUM:
       return launch_gsum_mr(M->d_gout.p + L.off, (int)L.n, M->d_pscale.p, M->d_pmr, aff, M->d_vmr, st);
     case Launch::FANOUT:   // the multi-RHS row-chunk kernel copies each multiplier row from its coefficient
       return cudaSuccess;
     case Launch::RGEMV:
-      return launch_rgemv_mr(L.mode, M->d_pieces.p + (size_t)MR_SHAPE * P.npieces, M->d_wbeg.p + L.woff[MR_SHAPE],
-                             L.nw[MR_SHAPE], M->d_pay.p, M->d_vmr, alpha, aff, beta, y, ldy, r, M->d_perm.p,
+      return launch_rgemv_mr(L.mode, M->mr_engine, M->d_pieces.p + (size_t)MR_SHAPE * P.npieces, M->d_wbeg.p + L.woff[MR_SHAPE],
+                             L.nw[MR_SHAPE], L.maxrows, M->d_pay.p, M->d_vmr, alpha, aff, beta, y, ldy, r, M->d_perm.p,
                              M->d_vmr, L.use_rowscale ? M->d_rowscale_ff.p : nullptr, M->d_fixmr, M->d_fixcnt,
                              M->d_splits.p, M->d_fan.p, (int32_t)P.fan_base, M->d_err, st);
   }
@@ -831,11 +833,39 @@ hm_status hm_autotune(hm_matrix* M, int32_t reps, void* stream) {
     }
     M->fuse = bestm;
   }
+  // multi-RHS panels (FP32 tier): the row-chunk engine, whole RP-wide panels timed
+  double *xp = nullptr, *yp = nullptr;
+  if (out == HM_OK && M->d_vmr) {
+    const size_t pb = (size_t)n * RP * sizeof(double);
+    if (cudaMalloc(&xp, pb) != cudaSuccess || cudaMalloc(&yp, pb) != cudaSuccess ||
+        cudaMemsetAsync(xp, 0, pb, st) != cudaSuccess)
+      out = HM_ERR_CUDA;
+    float best = 0.f;
+    int beste = M->mr_engine;
+    for (int eng = 0; eng <= 1 && out == HM_OK; ++eng) {
+      M->mr_engine = eng;
+      if (run_program_mr(M, 1.0, xp, n, 0.0, yp, n, RP, st) != HM_OK) out = HM_ERR_CUDA;
+      cudaEventRecord(e0, st);
+      for (int r = 0; r < reps && out == HM_OK; ++r)
+        if (run_program_mr(M, 1.0, xp, n, 0.0, yp, n, RP, st) != HM_OK) out = HM_ERR_CUDA;
+      cudaEventRecord(e1, st);
+      float ms = 0.f;
+      if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+        out = HM_ERR_CUDA;
+      if (eng == 0 || ms < best) {
+        best = ms;
+        beste = eng;
+      }
+    }
+    M->mr_engine = beste;
+  }
   if (cudaStreamSynchronize(st) != cudaSuccess && out == HM_OK) out = HM_ERR_CUDA;
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   if (x) cudaFree(x);
   if (y) cudaFree(y);
+  if (xp) cudaFree(xp);
+  if (yp) cudaFree(yp);
   M->drop_graph();
   return out;
 }
@@ -852,6 +882,19 @@ hm_status hm_launch_shapes(const hm_matrix* M, int32_t* shapes, int32_t cap, int
 hm_status hm_persistent_mode(const hm_matrix* M, int32_t* mode) {
   if (!M || !mode) return HM_ERR_ARG;
   *mode = M->fuse;
+  return HM_OK;
+}
+
+hm_status hm_set_multi_rhs_engine(hm_matrix* M, int32_t engine) {
+  if (!M || engine < 0 || engine > 1) return HM_ERR_ARG;
+  std::lock_guard<std::mutex> g(M->mu);
+  M->mr_engine = engine;
+  return HM_OK;
+}
+
+hm_status hm_multi_rhs_engine(const hm_matrix* M, int32_t* engine) {
+  if (!M || !engine) return HM_ERR_ARG;
+  *engine = M->mr_engine;
   return HM_OK;
 }
 

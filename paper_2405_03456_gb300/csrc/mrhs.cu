@@ -640,19 +640,903 @@ __global__ void __launch_bounds__(MR_THREADS, MR_BLOCKS_PER_SM)
   }
 }
 
+// ---------------------------------------------------------------- row chunks, register fragments
+// The row-chunk panel product for chunks of at most MP_ROWS rows with the piece
+// values decoded straight into mma.sync fragments: no shared-memory limb
+// tiles and no block barriers.  Two warps (a pair) own a range of pieces and a
+// ring of MP_NS stages (piece + its multiplier rows, filled by the pair's warp
+// 0); warp wi of the pair takes rows 32 wi .. 32 wi + 31 of every piece and all
+// RP right-hand sides.
+//
+// m16n8k16 fragments (lane = 4 g + tq): A (16 x 16) = piece values, B (16 x 8)
+// = multipliers T[column][rhs], C (16 x 8) = row sums.  A rows are permuted so
+// that fragment rows g (h = 0) and g + 8 (h = 1) of the warp's row tiles mt =
+// 0, 1 are the consecutive chunk rows 32 wi + 4 g + 2 mt + h: a lane decodes 4
+// consecutive codes of each of its columns k0 + 2 tq + {0, 1} (A registers 0,
+// 1) and k0 + 2 tq + 8 + {0, 1} (registers 2, 3).  B's n is the right-hand side
+// 8 nt + g.  C registers (c0, c1 | c2, c3) of tile (mt, nt) hold rows
+// 32 wi + 4 g + 2 mt (+ 1), right-hand sides 8 nt + 2 tq + {0, 1}.
+//
+// Values and multipliers are cut into three BF16 limbs by truncation (exact);
+// the products of limb order 0 and of orders 1 + 2 go into two FP32 chains,
+// added per piece and folded into float-float row sums.
+constexpr int MP_NS = 3;                                   // stages per pair
+constexpr int MP_TP = RP * 4 + 16;                         // multiplier row pitch in a stage (bytes)
+constexpr int MP_STAGE = STAGE_BYTES + PIECE_MAX_COLS * MP_TP;
+constexpr int MP_THREADS = MP_PAIRS * 64;
+static_assert(MP_STAGE % 128 == 0, "stage alignment");
+
+// x = t0 + t1 + t2 with BF16 limbs t by truncation (each step keeps the top 8
+// significant bits of the remainder; the remainders are exact FP32
+// differences); limbs of x in the low half, of y in the high half.
+__device__ __forceinline__ void limbs2(float x, float y, uint32_t& l0, uint32_t& l1, uint32_t& l2) {
+  const uint32_t xu = __float_as_uint(x), yu = __float_as_uint(y);
+  l0 = __byte_perm(xu, yu, 0x7632);
+  const float2 r1 = sub2(make_float2(x, y), make_float2(__uint_as_float(xu & 0xffff0000u), __uint_as_float(yu & 0xffff0000u)));
+  const uint32_t ru = __float_as_uint(r1.x), rv = __float_as_uint(r1.y);
+  l1 = __byte_perm(ru, rv, 0x7632);
+  const float2 r2 = sub2(r1, make_float2(__uint_as_float(ru & 0xffff0000u), __uint_as_float(rv & 0xffff0000u)));
+  l2 = __byte_perm(__float_as_uint(r2.x), __float_as_uint(r2.y), 0x7632);
+}
+
+// Named barrier of the 64 threads of pair bid - 1 / its OR vote.
+__device__ __forceinline__ void pair_sync(int bid) { asm volatile("bar.sync %0, 64;" ::"r"(bid) : "memory"); }
+__device__ __forceinline__ bool pair_any(int bid, bool v) {
+  int r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\tsetp.ne.s32 p, %1, 0;\n\tbar.red.or.pred q, %2, 64, p;\n\tselp.s32 %0, 1, 0, q;\n\t}"
+      : "=r"(r)
+      : "r"((int)v), "r"(bid)
+      : "memory");
+  return r != 0;
+}
+
+// One piece for warp wi of the pair: the products of its rows, folded into the
+// float-float sums fhi / flo [mt][nt][h] (rows 32 wi + 4 g + 2 mt + h, rhs
+// 8 nt + 2 tq + {0, 1}).
+template <int F, int B>
+__device__ __forceinline__ void mp_piece(uint32_t sa, const PieceHdr& H, F2 alpha_ff, int wi, int lane,
+                                         float2 (&fhi)[2][NT][2], float2 (&flo)[2][NT][2]) {
+  const int R = H.nrows, nc = H.ncols, la = H.limbs;
+  const bool tile = (H.flags & PH_TILE) != 0;
+  const uint32_t stride = pad8u((uint32_t)R * B);
+  const uint32_t cm = sa + (uint32_t)sizeof(PieceHdr);
+  const int g = lane >> 2, tq = lane & 3;
+  const uint32_t cb = cm + (tile ? 0u : pad8u(2u * nc)) + (uint32_t)((32 * wi + 4 * g) * B);
+  const uint32_t tv = sa + STAGE_BYTES + 4u * g;
+  const int e_t = H.em & 0xff, m_t = H.em >> 8;
+  float sc = 1.0f;
+  if (tile) {
+    FF f = {H.scale.hi, H.scale.lo};
+    if (H.flags & PH_TALPHA) f = ff_mul(f, FF{alpha_ff.hi, alpha_ff.lo});
+    sc = f.hi;
+  }
+  float big[2][NT][4], sml[2][NT][4];
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+    for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        big[mt][nt][u] = 0.f;
+        sml[mt][nt][u] = 0.f;
+      }
+  for (int k0 = 0; k0 < nc; k0 += 16) {
+    uint32_t af[3][2][4];
+    {
+      float v[4][4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int j = k0 + 2 * tq + (c & 1) + 8 * (c >> 1);
+        const bool on = j < nc;
+        const int jj = on ? j : 0;
+        int e = e_t, m = m_t;
+        if constexpr (F == 2) {
+          if (!tile) {
+            const uint32_t em = lds32((cm + 2u * jj) & ~3u) >> (16u * (jj & 1));
+            e = em & 0xff;
+            m = (em >> 8) & 0xff;
+          }
+        }
+        uint32_t w[B];
+#pragma unroll
+        for (int b = 0; b < B; ++b) w[b] = lds32(cb + (uint32_t)jj * stride + 4u * b);
+        float l[4];
+        decode4<TIER_F32, F, B>(w, e, m, v[c], l);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) v[c][u] = on ? v[c][u] : 0.f;
+      }
+#pragma unroll
+      for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          limbs2(v[0][2 * mt + h], v[1][2 * mt + h], af[0][mt][h], af[1][mt][h], af[2][mt][h]);
+          limbs2(v[2][2 * mt + h], v[3][2 * mt + h], af[0][mt][2 + h], af[1][mt][2 + h], af[2][mt][2 + h]);
+        }
+    }
+#pragma unroll
+    for (int nt = 0; nt < NT; ++nt) {
+      float t[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int j = k0 + 2 * tq + (c & 1) + 8 * (c >> 1);
+        t[c] = j < nc ? __uint_as_float(lds32(tv + (uint32_t)j * MP_TP + 32u * nt)) * sc : 0.f;
+      }
+      uint32_t bf[3][2];
+      limbs2(t[0], t[1], bf[0][0], bf[1][0], bf[2][0]);
+      limbs2(t[2], t[3], bf[0][1], bf[1][1], bf[2][1]);
+#pragma unroll
+      for (int mt = 0; mt < 2; ++mt) {
+        mma_bf16(big[mt][nt], af[0][mt], bf[0][0], bf[0][1]);
+        mma_bf16(sml[mt][nt], af[0][mt], bf[1][0], bf[1][1]);
+        mma_bf16(sml[mt][nt], af[0][mt], bf[2][0], bf[2][1]);
+        if (la > 1) {
+          mma_bf16(sml[mt][nt], af[1][mt], bf[0][0], bf[0][1]);
+          mma_bf16(sml[mt][nt], af[1][mt], bf[1][0], bf[1][1]);
+        }
+        if (la > 2) mma_bf16(sml[mt][nt], af[2][mt], bf[0][0], bf[0][1]);
+      }
+    }
+  }
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+    for (int nt = 0; nt < NT; ++nt) {
+      ff_add_f2(fhi[mt][nt][0], flo[mt][nt][0],
+                __fadd2_rn(make_float2(big[mt][nt][0], big[mt][nt][1]), make_float2(sml[mt][nt][0], sml[mt][nt][1])));
+      ff_add_f2(fhi[mt][nt][1], flo[mt][nt][1],
+                __fadd2_rn(make_float2(big[mt][nt][2], big[mt][nt][3]), make_float2(sml[mt][nt][2], sml[mt][nt][3])));
+    }
+}
+
+// The same piece on the FP32 pipes: every product is one FP32 FMA (FFMA2 over
+// right-hand-side pairs), as in the single-RHS kernels.  The lane keeps the
+// fragment kernel's output mapping (rows 32 wi + 4 g + u, u = 2 mt + h;
+// right-hand sides 8 nt + 2 tq + {0, 1}): per column it decodes its 4 codes
+// and reads its 8 multipliers.
+template <int F, int B>
+__device__ __forceinline__ void ms_piece(uint32_t sa, const PieceHdr& H, F2 alpha_ff, int wi, int lane,
+                                         float2 (&fhi)[2][NT][2], float2 (&flo)[2][NT][2]) {
+  const int R = H.nrows, nc = H.ncols;
+  const bool tile = (H.flags & PH_TILE) != 0;
+  const uint32_t stride = pad8u((uint32_t)R * B);
+  const uint32_t cm = sa + (uint32_t)sizeof(PieceHdr);
+  const int g = lane >> 2, tq = lane & 3;
+  const uint32_t cb = cm + (tile ? 0u : pad8u(2u * nc)) + (uint32_t)((32 * wi + 4 * g) * B);
+  const uint32_t tv = sa + STAGE_BYTES + 8u * tq;
+  const int e_t = H.em & 0xff, m_t = H.em >> 8;
+  float2 acc[4][NT];
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int nt = 0; nt < NT; ++nt) acc[u][nt] = make_float2(0.f, 0.f);
+#pragma unroll 2
+  for (int j = 0; j < nc; ++j) {
+    int e = e_t, m = m_t;
+    if constexpr (F == 2) {
+      if (!tile) {
+        const uint32_t em = lds32((cm + 2u * j) & ~3u) >> (16u * (j & 1));
+        e = em & 0xff;
+        m = (em >> 8) & 0xff;
+      }
+    }
+    uint32_t w[B];
+#pragma unroll
+    for (int b = 0; b < B; ++b) w[b] = lds32(cb + (uint32_t)j * stride + 4u * b);
+    float v[4], l[4];
+    decode4<TIER_F32, F, B>(w, e, m, v, l);
+    float2 t[NT];
+#pragma unroll
+    for (int nt = 0; nt < NT; ++nt) {
+      const uint2 q = lds64(tv + (uint32_t)j * MP_TP + 32u * nt);
+      t[nt] = make_float2(__uint_as_float(q.x), __uint_as_float(q.y));
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const float2 vv = make_float2(v[u], v[u]);
+#pragma unroll
+      for (int nt = 0; nt < NT; ++nt) acc[u][nt] = __ffma2_rn(vv, t[nt], acc[u][nt]);
+    }
+  }
+  float2 sc2 = make_float2(1.f, 1.f);
+  if (tile) {
+    FF f = {H.scale.hi, H.scale.lo};
+    if (H.flags & PH_TALPHA) f = ff_mul(f, FF{alpha_ff.hi, alpha_ff.lo});
+    sc2 = make_float2(f.hi, f.hi);
+  }
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+      for (int nt = 0; nt < NT; ++nt)
+        ff_add_f2(fhi[mt][nt][h], flo[mt][nt][h], tile ? __fmul2_rn(acc[2 * mt + h][nt], sc2) : acc[2 * mt + h][nt]);
+}
+
+// ENG 0: tensor-core fragments (mp_piece); 1: FP32 pipes (ms_piece).
+template <int MODE, int ENG>
+__global__ void __launch_bounds__(MP_THREADS, 1)
+    k_rgemv_mp(const PieceCopy* __restrict__ cps, const int32_t* __restrict__ wbeg, int nrange,
+               const uint8_t* __restrict__ pay, const float* __restrict__ vec, double alpha, F2 alpha_ff,
+               double beta, double* __restrict__ y, int64_t ldy, int r, const int32_t* __restrict__ perm,
+               float* __restrict__ vout, const F2* __restrict__ rowscale, F2* __restrict__ fix,
+               int32_t* __restrict__ fixcnt, const Split* __restrict__ splits, const int32_t* __restrict__ fan,
+               int32_t fan_base, int* err) {
+  extern __shared__ __align__(128) uint8_t smem[];
+  __shared__ int4 info[MP_PAIRS][MP_NS];
+  __shared__ int s_last[MP_PAIRS];
+  const int pair = threadIdx.x >> 6, wi = (threadIdx.x >> 5) & 1, lane = threadIdx.x & 31;
+  const int gp = blockIdx.x * MP_PAIRS + pair;
+  if (gp >= nrange) return;   // the whole pair
+  const int p0 = wbeg[gp], n = wbeg[gp + 1] - p0;
+  if (n <= 0) return;
+  uint8_t* ring = smem + (size_t)pair * MP_NS * MP_STAGE;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + (size_t)MP_PAIRS * MP_NS * MP_STAGE) + pair * MP_NS;
+  const int bid = 1 + pair;
+  const uint64_t pol = policy_evict_first();
+  // warp 0 of the pair issues the copies; its lanes hold the copy descriptors 32 at a time
+  const PieceCopy zero{0, 0, 0, -1};
+  PieceCopy dc = zero, dn = zero;
+  int dbase = 0;
+  if (wi == 0) {
+    dc = lane < n ? cps[p0 + lane] : zero;
+    dn = 32 + lane < n ? cps[p0 + 32 + lane] : zero;
+  }
+  auto issue = [&](int i) {   // warp 0 of the pair
+    if (i - dbase >= 32) {
+      dc = dn;
+      dbase += 32;
+      dn = dbase + 32 + lane < n ? cps[p0 + dbase + 32 + lane] : zero;
+    }
+    const int sl = i - dbase;
+    const uint32_t off16 = __shfl_sync(HM_FULL, dc.off16, sl), bf = __shfl_sync(HM_FULL, dc.bytes_flags, sl);
+    const int32_t moff = __shfl_sync(HM_FULL, dc.moff, sl), sp = __shfl_sync(HM_FULL, dc.split_part, sl);
+    const int s = i % MP_NS;
+    uint8_t* st = ring + (size_t)s * MP_STAGE;
+    const uint32_t nc = bf >> 24, pb = pad16m(bf & 0xffffu);
+    fence_proxy_async();
+    if (lane == 0) {
+      info[pair][s] = make_int4((int)((bf >> 16) & 0xffu), sp, 0, 0);
+      mbar_expect_tx(&bars[s], pb + nc * RP * 4u);
+      bulk_g2s_hint(st, pay + (uint64_t)off16 * 16u, pb, &bars[s], pol);
+    }
+    __syncwarp();
+    // multiplier row j: the RP values of vector entry moff + j, or of fan[moff - fan_base + j] for a fan-out run
+    const bool fan_run = moff >= fan_base;
+    for (int j = lane; j < (int)nc; j += 32) {
+      const int32_t src = fan_run ? __ldg(fan + (moff - fan_base) + j) : moff + j;
+      bulk_g2s(st + STAGE_BYTES + j * MP_TP, vec + (int64_t)src * RP, RP * 4u, &bars[s]);
+    }
+  };
+  if (wi == 0) {
+    if (lane == 0) {
+      for (int s = 0; s < MP_NS; ++s) mbar_init(&bars[s], 1);
+      mbar_init_fence();
+    }
+    __syncwarp();
+    for (int i = 0; i < MP_NS && i < n; ++i) issue(i);
+  }
+  pair_sync(bid);   // the barriers are initialised before warp 1 waits on them
+  const int g = lane >> 2, tq = lane & 3;
+  float2 fhi[2][NT][2], flo[2][NT][2];
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+    for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        fhi[mt][nt][h] = make_float2(0.f, 0.f);
+        flo[mt][nt][h] = make_float2(0.f, 0.f);
+      }
+  for (int i = 0; i < n; ++i) {
+    const int s = i % MP_NS;
+    const bool ok = mbar_wait(&bars[s], (uint32_t)((i / MP_NS) & 1));
+    if (pair_any(bid, !ok)) {   // a copy did not arrive in time: wait (bounded) for those in flight, give up
+      if (wi == 0 && lane == 0) {
+        latch_error(err, 99);
+        for (int j = i; j < n && j < i + MP_NS; ++j)
+          mbar_wait(&bars[j % MP_NS], (uint32_t)((j / MP_NS) & 1), 50u);
+      }
+      return;
+    }
+    const uint32_t sa = smem_u32(ring + (size_t)s * MP_STAGE);
+    PieceHdr H;
+    {
+      const uint4 a = lds128(sa), b = lds128(sa + 16);
+      H.row0 = (int32_t)a.x;
+      H.nrows = (uint16_t)(a.y & 0xffffu);
+      H.flags = (uint16_t)(a.y >> 16);
+      H.fb = (uint16_t)(a.z & 0xffffu);
+      H.em = (uint16_t)(a.z >> 16);
+      H.vin0 = (int32_t)a.w;
+      H.ncols = (uint16_t)(b.x & 0xffffu);
+      H.limbs = (uint16_t)(b.x >> 16);
+      H.scale = F2{__uint_as_float(b.z), __uint_as_float(b.w)};
+    }
+    const int4 rinfo = info[pair][s];
+    const int R = H.nrows;
+    if (rinfo.x & PD_FIRST) {
+#pragma unroll
+      for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            fhi[mt][nt][h] = make_float2(0.f, 0.f);
+            flo[mt][nt][h] = make_float2(0.f, 0.f);
+          }
+    }
+    if (32 * wi < R) {
+      switch (H.fb) {
+#define HM_MP(FF_, BB_)                                          \
+  case ((FF_) << 4) | (BB_):                                     \
+    if constexpr (ENG == 0)                                      \
+      mp_piece<FF_, BB_>(sa, H, alpha_ff, wi, lane, fhi, flo);   \
+    else                                                         \
+      ms_piece<FF_, BB_>(sa, H, alpha_ff, wi, lane, fhi, flo);   \
+    break;
+        HM_FORMATS(HM_MP)
+#undef HM_MP
+        default:
+          latch_error(err, 13);
+      }
+    }
+    if (rinfo.x & PD_LAST) {
+      const bool calpha = (H.flags & PH_CALPHA) != 0;
+      const bool split = (rinfo.x & PD_SPLIT) != 0;
+      const Split sp = split ? splits[rinfo.y >> 8] : Split{0, 1};
+      bool emit = !split;
+      if (split) {   // this part's rows, then the last part to arrive adds them all in part order
+        F2* mine = fix + (size_t)(sp.slot0 + (rinfo.y & 0xff)) * CHUNK_ROWS * RP;
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int row = 32 * wi + 4 * g + 2 * mt + h;
+            if (row < R) {
+#pragma unroll
+              for (int nt = 0; nt < NT; ++nt) {
+                const int k = 8 * nt + 2 * tq;
+                *reinterpret_cast<float4*>(mine + row * RP + k) =
+                    make_float4(fhi[mt][nt][h].x, flo[mt][nt][h].x, fhi[mt][nt][h].y, flo[mt][nt][h].y);
+              }
+            }
+          }
+        pair_sync(bid);   // both warps' rows before warp 0's release
+        if (wi == 0 && lane == 0) s_last[pair] = atom_add_acq_rel(&fixcnt[rinfo.y >> 8], 1) == sp.nparts - 1;
+        pair_sync(bid);   // the acquire before the parts are read
+        emit = s_last[pair] != 0;
+      }
+      if (emit) {
+        if (split) {
+#pragma unroll
+          for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+            for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+              for (int h = 0; h < 2; ++h) {
+                fhi[mt][nt][h] = make_float2(0.f, 0.f);
+                flo[mt][nt][h] = make_float2(0.f, 0.f);
+              }
+          for (int part = 0; part < sp.nparts; ++part) {
+            const F2* src = fix + (size_t)(sp.slot0 + part) * CHUNK_ROWS * RP;
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+              for (int h = 0; h < 2; ++h) {
+                const int row = 32 * wi + 4 * g + 2 * mt + h;
+                if (row < R) {
+#pragma unroll
+                  for (int nt = 0; nt < NT; ++nt) {
+                    const float4 v = __ldcg(reinterpret_cast<const float4*>(src + row * RP + 8 * nt + 2 * tq));
+                    const FF a = ff_add(FF{fhi[mt][nt][h].x, flo[mt][nt][h].x}, FF{v.x, v.y});
+                    const FF b = ff_add(FF{fhi[mt][nt][h].y, flo[mt][nt][h].y}, FF{v.z, v.w});
+                    fhi[mt][nt][h] = make_float2(a.hi, b.hi);
+                    flo[mt][nt][h] = make_float2(a.lo, b.lo);
+                  }
+                }
+              }
+          }
+        }
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int row = 32 * wi + 4 * g + 2 * mt + h;
+            if (row >= R) continue;
+            if constexpr (MODE == MODE_Y) {
+              const int o = __ldg(perm + H.row0 + row);
+              double yo[NT][2];
+#pragma unroll
+              for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                  const int k = 8 * nt + 2 * tq + c;
+                  yo[nt][c] = (beta != 0.0 && k < r) ? y[o + (int64_t)k * ldy] : 0.0;
+                }
+#pragma unroll
+              for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                  const int k = 8 * nt + 2 * tq + c;
+                  if (k < r) {
+                    const double val = ff_to_d(FF{c ? fhi[mt][nt][h].y : fhi[mt][nt][h].x,
+                                                  c ? flo[mt][nt][h].y : flo[mt][nt][h].x});
+                    y[o + (int64_t)k * ldy] = (beta == 0.0) ? val : fma(beta, yo[nt][c], val);
+                  }
+                }
+            } else {   // coefficient panels: float-float updates, one rounding to FP32
+              const int gg = H.row0 + row;
+              const F2 rsc = rowscale ? rowscale[gg] : F2{1.f, 0.f};
+#pragma unroll
+              for (int nt = 0; nt < NT; ++nt) {
+                const int k0 = 8 * nt + 2 * tq;
+                const float2 old = (MODE == MODE_VEC_ADD) ? *reinterpret_cast<const float2*>(vout + (int64_t)gg * RP + k0)
+                                                          : make_float2(0.f, 0.f);
+#pragma unroll
+                for (int c = 0; c < 2; ++c)
+                  if (k0 + c < r) {
+                    FF v = {c ? fhi[mt][nt][h].y : fhi[mt][nt][h].x, c ? flo[mt][nt][h].y : flo[mt][nt][h].x};
+                    if constexpr (MODE == MODE_VEC_ADD) v = ff_add_f(v, c ? old.y : old.x);
+                    if (rowscale) v = ff_mul(v, FF{rsc.hi, rsc.lo});
+                    if (calpha) v = ff_mul(v, FF{alpha_ff.hi, alpha_ff.lo});
+                    vout[(int64_t)gg * RP + k0 + c] = v.hi + v.lo;
+                  }
+              }
+            }
+          }
+      }
+      if (split && emit && wi == 0 && lane == 0) fixcnt[rinfo.y >> 8] = 0;
+    }
+    pair_sync(bid);   // both warps are done with stage s
+    if (wi == 0 && i + MP_NS < n) issue(i + MP_NS);
+  }
+}
+
+// ---------------------------------------------------------------- column dots, register fragments
+// out (nc x RP) = A^T (nc x R) X (R x RP) for each piece, with the piece values
+// decoded straight into mma.sync A fragments.  A pair of warps owns a range of
+// pieces and a ring of MP_NS stages (piece, and the input segment's RP-wide
+// rows when the segment changes); warp wi takes the piece's columns
+// 32 wi .. 32 wi + 31.  The B fragments of the input segment (its rows x RP,
+// three BF16 limbs) are built once per segment into a per-pair cache.
+//
+// m16n8k16 fragments (lane = 4 g + tq): A (16 x 16) rows = columns
+// 32 wi + 16 mt + g (+ 8), A columns = segment rows, permuted so that fragment
+// k = 2 tq + {0, 1} / 2 tq + 8 + {0, 1} of k step ks are the rows
+// 16 ks + 4 tq + {0, 1} / + {2, 3}: a lane decodes 4 consecutive codes of each
+// of its two columns.  B (16 x 8) = X rows x right-hand sides 8 nt + g.  C
+// registers (c0, c1 | c2, c3) of tile (mt, nt) hold column 32 wi + 16 mt + g
+// (| + 8), right-hand sides 8 nt + 2 tq + {0, 1}.
+constexpr int CP_STAGE = STAGE_BYTES + SEG_ROWS * RP * 4;            // piece + input segment rows
+constexpr int CP_XF = (SEG_ROWS / 16) * 3 * 2 * 32 * 16;             // B-fragment cache of one pair
+constexpr size_t CP_SMEM = (size_t)MP_PAIRS * (MP_NS * CP_STAGE + CP_XF) + (size_t)MP_PAIRS * MP_NS * 8;
+static_assert(CP_STAGE % 128 == 0 && CP_XF % 128 == 0, "stage alignment");
+static_assert(CP_SMEM <= 227 * 1024, "register-fragment column-dot kernel: one block per SM");
+
+// B fragments of k step ks of the segment whose rows (R of them, RP values each)
+// start at shared address xa, for this lane: limb l, rhs tiles 4 h + {0..3}...
+// stored as uint4 q = (ks * 3 + l) * 2 + h at xf + (q * 32 + lane) * 16 holding
+// (nt = 2 h, r0), (2 h, r1), (2 h + 1, r0), (2 h + 1, r1).
+__device__ __forceinline__ void cp_build_xf(uint32_t xa, uint32_t xf, int ks, int R, int lane) {
+  const int g = lane >> 2, tq = lane & 3;
+  uint32_t b[3][NT][2];
+#pragma unroll
+  for (int nt = 0; nt < NT; ++nt) {
+    float x[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int row = 16 * ks + 4 * tq + u;
+      x[u] = row < R ? __uint_as_float(lds32(xa + (uint32_t)(row * RP + 8 * nt + g) * 4u)) : 0.f;
+    }
+    limbs2(x[0], x[1], b[0][nt][0], b[1][nt][0], b[2][nt][0]);
+    limbs2(x[2], x[3], b[0][nt][1], b[1][nt][1], b[2][nt][1]);
+  }
+#pragma unroll
+  for (int l = 0; l < 3; ++l)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const uint32_t q = (uint32_t)((ks * 3 + l) * 2 + h);
+      asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(xf + (q * 32u + (uint32_t)lane) * 16u),
+                   "r"(b[l][2 * h][0]), "r"(b[l][2 * h][1]), "r"(b[l][2 * h + 1][0]), "r"(b[l][2 * h + 1][1])
+                   : "memory");
+    }
+}
+
+template <int F, int B>
+__device__ __forceinline__ void cp_piece(uint32_t sa, uint32_t xf, int R, int nc, int flags, int la, F2 alpha,
+                                         int wi, int lane, float* __restrict__ partial, float* __restrict__ vout) {
+  const int g = lane >> 2, tq = lane & 3;
+  const bool fin = (flags & ITEM_FINAL) != 0;
+  const int Rp = (R + 15) & ~15;   // rows R .. Rp - 1 hold zero codes
+  const uint32_t stride = (uint32_t)Rp * B;
+  const uint32_t cm = sa + (uint32_t)sizeof(CPieceHdr);
+  const uint32_t scl = cm + 8u * nc;
+  const uint32_t cb = cm + (fin ? 16u : 8u) * nc + (uint32_t)(4 * tq * B);
+  float big[2][NT][4], sml[2][NT][4];
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+    for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        big[mt][nt][u] = 0.f;
+        sml[mt][nt][u] = 0.f;
+      }
+  // decode parameters and code addresses of the lane's 4 columns (mt, +8)
+  int ee[2][2], mm[2][2];
+  uint32_t ca[2][2];
+  bool on[2][2];
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const int j = 32 * wi + 16 * mt + g + 8 * c;
+      on[mt][c] = j < nc;
+      const int jj = on[mt][c] ? j : 0;
+      ee[mt][c] = 0;
+      mm[mt][c] = 0;
+      if constexpr (F == 2) {
+        const uint32_t em = lds32(cm + 8u * jj) & 0xffffu;
+        ee[mt][c] = em & 0xff;
+        mm[mt][c] = em >> 8;
+      }
+      ca[mt][c] = cb + (uint32_t)jj * stride;
+    }
+  const bool mt1 = 32 * wi + 16 < nc;   // the second column tile holds a column
+  for (int ks = 0; ks < Rp / 16; ++ks) {
+    uint32_t bx[3][NT][2];
+#pragma unroll
+    for (int l = 0; l < 3; ++l)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const uint4 v = lds128(xf + ((uint32_t)((ks * 3 + l) * 2 + h) * 32u + (uint32_t)lane) * 16u);
+        bx[l][2 * h][0] = v.x;
+        bx[l][2 * h][1] = v.y;
+        bx[l][2 * h + 1][0] = v.z;
+        bx[l][2 * h + 1][1] = v.w;
+      }
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt) {
+      if (mt == 1 && !mt1) break;
+      float v[2][4];
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        uint32_t w[B];
+#pragma unroll
+        for (int b = 0; b < B; ++b) w[b] = lds32(ca[mt][c] + (uint32_t)(16 * ks * B) + 4u * b);
+        float l[4];
+        decode4<TIER_F32, F, B>(w, ee[mt][c], mm[mt][c], v[c], l);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) v[c][u] = on[mt][c] ? v[c][u] : 0.f;
+      }
+      uint32_t af[3][4];
+      limbs2(v[0][0], v[0][1], af[0][0], af[1][0], af[2][0]);
+      limbs2(v[1][0], v[1][1], af[0][1], af[1][1], af[2][1]);
+      limbs2(v[0][2], v[0][3], af[0][2], af[1][2], af[2][2]);
+      limbs2(v[1][2], v[1][3], af[0][3], af[1][3], af[2][3]);
+#pragma unroll
+      for (int nt = 0; nt < NT; ++nt) {
+        mma_bf16(big[mt][nt], af[0], bx[0][nt][0], bx[0][nt][1]);
+        mma_bf16(sml[mt][nt], af[0], bx[1][nt][0], bx[1][nt][1]);
+        mma_bf16(sml[mt][nt], af[0], bx[2][nt][0], bx[2][nt][1]);
+        if (la > 1) {
+          mma_bf16(sml[mt][nt], af[1], bx[0][nt][0], bx[0][nt][1]);
+          mma_bf16(sml[mt][nt], af[1], bx[1][nt][0], bx[1][nt][1]);
+        }
+        if (la > 2) mma_bf16(sml[mt][nt], af[2], bx[0][nt][0], bx[0][nt][1]);
+      }
+    }
+  }
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      if (!on[mt][c]) continue;
+      const int j = 32 * wi + 16 * mt + g + 8 * c;
+      const int32_t out = (int32_t)lds32(cm + 8u * j + 4u);
+      FF sc = {1.f, 0.f};
+      if (fin) {
+        const uint2 f = lds64(scl + 8u * j);
+        sc = FF{__uint_as_float(f.x), __uint_as_float(f.y)};
+        if (flags & ITEM_ALPHA) sc = ff_mul(sc, FF{alpha.hi, alpha.lo});
+      }
+#pragma unroll
+      for (int nt = 0; nt < NT; ++nt) {
+        const float2 r2 = __fadd2_rn(make_float2(big[mt][nt][2 * c], big[mt][nt][2 * c + 1]),
+                                     make_float2(sml[mt][nt][2 * c], sml[mt][nt][2 * c + 1]));
+        const int k = 8 * nt + 2 * tq;
+        if (fin) {
+          const FF v0 = ff_mul(FF{r2.x, 0.f}, sc), v1 = ff_mul(FF{r2.y, 0.f}, sc);
+          *reinterpret_cast<float2*>(vout + (int64_t)out * RP + k) = make_float2(v0.hi + v0.lo, v1.hi + v1.lo);
+        } else {
+          *reinterpret_cast<float2*>(partial + (int64_t)out * RP + k) = r2;
+        }
+      }
+    }
+}
+
+__global__ void __launch_bounds__(MP_THREADS, 1)
+    k_cdot_mp(const ItemCopy* __restrict__ cps, const int32_t* __restrict__ wbeg, int nrange,
+              const uint8_t* __restrict__ pay, const float* __restrict__ vec, F2 alpha, float* __restrict__ partial,
+              float* __restrict__ vout, int* err) {
+  extern __shared__ __align__(128) uint8_t smem[];
+  const int pair = threadIdx.x >> 6, wi = (threadIdx.x >> 5) & 1, lane = threadIdx.x & 31;
+  const int gp = blockIdx.x * MP_PAIRS + pair;
+  if (gp >= nrange) return;   // the whole pair
+  const int p0 = wbeg[gp], n = wbeg[gp + 1] - p0;
+  if (n <= 0) return;
+  uint8_t* ring = smem + (size_t)pair * (MP_NS * CP_STAGE + CP_XF);
+  const uint32_t xf = smem_u32(ring + (size_t)MP_NS * CP_STAGE);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + (size_t)MP_PAIRS * (MP_NS * CP_STAGE + CP_XF)) + pair * MP_NS;
+  const int bid = 1 + pair;
+  const uint64_t pol = policy_evict_first();
+  const ItemCopy zero{0, 0, -1, 0};
+  ItemCopy dc = zero, dn = zero;
+  int dbase = 0;
+  int32_t last_vin = -1, last_rows = -1;   // input segment of the last issued piece
+  if (wi == 0) {
+    dc = lane < n ? cps[p0 + lane] : zero;
+    dn = 32 + lane < n ? cps[p0 + 32 + lane] : zero;
+  }
+  auto issue = [&](int i) {   // warp 0 of the pair
+    if (i - dbase >= 32) {
+      dc = dn;
+      dbase += 32;
+      dn = dbase + 32 + lane < n ? cps[p0 + dbase + 32 + lane] : zero;
+    }
+    const int sl = i - dbase;
+    const uint32_t off16 = __shfl_sync(HM_FULL, dc.off16, sl), bytes = __shfl_sync(HM_FULL, dc.bytes, sl);
+    const int32_t vin = __shfl_sync(HM_FULL, dc.vin, sl), nrows = __shfl_sync(HM_FULL, dc.nrows, sl);
+    const bool newx = vin != last_vin || nrows != last_rows;
+    last_vin = vin;
+    last_rows = nrows;
+    if (lane == 0) {
+      const int s = i % MP_NS;
+      uint8_t* st = ring + (size_t)s * CP_STAGE;
+      const uint32_t pb = pad16m(bytes), xb = newx ? (uint32_t)nrows * RP * 4u : 0u;
+      fence_proxy_async();
+      mbar_expect_tx(&bars[s], pb + xb);
+      bulk_g2s_hint(st, pay + (uint64_t)off16 * 16u, pb, &bars[s], pol);
+      if (newx) bulk_g2s(st + STAGE_BYTES, vec + (int64_t)vin * RP, xb, &bars[s]);
+    }
+  };
+  if (wi == 0) {
+    if (lane == 0) {
+      for (int s = 0; s < MP_NS; ++s) mbar_init(&bars[s], 1);
+      mbar_init_fence();
+    }
+    __syncwarp();
+    for (int i = 0; i < MP_NS && i < n; ++i) issue(i);
+  }
+  pair_sync(bid);   // the barriers are initialised before warp 1 waits on them
+  int32_t xv = -1, xr = -1;   // segment of the fragment cache
+  for (int i = 0; i < n; ++i) {
+    const int s = i % MP_NS;
+    const bool ok = mbar_wait(&bars[s], (uint32_t)((i / MP_NS) & 1));
+    if (pair_any(bid, !ok)) {   // a copy did not arrive in time: wait (bounded) for those in flight, give up
+      if (wi == 0 && lane == 0) {
+        latch_error(err, 99);
+        for (int j = i; j < n && j < i + MP_NS; ++j)
+          mbar_wait(&bars[j % MP_NS], (uint32_t)((j / MP_NS) & 1), 50u);
+      }
+      return;
+    }
+    const uint32_t sa = smem_u32(ring + (size_t)s * CP_STAGE);
+    const uint4 hw = lds128(sa);   // CPieceHdr
+    const int32_t hvin = (int32_t)hw.x;
+    const int R = (int)(hw.y & 0xffffu), nc = (int)(hw.y >> 16);
+    const uint32_t fb = hw.z & 0xffffu, flags = hw.z >> 16;
+    const int la = (int)hw.w;
+    if (hvin != xv || R != xr) {   // this piece brought a new input segment: rebuild the cache
+      for (int ks = wi; ks < (R + 15) / 16; ks += 2) cp_build_xf(sa + STAGE_BYTES, xf, ks, R, lane);
+      xv = hvin;
+      xr = R;
+      pair_sync(bid);
+    }
+    if (32 * wi < nc) {
+      switch (fb) {
+#define HM_CP(FF_, BB_) \
+  case ((FF_) << 4) | (BB_): cp_piece<FF_, BB_>(sa, xf, R, nc, (int)flags, la, alpha, wi, lane, partial, vout); break;
+        HM_FORMATS(HM_CP)
+#undef HM_CP
+        default:
+          latch_error(err, 14);
+      }
+    }
+    pair_sync(bid);   // both warps are done with stage s and the cache
+    if (wi == 0 && i + MP_NS < n) issue(i + MP_NS);
+  }
+}
+
+// ---------------------------------------------------------------- column dots, FP32 pipes
+// out (nc x RP) = A^T (nc x R) X (R x RP) with one FP32 FMA per product, one
+// warp per range of pieces (its own ring of CW_NS stages, pieces only).  Lane
+// (tq = lane / 8, g = lane % 8) holds the input rows 8 g .. 8 g + 7 of the
+// segment for the right-hand sides 8 tq .. 8 tq + 7 in registers (read from
+// the panel when the segment changes); per column it decodes its 8 codes,
+// forms the 8 partial dots over its rows (FFMA2) and a reduce-scatter over the
+// 8 lanes g leaves lane g with the column's total for right-hand side 8 tq + g
+// (each column sums its <= 64 rows in FP32, as the single-RHS kernel).
+constexpr int CW_WARPS = 16;
+constexpr int CW_NS = 2;
+constexpr size_t CW_SMEM = (size_t)CW_WARPS * CW_NS * STAGE_BYTES + (size_t)CW_WARPS * CW_NS * 8;
+static_assert(CW_SMEM <= 227 * 1024, "column-dot warps per block");
+
+// Reduce-scatter of 8 values over the 8 lanes q = lane bits 0..2 (fixed
+// pattern): returns the lanes' total of value q.
+__device__ __forceinline__ float rs8(float (&p)[8], int q) {
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const bool up = (q & 4) != 0;
+    const float send = up ? p[k] : p[k + 4], keep = up ? p[k + 4] : p[k];
+    p[k] = keep + __shfl_xor_sync(HM_FULL, send, 4);
+  }
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const bool up = (q & 2) != 0;
+    const float send = up ? p[k] : p[k + 2], keep = up ? p[k + 2] : p[k];
+    p[k] = keep + __shfl_xor_sync(HM_FULL, send, 2);
+  }
+  const bool up = (q & 1) != 0;
+  const float send = up ? p[0] : p[1], keep = up ? p[1] : p[0];
+  return keep + __shfl_xor_sync(HM_FULL, send, 1);
+}
+
+template <int F, int B>
+__device__ __forceinline__ void cw_piece(uint32_t sa, int R, int nc, int flags, const float2 (&xr)[8][4], int lane,
+                                         F2 alpha, float* __restrict__ partial, float* __restrict__ vout) {
+  const int tq = lane >> 3, g = lane & 7;
+  const bool fin = (flags & ITEM_FINAL) != 0;
+  const int Rp = (R + 15) & ~15;   // rows R .. Rp - 1 hold zero codes
+  const uint32_t stride = (uint32_t)Rp * B;
+  const uint32_t cm = sa + (uint32_t)sizeof(CPieceHdr);
+  const uint32_t scl = cm + 8u * nc;
+  const uint32_t cb = cm + (fin ? 16u : 8u) * nc + (uint32_t)(8 * g * B);
+  const bool rows_on = 8 * g < Rp;
+  const FF fa = {alpha.hi, alpha.lo};
+#pragma unroll 2
+  for (int j = 0; j < nc; ++j) {
+    int e = 0, m = 0;
+    if constexpr (F == 2) {
+      const uint32_t em = lds32(cm + 8u * j) & 0xffffu;
+      e = em & 0xff;
+      m = em >> 8;
+    }
+    float2 h2[4] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+    if (rows_on) decode8p<F, B>(cb + (uint32_t)j * stride, e, m, h2);
+    float2 p2[4] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const float v = (u & 1) ? h2[u >> 1].y : h2[u >> 1].x;
+      const float2 vv = make_float2(v, v);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) p2[k] = __ffma2_rn(vv, xr[u][k], p2[k]);
+    }
+    float p[8] = {p2[0].x, p2[0].y, p2[1].x, p2[1].y, p2[2].x, p2[2].y, p2[3].x, p2[3].y};
+    const float tot = rs8(p, g);
+    const int32_t out = (int32_t)lds32(cm + 8u * j + 4u);
+    const int64_t o = (int64_t)out * RP + 8 * tq + g;
+    if (fin) {
+      const uint2 f = lds64(scl + 8u * j);
+      FF sc = {__uint_as_float(f.x), __uint_as_float(f.y)};
+      if (flags & ITEM_ALPHA) sc = ff_mul(sc, fa);
+      const FF v = ff_mul(FF{tot, 0.f}, sc);
+      vout[o] = v.hi + v.lo;
+    } else {
+      partial[o] = tot;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(CW_WARPS * 32, 1)
+    k_cdot_ws(const ItemCopy* __restrict__ cps, const int32_t* __restrict__ wbeg, int nrange,
+              const uint8_t* __restrict__ pay, const float* __restrict__ vec, F2 alpha, float* __restrict__ partial,
+              float* __restrict__ vout, int* err) {
+  extern __shared__ __align__(128) uint8_t smem[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int gw = blockIdx.x * CW_WARPS + warp;
+  if (gw >= nrange) return;
+  const int p0 = wbeg[gw], n = wbeg[gw + 1] - p0;
+  if (n <= 0) return;
+  uint8_t* ring = smem + (size_t)warp * CW_NS * STAGE_BYTES;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + (size_t)CW_WARPS * CW_NS * STAGE_BYTES) + warp * CW_NS;
+  const uint64_t pol = policy_evict_first();
+  const ItemCopy zero{0, 0, -1, 0};
+  ItemCopy dc = lane < n ? cps[p0 + lane] : zero;
+  ItemCopy dn = 32 + lane < n ? cps[p0 + 32 + lane] : zero;
+  int dbase = 0;
+  auto issue = [&](int i) {   // all lanes
+    if (i - dbase >= 32) {
+      dc = dn;
+      dbase += 32;
+      dn = dbase + 32 + lane < n ? cps[p0 + dbase + 32 + lane] : zero;
+    }
+    const int sl = i - dbase;
+    const uint32_t off16 = __shfl_sync(HM_FULL, dc.off16, sl), bytes = __shfl_sync(HM_FULL, dc.bytes, sl);
+    if (lane == 0) {
+      const int s = i % CW_NS;
+      const uint32_t pb = pad16m(bytes);
+      fence_proxy_async();
+      mbar_expect_tx(&bars[s], pb);
+      bulk_g2s_hint(ring + (size_t)s * STAGE_BYTES, pay + (uint64_t)off16 * 16u, pb, &bars[s], pol);
+    }
+  };
+  if (lane == 0) {
+    for (int s = 0; s < CW_NS; ++s) mbar_init(&bars[s], 1);
+    mbar_init_fence();
+  }
+  __syncwarp();
+  for (int i = 0; i < CW_NS && i < n; ++i) issue(i);
+  const int tq = lane >> 3, g = lane & 7;
+  float2 xr[8][4];
+  int32_t xv = -1, xn = -1;
+  for (int i = 0; i < n; ++i) {
+    const int s = i % CW_NS;
+    if (!mbar_wait(&bars[s], (uint32_t)((i / CW_NS) & 1))) {   // wait (bounded) for the copies in flight, give up
+      if (lane == 0) {
+        latch_error(err, 99);
+        for (int j = i; j < n && j < i + CW_NS; ++j)
+          mbar_wait(&bars[j % CW_NS], (uint32_t)((j / CW_NS) & 1), 50u);
+      }
+      return;
+    }
+    const uint32_t sa = smem_u32(ring + (size_t)s * STAGE_BYTES);
+    const uint4 hw = lds128(sa);   // CPieceHdr
+    const int32_t hvin = (int32_t)hw.x;
+    const int R = (int)(hw.y & 0xffffu), nc = (int)(hw.y >> 16);
+    const uint32_t fb = hw.z & 0xffffu, flags = hw.z >> 16;
+    if (hvin != xv || R != xn) {   // the input rows of a new segment
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int row = 8 * g + u;
+        float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
+        if (row < R) {
+          const float4* src = reinterpret_cast<const float4*>(vec + (int64_t)(hvin + row) * RP + 8 * tq);
+          a = __ldg(src);
+          b = __ldg(src + 1);
+        }
+        xr[u][0] = make_float2(a.x, a.y);
+        xr[u][1] = make_float2(a.z, a.w);
+        xr[u][2] = make_float2(b.x, b.y);
+        xr[u][3] = make_float2(b.z, b.w);
+      }
+      xv = hvin;
+      xn = R;
+    }
+    switch (fb) {
+#define HM_CW(FF_, BB_) \
+  case ((FF_) << 4) | (BB_): cw_piece<FF_, BB_>(sa, R, nc, (int)flags, xr, lane, alpha, partial, vout); break;
+      HM_FORMATS(HM_CW)
+#undef HM_CW
+      default:
+        latch_error(err, 15);
+    }
+    __syncwarp();
+    if (i + CW_NS < n) issue(i + CW_NS);
+  }
+}
+
 // ---------------------------------------------------------------- launchers
 constexpr size_t MR_SMEM_C = (size_t)MR_STAGES * MR_STAGE + 64 + MR_TILES;
 constexpr size_t MR_SMEM_R = (size_t)MR_STAGES * MR_STAGE + 64 + MR_TILES;
 static_assert(MR_SMEM_R <= 227 * 1024 / MR_BLOCKS_PER_SM, "multi-RHS blocks per SM");
+constexpr size_t MP_SMEM = (size_t)MP_PAIRS * MP_NS * MP_STAGE + (size_t)MP_PAIRS * MP_NS * 8;
+static_assert(MP_SMEM <= 227 * 1024, "register-fragment row-chunk kernel: one block per SM");
 
 cudaError_t mr_init() {
-  cudaError_t e = cudaFuncSetAttribute(k_cdot_mr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MR_SMEM_C);
+  cudaError_t e = cudaFuncSetAttribute(k_cdot_mp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CP_SMEM);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_cdot_ws, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CW_SMEM);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_rgemv_mr<MODE_Y>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MR_SMEM_R);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_rgemv_mr<MODE_VEC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MR_SMEM_R);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_rgemv_mr<MODE_VEC_ADD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MR_SMEM_R);
+#define HM_MPA(M, E) \
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rgemv_mp<M, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MP_SMEM);
+  HM_MPA(MODE_Y, 0) HM_MPA(MODE_VEC, 0) HM_MPA(MODE_VEC_ADD, 0) HM_MPA(MODE_Y, 1) HM_MPA(MODE_VEC, 1) HM_MPA(MODE_VEC_ADD, 1)
+#undef HM_MPA
   return e;
 }
 
@@ -672,18 +1556,52 @@ cudaError_t launch_gsum_mr(const GsumOut* outs, int nouts, const F2* pscale, con
   return cudaGetLastError();
 }
 
-cudaError_t launch_cdot_mr(const ItemCopy* items, const int32_t* wbeg, int nblk, const uint8_t* pay, const float* vec,
-                           F2 alpha, float* partial, float* vout, int* err, cudaStream_t st) {
+// nblk ranges; engine 0: tensor-core fragments (one range per warp pair),
+// 1: FP32 pipes (one range per warp)
+cudaError_t launch_cdot_mr(int engine, const ItemCopy* items, const int32_t* wbeg, int nblk, const uint8_t* pay,
+                           const float* vec, F2 alpha, float* partial, float* vout, int* err, cudaStream_t st) {
   if (nblk <= 0) return cudaSuccess;
-  k_cdot_mr<<<nblk, MR_THREADS, MR_SMEM_C, st>>>(items, wbeg, nblk, pay, vec, alpha, partial, vout, err);
+  if (engine == 0)
+    k_cdot_mp<<<(unsigned)((nblk + MP_PAIRS - 1) / MP_PAIRS), MP_THREADS, CP_SMEM, st>>>(items, wbeg, nblk, pay, vec,
+                                                                                          alpha, partial, vout, err);
+  else
+    k_cdot_ws<<<(unsigned)((nblk + CW_WARPS - 1) / CW_WARPS), CW_WARPS * 32, CW_SMEM, st>>>(items, wbeg, nblk, pay,
+                                                                                             vec, alpha, partial, vout,
+                                                                                             err);
   return cudaGetLastError();
 }
 
-cudaError_t launch_rgemv_mr(int mode, const PieceCopy* pieces, const int32_t* wbeg, int nblk, const uint8_t* pay,
-                            const float* vec, double alpha, F2 alpha_ff, double beta, double* y, int64_t ldy, int r,
-                            const int32_t* perm, float* vout, const F2* rowscale, F2* fix, int32_t* fixcnt,
-                            const Split* splits, const int32_t* fan, int32_t fan_base, int* err, cudaStream_t st) {
+// nblk ranges (one per warp pair); maxrows = rows of the launch's widest chunk;
+// engine 0: tensor-core fragments, 1: FP32 pipes (chunks of at most MP_ROWS rows)
+cudaError_t launch_rgemv_mr(int mode, int engine, const PieceCopy* pieces, const int32_t* wbeg, int nblk, int maxrows,
+                            const uint8_t* pay, const float* vec, double alpha, F2 alpha_ff, double beta, double* y,
+                            int64_t ldy, int r, const int32_t* perm, float* vout, const F2* rowscale, F2* fix,
+                            int32_t* fixcnt, const Split* splits, const int32_t* fan, int32_t fan_base, int* err,
+                            cudaStream_t st) {
   if (nblk <= 0) return cudaSuccess;
+  if (maxrows <= MP_ROWS) {
+    const unsigned grid = (unsigned)((nblk + MP_PAIRS - 1) / MP_PAIRS);
+#define HM_MPG(M, E)                                                                                         \
+  k_rgemv_mp<M, E><<<grid, MP_THREADS, MP_SMEM, st>>>(pieces, wbeg, nblk, pay, vec, alpha, alpha_ff, beta, y, ldy, \
+                                                      r, perm, vout, rowscale, fix, fixcnt, splits, fan, fan_base, err)
+    if (engine == 0) {
+      if (mode == MODE_Y)
+        HM_MPG(MODE_Y, 0);
+      else if (mode == MODE_VEC)
+        HM_MPG(MODE_VEC, 0);
+      else
+        HM_MPG(MODE_VEC_ADD, 0);
+    } else {
+      if (mode == MODE_Y)
+        HM_MPG(MODE_Y, 1);
+      else if (mode == MODE_VEC)
+        HM_MPG(MODE_VEC, 1);
+      else
+        HM_MPG(MODE_VEC_ADD, 1);
+    }
+#undef HM_MPG
+    return cudaGetLastError();
+  }
 #define HM_MRG(M)                                                                                           \
   k_rgemv_mr<M><<<nblk, MR_THREADS, MR_SMEM_R, st>>>(pieces, wbeg, nblk, pay, vec, alpha, alpha_ff, beta, y, ldy, r, \
                                                      perm, vout, rowscale, fix, fixcnt, splits, fan, fan_base, err)

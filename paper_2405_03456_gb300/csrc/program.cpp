@@ -372,6 +372,7 @@ void add_rgemv(Ctx& cx, std::vector<ChunkWork>& cw, int mode, bool rowscale) {
   L.use_rowscale = rowscale;
   L.off = P.npieces;
   L.n = (int64_t)pw.size();
+  for (const ChunkWork& c : cw) L.maxrows = std::max<int>(L.maxrows, (int)c.nrows);
   const int64_t fan0 = (int64_t)P.fan_src.size();
   // lay out (partition-independent headers, decode parameters, columns)
   std::vector<PieceCopy> base(pw.size());
@@ -467,7 +468,7 @@ void add_rgemv(Ctx& cx, std::vector<ChunkWork>& cw, int mode, bool rowscale) {
       L.nw[cf] = 0;
       continue;
     }
-    L.nw[cf] = partition(pb, L.off, cx.nsm * (cf == MR_SHAPE ? MR_BLOCKS_PER_SM : RS_CFG_WARPS[cf]), P.wbeg);
+    L.nw[cf] = partition(pb, L.off, cx.nsm * (cf == MR_SHAPE ? MP_PAIRS : RS_CFG_WARPS[cf]), P.wbeg);
     std::vector<PieceCopy> d = base;
     std::vector<int32_t> nparts(cw.size(), 0), partof(pw.size(), 0);
     const int32_t* wb = P.wbeg.data() + L.woff[cf];
@@ -1018,7 +1019,7 @@ void finish_launches(Ctx& cx) {
         }
         for (int cf = 0; cf < NSHAPES; ++cf) {
           L.woff[cf] = (int64_t)P.wbeg.size();
-          const int nmax = cx.nsm * (cf == MR_SHAPE ? MR_BLOCKS_PER_SM : CS_CFG_WARPS[cf]);
+          const int nmax = cx.nsm * (cf == MR_SHAPE ? MR_CDOT_RANGES : CS_CFG_WARPS[cf]);
           L.nw[cf] = L.n > 0 ? partition(ib, L.off, nmax, P.wbeg) : 0;
         }
         break;

@@ -68,6 +68,7 @@ struct Launch {
   int64_t woff[NSHAPES] = {};     // CDOT / RGEMV, per launch shape: ranges wbeg[woff .. woff + nw]
   int nw[NSHAPES] = {};           // ranges (warps; blocks for the multi-RHS shape) per launch shape
   int cfg = 0;                    // launch shape in use (autotuner choice)
+  int maxrows = 0;                // RGEMV: rows of its widest chunk
 };
 
 struct Program {

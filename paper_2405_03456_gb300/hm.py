@@ -27,7 +27,8 @@ DECLARED = ["hm_build", "hm_compress", "hm_matvec", "hm_matvec_host", "hm_free",
             "hm_profile", "hm_profile_read", "hm_alg_bytes", "hm_matvec_host_noalloc", "hm_graph",
             "hm_autotune", "hm_launch_shapes", "hm_set_launch_shapes", "hm_persistent", "hm_matvec_adjoint",
             "hm_decompress_debug", "hm_save", "hm_load", "hm_lu_build", "hm_lu_compress", "hm_lu_solve",
-            "hm_lu_sync_status", "hm_lu_info", "hm_lu_free", "hm_persistent_mode"]
+            "hm_lu_sync_status", "hm_lu_info", "hm_lu_free", "hm_persistent_mode", "hm_set_multi_rhs_engine",
+            "hm_multi_rhs_engine"]
 NSHAPES = 3
 HM_NOALLOC_MAX_ENTRIES = 1 << 20
 KERNEL_KINDS = ["gather", "cdot", "gsum", "rgemv", "fanout"]
@@ -104,6 +105,8 @@ def load(path: str | None = None) -> C.CDLL:
         "hm_launch_shapes": ([vp, vp, i32, C.POINTER(i32)], i32),
         "hm_set_launch_shapes": ([vp, i32], i32),
         "hm_persistent_mode": ([vp, C.POINTER(i32)], i32),
+        "hm_set_multi_rhs_engine": ([vp, i32], i32),
+        "hm_multi_rhs_engine": ([vp, C.POINTER(i32)], i32),
         "hm_decompress_debug": ([vp, i32, i64, i64, i64, vp, vp, vp, vp, C.POINTER(i64), vp], i32),
         "hm_save": ([vp, C.c_char_p], i32),
         "hm_lu_build": ([C.POINTER(hm_build_params), vp, i64, C.POINTER(vp)], i32),
@@ -397,6 +400,14 @@ class HMatrix:
     def persistent_mode(self):
         m = C.c_int32()
         check(load().hm_persistent_mode(self.h, C.byref(m)), "hm_persistent_mode")
+        return m.value
+
+    def multi_rhs_engine(self, engine=None):
+        """Set (0: tensor cores, 1: FP32 pipes) and/or return the multi-RHS row-chunk engine."""
+        if engine is not None:
+            check(load().hm_set_multi_rhs_engine(self.h, int(engine)), "hm_set_multi_rhs_engine")
+        m = C.c_int32()
+        check(load().hm_multi_rhs_engine(self.h, C.byref(m)), "hm_multi_rhs_engine")
         return m.value
 
     def persistent(self, enable=True):

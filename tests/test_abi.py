@@ -82,5 +82,11 @@ def test_newer_entry_points_check_arguments_and_order(lib):
         assert lib.hm_matvec_adjoint(h, 1.0, buf.ctypes.data, 64, 0.0, buf.ctypes.data, 64, 65, None) == 1
         assert lib.hm_persistent(h, 0) == 0 and lib.hm_persistent(h, 1) == 0 and lib.hm_persistent(h, 2) == 0
         assert lib.hm_persistent(h, 3) == 1 and lib.hm_persistent(h, -1) == 1
+        eng = C.c_int32(-1)
+        assert lib.hm_multi_rhs_engine(h, C.byref(eng)) == 0 and eng.value == 1
+        assert lib.hm_set_multi_rhs_engine(h, 0) == 0 and lib.hm_multi_rhs_engine(h, C.byref(eng)) == 0
+        assert eng.value == 0
+        assert lib.hm_set_multi_rhs_engine(h, 2) == 1 and lib.hm_set_multi_rhs_engine(h, -1) == 1
+        assert lib.hm_set_multi_rhs_engine(None, 0) == 1 and lib.hm_multi_rhs_engine(h, None) == 1
     finally:
         assert lib.hm_free(h) == 0

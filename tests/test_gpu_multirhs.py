@@ -1,5 +1,5 @@
-"""Multi-RHS products (panels of 32 right-hand sides through the block-cooperative
-tensor-core kernels, FP32 tier) against the CPU oracle, through the C ABI.
+"""Multi-RHS products (panels of 32 right-hand sides through the tensor-core
+kernels, FP32 tier) against the CPU oracle, through the C ABI.
 
 Each column of Y := alpha*M*X + beta*Y must be within 4*eps of the oracle's
 uncompressed FP64 product of that column, for RHS counts that give partial
@@ -89,5 +89,38 @@ def test_multi_rhs_matches_single_rhs(hm, oracle_mats):
             ys = torch.zeros(N, dtype=torch.float64, device="cuda")
             M.matvec(1.0, torch.from_numpy(x[:, k].copy()).cuda(), 0.0, ys)
             assert rel(ym[:, k], ys.cpu().numpy()) <= 1e-6
+    finally:
+        M.close()
+
+
+@pytest.mark.parametrize("engine", [0, 1])
+@pytest.mark.parametrize("fmt", ["h", "uh", "h2"])
+@pytest.mark.parametrize("leaf", [32, 64, 128])
+def test_multi_rhs_wide_chunks(hm, fmt, leaf, engine):
+    """Both row-chunk engines (0: tensor-core fragments, 1: FP32 pipes), with
+    leaves of 32 and 64 rows (one and both warps of a pair) and of 128 rows (the
+    shared-tile kernel, for chunks wider than 64 rows): every column of a
+    40-column product equals the single-RHS product of that column to well
+    within the compression tolerance, and repeated panels are bitwise equal."""
+    r = 40
+    pts = synth.sphere_points(N)
+    x = synth.rhs(N, r, seed=11 + leaf)
+    y0 = synth.rhs(N, r, seed=12 + leaf)
+    M = hm.HMatrix(pts, "laplace", leaf, 2.0, fmt, EPS)
+    try:
+        M.compress(EPS, "aflp")
+        assert M.multi_rhs_engine(engine) == engine
+        outs = []
+        for _ in range(2):
+            yd = device_cols(y0)
+            M.matvec(0.75, device_cols(x), 0.5, yd)
+            torch.cuda.synchronize()
+            outs.append(yd.cpu().numpy())
+        assert M.sync_status() == 0
+        assert np.array_equal(outs[0].view(np.uint64), outs[1].view(np.uint64))
+        for k in range(r):
+            ys = torch.from_numpy(y0[:, k].copy()).cuda()
+            M.matvec(0.75, torch.from_numpy(x[:, k].copy()).cuda(), 0.5, ys)
+            assert rel(outs[0][:, k], ys.cpu().numpy()) <= 1e-6, k
     finally:
         M.close()
