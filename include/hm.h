@@ -180,15 +180,16 @@ hm_status hm_persistent_mode(const hm_matrix* m, int32_t* mode);
 
 /*
  * hm_set_multi_rhs_engine -- how the row-chunk steps of multi-RHS panels (the
- * precision / multi-RHS form, FP32 tier) multiply, for chunks of at most 64
- * rows (wider chunks always take the shared-tile tensor-core kernel):
- *   0: tensor cores -- each decoded value and multiplier cut into three exact
- *      BF16 limbs, mma.sync products of limb order <= 2 in FP32;
+ * precision / multi-RHS form, FP32 tier) multiply:
+ *   0: tensor cores (tcgen05) -- each decoded value and multiplier cut into
+ *      three exact BF16 limbs in shared memory, the limb products of order <= 2
+ *      accumulated in TMEM (FP32, orders 0 and 1 + 2 apart);
  *   1 (the default): FP32 pipes -- one FP32 FMA per product, as the single-RHS
- *      kernels.
+ *      kernels, for chunks of at most 64 rows (wider chunks as 0).
  * Both sum per piece in FP32 and across pieces in float-float; results differ
- * only in rounding.  hm_autotune times both on an RP-wide panel and keeps the
- * faster.  Errors: HM_ERR_ARG (engine outside 0..1).
+ * only in rounding.  The column dots of a panel run on the FP32 pipes either
+ * way.  hm_autotune times both engines on an RP-wide panel and keeps the faster.
+ * Errors: HM_ERR_ARG (engine outside 0..1).
  */
 hm_status hm_set_multi_rhs_engine(hm_matrix* m, int32_t engine);
 /* hm_multi_rhs_engine -- the engine in use (0 or 1). */

@@ -22,7 +22,7 @@ NVCC = shutil.which("nvcc") or os.path.join(CUDA, "bin", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 CPP = ["trees.cpp", "linalg.cpp", "build.cpp", "codec.cpp", "program.cpp", "matrix.cpp", "persist.cpp", "lu_factor.cpp", "hlu.cpp"]
-CU = ["kernels.cu", "mrhs.cu", "noalloc.cu", "hlu.cu"]
+CU = ["kernels.cu", "mrhs.cu", "mrhs_tc.cu", "noalloc.cu", "hlu.cu"]
 HDRS = ["hm_internal.h", "dev_types.h", "program.h", "decode.cuh"]
 
 

@@ -420,6 +420,19 @@ __device__ __forceinline__ void split_bf16x3(float a, uint16_t& l0, uint16_t& l1
   l2 = h;
 }
 
+// x = t0 + t1 + t2 with BF16 limbs t by truncation (each step keeps the top 8
+// significant bits of the remainder; the remainders are exact FP32
+// differences); limbs of x in the low half, of y in the high half.
+__device__ __forceinline__ void limbs2(float x, float y, uint32_t& l0, uint32_t& l1, uint32_t& l2) {
+  const uint32_t xu = __float_as_uint(x), yu = __float_as_uint(y);
+  l0 = __byte_perm(xu, yu, 0x7632);
+  const float2 r1 = sub2(make_float2(x, y), make_float2(__uint_as_float(xu & 0xffff0000u), __uint_as_float(yu & 0xffff0000u)));
+  const uint32_t ru = __float_as_uint(r1.x), rv = __float_as_uint(r1.y);
+  l1 = __byte_perm(ru, rv, 0x7632);
+  const float2 r2 = sub2(r1, make_float2(__uint_as_float(ru & 0xffff0000u), __uint_as_float(rv & 0xffff0000u)));
+  l2 = __byte_perm(__float_as_uint(r2.x), __float_as_uint(r2.y), 0x7632);
+}
+
 // ldmatrix: four 8x8 b16 matrices, row addresses supplied by lanes 0..31.
 __device__ __forceinline__ void ldsm_x4(uint32_t a, uint32_t (&r)[4]) {
   asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];"
@@ -486,6 +499,11 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32
 // earlier writes, and those of threads ordered before it by a barrier, become
 // visible to whoever acquires the counter) and acquire semantics (writes
 // released by earlier arrivals become visible to this thread).
+// arrive (release, CTA scope) on an mbarrier
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
 __device__ __forceinline__ int atom_add_acq_rel(int* p, int v) {
   int old;
   asm volatile("atom.acq_rel.gpu.global.add.s32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
@@ -506,6 +524,19 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
           smem_u32(dst)),
       "l"(src), "r"(bytes), "r"(smem_u32(bar))
       : "memory");
+}
+
+// One RP-wide FP32 row (RP * 4 bytes, 16-byte aligned at both ends) copied by
+// this thread with 16-byte cp.async (L2 only), and the arrival of this thread
+// on an mbarrier once all its earlier cp.async have landed (noinc: the barrier's
+// expected count includes one such arrival per thread).
+__device__ __forceinline__ void cp_row(uint32_t dst, const float* src) {
+#pragma unroll
+  for (int c = 0; c < RP / 4; ++c)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst + 16u * c), "l"(src + 4 * c) : "memory");
+}
+__device__ __forceinline__ void cp_arrive(uint64_t* bar) {
+  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
 // L2 policy for data read exactly once (the packed payload): evict it first,

@@ -56,10 +56,28 @@ __global__ void k_gsum_mr(const GsumOut* __restrict__ outs, int nouts, const F2*
   if (t >= (int64_t)nouts * RP) return;
   const GsumOut O = outs[t / RP];
   const int k = (int)(t % RP);
+  const bool ws = (O.flags & 2) != 0;
   FF s = {0.f, 0.f};
-  for (int p = O.p0; p < O.p1; ++p) {
-    const float x = partial[(int64_t)p * RP + k];
-    if (O.flags & 2) {
+  // partials in order p0, p0 + 1, ...; four loads in flight per step
+  int p = O.p0;
+  for (; p + 4 <= O.p1; p += 4) {
+    float x[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) x[u] = __ldcs(partial + (int64_t)(p + u) * RP + k);
+    if (ws) {
+      F2 wv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) wv[u] = pscale[O.ps + (p + u - O.p0)];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) s = ff_add(s, ff_mul(FF{x[u], 0.f}, FF{wv[u].hi, wv[u].lo}));
+    } else {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) s = ff_add_f(s, x[u]);
+    }
+  }
+  for (; p < O.p1; ++p) {
+    const float x = __ldcs(partial + (int64_t)p * RP + k);
+    if (ws) {
       const F2 w = pscale[O.ps + (p - O.p0)];
       s = ff_add(s, ff_mul(FF{x, 0.f}, FF{w.hi, w.lo}));
     } else {
@@ -666,19 +684,6 @@ constexpr int MP_STAGE = STAGE_BYTES + PIECE_MAX_COLS * MP_TP;
 constexpr int MP_THREADS = MP_PAIRS * 64;
 static_assert(MP_STAGE % 128 == 0, "stage alignment");
 
-// x = t0 + t1 + t2 with BF16 limbs t by truncation (each step keeps the top 8
-// significant bits of the remainder; the remainders are exact FP32
-// differences); limbs of x in the low half, of y in the high half.
-__device__ __forceinline__ void limbs2(float x, float y, uint32_t& l0, uint32_t& l1, uint32_t& l2) {
-  const uint32_t xu = __float_as_uint(x), yu = __float_as_uint(y);
-  l0 = __byte_perm(xu, yu, 0x7632);
-  const float2 r1 = sub2(make_float2(x, y), make_float2(__uint_as_float(xu & 0xffff0000u), __uint_as_float(yu & 0xffff0000u)));
-  const uint32_t ru = __float_as_uint(r1.x), rv = __float_as_uint(r1.y);
-  l1 = __byte_perm(ru, rv, 0x7632);
-  const float2 r2 = sub2(r1, make_float2(__uint_as_float(ru & 0xffff0000u), __uint_as_float(rv & 0xffff0000u)));
-  l2 = __byte_perm(__float_as_uint(r2.x), __float_as_uint(r2.y), 0x7632);
-}
-
 // Named barrier of the 64 threads of pair bid - 1 / its OR vote.
 __device__ __forceinline__ void pair_sync(int bid) { asm volatile("bar.sync %0, 64;" ::"r"(bid) : "memory"); }
 __device__ __forceinline__ bool pair_any(int bid, bool v) {
@@ -882,7 +887,23 @@ __global__ void __launch_bounds__(MP_THREADS, 1)
     dc = lane < n ? cps[p0 + lane] : zero;
     dn = 32 + lane < n ? cps[p0 + 32 + lane] : zero;
   }
-  auto issue = [&](int i) {   // warp 0 of the pair
+  // the sources of a piece's multiplier rows j = lane, lane + 32 (vector entries
+  // moff + j, or fan[moff - fan_base + j] for a fan-out run), loaded one piece
+  // ahead so that their latency overlaps the work on the pieces before
+  int32_t src[2] = {0, 0};
+  auto sources = [&](int i) {   // warp 0 of the pair
+    const int sl = i - dbase;   // < 64: within dc / dn
+    const uint32_t bf = __shfl_sync(HM_FULL, sl < 32 ? dc.bytes_flags : dn.bytes_flags, sl & 31);
+    const int32_t moff = __shfl_sync(HM_FULL, sl < 32 ? dc.moff : dn.moff, sl & 31);
+    const int nc = (int)(bf >> 24);
+    const bool fan_run = moff >= fan_base;
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int j = lane + 32 * u;
+      src[u] = j < nc ? (fan_run ? __ldg(fan + (moff - fan_base) + j) : moff + j) : 0;
+    }
+  };
+  auto issue = [&](int i) {   // warp 0 of the pair; src holds piece i's sources
     if (i - dbase >= 32) {
       dc = dn;
       dbase += 32;
@@ -890,30 +911,33 @@ __global__ void __launch_bounds__(MP_THREADS, 1)
     }
     const int sl = i - dbase;
     const uint32_t off16 = __shfl_sync(HM_FULL, dc.off16, sl), bf = __shfl_sync(HM_FULL, dc.bytes_flags, sl);
-    const int32_t moff = __shfl_sync(HM_FULL, dc.moff, sl), sp = __shfl_sync(HM_FULL, dc.split_part, sl);
+    const int32_t sp = __shfl_sync(HM_FULL, dc.split_part, sl);
     const int s = i % MP_NS;
     uint8_t* st = ring + (size_t)s * MP_STAGE;
     const uint32_t nc = bf >> 24, pb = pad16m(bf & 0xffffu);
     fence_proxy_async();
     if (lane == 0) {
       info[pair][s] = make_int4((int)((bf >> 16) & 0xffu), sp, 0, 0);
-      mbar_expect_tx(&bars[s], pb + nc * RP * 4u);
+      mbar_expect_tx(&bars[s], pb);
       bulk_g2s_hint(st, pay + (uint64_t)off16 * 16u, pb, &bars[s], pol);
     }
     __syncwarp();
-    // multiplier row j: the RP values of vector entry moff + j, or of fan[moff - fan_base + j] for a fan-out run
-    const bool fan_run = moff >= fan_base;
-    for (int j = lane; j < (int)nc; j += 32) {
-      const int32_t src = fan_run ? __ldg(fan + (moff - fan_base) + j) : moff + j;
-      bulk_g2s(st + STAGE_BYTES + j * MP_TP, vec + (int64_t)src * RP, RP * 4u, &bars[s]);
+    // multiplier rows lane, lane + 32 by cp.async (one bulk copy per piece only)
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int j = lane + 32 * u;
+      if (j < (int)nc) cp_row(smem_u32(st + STAGE_BYTES + j * MP_TP), vec + (int64_t)src[u] * RP);
     }
+    cp_arrive(&bars[s]);
+    if (i + 1 < n) sources(i + 1);
   };
   if (wi == 0) {
     if (lane == 0) {
-      for (int s = 0; s < MP_NS; ++s) mbar_init(&bars[s], 1);
+      for (int s = 0; s < MP_NS; ++s) mbar_init(&bars[s], 1 + 32);   // expect-tx arrival + 32 cp.async arrivals
       mbar_init_fence();
     }
     __syncwarp();
+    sources(0);
     for (int i = 0; i < MP_NS && i < n; ++i) issue(i);
   }
   pair_sync(bid);   // the barriers are initialised before warp 1 waits on them
