@@ -405,21 +405,6 @@ __device__ __forceinline__ void decode8p(uint32_t a, int e, int m, float2 (&h2)[
 }
 
 // ---------------------------------------------------------------- tensor-core helpers
-// Exact split of an FP32 value into three BF16 limbs (a = l0 + l1 + l2 for
-// every FP32 a of normal range: each round-to-nearest step removes at least
-// 8 significant bits and the remainders are exact FP32 differences).
-__device__ __forceinline__ void split_bf16x3(float a, uint16_t& l0, uint16_t& l1, uint16_t& l2) {
-  uint16_t h;
-  asm("cvt.rn.bf16.f32 %0, %1;" : "=h"(h) : "f"(a));
-  l0 = h;
-  const float r1 = a - __uint_as_float((uint32_t)h << 16);
-  asm("cvt.rn.bf16.f32 %0, %1;" : "=h"(h) : "f"(r1));
-  l1 = h;
-  const float r2 = r1 - __uint_as_float((uint32_t)h << 16);
-  asm("cvt.rn.bf16.f32 %0, %1;" : "=h"(h) : "f"(r2));
-  l2 = h;
-}
-
 // x = t0 + t1 + t2 with BF16 limbs t by truncation (each step keeps the top 8
 // significant bits of the remainder; the remainders are exact FP32
 // differences); limbs of x in the low half, of y in the high half.
@@ -431,27 +416,6 @@ __device__ __forceinline__ void limbs2(float x, float y, uint32_t& l0, uint32_t&
   l1 = __byte_perm(ru, rv, 0x7632);
   const float2 r2 = sub2(r1, make_float2(__uint_as_float(ru & 0xffff0000u), __uint_as_float(rv & 0xffff0000u)));
   l2 = __byte_perm(__float_as_uint(r2.x), __float_as_uint(r2.y), 0x7632);
-}
-
-// ldmatrix: four 8x8 b16 matrices, row addresses supplied by lanes 0..31.
-__device__ __forceinline__ void ldsm_x4(uint32_t a, uint32_t (&r)[4]) {
-  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-               : "r"(a));
-}
-__device__ __forceinline__ void ldsm_x4_t(uint32_t a, uint32_t (&r)[4]) {
-  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0, %1, %2, %3}, [%4];"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-               : "r"(a));
-}
-
-// D += A (16x16 bf16, row) * B (16x8 bf16, col), FP32 accumulate.
-__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
-      "{%0, %1, %2, %3};"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
 // The decode classes (F, B) the kernels instantiate.

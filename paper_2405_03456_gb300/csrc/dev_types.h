@@ -52,17 +52,14 @@ constexpr int CS_CFG_STAGES[NCFG] = {2, 3, 4};
 constexpr int RS_CFG_WARPS[NCFG] = {16, 11, 8};
 constexpr int RS_CFG_STAGES[NCFG] = {2, 3, 4};
 // Multi-RHS products run in panels of RP right-hand sides on a separate split
-// of every launch into one range per block (MR_BLOCKS_PER_SM blocks per SM);
-// its descriptors are the extra launch shape index MR_SHAPE.
+// of every launch (launch shape index MR_SHAPE): row-chunk launches into
+// MP_PAIRS ranges per SM (one per warp pair of the FP32-pipe kernel; the
+// tensor-core kernel takes MP_PAIRS consecutive ranges per CTA), column-dot
+// launches into MR_CDOT_RANGES ranges per SM.  Chunks of at most MP_ROWS rows
+// may run on the FP32-pipe kernel; wider ones run on the tensor-core kernel.
 constexpr int RP = 32;
-constexpr int MR_BLOCKS_PER_SM = 2;
-// Row-chunk launches of the multi-RHS shape are split into one range per warp
-// pair (MP_PAIRS pairs per SM); chunks of at most MP_ROWS rows run on the
-// register-fragment kernel, wider ones on the shared-tile kernel (one block per range).
 constexpr int MP_PAIRS = 4;
 constexpr int MP_ROWS = 64;
-// Column-dot launches of the multi-RHS shape: ranges per SM (one per warp of
-// the FP32-pipe kernel; the tensor-core kernel takes one per warp pair).
 constexpr int MR_CDOT_RANGES = 16;
 constexpr int MR_SHAPE = NCFG;
 constexpr int NSHAPES = NCFG + 1;

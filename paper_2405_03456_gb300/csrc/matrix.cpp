@@ -41,6 +41,8 @@ cudaError_t launch_prog(int tier, int nblk, const ProgPhase* phases, int nphases
 int prog_max_blocks();
 cudaError_t mr_init();
 cudaError_t tc_init();
+cudaError_t launch_cdot_tc(const ItemCopy* items, const int32_t* wbeg, int nrange, const uint8_t* pay, const float* vec,
+                           F2 alpha, float* partial, float* vout, int* err, cudaStream_t st);
 cudaError_t launch_rgemv_tc(int mode, const PieceCopy* pieces, const int32_t* wbeg, int nrange, const uint8_t* pay,
                             const float* vec, double alpha, F2 alpha_ff, double beta, double* y, int64_t ldy, int r,
                             const int32_t* perm, float* vout, const F2* rowscale, F2* fix, int32_t* fixcnt,
@@ -49,13 +51,12 @@ cudaError_t launch_gather_mr(const double* x, int64_t ldx, int r, const int32_t*
                              cudaStream_t st);
 cudaError_t launch_gsum_mr(const GsumOut* outs, int nouts, const F2* pscale, const float* partial, F2 alpha, float* v,
                            cudaStream_t st);
-cudaError_t launch_cdot_mr(int engine, const ItemCopy* items, const int32_t* wbeg, int nblk, const uint8_t* pay,
-                           const float* vec, F2 alpha, float* partial, float* vout, int* err, cudaStream_t st);
-cudaError_t launch_rgemv_mr(int mode, int engine, const PieceCopy* pieces, const int32_t* wbeg, int nblk, int maxrows,
-                            const uint8_t* pay, const float* vec, double alpha, F2 alpha_ff, double beta, double* y,
-                            int64_t ldy, int r, const int32_t* perm, float* vout, const F2* rowscale, F2* fix,
-                            int32_t* fixcnt, const Split* splits, const int32_t* fan, int32_t fan_base, int* err,
-                            cudaStream_t st);
+cudaError_t launch_cdot_ws(const ItemCopy* items, const int32_t* wbeg, int nblk, const uint8_t* pay, const float* vec,
+                           F2 alpha, float* partial, float* vout, int* err, cudaStream_t st);
+cudaError_t launch_rgemv_ms(int mode, const PieceCopy* pieces, const int32_t* wbeg, int nblk, const uint8_t* pay,
+                            const float* vec, double alpha, F2 alpha_ff, double beta, double* y, int64_t ldy, int r,
+                            const int32_t* perm, float* vout, const F2* rowscale, F2* fix, int32_t* fixcnt,
+                            const Split* splits, const int32_t* fan, int32_t fan_base, int* err, cudaStream_t st);
 cudaError_t launch_decode(const uint8_t* p, int64_t n, int B, int fmt, int e, int m, double vmin,
                           double* out, cudaStream_t st);
 cudaError_t launch_decode_debug(int tier, const DbgTask* tasks, int64_t ntask, const uint8_t* pay, float2* out,
@@ -562,7 +563,10 @@ static cudaError_t run_launch_mr(hm_matrix* M, const Launch& L, double alpha, co
     case Launch::GATHER:
       return launch_gather_mr(x, ldx, r, M->d_perm.p, (int)L.n, M->d_vmr, st);
     case Launch::CDOT:
-      return launch_cdot_mr(1, M->d_items.p, M->d_wbeg.p + L.woff[MR_SHAPE], L.nw[MR_SHAPE], M->d_pay.p, M->d_vmr, aff,
+      if (M->mr_engine == 0)
+        return launch_cdot_tc(M->d_items.p, M->d_wbeg.p + L.woff[MR_SHAPE], L.nw[MR_SHAPE], M->d_pay.p, M->d_vmr, aff,
+                              M->d_pmr, M->d_vmr, M->d_err, st);
+      return launch_cdot_ws(M->d_items.p, M->d_wbeg.p + L.woff[MR_SHAPE], L.nw[MR_SHAPE], M->d_pay.p, M->d_vmr, aff,
                             M->d_pmr, M->d_vmr, M->d_err, st);
     case Launch::GSUM:
       return launch_gsum_mr(M->d_gout.p + L.off, (int)L.n, M->d_pscale.p, M->d_pmr, aff, M->d_vmr, st);
@@ -574,10 +578,10 @@ static cudaError_t run_launch_mr(hm_matrix* M, const Launch& L, double alpha, co
                                L.nw[MR_SHAPE], M->d_pay.p, M->d_vmr, alpha, aff, beta, y, ldy, r, M->d_perm.p,
                                M->d_vmr, L.use_rowscale ? M->d_rowscale_ff.p : nullptr, M->d_fixmr, M->d_fixcnt,
                                M->d_splits.p, M->d_fan.p, (int32_t)P.fan_base, M->d_err, st);
-      return launch_rgemv_mr(L.mode, M->mr_engine, M->d_pieces.p + (size_t)MR_SHAPE * P.npieces, M->d_wbeg.p + L.woff[MR_SHAPE],
-                             L.nw[MR_SHAPE], L.maxrows, M->d_pay.p, M->d_vmr, alpha, aff, beta, y, ldy, r, M->d_perm.p,
-                             M->d_vmr, L.use_rowscale ? M->d_rowscale_ff.p : nullptr, M->d_fixmr, M->d_fixcnt,
-                             M->d_splits.p, M->d_fan.p, (int32_t)P.fan_base, M->d_err, st);
+      return launch_rgemv_ms(L.mode, M->d_pieces.p + (size_t)MR_SHAPE * P.npieces, M->d_wbeg.p + L.woff[MR_SHAPE],
+                             L.nw[MR_SHAPE], M->d_pay.p, M->d_vmr, alpha, aff, beta, y, ldy, r, M->d_perm.p, M->d_vmr,
+                             L.use_rowscale ? M->d_rowscale_ff.p : nullptr, M->d_fixmr, M->d_fixcnt, M->d_splits.p,
+                             M->d_fan.p, (int32_t)P.fan_base, M->d_err, st);
   }
   return cudaErrorInvalidValue;
 }

@@ -2,7 +2,7 @@
 // FP32 tier): y (or a coefficient panel) := the chunk rows of A times the
 // multiplier panel T, for panels of RP right-hand sides.
 //
-// One CTA owns a range of pieces; its warps have fixed roles and hand work on
+// One CTA owns MP_PAIRS consecutive ranges of pieces; its warps have fixed roles and hand work on
 // through mbarriers (no block-wide barrier in the loop):
 //  * warp 0 streams every piece (one bulk copy) and its multiplier rows (RP
 //    values each, taken from the coefficient they stand for; 16-byte cp.async)
@@ -149,9 +149,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   __shared__ uint32_t tbase;
   __shared__ int s_last;
   const int t = threadIdx.x, w = t >> 5, lane = t & 31;
-  const int gr = blockIdx.x;
-  if (gr >= nrange) return;
-  const int p0 = wbeg[gr], n = wbeg[gr + 1] - p0;
+  // the CTA takes MP_PAIRS consecutive ranges as one stream of pieces (the
+  // ranges' part flags still hold: a chunk part closed at a range end goes
+  // through its fix-up slot like any other)
+  const int r0 = blockIdx.x * MP_PAIRS, r1 = min(r0 + MP_PAIRS, nrange);
+  if (r0 >= nrange) return;
+  const int p0 = wbeg[r0], n = wbeg[r1] - p0;
   if (n <= 0) return;
   uint8_t* ring = smem;
   const uint32_t tiles0 = smem_u32(smem + (size_t)TC_NS * TC_STAGE);
@@ -492,23 +495,331 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS) : "memory");
 }
 
+// ---------------------------------------------------------------- column dots
+// out (nc x RP) = A^T X for each column-dot piece, on the same four roles:
+// D (M = the piece's columns, N = RP, K = segment rows) = A (columns x rows,
+// K-major: a column's codes are its rows) times the input rows X (rows x RP,
+// MN-major), copied with every piece (cp.async).  The fold warps read TMEM lane
+// (= column) and write its RP results: the partial sums, or (a column set that
+// fits one segment) the scaled coefficients.
+constexpr int TCC_ALBO = 144;                                 // A (K-major): K-direction core stride
+constexpr int TCC_ASBO = (SEG_ROWS / 8) * TCC_ALBO;           // A: M-direction core stride
+static_assert(TCC_ASBO * (CHUNK_ROWS / 8) <= TC_ATILE && SEG_ROWS <= PIECE_MAX_COLS, "column-dot tiles");
+// instruction descriptor: D FP32, A and B BF16, A K-major, B MN-major, N = RP, M = 128
+constexpr uint32_t TCC_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 16) | ((uint32_t)(RP >> 3) << 17) |
+                               ((uint32_t)(CHUNK_ROWS >> 4) << 24);
+
+__device__ __forceinline__ void tcc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\ttcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+      "l"(a), "l"(b), "r"(TCC_IDESC), "r"(acc)
+      : "memory");
+}
+
+// Decode of column-dot piece values: task (column j < nc, row group q < Rp / 8)
+// writes rows 8 q .. 8 q + 7 of column j as one 16-byte core row per limb.
+template <int F, int B>
+__device__ __forceinline__ void tcc_decode(uint32_t sa, int R, int nc, int flags, int la, uint32_t sA, int td) {
+  const int Rp = (R + 15) & ~15, G = Rp >> 3;
+  const uint32_t stride = (uint32_t)Rp * B;
+  const uint32_t cm = sa + (uint32_t)sizeof(CPieceHdr);
+  const uint32_t cb = cm + ((flags & ITEM_FINAL) ? 16u : 8u) * nc;
+  const int dG = (int)c_tcdiv[G];
+  for (int task = td; task < nc * G; task += 32 * TC_NDEC) {
+    const int j = (task * dG) >> 14, q = task - j * G;
+    int e = 0, m = 0;
+    if constexpr (F == 2) {
+      const uint32_t em = lds32(cm + 8u * j) & 0xffffu;
+      e = em & 0xff;
+      m = em >> 8;
+    }
+    float2 h2[4];
+    decode8p<F, B>(cb + (uint32_t)j * stride + (uint32_t)(8 * q * B), e, m, h2);
+    uint32_t l0[4], l1[4], l2[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) limbs2(h2[u].x, h2[u].y, l0[u], l1[u], l2[u]);
+    const uint32_t a = sA + (uint32_t)((j >> 3) * TCC_ASBO + q * TCC_ALBO + (j & 7) * 16);
+    st_shared_v4(a, l0[0], l0[1], l0[2], l0[3]);
+    if (la > 1) st_shared_v4(a + TC_ATILE, l1[0], l1[1], l1[2], l1[3]);
+    if (la > 2) st_shared_v4(a + 2 * TC_ATILE, l2[0], l2[1], l2[2], l2[3]);
+  }
+}
+
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    k_cdot_tc(const ItemCopy* __restrict__ cps, const int32_t* __restrict__ wbeg, int nrange,
+              const uint8_t* __restrict__ pay, const float* __restrict__ vec, F2 alpha, float* __restrict__ partial,
+              float* __restrict__ vout, int* err) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  __shared__ TcInfo tinfo[2], dinfo[2];         // R, vin, flags, nc | limbs << 16
+  __shared__ int32_t cout_[2][CPIECE_MAX_COLS];  // per accumulator buffer: output of column j
+  __shared__ F2 cscl[2][CPIECE_MAX_COLS];        // and its scale (sets that fit one segment)
+  __shared__ __align__(8) uint64_t full[TC_NS], empty[TC_NS], tfull[2], tempty[2], dfull[2], dempty[2];
+  __shared__ uint32_t tbase;
+  const int t = threadIdx.x, w = t >> 5, lane = t & 31;
+  const int r0 = blockIdx.x * MR_CDOT_RANGES, r1 = min(r0 + MR_CDOT_RANGES, nrange);
+  if (r0 >= nrange) return;
+  const int p0 = wbeg[r0], n = wbeg[r1] - p0;
+  if (n <= 0) return;
+  uint8_t* ring = smem;
+  const uint32_t tiles0 = smem_u32(smem + (size_t)TC_NS * TC_STAGE);
+  if (w == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tbase)),
+                 "r"(TC_TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (t == 0) {
+    for (int s = 0; s < TC_NS; ++s) {
+      mbar_init(&full[s], 1 + 32);
+      mbar_init(&empty[s], TC_NDEC);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull[b], TC_NDEC);
+      mbar_init(&tempty[b], 1);
+      mbar_init(&dfull[b], 2);
+      mbar_init(&dempty[b], TC_NEPI);
+    }
+    mbar_init_fence();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tbase;
+  bool failed = false;
+  if (w == 0) {
+    // ---------------------------------------------------------------- copies: piece (bulk) + input rows (cp.async)
+    const uint64_t pol = policy_evict_first();
+    const ItemCopy zero{0, 0, -1, 0};
+    ItemCopy dc = lane < n ? cps[p0 + lane] : zero;
+    ItemCopy dn = 32 + lane < n ? cps[p0 + 32 + lane] : zero;
+    int dbase = 0;
+    for (int i = 0; i < n; ++i) {
+      const int s = i % TC_NS;
+      if (i >= TC_NS && !__all_sync(HM_FULL, mbar_wait(&empty[s], (uint32_t)(((i / TC_NS) + 1) & 1)))) {
+        failed = true;
+        break;
+      }
+      if (i - dbase >= 32) {
+        dc = dn;
+        dbase += 32;
+        dn = dbase + 32 + lane < n ? cps[p0 + dbase + 32 + lane] : zero;
+      }
+      const int sl = i - dbase;
+      const uint32_t off16 = __shfl_sync(HM_FULL, dc.off16, sl), bytes = __shfl_sync(HM_FULL, dc.bytes, sl);
+      const int32_t vin = __shfl_sync(HM_FULL, dc.vin, sl), nrows = __shfl_sync(HM_FULL, dc.nrows, sl);
+      uint8_t* st = ring + (size_t)s * TC_STAGE;
+      const uint32_t pb = (bytes + 15u) & ~15u;
+      fence_proxy_async();
+      if (lane == 0) {
+        mbar_expect_tx(&full[s], pb);
+        bulk_g2s_hint(st, pay + (uint64_t)off16 * 16u, pb, &full[s], pol);
+      }
+      __syncwarp();
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int k = lane + 32 * u;
+        if (k < nrows) cp_row(smem_u32(st + STAGE_BYTES + k * TC_TP), vec + (int64_t)(vin + k) * RP);
+      }
+      cp_arrive(&full[s]);
+    }
+    if (failed && lane == 0) latch_error(err, 99);
+    if (lane == 0)
+      for (int i = n - TC_NS < 0 ? 0 : n - TC_NS; i < n; ++i)
+        mbar_wait(&full[i % TC_NS], (uint32_t)((i / TC_NS) & 1), failed ? 50u : 2000u);
+  } else if (w == 1) {
+    // ---------------------------------------------------------------- tensor-core issue
+    if (lane == 0) {
+      int i = 0;
+      for (; i < n; ++i) {
+        const int b = i & 1;
+        if (!mbar_wait(&tfull[b], (uint32_t)((i >> 1) & 1)) ||
+            (i >= 2 && !mbar_wait(&dempty[b], (uint32_t)(((i >> 1) + 1) & 1)))) {
+          failed = true;
+          break;
+        }
+        const TcInfo pi = tinfo[b];
+        dinfo[b] = pi;
+        const int Rp = (pi.R + 15) & ~15, la = pi.ncl >> 16;
+        tc_fence_after();
+        const uint32_t sA = tiles0 + (uint32_t)(b * TC_TILES), sB = sA + 3u * TC_ATILE;
+        const uint32_t d = tmem + (uint32_t)(b * 64);
+        for (int k = 0; k < Rp / 16; ++k) {
+          uint64_t a[3], bd[3];
+#pragma unroll
+          for (int l = 0; l < 3; ++l) {
+            a[l] = tc_desc(sA + (uint32_t)(l * TC_ATILE + 2 * k * TCC_ALBO), TCC_ALBO, TCC_ASBO);
+            bd[l] = tc_desc(sB + (uint32_t)(l * TC_BTILE + 2 * k * TC_BLBO), TC_BLBO, TC_BSBO);
+          }
+          tcc_mma(d, a[0], bd[0], k > 0);
+          tcc_mma(d + 32u, a[0], bd[1], k > 0);
+          tcc_mma(d + 32u, a[0], bd[2], 1u);
+          if (la > 1) {
+            tcc_mma(d + 32u, a[1], bd[0], 1u);
+            tcc_mma(d + 32u, a[1], bd[1], 1u);
+          }
+          if (la > 2) tcc_mma(d + 32u, a[2], bd[0], 1u);
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         smem_u32(&tempty[b]))
+                     : "memory");
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         smem_u32(&dfull[b]))
+                     : "memory");
+        mbar_arrive(&dfull[b]);
+      }
+      if (failed) latch_error(err, 99);
+      for (int j = i - 2; j < i; ++j)
+        if (j >= 0) mbar_wait(&tempty[j & 1], (uint32_t)((j >> 1) & 1), failed ? 200u : 2000u);
+    }
+    __syncwarp();
+  } else if (w < TC_EPI0) {
+    // ---------------------------------------------------------------- decode
+    const int td = t - 32 * TC_DEC0;
+    for (int i = 0; i < n; ++i) {
+      const int s = i % TC_NS, b = i & 1;
+      // the stage; tiles b (products of piece i - 2 done); column outputs b (piece i - 2 folded)
+      const bool ok = mbar_wait(&full[s], (uint32_t)((i / TC_NS) & 1)) &&
+                      (i < 2 || (mbar_wait(&tempty[b], (uint32_t)(((i >> 1) + 1) & 1)) &&
+                                 mbar_wait(&dempty[b], (uint32_t)(((i >> 1) + 1) & 1))));
+      if (!__all_sync(HM_FULL, ok)) {
+        failed = true;
+        break;
+      }
+      const uint32_t sa = smem_u32(ring + (size_t)s * TC_STAGE);
+      const uint4 hw = lds128(sa);   // CPieceHdr
+      const int R = (int)(hw.y & 0xffffu), nc = (int)(hw.y >> 16);
+      const uint32_t fb = hw.z & 0xffffu;
+      const int flags = (int)(hw.z >> 16), la = (int)hw.w;
+      const int Rp = (R + 15) & ~15;
+      const uint32_t sA = tiles0 + (uint32_t)(b * TC_TILES), sB = sA + 3u * TC_ATILE;
+      switch (fb) {
+#define HM_TCD(FF_, BB_) \
+  case ((FF_) << 4) | (BB_): tcc_decode<FF_, BB_>(sa, R, nc, flags, la, sA, td); break;
+        HM_FORMATS(HM_TCD)
+#undef HM_TCD
+        default:
+          latch_error(err, 17);
+      }
+      if (td < Rp * (RP / 8)) {   // input rows: task (row k, rhs group ng of 8); zero for k >= R
+        const int k = td % Rp, ng = td / Rp;
+        uint32_t l0[4] = {0u, 0u, 0u, 0u}, l1[4] = {0u, 0u, 0u, 0u}, l2[4] = {0u, 0u, 0u, 0u};
+        if (k < R) {
+          const uint32_t xa = sa + STAGE_BYTES + (uint32_t)(k * TC_TP + 32 * ng);
+          const uint4 a = lds128(xa), bb = lds128(xa + 16);
+          limbs2(__uint_as_float(a.x), __uint_as_float(a.y), l0[0], l1[0], l2[0]);
+          limbs2(__uint_as_float(a.z), __uint_as_float(a.w), l0[1], l1[1], l2[1]);
+          limbs2(__uint_as_float(bb.x), __uint_as_float(bb.y), l0[2], l1[2], l2[2]);
+          limbs2(__uint_as_float(bb.z), __uint_as_float(bb.w), l0[3], l1[3], l2[3]);
+        }
+        const uint32_t ba = sB + (uint32_t)(ng * TC_BSBO + (k >> 3) * TC_BLBO + (k & 7) * 16);
+        st_shared_v4(ba, l0[0], l0[1], l0[2], l0[3]);
+        st_shared_v4(ba + TC_BTILE, l1[0], l1[1], l1[2], l1[3]);
+        st_shared_v4(ba + 2 * TC_BTILE, l2[0], l2[1], l2[2], l2[3]);
+      }
+      if (td < nc) {   // the column's output index and scale, for the fold warps
+        const uint32_t cm = sa + (uint32_t)sizeof(CPieceHdr);
+        cout_[b][td] = (int32_t)lds32(cm + 8u * td + 4u);
+        if (flags & ITEM_FINAL) {
+          const uint2 f = lds64(cm + 8u * nc + 8u * td);
+          cscl[b][td] = F2{__uint_as_float(f.x), __uint_as_float(f.y)};
+        }
+      }
+      if (td == 0) tinfo[b] = TcInfo{R, (int32_t)hw.x, flags, nc | (la << 16), 0, 0, 0, 0};
+      fence_proxy_async();
+      __syncwarp();
+      if (lane == 0) {
+        mbar_arrive(&tfull[b]);
+        mbar_arrive(&empty[s]);
+      }
+    }
+    if (failed && lane == 0) latch_error(err, 99);
+  } else {
+    // ---------------------------------------------------------------- write the column results
+    const int te = t - 32 * TC_EPI0;
+    const int j = 32 * (w & 3) + lane, half = te >> 7;   // TMEM lane = column
+    const uint32_t tl = tmem + ((uint32_t)(32 * (w & 3)) << 16) + 16u * (uint32_t)half;
+    const FF fa = {alpha.hi, alpha.lo};
+    for (int i = 0; i < n; ++i) {
+      const int b = i & 1;
+      if (!__all_sync(HM_FULL, mbar_wait(&dfull[b], (uint32_t)((i >> 1) & 1)))) {
+        failed = true;
+        break;
+      }
+      tc_fence_after();
+      const TcInfo pi = dinfo[b];
+      const int nc = pi.ncl & 0xffff;
+      uint32_t vb[16], vs[16];
+      tc_ld16(tl + (uint32_t)(b * 64), vb);
+      tc_ld16(tl + (uint32_t)(b * 64 + 32), vs);
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      int32_t out = 0;
+      FF sc = {1.f, 0.f};
+      if (j < nc) {
+        out = cout_[b][j];
+        if (pi.flags & ITEM_FINAL) {
+          sc = FF{cscl[b][j].hi, cscl[b][j].lo};
+          if (pi.flags & ITEM_ALPHA) sc = ff_mul(sc, fa);
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&dempty[b]);
+      if (j < nc) {
+        float r2[16];
+#pragma unroll
+        for (int e = 0; e < 16; ++e) r2[e] = __uint_as_float(vb[e]) + __uint_as_float(vs[e]);
+        if (pi.flags & ITEM_FINAL) {
+#pragma unroll
+          for (int e = 0; e < 16; ++e) {
+            const FF v = ff_mul(FF{r2[e], 0.f}, sc);
+            r2[e] = v.hi + v.lo;
+          }
+          float4* o = reinterpret_cast<float4*>(vout + (int64_t)out * RP + 16 * half);
+#pragma unroll
+          for (int e = 0; e < 4; ++e) o[e] = make_float4(r2[4 * e], r2[4 * e + 1], r2[4 * e + 2], r2[4 * e + 3]);
+        } else {
+          float4* o = reinterpret_cast<float4*>(partial + (int64_t)out * RP + 16 * half);
+#pragma unroll
+          for (int e = 0; e < 4; ++e) o[e] = make_float4(r2[4 * e], r2[4 * e + 1], r2[4 * e + 2], r2[4 * e + 3]);
+        }
+      }
+    }
+    if (failed && lane == 0) latch_error(err, 99);
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (w == 1)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS) : "memory");
+}
+
 cudaError_t tc_init() {
   cudaError_t e = cudaFuncSetAttribute(k_rgemv_tc<MODE_Y>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_rgemv_tc<MODE_VEC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_rgemv_tc<MODE_VEC_ADD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_cdot_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
   return e;
 }
 
-// nrange ranges, one CTA each
+// nrange ranges, MR_CDOT_RANGES consecutive ones per CTA
+cudaError_t launch_cdot_tc(const ItemCopy* items, const int32_t* wbeg, int nrange, const uint8_t* pay, const float* vec,
+                           F2 alpha, float* partial, float* vout, int* err, cudaStream_t st) {
+  if (nrange <= 0) return cudaSuccess;
+  k_cdot_tc<<<(unsigned)((nrange + MR_CDOT_RANGES - 1) / MR_CDOT_RANGES), TC_THREADS, TC_SMEM, st>>>(
+      items, wbeg, nrange, pay, vec, alpha, partial, vout, err);
+  return cudaGetLastError();
+}
+
+// nrange ranges, MP_PAIRS consecutive ones per CTA
 cudaError_t launch_rgemv_tc(int mode, const PieceCopy* pieces, const int32_t* wbeg, int nrange, const uint8_t* pay,
                             const float* vec, double alpha, F2 alpha_ff, double beta, double* y, int64_t ldy, int r,
                             const int32_t* perm, float* vout, const F2* rowscale, F2* fix, int32_t* fixcnt,
                             const Split* splits, const int32_t* fan, int32_t fan_base, int* err, cudaStream_t st) {
   if (nrange <= 0) return cudaSuccess;
 #define HM_TCG(M)                                                                                              \
-  k_rgemv_tc<M><<<(unsigned)nrange, TC_THREADS, TC_SMEM, st>>>(pieces, wbeg, nrange, pay, vec, alpha, alpha_ff, \
+  k_rgemv_tc<M><<<(unsigned)((nrange + MP_PAIRS - 1) / MP_PAIRS), TC_THREADS, TC_SMEM, st>>>(pieces, wbeg, nrange, pay, vec, alpha, alpha_ff, \
                                                                beta, y, ldy, r, perm, vout, rowscale, fix, fixcnt, \
                                                                splits, fan, fan_base, err)
   if (mode == MODE_Y)

@@ -95,26 +95,27 @@ uint16_t format16(int B, int fmt, uint16_t em) {
 
 double ff(const F2& v) { return (double)v.hi + (double)v.lo; }
 
-// Round an FP32 value to BF16, to nearest with ties to even, as its FP32 value.
-float bf16_rn(float a) {
+// Cut an FP32 value to BF16 (its top 16 bits), as its FP32 value.
+float bf16_cut(float a) {
   uint32_t b;
   std::memcpy(&b, &a, 4);
-  b = (b + 0x7fffu + ((b >> 16) & 1u)) & 0xffff0000u;
+  b &= 0xffff0000u;
   float r;
   std::memcpy(&r, &b, 4);
   return r;
 }
 
-// The multi-RHS path splits each decoded value a (FP32) into BF16 limbs,
-// a = l0 + l1 + l2 with l0 = bf16(a), l1 = bf16(a - l0), l2 = bf16(a - l0 - l1),
-// and multiplies only the first `limbs` of them: true if those are exactly a.
-// Three limbs hold every FP32 value; a piece that keeps fewer must hold values
-// of at most 8 * limbs significant bits, exact in FP32.
+// The multi-RHS kernels split each decoded value a (FP32) into BF16 limbs by
+// truncation, a = l0 + l1 + l2 with l0 = cut(a), l1 = cut(a - l0),
+// l2 = cut(a - l0 - l1) (the differences are exact), and multiply only the
+// first `limbs` of them: true if those are exactly a.  Three limbs hold every
+// FP32 value; a piece that keeps fewer must hold values of at most 8 * limbs
+// significant bits, exact in FP32.
 bool limbs_exact(double v, int limbs) {
   if (limbs >= 3) return true;
   const float a = (float)v;
   if ((double)a != v) return false;
-  const float l0 = bf16_rn(a), r1 = a - l0, l1 = bf16_rn(r1), r2 = r1 - l1, l2 = bf16_rn(r2);
+  const float l0 = bf16_cut(a), r1 = a - l0, l1 = bf16_cut(r1), r2 = r1 - l1, l2 = bf16_cut(r2);
   const double sum = limbs == 1 ? (double)l0 : limbs == 2 ? (double)l0 + l1 : ((double)l0 + l1) + l2;
   return sum == v;
 }
