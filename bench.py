@@ -427,6 +427,7 @@ def gpu_arm(args, rank, world):
                     M.profile(False)
                     headline["by_nrhs"] = time_multi_rhs(torch, M, n, (1, 8, 32, 64), max(5, min(50, args.steps // 10)),
                                                          3, stream)
+                    headline["multi_rhs_engine"] = ("tensor cores (tcgen05)", "FP32 pipes")[M.multi_rhs_engine()]
                     M.profile(True)
                 M.profile(False)
                 headline["kernels"] = prof
@@ -502,7 +503,8 @@ def gpu_arm(args, rank, world):
                   "payload_mb": round(info["bytes_payload"] / 1e6, 1), "fp64_mb": round(info["bytes_fp64"] / 1e6, 1),
                   "build_s": round(build_s, 1), "single_rhs": single,
                   "by_nrhs": time_multi_rhs(torch, M, nm, (1, 8, 32, 64), max(3, min(20, args.steps // 20)), 2,
-                                            stream)}
+                                            stream),
+                  "multi_rhs_engine": ("tensor cores (tcgen05)", "FP32 pipes")[M.multi_rhs_engine()]}
         M.compress(1e-6, "none", True)   # the uncompressed FP64 product of the same matrix
         if not args.no_tune:
             M.autotune(3, stream.cuda_stream)
