@@ -222,8 +222,8 @@ def time_variant(torch, M, x, y, steps, warmup, stream, world=1, adjoint=False):
 
 
 def time_multi_rhs(torch, M, n, r_list, steps, warmup, stream, seed=5):
-    """Products Y := M X of r right-hand sides (panels of 32 on the tensor cores):
-    median ms and right-hand sides per second for each r."""
+    """Products Y := M X of r right-hand sides (panels of 32, on the multi-RHS
+    engine the autotuner chose): median ms and right-hand sides per second for each r."""
     import numpy as np
     import synth
     out = {}
@@ -401,6 +401,8 @@ def gpu_arm(args, rank, world):
             M.compress(eps, codec, True)
             if not args.no_tune:
                 M.autotune(5, stream.cuda_stream)
+            if args.mr_engine != "auto":    # the multi-RHS engine, fixed instead of autotuned
+                M.multi_rhs_engine({"tcgen05": 0, "fp32": 1}[args.mr_engine])
             M.graph(not args.no_graph)
             info = M.info()
             ab = info["bytes_alg"]          # the method's bytes (codes, their metadata, vectors)
@@ -609,8 +611,10 @@ def gpu_arm(args, rank, world):
         "gpu_launches": int(headline["launches"] * args.steps),
         "clocks": clk,
         "by_eps": by_eps,
-        "by_nrhs": {"workload": "the headline matrix, Y := M X with r right-hand sides (panels of 32: BF16-limb "
-                                "tensor-core products, FP32 accumulation, float-float sums; r < 9 as single products)",
+        "by_nrhs": {"workload": "the headline matrix, Y := M X with r right-hand sides (panels of 32 on the "
+                               "multi-RHS engine the autotuner chose: FP32 pipes, or tcgen05 tensor cores with exact "
+                               "BF16 limbs; per-piece FP32 sums, float-float across pieces; r < 9 as single products)",
+                    "engine": headline.get("multi_rhs_engine"),
                     **headline.get("by_nrhs", {})},
         "by_format": {f"{f}-{c}": {"gbs": round(r["gbs"], 1), "ms_p50": round(r["ms_p50"], 4),
                                    "ms_p99": round(r["ms_p99"], 4), "payload_mb": round(r["payload_bytes"] / 1e6, 1),
@@ -678,6 +682,8 @@ def main():
     ap.add_argument("--formats", default="uh,uh_sep,h2")
     ap.add_argument("--no-tune", action="store_true", help="keep the default launch shape (no autotuning)")
     ap.add_argument("--no-multi-rhs", action="store_true", help="skip the multi-RHS timings")
+    ap.add_argument("--mr-engine", default="auto", choices=["auto", "tcgen05", "fp32"],
+                    help="multi-RHS engine of the headline matrices (auto: the autotuner's choice)")
     ap.add_argument("--adm-legs", type=int, default=0,
                     help="also time HODLR and BLR H-matrices of the sphere problem at this N (opt-in)")
     ap.add_argument("--serving", default="small", choices=["none", "small", "full"],

@@ -135,8 +135,9 @@ def test_uh_sep_full_size(hm, sphere):
 
 
 def test_multi_rhs_panel_full_size(hm, sphere):
-    """A 32-wide panel (BF16-limb tensor-core products) on the headline matrix:
-    every column within 4 eps of the exact rows."""
+    """A 32-wide panel on the headline matrix, on both multi-RHS engines (the
+    FP32 pipes; tcgen05 with BF16 limbs): every column within 4 eps of the exact
+    rows, and the two engines within 1e-6 of each other."""
     eps = 1e-6
     X = synth.rhs(N, 32, seed=21)
     rows = np.random.default_rng(13).choice(N, 64, replace=False)
@@ -144,9 +145,16 @@ def test_multi_rhs_panel_full_size(hm, sphere):
     M = hm.HMatrix(sphere, "laplace", 64, 2.0, "h", eps)
     try:
         M.compress(eps, "aflp", True)
-        Y = device_product(M, X)
+        Ys = []
+        for engine in (1, 0):
+            assert M.multi_rhs_engine(engine) == engine
+            Y = device_product(M, X)
+            assert M.sync_status() == 0
+            for k in range(32):
+                assert rel(Y[rows, k], ye[:, k]) <= 4 * eps, (engine, k)
+            Ys.append(Y)
         for k in range(32):
-            assert rel(Y[rows, k], ye[:, k]) <= 4 * eps, k
+            assert rel(Ys[1][:, k], Ys[0][:, k]) <= 1e-6, k
     finally:
         M.close()
 

@@ -124,3 +124,30 @@ def test_multi_rhs_wide_chunks(hm, fmt, leaf, engine):
             assert rel(outs[0][:, k], ys.cpu().numpy()) <= 1e-6, k
     finally:
         M.close()
+
+
+@pytest.mark.parametrize("engine", [0, 1])
+@pytest.mark.parametrize("codec,eps", [("aflp", 1e-4), ("fpx", 1e-4), ("fpx", 1e-6)])
+def test_multi_rhs_codecs_and_limbs(hm, engine, codec, eps):
+    """Both engines on AFLP / FPX payloads whose pieces keep 1, 2 or 3 BF16 limbs
+    (eps = 1e-4 leaves short mantissas): every column of a 33-column product
+    within 4 eps of the oracle's uncompressed product."""
+    r = 33
+    pts = synth.sphere_points(N)
+    h = hmatrix.build_h(pts, "laplace", 32, 2.0, eps)
+    x = synth.rhs(N, r, seed=41)
+    y0 = synth.rhs(N, r, seed=42)
+    ref = matvec.h_mvm(h, 1.25, x, 0.5, y0)
+    M = hm.HMatrix(pts, "laplace", 32, 2.0, "h", eps)
+    try:
+        M.compress(eps, codec)
+        assert M.multi_rhs_engine(engine) == engine
+        yd = device_cols(y0)
+        M.matvec(1.25, device_cols(x), 0.5, yd)
+        torch.cuda.synchronize()
+        assert M.sync_status() == 0
+        out = yd.cpu().numpy()
+        for k in range(r):
+            assert rel(out[:, k], ref[:, k]) <= 4 * eps, k
+    finally:
+        M.close()
