@@ -128,7 +128,7 @@ struct hm_matrix {
   // executed as the phases of one cooperative launch (dataflow between phases)
   int64_t width_bytes[8] = {};  // packed code bytes by code width B (set at compress time)
   int fuse = 1;                // 0 per launch, 1 runs of row-chunk launches fused, 2 the whole product
-  int mr_engine = 1;           // multi-RHS row chunks: 0 tensor-core fragments, 1 FP32 pipes
+  int mr_engine = 1;           // multi-RHS panels: 0 tensor cores (tcgen05), 1 FP32 pipes
   DevArr<ProgPhase> d_prog;    // phases of the whole-product launch
   unsigned* d_pstate = nullptr;  // its barrier counter, abort word and the runs' state
   int pstate_n = 0;

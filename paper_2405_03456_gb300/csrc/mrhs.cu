@@ -96,11 +96,11 @@ __device__ __forceinline__ bool pair_any(int bid, bool v) {
   return r != 0;
 }
 
-// The same piece on the FP32 pipes: every product is one FP32 FMA (FFMA2 over
-// right-hand-side pairs), as in the single-RHS kernels.  The lane keeps the
-// fragment kernel's output mapping (rows 32 wi + 4 g + u, u = 2 mt + h;
-// right-hand sides 8 nt + 2 tq + {0, 1}): per column it decodes its 4 codes
-// and reads its 8 multipliers.
+// One piece for warp wi of the pair on the FP32 pipes: every product is one
+// FP32 FMA (FFMA2 over right-hand-side pairs), as in the single-RHS kernels,
+// summed per piece in FP32 and folded into the float-float sums fhi / flo
+// [mt][nt][h] of rows 32 wi + 4 g + 2 mt + h, right-hand sides 8 nt + 2 tq +
+// {0, 1}.  Per column the lane decodes its 4 codes and reads its 8 multipliers.
 template <int F, int B>
 __device__ __forceinline__ void ms_piece(uint32_t sa, const PieceHdr& H, F2 alpha_ff, int wi, int lane,
                                          float2 (&fhi)[2][NT][2], float2 (&flo)[2][NT][2]) {

@@ -67,7 +67,7 @@ def test_noalloc_matches_matvec_bitwise(hm):
         cases = [(synth.rhs(n, 1, seed=11)[:, 0], synth.rhs(n, 1, seed=12)[:, 0], 1.0, 1.0),
                  (synth.rhs(n, 3, seed=13), synth.rhs(n, 3, seed=14), 0.5, -2.0),
                  (synth.rhs(n, 1, seed=15)[:, 0], nan_y, 1.25, 0.0),           # leftover scratch, y unread
-                 (synth.rhs(n, 12, seed=16), synth.rhs(n, 12, seed=17), -0.75, 0.5)]   # tensor-core panel
+                 (synth.rhs(n, 12, seed=16), synth.rhs(n, 12, seed=17), -0.75, 0.5)]   # multi-RHS panel
         wants = [_device_product(M, x, np.nan_to_num(y0, nan=0.0) if beta == 0.0 else y0, a, beta)
                  for x, y0, a, beta in cases]
         xs = [np.asfortranarray(x) for x, _, _, _ in cases]
