@@ -324,6 +324,23 @@ hm_status hm_launch_shapes(const hm_matrix* m, int32_t* shapes, int32_t cap, int
 hm_status hm_set_launch_shapes(hm_matrix* m, int32_t shape);
 
 /*
+ * Tuning records: what hm_autotune chose for a compressed matrix (every
+ * launch's shape, the hm_persistent mode, the multi-RHS engine), as an opaque
+ * int32 array, so that a caller can keep it per device and apply it to an
+ * identical matrix later without timing again.  The record carries a
+ * fingerprint of the device (SM count, name) and of the matrix's launch
+ * program (tier, every launch's kind, output mode, units and warp ranges).
+ * hm_tuning -- writes the record to rec[0 .. min(cap, *len)); *len = its length
+ *   (5 + launches + 2).  Host only.  Errors: HM_ERR_ARG, HM_ERR_STATE (not
+ *   compressed).
+ * hm_set_tuning -- applies a record; HM_ERR_ARG if it was taken on another
+ *   device or program (fingerprint or launch count differ) or holds a value out
+ *   of range; HM_ERR_STATE if m is not compressed.  Discards a captured graph.
+ */
+hm_status hm_tuning(const hm_matrix* m, int32_t* rec, int32_t cap, int32_t* len);
+hm_status hm_set_tuning(hm_matrix* m, const int32_t* rec, int32_t len);
+
+/*
  * Kernel profiling.  hm_profile(m, 1) makes every later hm_matvec record a
  * CUDA event pair around each of its kernel launches, on the caller's stream;
  * hm_profile_read synchronises those events, returns per kernel kind the

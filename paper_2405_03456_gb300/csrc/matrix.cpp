@@ -913,6 +913,73 @@ hm_status hm_multi_rhs_engine(const hm_matrix* M, int32_t* engine) {
   return HM_OK;
 }
 
+// Tuning record: TUNE_MAGIC, version, the fingerprint (2 words), the launch
+// count, every launch's shape, the launch mode, the multi-RHS engine.  The
+// fingerprint hashes (FNV-1a) the device's SM count and name and the program's
+// structure (tier, every launch's kind, mode, unit range and warp-range counts),
+// so a record applies only to a matrix whose launches it was timed on.
+constexpr int32_t TUNE_MAGIC = 0x484d5455;   // "HMTU"
+constexpr int32_t TUNE_VERSION = 1;
+
+static uint64_t tuning_fingerprint(const hm_matrix* M) {
+  uint64_t h = 1469598103934665603ull;
+  auto mix = [&](uint64_t v) {
+    for (int b = 0; b < 8; ++b) {
+      h ^= (v >> (8 * b)) & 0xffu;
+      h *= 1099511628211ull;
+    }
+  };
+  int dev = 0;
+  cudaDeviceProp prop{};
+  if (cudaGetDevice(&dev) == cudaSuccess && cudaGetDeviceProperties(&prop, dev) == cudaSuccess)
+    for (const char* c = prop.name; *c; ++c) mix((uint64_t)(unsigned char)*c);
+  mix((uint64_t)M->nsm);
+  const Program& P = M->prog;
+  mix((uint64_t)P.tier);
+  for (const Launch& L : P.launches) {
+    mix((uint64_t)L.kind | ((uint64_t)L.mode << 8));
+    mix((uint64_t)L.off);
+    mix((uint64_t)L.n);
+    for (int cf = 0; cf < NSHAPES; ++cf) mix((uint64_t)L.nw[cf]);
+  }
+  return h;
+}
+
+hm_status hm_tuning(const hm_matrix* M, int32_t* rec, int32_t cap, int32_t* len) {
+  if (!M || !len || cap < 0 || (cap > 0 && !rec)) return HM_ERR_ARG;
+  if (!M->compressed) return HM_ERR_STATE;
+  const auto& Ls = M->prog.launches;
+  const uint64_t fp = tuning_fingerprint(M);
+  std::vector<int32_t> v = {TUNE_MAGIC, TUNE_VERSION, (int32_t)(uint32_t)fp, (int32_t)(uint32_t)(fp >> 32),
+                            (int32_t)Ls.size()};
+  for (const Launch& L : Ls) v.push_back(L.cfg);
+  v.push_back(M->fuse);
+  v.push_back(M->mr_engine);
+  *len = (int32_t)v.size();
+  for (int32_t i = 0; i < cap && i < (int32_t)v.size(); ++i) rec[i] = v[i];
+  return HM_OK;
+}
+
+hm_status hm_set_tuning(hm_matrix* M, const int32_t* rec, int32_t len) {
+  if (!M || !rec || len < 7) return HM_ERR_ARG;
+  std::lock_guard<std::mutex> g(M->mu);
+  if (!M->compressed) return HM_ERR_STATE;
+  auto& Ls = M->prog.launches;
+  const uint64_t fp = tuning_fingerprint(M);
+  if (rec[0] != TUNE_MAGIC || rec[1] != TUNE_VERSION || rec[2] != (int32_t)(uint32_t)fp ||
+      rec[3] != (int32_t)(uint32_t)(fp >> 32) || rec[4] != (int32_t)Ls.size() || len != 7 + (int32_t)Ls.size())
+    return HM_ERR_ARG;
+  for (size_t i = 0; i < Ls.size(); ++i)
+    if (rec[5 + i] < 0 || rec[5 + i] >= NCFG) return HM_ERR_ARG;
+  const int32_t mode = rec[5 + Ls.size()], eng = rec[6 + Ls.size()];
+  if (mode < 0 || mode > 2 || eng < 0 || eng > 1) return HM_ERR_ARG;
+  for (size_t i = 0; i < Ls.size(); ++i) Ls[i].cfg = rec[5 + i];
+  M->fuse = mode;
+  M->mr_engine = eng;
+  M->drop_graph();
+  return HM_OK;
+}
+
 hm_status hm_set_launch_shapes(hm_matrix* M, int32_t shape) {
   if (!M || shape < 0 || shape >= NCFG) return HM_ERR_ARG;
   std::lock_guard<std::mutex> g(M->mu);

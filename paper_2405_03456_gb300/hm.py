@@ -28,7 +28,7 @@ DECLARED = ["hm_build", "hm_compress", "hm_matvec", "hm_matvec_host", "hm_free",
             "hm_autotune", "hm_launch_shapes", "hm_set_launch_shapes", "hm_persistent", "hm_matvec_adjoint",
             "hm_decompress_debug", "hm_save", "hm_load", "hm_lu_build", "hm_lu_compress", "hm_lu_solve",
             "hm_lu_sync_status", "hm_lu_info", "hm_lu_free", "hm_persistent_mode", "hm_set_multi_rhs_engine",
-            "hm_multi_rhs_engine"]
+            "hm_multi_rhs_engine", "hm_tuning", "hm_set_tuning"]
 NSHAPES = 3
 HM_NOALLOC_MAX_ENTRIES = 1 << 20
 KERNEL_KINDS = ["gather", "cdot", "gsum", "rgemv", "fanout"]
@@ -106,6 +106,8 @@ def load(path: str | None = None) -> C.CDLL:
         "hm_set_launch_shapes": ([vp, i32], i32),
         "hm_persistent_mode": ([vp, C.POINTER(i32)], i32),
         "hm_set_multi_rhs_engine": ([vp, i32], i32),
+        "hm_tuning": ([vp, vp, i32, C.POINTER(i32)], i32),
+        "hm_set_tuning": ([vp, vp, i32], i32),
         "hm_multi_rhs_engine": ([vp, C.POINTER(i32)], i32),
         "hm_decompress_debug": ([vp, i32, i64, i64, i64, vp, vp, vp, vp, C.POINTER(i64), vp], i32),
         "hm_save": ([vp, C.c_char_p], i32),
@@ -416,9 +418,45 @@ class HMatrix:
         hm_persistent(self.h, int(enable))
         return self
 
-    def autotune(self, reps=5, stream=0):
+    def autotune(self, reps=5, stream=0, cache=None):
+        """Time the launch shapes, launch modes and multi-RHS engines and keep the
+        fastest.  cache: a JSON file of tuning records (one per device and launch
+        program); a record found there is applied instead of timing, a new one is
+        added to it."""
+        if cache is None:
+            hm_autotune(self.h, reps, stream)
+            return self
+        import json
+        import os
+        try:
+            with open(cache) as f:
+                recs = json.load(f)
+        except (OSError, ValueError):
+            recs = {}
+        rec = self.tuning()
+        key = f"{rec[2] & 0xffffffff:08x}{rec[3] & 0xffffffff:08x}"
+        if key in recs and self.set_tuning(recs[key]):
+            return self
         hm_autotune(self.h, reps, stream)
+        recs[key] = self.tuning()
+        tmp = f"{cache}.{os.getpid()}.tmp"
+        with open(tmp, "w") as f:
+            json.dump(recs, f)
+        os.replace(tmp, cache)
         return self
+
+    def tuning(self):
+        """The current tuning record (list of int)."""
+        n = C.c_int32()
+        check(load().hm_tuning(self.h, None, 0, C.byref(n)), "hm_tuning")
+        buf = (C.c_int32 * n.value)()
+        check(load().hm_tuning(self.h, buf, n.value, C.byref(n)), "hm_tuning")
+        return list(buf)
+
+    def set_tuning(self, rec):
+        """Apply a tuning record; False if it belongs to another device or program."""
+        buf = (C.c_int32 * len(rec))(*rec)
+        return load().hm_set_tuning(self.h, buf, len(rec)) == 0
 
     def launch_shapes(self):
         return hm_launch_shapes(self.h)

@@ -88,5 +88,13 @@ def test_newer_entry_points_check_arguments_and_order(lib):
         assert eng.value == 0
         assert lib.hm_set_multi_rhs_engine(h, 2) == 1 and lib.hm_set_multi_rhs_engine(h, -1) == 1
         assert lib.hm_set_multi_rhs_engine(None, 0) == 1 and lib.hm_multi_rhs_engine(h, None) == 1
+        rec = (C.c_int32 * 16)()
+        n = C.c_int32(-1)
+        # tuning records: argument errors first, then call order (not compressed)
+        assert lib.hm_tuning(None, rec, 16, C.byref(n)) == 1 and lib.hm_tuning(h, None, 4, C.byref(n)) == 1
+        assert lib.hm_tuning(h, rec, -1, C.byref(n)) == 1 and lib.hm_tuning(h, rec, 16, None) == 1
+        assert lib.hm_tuning(h, rec, 16, C.byref(n)) == 4
+        assert lib.hm_set_tuning(h, rec, 6) == 1 and lib.hm_set_tuning(h, None, 16) == 1
+        assert lib.hm_set_tuning(None, rec, 16) == 1 and lib.hm_set_tuning(h, rec, 16) == 4
     finally:
         assert lib.hm_free(h) == 0

@@ -7,6 +7,8 @@
   size (N = 131072), on sampled rows of the exact dense product.
 * Determinism (no atomics), host path, beta = 0, multi-RHS, error word.
 """
+import json
+
 import numpy as np
 import pytest
 
@@ -221,6 +223,56 @@ def test_launch_shapes_and_autotune(hm, problem, fmt):
         assert M.sync_status() == 0
     finally:
         M.close()
+
+
+def test_tuning_record_cache(hm, problem, tmp_path):
+    """The autotuner's choices (launch shapes, launch mode, multi-RHS engine) round
+    trip through a tuning record: a cache file written by one matrix is applied to
+    an identical one without timing, a record of another launch program or with a
+    value out of range is refused and leaves the settings as they were."""
+    pts, x, y0 = problem
+    eps = 1e-6
+    ref = oracle_ref(pts, "h", eps, x[:, 0], 1.0, y0[:, 0], 1.0)
+    cache = tmp_path / "tuning.json"
+    A = hm.HMatrix(pts, "laplace", 32, 2.0, "h", eps)
+    B = hm.HMatrix(pts, "laplace", 32, 2.0, "h", eps)
+    U = hm.HMatrix(pts, "laplace", 32, 2.0, "uh", eps)
+    try:
+        for M in (A, B, U):
+            M.compress(eps, "aflp")
+        A.autotune(2, cache=str(cache))
+        rec = A.tuning()
+        nl = A.info()["nlaunches"]
+        assert len(rec) == 7 + nl and rec[4] == nl
+        assert all(rec[5 + i] == s for i, s in enumerate(A.launch_shapes()) if s >= 0)
+        assert rec[5 + nl] == A.persistent_mode() and rec[6 + nl] == A.multi_rhs_engine()
+        assert len(json.loads(cache.read_text())) == 1
+        # B differs from A's record before, and takes it from the cache without timing
+        B.set_launch_shapes((rec[5] + 1) % hm.NSHAPES)
+        B.autotune(2, cache=str(cache))
+        assert B.tuning() == rec
+        assert len(json.loads(cache.read_text())) == 1
+        xd = torch.from_numpy(x[:, 0].copy()).cuda()
+        yd = torch.from_numpy(y0[:, 0].copy()).cuda()
+        B.matvec(1.0, xd, 1.0, yd)
+        assert rel(yd.cpu().numpy(), ref) <= 4 * eps
+        # another launch program (UH) refuses A's record; bad values are refused
+        before = U.tuning()
+        assert not U.set_tuning(rec)
+        bad = list(rec)
+        bad[5] = 7
+        assert not B.set_tuning(bad) and not B.set_tuning(rec[:-1]) and not B.set_tuning(bad[:4])
+        bad = list(rec)
+        bad[6 + nl] = 2
+        assert not B.set_tuning(bad)
+        assert U.tuning() == before and B.tuning() == rec
+        # a second program adds its own record to the same file
+        U.autotune(2, cache=str(cache))
+        assert len(json.loads(cache.read_text())) == 2
+        assert B.sync_status() == 0 and U.sync_status() == 0
+    finally:
+        for M in (A, B, U):
+            M.close()
 
 
 @pytest.mark.parametrize("fmt", ["h", "uh", "h2", "uh_sep"])
