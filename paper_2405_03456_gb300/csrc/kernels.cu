@@ -882,22 +882,30 @@ __global__ void k_fanout(const int32_t* __restrict__ src, int n, float2* __restr
 // fixed xor tree combines the lanes (deterministic order).
 constexpr int GS_LANES = 8;
 // Output t / GS_LANES, lane t % GS_LANES of its group (whole warps call this).
+// fan_dst non-null: a folded fan-out -- the group also writes the output's
+// slots fan_dst[O.pad .. O.pad + (O.flags >> 8)) (lane k: slots k, k + 8, ...;
+// the first slot index is loaded beside the partials).
 __device__ __forceinline__ void gsum_one(const GsumOut* __restrict__ outs, int nouts, const F2* __restrict__ pscale,
                                          const F2* __restrict__ partial, F2 alpha, float2* __restrict__ vout,
-                                         int64_t t) {
+                                         const int32_t* __restrict__ fan_dst, int64_t t) {
   const int64_t i = t / GS_LANES;
   const int k = (int)(t % GS_LANES);
   const bool on = i < nouts;
   GsumOut O{};
   if (on) O = outs[i];
+  const int nslot = fan_dst ? (O.flags >> 8) : 0;
+  const int32_t slot0 = k < nslot ? fan_dst[O.pad + k] : -1;
   FF s = {0.f, 0.f};
+  // (unrolled: several partials in flight per lane; the sum order is unchanged)
   if (O.flags & 2) {
+#pragma unroll 4
     for (int p = O.p0 + k; p < O.p1; p += GS_LANES) {
       const F2 v = partial[p];
       const F2 w = pscale[O.ps + (p - O.p0)];
       s = ff_add(s, ff_mul(FF{v.hi, v.lo}, FF{w.hi, w.lo}));
     }
   } else {
+#pragma unroll 4
     for (int p = O.p0 + k; p < O.p1; p += GS_LANES) {
       const F2 v = partial[p];
       s = ff_add(s, FF{v.hi, v.lo});
@@ -909,17 +917,49 @@ __device__ __forceinline__ void gsum_one(const GsumOut* __restrict__ outs, int n
     const float lo = __shfl_xor_sync(HM_FULL, s.lo, m);
     s = (k & m) ? ff_add(FF{hi, lo}, s) : ff_add(s, FF{hi, lo});
   }
-  if (!on || k != 0) return;
+  if (!on) return;
+  if (nslot == 0 && k != 0) return;
+  // every lane of the group holds the same sum: lane 0 writes the coefficient,
+  // the group its slots
   s = ff_mul(s, FF{O.scale.hi, O.scale.lo});
   if (O.flags & 1) s = ff_mul(s, FF{alpha.hi, alpha.lo});
-  vout[O.out] = make_float2(s.hi, s.lo);
+  const float2 val = make_float2(s.hi, s.lo);
+  if (k == 0) vout[O.out] = val;
+  if (slot0 >= 0) vout[slot0] = val;
+  for (int q = k + GS_LANES; q < nslot; q += GS_LANES) vout[fan_dst[O.pad + q]] = val;
 }
 
+// Copy entries of a folded fan-out: slot cdst[i] takes v[csrc[i]] (FAN_PER per
+// thread: all index loads, then the gathers, then the stores).
+__device__ __forceinline__ void fcopy_one(const int32_t* __restrict__ csrc, const int32_t* __restrict__ cdst, int n,
+                                          float2* __restrict__ vec, int base, int stride) {
+  int ix[FAN_PER], dx[FAN_PER];
+#pragma unroll
+  for (int q = 0; q < FAN_PER; ++q) {
+    const int i = base + q * stride;
+    ix[q] = i < n ? __ldg(csrc + i) : -1;
+    dx[q] = i < n ? __ldg(cdst + i) : -1;
+  }
+  float2 v[FAN_PER];
+#pragma unroll
+  for (int q = 0; q < FAN_PER; ++q) v[q] = ix[q] >= 0 ? vec[ix[q]] : make_float2(0.f, 0.f);
+#pragma unroll
+  for (int q = 0; q < FAN_PER; ++q)
+    if (ix[q] >= 0) vec[dx[q]] = v[q];
+}
+
+// Blocks [0, gblocks) take the segment sums; the rest the copy entries of a
+// folded fan-out (ncopy of them).
 __global__ void k_gsum(const GsumOut* __restrict__ outs, int nouts, const F2* __restrict__ pscale,
-                       const F2* __restrict__ partial, F2 alpha, float2* __restrict__ vout) {
+                       const F2* __restrict__ partial, F2 alpha, float2* __restrict__ vout,
+                       const int32_t* __restrict__ fan_dst, const int32_t* __restrict__ csrc,
+                       const int32_t* __restrict__ cdst, int ncopy, int gblocks) {
   pdl_trigger();
   pdl_wait();
-  gsum_one(outs, nouts, pscale, partial, alpha, vout, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+  if ((int)blockIdx.x < gblocks)
+    gsum_one(outs, nouts, pscale, partial, alpha, vout, fan_dst, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+  else
+    fcopy_one(csrc, cdst, ncopy, vout, ((int)blockIdx.x - gblocks) * blockDim.x * FAN_PER + threadIdx.x, blockDim.x);
 }
 
 // ---------------------------------------------------------------- gather x
@@ -956,6 +996,9 @@ struct ProgArgs {
   const SeqDep* deps;
   unsigned* state;     // [0]: barrier counter, [1]: abort word, then the runs' versions / abort / claims
   const F2* rowscale;
+  const int32_t* fan_dst;       // folded fan-outs (segment-sum phases with aux = 1)
+  const int32_t* fan_copy_src;
+  const int32_t* fan_copy_dst;
 };
 
 // Grid barrier number b (0, 1, ...): the block's warps meet, thread 0 publishes
@@ -1032,7 +1075,14 @@ __global__ void __launch_bounds__(SEQ_NW * 32, 1) k_prog(RsArgs A, ProgArgs P) {
         case PP_GSUM: {
           const int64_t total = (int64_t)Ph.n * GS_LANES;
           for (int64_t t0 = (int64_t)gw * 32; t0 < total; t0 += (int64_t)nwarps * 32)
-            gsum_one(P.gouts + Ph.off, Ph.n, P.pscale, P.partial, A.alpha_ff, A.vout, t0 + lane);
+            gsum_one(P.gouts + Ph.off, Ph.n, P.pscale, P.partial, A.alpha_ff, A.vout, Ph.aux ? P.fan_dst : nullptr,
+                     t0 + lane);
+          if (Ph.aux) {   // copy entries [mode, mode + nchunks) of the folded fan-out
+            const int64_t per = (int64_t)blockDim.x * FAN_PER;
+            for (int64_t c = blockIdx.x; c * per < Ph.nchunks; c += gridDim.x)
+              fcopy_one(P.fan_copy_src + Ph.mode, P.fan_copy_dst + Ph.mode, Ph.nchunks, A.vout,
+                        (int)(c * per) + threadIdx.x, blockDim.x);
+          }
           break;
         }
         case PP_FANOUT: {
@@ -1294,11 +1344,12 @@ cudaError_t launch_fanout(const int32_t* src, int n, float2* dst, const float2* 
 }
 
 cudaError_t launch_gsum(const GsumOut* outs, int nouts, const F2* pscale, const F2* partial, F2 alpha, float2* vout,
-                        cudaStream_t st) {
-  if (nouts <= 0) return cudaSuccess;
+                        const int32_t* fan_dst, const int32_t* csrc, const int32_t* cdst, int ncopy, cudaStream_t st) {
+  if (nouts <= 0 && ncopy <= 0) return cudaSuccess;
   const int64_t threads = (int64_t)nouts * GS_LANES;
-  const cudaError_t e =
-      launch_pdl(k_gsum, (unsigned)((threads + 255) / 256), 256, 0, st, outs, nouts, pscale, partial, alpha, vout);
+  const int gblocks = (int)((threads + 255) / 256), cblocks = (ncopy + 256 * FAN_PER - 1) / (256 * FAN_PER);
+  const cudaError_t e = launch_pdl(k_gsum, (unsigned)(gblocks + cblocks), 256, 0, st, outs, nouts, pscale, partial,
+                                   alpha, vout, fan_dst, csrc, cdst, ncopy, gblocks);
   return e != cudaSuccess ? e : cudaGetLastError();
 }
 
@@ -1379,13 +1430,16 @@ cudaError_t launch_prog(int tier, int nblk, const ProgPhase* phases, int nphases
                         const int32_t* fan, const PieceCopy* pieces, const int32_t* wbeg, const SeqPhase* seqph,
                         const SeqDep* deps, unsigned* state, int nstate, const uint8_t* pay, float2* vec,
                         double alpha, double beta, double* y, const int32_t* perm, const F2* rowscale, F2* fix,
-                        int32_t* fixcnt, const Split* splits, int* err, cudaStream_t st) {
+                        int32_t* fixcnt, const Split* splits, const int32_t* fan_dst, const int32_t* fan_copy_src,
+                        const int32_t* fan_copy_dst, int* err, cudaStream_t st) {
   if (nphases <= 0 || nblk <= 0) return cudaSuccess;
   cudaError_t e = cudaMemsetAsync(state, 0, (size_t)nstate * sizeof(unsigned), st);
   if (e != cudaSuccess) return e;
   const F2 aff{(float)alpha, (float)(alpha - (double)(float)alpha)};
   const RsArgs A{pieces, pay, vec, alpha, aff, beta, y, perm, vec, nullptr, fix, fixcnt, splits, err};
-  const ProgArgs P{phases, nphases, x, items, gouts, pscale, partial, fan, wbeg, seqph, deps, state, rowscale};
+  const ProgArgs P{phases, nphases, x,        items,   gouts,        pscale,      partial,
+                   fan,    wbeg,    seqph,    deps,    state,        rowscale,    fan_dst,
+                   fan_copy_src, fan_copy_dst};
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)nblk);
   cfg.blockDim = dim3(SEQ_NW * 32);

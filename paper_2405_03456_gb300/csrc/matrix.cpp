@@ -21,7 +21,7 @@ cudaError_t launch_cdot(int tier, int cfg, const ItemCopy* items, const int32_t*
                         const float2* vec, F2 alpha, F2* partial, float2* vout, int* err, cudaStream_t st);
 cudaError_t launch_fanout(const int32_t* src, int n, float2* dst, const float2* vec, cudaStream_t st);
 cudaError_t launch_gsum(const GsumOut* outs, int nouts, const F2* pscale, const F2* partial, F2 alpha, float2* vout,
-                        cudaStream_t st);
+                        const int32_t* fan_dst, const int32_t* csrc, const int32_t* cdst, int ncopy, cudaStream_t st);
 cudaError_t launch_rgemv(int tier, int mode, int cfg, const PieceCopy* pieces, const int32_t* wbeg, int nw,
                          const uint8_t* pay, const float2* vec, double alpha, F2 alpha_ff, double beta, double* y,
                          const int32_t* perm, float2* vout, const F2* rowscale, F2* fix, int32_t* fixcnt,
@@ -37,7 +37,8 @@ cudaError_t launch_prog(int tier, int nblk, const ProgPhase* phases, int nphases
                         const int32_t* fan, const PieceCopy* pieces, const int32_t* wbeg, const SeqPhase* seqph,
                         const SeqDep* deps, unsigned* state, int nstate, const uint8_t* pay, float2* vec,
                         double alpha, double beta, double* y, const int32_t* perm, const F2* rowscale, F2* fix,
-                        int32_t* fixcnt, const Split* splits, int* err, cudaStream_t st);
+                        int32_t* fixcnt, const Split* splits, const int32_t* fan_dst, const int32_t* fan_copy_src,
+                        const int32_t* fan_copy_dst, int* err, cudaStream_t st);
 int prog_max_blocks();
 cudaError_t mr_init();
 cudaError_t tc_init();
@@ -107,6 +108,7 @@ struct hm_matrix {
   DevArr<PieceCopy> d_pieces;
   DevArr<int32_t> d_wbeg;
   DevArr<int32_t> d_fan;
+  DevArr<int32_t> d_fan_dst, d_fcopy_src, d_fcopy_dst;   // folded fan-outs
   DevArr<Split> d_splits;
   DevArr<F2> d_rowscale_ff;     // row scales of coefficient vectors (float-float pairs)
   DevArr<int32_t> d_perm;
@@ -191,6 +193,9 @@ struct hm_matrix {
     d_pieces.release();
     d_wbeg.release();
     d_fan.release();
+    d_fan_dst.release();
+    d_fcopy_src.release();
+    d_fcopy_dst.release();
     d_splits.release();
     d_rowscale_ff.release();
     d_phases.release();
@@ -265,6 +270,9 @@ hm_status upload(hm_matrix* M) {
   }
   UP(d_wbeg, P.wbeg)
   UP(d_fan, P.fan_src)
+  UP(d_fan_dst, P.fan_dst)
+  UP(d_fcopy_src, P.fan_copy_src)
+  UP(d_fcopy_dst, P.fan_copy_dst)
   UP(d_splits, P.splits)
   {
     std::vector<F2> rs(P.rowscale.size());
@@ -358,7 +366,10 @@ hm_status upload(hm_matrix* M) {
       switch (L.kind) {
         case Launch::GATHER: ph = ProgPhase{PP_GATHER, 0, (int32_t)L.n, 0, 0, 0, 0, 0}; break;
         case Launch::CDOT: ph = ProgPhase{PP_CDOT, (int32_t)L.woff[0], L.nw[0], 0, 0, 0, 0, 0}; break;
-        case Launch::GSUM: ph = ProgPhase{PP_GSUM, (int32_t)L.off, (int32_t)L.n, 0, 0, 0, 0, 0}; break;
+        case Launch::GSUM:
+          ph = ProgPhase{PP_GSUM, (int32_t)L.off, (int32_t)L.n, (int32_t)L.copy_off, 0, L.scatter ? 1 : 0,
+                         (int32_t)L.copy_n, 0};
+          break;
         case Launch::FANOUT:
           ph = ProgPhase{PP_FANOUT, (int32_t)L.off, (int32_t)L.n, 0, 0, (int32_t)P.fan_base, 0, 0};
           break;
@@ -541,7 +552,11 @@ static cudaError_t run_launch(hm_matrix* M, const Launch& L, double alpha, const
       return launch_cdot(P.tier, cf, M->d_items.p, M->d_wbeg.p + L.woff[cf], L.nw[cf], M->d_pay.p, M->d_vec, aff,
                          M->d_part, M->d_vec, M->d_err, st);
     case Launch::GSUM:
-      return launch_gsum(M->d_gout.p + L.off, (int)L.n, M->d_pscale.p, M->d_part, aff, M->d_vec, st);
+      if (L.scatter)   // with the fan-out folded into it
+        return launch_gsum(M->d_gout.p + L.off, (int)L.n, M->d_pscale.p, M->d_part, aff, M->d_vec, M->d_fan_dst.p,
+                           M->d_fcopy_src.p + L.copy_off, M->d_fcopy_dst.p + L.copy_off, (int)L.copy_n, st);
+      return launch_gsum(M->d_gout.p + L.off, (int)L.n, M->d_pscale.p, M->d_part, aff, M->d_vec, nullptr, nullptr,
+                         nullptr, 0, st);
     case Launch::FANOUT:
       return launch_fanout(M->d_fan.p + L.off, (int)L.n, M->d_vec + P.fan_base + L.off, M->d_vec, st);
     case Launch::RGEMV:
@@ -633,7 +648,8 @@ static hm_status run_program(hm_matrix* M, double alpha, const double* x, double
     return launch_prog(P.tier, M->nsm, M->d_prog.p, (int)M->d_prog.n, x, M->d_items.p, M->d_gout.p, M->d_pscale.p,
                        M->d_part, M->d_fan.p, M->d_pieces.p + (size_t)SEQ_SHAPE * P.npieces, M->d_wbeg.p,
                        M->d_phases.p, M->d_deps.p, M->d_pstate, M->pstate_n, M->d_pay.p, M->d_vec, alpha, beta, y,
-                       M->d_perm.p, M->d_rowscale_ff.p, M->d_fix, M->d_fixcnt, M->d_splits.p, M->d_err,
+                       M->d_perm.p, M->d_rowscale_ff.p, M->d_fix, M->d_fixcnt, M->d_splits.p, M->d_fan_dst.p,
+                       M->d_fcopy_src.p, M->d_fcopy_dst.p, M->d_err,
                        st) == cudaSuccess
                ? HM_OK
                : HM_ERR_CUDA;
@@ -1080,7 +1096,8 @@ hm_status hm_info(const hm_matrix* M, hm_info_t* o) {
   o->bytes_meta = P.pk.meta_bytes +
                   (int64_t)(P.items.size() * sizeof(ItemCopy) + NSHAPES * P.npieces * sizeof(PieceCopy) +
                             P.wbeg.size() * 4 + P.splits.size() * sizeof(Split) + P.gouts.size() * sizeof(GsumOut) +
-                            P.pscale.size() * 8 + P.rowscale.size() * 8 + P.fan_src.size() * 4) +
+                            P.pscale.size() * 8 + P.rowscale.size() * 8 +
+                            (P.fan_src.size() + P.fan_dst.size() + 2 * P.fan_copy_src.size()) * 4) +
                   H.n * 4;
   o->bytes_workspace = P.nvec * 8 + P.npartial * 8 + P.nfix * CHUNK_ROWS * 8;
   if (M->d_vmr)

@@ -1003,6 +1003,79 @@ bool program_h2(Ctx& cx) {
 // Algorithmic bytes of every launch (packed values without padding, inline
 // metadata, descriptors, vector reads and writes) and the warp ranges of the
 // column-dot launches.
+// A fan-out launch right after a segment-sum launch (which follows its column
+// dots) is folded into the segment sums when every slot takes a coefficient that
+// one of the two wrote: each segment-sum output also writes its own slots, and
+// the slots of one-segment column-dot outputs become copy entries run by the
+// same launch.  The slot values are the same; the launch goes.  A fan-out of
+// coefficients that a row-chunk launch writes stays.
+void fold_fanouts(Program& P) {
+  std::vector<int32_t> by_gsum((size_t)P.fan_base, -1);   // coefficient -> its GsumOut, or -2: one-segment dot
+  std::vector<char> gone(P.launches.size(), 0);
+  for (size_t li = 2; li < P.launches.size(); ++li) {
+    const Launch& F = P.launches[li];
+    Launch& G = P.launches[li - 1];
+    const Launch& C = P.launches[li - 2];
+    if (F.kind != Launch::FANOUT || G.kind != Launch::GSUM || C.kind != Launch::CDOT || G.scatter) continue;
+    std::vector<int32_t> marks;
+    for (int64_t it = C.off; it < C.off + C.n; ++it) {
+      const uint8_t* p = P.pk.pay.data() + (uint64_t)P.items[it].off16 * 16;
+      CPieceHdr h;
+      std::memcpy(&h, p, sizeof h);
+      if (!(h.flags & ITEM_FINAL)) continue;
+      for (int j = 0; j < h.ncols; ++j) {
+        CColMeta m;
+        std::memcpy(&m, p + sizeof h + (size_t)j * sizeof m, sizeof m);
+        if (m.out >= 0 && m.out < P.fan_base && by_gsum[m.out] == -1) {
+          by_gsum[m.out] = -2;
+          marks.push_back(m.out);
+        }
+      }
+    }
+    for (int64_t i = G.off; i < G.off + G.n; ++i) {
+      const int32_t o = P.gouts[i].out;
+      if (o >= 0 && o < P.fan_base && by_gsum[o] == -1) {
+        by_gsum[o] = (int32_t)i;
+        marks.push_back(o);
+      }
+    }
+    bool all = true;
+    for (int64_t i = F.off; i < F.off + F.n && all; ++i)
+      all = P.fan_src[i] >= 0 && P.fan_src[i] < P.fan_base && by_gsum[P.fan_src[i]] != -1;
+    if (all) {
+      // slots per segment-sum output, in slot order; copy entries in slot order
+      std::vector<std::vector<int32_t>> lists((size_t)G.n);
+      G.copy_off = (int64_t)P.fan_copy_src.size();
+      for (int64_t i = F.off; i < F.off + F.n; ++i) {
+        const int32_t src = P.fan_src[i], dst = (int32_t)(P.fan_base + i);
+        if (by_gsum[src] >= 0) {
+          lists[(size_t)(by_gsum[src] - G.off)].push_back(dst);
+        } else {
+          P.fan_copy_src.push_back(src);
+          P.fan_copy_dst.push_back(dst);
+        }
+      }
+      G.copy_n = (int64_t)P.fan_copy_src.size() - G.copy_off;
+      for (int64_t i = G.off; i < G.off + G.n; ++i) {
+        GsumOut& o = P.gouts[i];
+        const auto& l = lists[(size_t)(i - G.off)];
+        o.pad = (int32_t)P.fan_dst.size();
+        o.flags = (o.flags & 0xff) | (int32_t)(l.size() << 8);
+        P.fan_dst.insert(P.fan_dst.end(), l.begin(), l.end());
+        G.xbytes += 12 * (int64_t)l.size();   // slot index read, value written
+      }
+      G.xbytes += 24 * G.copy_n;                // source and slot index, value read and written
+      G.scatter = true;
+      gone[li] = 1;
+    }
+    for (int32_t o : marks) by_gsum[o] = -1;
+  }
+  std::vector<Launch> keep;
+  for (size_t li = 0; li < P.launches.size(); ++li)
+    if (!gone[li]) keep.push_back(P.launches[li]);
+  P.launches.swap(keep);
+}
+
 void finish_launches(Ctx& cx) {
   Program& P = cx.P;
   for (Launch& L : P.launches) {
@@ -1037,7 +1110,7 @@ void finish_launches(Ctx& cx) {
         b = L.n * (4 + 8 + 8);
         break;
     }
-    L.bytes = b;
+    L.bytes = b + L.xbytes;
   }
 }
 
@@ -1080,11 +1153,13 @@ bool build_program(const HostMatrix& H, int codec, double eps, int valr, int nsm
     P.too_large = true;
     return false;
   }
+  fold_fanouts(P);
   finish_launches(cx);
   // levels without work (empty top levels of the sweeps) launch nothing
   P.launches.erase(std::remove_if(P.launches.begin(), P.launches.end(),
                                   [](const Launch& L) {
-                                    return L.n == 0 && !(L.kind == Launch::RGEMV && L.mode == MODE_Y);
+                                    return L.n == 0 && !(L.kind == Launch::RGEMV && L.mode == MODE_Y) &&
+                                           !(L.kind == Launch::GSUM && L.copy_n > 0);
                                   }),
                    P.launches.end());
   return true;

@@ -69,6 +69,9 @@ struct Launch {
   int nw[NSHAPES] = {};           // ranges (warps; blocks for the multi-RHS shape) per launch shape
   int cfg = 0;                    // launch shape in use (autotuner choice)
   int maxrows = 0;                // RGEMV: rows of its widest chunk
+  bool scatter = false;           // GSUM: also fills the slots of the folded fan-out after it
+  int64_t copy_off = 0, copy_n = 0;  // GSUM with scatter: its copy entries fan_copy_{src,dst}[copy_off ..)
+  int64_t xbytes = 0;             // bytes of that scatter (slot lists read, slots written)
 };
 
 struct Program {
@@ -90,6 +93,12 @@ struct Program {
   int64_t nchunks = 0;
   std::vector<int32_t> fan_src;   // fan-out: slot s takes v[fan_src[s]]; slot s is v[fan_base + s]
   int64_t fan_base = 0;
+  // Folded fan-outs (a fan-out launch right after a segment-sum launch whose
+  // slots all take coefficients of that launch or of the column dots before it):
+  // a segment-sum output writes its slots fan_dst[pad .. pad + (flags >> 8)) of
+  // its GsumOut; the slot fan_copy_dst[i] of a one-segment column-dot output
+  // takes v[fan_copy_src[i]] in the same launch (vector indices throughout).
+  std::vector<int32_t> fan_dst, fan_copy_src, fan_copy_dst;
   std::vector<double> rowscale;   // per vector entry (1 where unused)
   int64_t nvec = 0;               // float2 vector workspace entries (x first)
   int64_t npartial = 0;           // partials of the largest column-dot launch

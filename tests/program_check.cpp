@@ -225,7 +225,26 @@ struct Replay {
       if (o.flags & 1) s *= alpha;
       CHECK(o.out >= 0 && o.out < P.nvec, "segment sum %ld: output outside v", (long)i);
       if (o.out >= 0 && o.out < P.nvec) v[o.out] = s;
+      if (L.scatter) {   // a folded fan-out: the output's own slots
+        const int64_t a = o.pad, b = (int64_t)o.pad + (o.flags >> 8);
+        CHECK(a >= 0 && b <= (int64_t)P.fan_dst.size(), "segment sum %ld: slot list outside", (long)i);
+        for (int64_t q = a; q < b && q < (int64_t)P.fan_dst.size(); ++q) {
+          const int32_t d = P.fan_dst[q];
+          CHECK(d >= P.fan_base && d < P.nvec && P.fan_src[d - P.fan_base] == o.out, "segment sum %ld: slot %d",
+                (long)i, d);
+          if (d >= P.fan_base && d < P.nvec) v[d] = s;
+        }
+      }
     }
+    if (L.scatter)   // and the copy entries of the one-segment column-dot outputs
+      for (int64_t i = L.copy_off; i < L.copy_off + L.copy_n; ++i) {
+        CHECK(i >= 0 && i < (int64_t)P.fan_copy_src.size(), "copy entry %ld outside its list", (long)i);
+        if (i < 0 || i >= (int64_t)P.fan_copy_src.size()) break;
+        const int32_t c = P.fan_copy_src[i], d = P.fan_copy_dst[i];
+        CHECK(c >= 0 && c < P.fan_base && d >= P.fan_base && d < P.nvec && P.fan_src[d - P.fan_base] == c,
+              "copy entry %ld: %d -> %d", (long)i, c, d);
+        if (c >= 0 && c < P.fan_base && d >= P.fan_base && d < P.nvec) v[d] = v[c];
+      }
     std::fill(part.begin(), part.end(), NAN);   // partials are consumed by the launch
   }
 
@@ -413,7 +432,9 @@ struct Replay {
         for (int64_t i = L.off; i < L.off + L.n; ++i) {
           const GsumOut& o = P.gouts[i];
           b += (int64_t)(o.p1 - o.p0) * ((o.flags & 2) ? 16 : 8) + 40;
+          if (L.scatter) b += 12 * (int64_t)(o.flags >> 8);   // slot index, value written
         }
+        if (L.scatter) b += 24 * L.copy_n;                      // indices, value read and written
         return b;
       case Launch::CDOT:
         for (int64_t it = L.off; it < L.off + L.n; ++it) {

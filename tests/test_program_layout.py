@@ -154,3 +154,21 @@ def test_h2_hodlr_basis_rank_above_the_kernel_limit(checker):
     # built (hm_compress reports HM_ERR_CAPACITY)
     r = _run(checker, "sphere", 3000, "h2", 1e-6, "aflp", 32, 152, "hodlr")
     assert r.returncode == 1 and "build_program failed" in r.stdout
+
+
+@pytest.mark.parametrize("fmt", list(FORMATS))
+def test_fanout_folded_into_segment_sums(checker, fmt):
+    # the fan-out right after the segment sums (H: the multipliers of the W factors)
+    # is folded into them; a fan-out of row-chunk outputs (UH / H^2 backward) stays.
+    # The replay above checks the values; here the launch list.
+    r = _run(checker, "sphere", 3000, fmt, 1e-6, "aflp", 32, 152, "std")
+    assert r.returncode == 0 and r.stdout.rstrip().endswith("ok"), r.stdout[-2000:]
+    kinds = [line.split()[2] for line in r.stdout.splitlines() if line.startswith("launch ")]
+    assert kinds[:2] == ["gather", "cdot"]
+    for i, k in enumerate(kinds):
+        if k == "fanout":
+            assert kinds[i - 1] == "rgemv"
+    if fmt == "h":
+        assert kinds == ["gather", "cdot", "gsum", "rgemv"]
+    else:
+        assert "fanout" in kinds
