@@ -349,7 +349,10 @@ hm_status hm_set_tuning(hm_matrix* m, const int32_t* rec, int32_t len);
  * and clears the record.  Kinds: 0 gather, 1 column dots (phase A),
  * 2 segment sums, 3 row chunks (phase C / couplings / sweeps), 4 multiplier
  * fan-out (copies the coefficients each row-chunk piece multiplies into
- * contiguous runs).  out : host array of nout (<= 5) entries.
+ * contiguous runs; where the column dots and segment sums right before it wrote
+ * every such coefficient -- the H product -- the segment-sum launch fills
+ * these slots itself and kind 4 has no launch).  out : host array of nout
+ * (<= 5) entries.
  * Errors: HM_ERR_ARG, HM_ERR_CUDA.
  */
 typedef struct { double ms; int64_t launches; int64_t bytes; } hm_kernel_stat;
