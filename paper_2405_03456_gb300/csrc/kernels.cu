@@ -880,7 +880,7 @@ __global__ void k_fanout(const int32_t* __restrict__ src, int n, float2* __restr
 // Segment sums: GS_LANES lanes per output; lane k sums the partials p0 + k,
 // p0 + k + GS_LANES, ... (consecutive lanes read consecutive partials), then a
 // fixed xor tree combines the lanes (deterministic order).
-constexpr int GS_LANES = 8;
+constexpr int GS_LANES = 4;
 // Output t / GS_LANES, lane t % GS_LANES of its group (whole warps call this).
 // fan_dst non-null: a folded fan-out -- the group also writes the output's
 // slots fan_dst[O.pad .. O.pad + (O.flags >> 8)) (lane k: slots k, k + 8, ...;
